@@ -1,0 +1,109 @@
+"""CPU oracle for C = A·Aᵀ mod p (arXiv 2001.04109) -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py`` (its CPU
+baseline / reference arm) may import this package.  It shares no code with
+the CUDA library in ``paper_2001_04109_gb300``: it neither imports it nor is
+imported by it.
+
+Contents
+--------
+* ``syrk_oracle.c`` / :func:`syrk` / :func:`syrk_rows` -- the plain
+  schoolbook definition of lower(A·Aᵀ) mod p in 64-bit integers (the result
+  Algorithm 2 of the paper reaches exactly, Section 3).
+* :mod:`oracle.field` -- primality, Legendre symbols, square roots and the
+  skew-orthogonal Y of Section 3.1 (Prop. 3.2, Prop. 3.3, Algorithm 3).
+* :mod:`oracle.alg2` -- Algorithm 2 itself written step by step over F_p in
+  Python integers, for the block identities of the appendix proof.
+* :mod:`oracle.cost` -- the operation-count recurrences behind Table 5 and
+  Eq. (complexity) of Theorem 4.1.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "syrk_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``syrk_oracle.c`` with gcc into ``oracle/liboracle.so``."""
+    with _lock:
+        if (not force and os.path.exists(_LIB_PATH)
+                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            return _LIB_PATH
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        i64, u32, p = ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p
+        lib.oracle_syrk_modp.argtypes = [i64, i64, u32, p, i64, p, i64, ctypes.c_int, ctypes.c_int]
+        lib.oracle_syrk_modp.restype = ctypes.c_int
+        lib.oracle_syrk_rows.argtypes = [i64, i64, u32, p, i64, p, i64, p, i64, ctypes.c_int]
+        lib.oracle_syrk_rows.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def _as_u32(A) -> np.ndarray:
+    A = np.asarray(A)
+    if A.dtype in (np.int32, np.uint32):
+        A = A.view(np.uint32)
+    elif A.dtype.kind in "iu":
+        A = A.astype(np.uint64).astype(np.uint32)
+    else:
+        raise TypeError(f"integer matrix expected, got {A.dtype}")
+    return np.ascontiguousarray(A)
+
+
+def syrk(A, p: int, uplo: str = "lower", threads: int | None = None) -> np.ndarray:
+    """Schoolbook A·Aᵀ mod p of an n×k matrix (entries any uint32).
+
+    ``uplo`` is ``"lower"`` (j ≤ i written), ``"upper"`` (j ≥ i) or
+    ``"full"`` (every entry computed on its own).  Unwritten entries are 0.
+    Returns an n×n uint32 array.
+    """
+    A = _as_u32(A)
+    if A.ndim != 2:
+        raise ValueError("A must be 2-D")
+    n, k = A.shape
+    C = np.zeros((n, n), dtype=np.uint32)
+    code = {"lower": 0, "upper": 1, "full": 2}[uplo]
+    lib = _load()
+    rc = lib.oracle_syrk_modp(n, k, p, A.ctypes.data, max(k, 1), C.ctypes.data, max(n, 1), code,
+                              threads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle_syrk_modp rejected its arguments")
+    return C
+
+
+def syrk_rows(A, p: int, rows, threads: int | None = None) -> np.ndarray:
+    """Full rows ``rows`` of A·Aᵀ mod p, as a len(rows)×n uint32 array."""
+    A = _as_u32(A)
+    n, k = A.shape
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    out = np.zeros((len(rows), n), dtype=np.uint32)
+    lib = _load()
+    rc = lib.oracle_syrk_rows(n, k, p, A.ctypes.data, max(k, 1), rows.ctypes.data, len(rows),
+                              out.ctypes.data, max(n, 1), threads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle_syrk_rows rejected its arguments")
+    return out

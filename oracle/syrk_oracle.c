@@ -1,0 +1,158 @@
+/*
+ * Schoolbook oracle for C = A·Aᵀ mod p (TEST INFRASTRUCTURE ONLY).
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
+ * load this file's library.  It shares no code, header, table or constant
+ * with the CUDA path; it is the plain definition of the product that the
+ * paper's Algorithm 2 reaches exactly (Section 3, "the lower left triangular
+ * part of C = A·Aᵀ"; the SYRK terminology of Section 1):
+ *
+ *     C[i][j] = ( Σ_{l<k} (A[i][l] mod p) · (A[j][l] mod p) ) mod p.
+ *
+ * Every entry of A may be any uint32; it is reduced mod p first.  Each
+ * product is < p² < 2^48 (p < 2^24), so a uint64 running sum is reduced
+ * every 2^15 terms (2^15 · 2^48 = 2^63 < 2^64) and can never wrap.
+ * Work is split over POSIX threads by output rows; the arithmetic of each
+ * entry is independent of the split.
+ */
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_REDUCE_EVERY 32768
+
+/* One entry: the dot product of rows i and j of A, mod p. */
+static uint32_t dot_mod_p(const uint32_t *ri, const uint32_t *rj, int64_t k, uint64_t p) {
+    uint64_t acc = 0;
+    int64_t since = 0;
+    for (int64_t l = 0; l < k; ++l) {
+        uint64_t a = (uint64_t)ri[l] % p;
+        uint64_t b = (uint64_t)rj[l] % p;
+        acc += a * b;
+        if (++since == ORACLE_REDUCE_EVERY) {
+            acc %= p;
+            since = 0;
+        }
+    }
+    return (uint32_t)(acc % p);
+}
+
+enum { JOB_LOWER = 0, JOB_UPPER = 1, JOB_FULL = 2, JOB_ROWS = 3 };
+
+typedef struct {
+    int kind;
+    int64_t n, k;
+    uint64_t p;
+    const uint32_t *A;
+    int64_t lda;
+    uint32_t *C;
+    int64_t ldc;
+    const int64_t *rows; /* JOB_ROWS: the sampled rows */
+    int64_t nrows;
+    int64_t t, nthreads;
+} job_t;
+
+static void *worker(void *arg) {
+    const job_t *j = (const job_t *)arg;
+    int64_t count = (j->kind == JOB_ROWS) ? j->nrows : j->n;
+    /* cyclic split so that triangular rows balance */
+    for (int64_t r = j->t; r < count; r += j->nthreads) {
+        if (j->kind == JOB_ROWS) {
+            int64_t i = j->rows[r];
+            const uint32_t *ri = j->A + i * j->lda;
+            uint32_t *out = j->C + r * j->ldc;
+            for (int64_t c = 0; c < j->n; ++c)
+                out[c] = dot_mod_p(ri, j->A + c * j->lda, j->k, j->p);
+        } else {
+            int64_t i = r;
+            const uint32_t *ri = j->A + i * j->lda;
+            int64_t c0 = 0, c1 = j->n; /* columns [c0, c1) of row i */
+            if (j->kind == JOB_LOWER) c1 = i + 1;
+            if (j->kind == JOB_UPPER) c0 = i;
+            for (int64_t c = c0; c < c1; ++c)
+                j->C[i * j->ldc + c] = dot_mod_p(ri, j->A + c * j->lda, j->k, j->p);
+        }
+    }
+    return NULL;
+}
+
+static int run(job_t proto, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 1024) nthreads = 1024;
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    job_t *jobs = (job_t *)calloc((size_t)nthreads, sizeof(job_t));
+    if (!th || !jobs) {
+        free(th);
+        free(jobs);
+        return -1;
+    }
+    int started = 0, rc = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t] = proto;
+        jobs[t].t = t;
+        jobs[t].nthreads = nthreads;
+        if (pthread_create(&th[t], NULL, worker, &jobs[t]) != 0) {
+            rc = -1;
+            break;
+        }
+        ++started;
+    }
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    /* threads that failed to start: finish their share here */
+    for (int t = started; t < nthreads; ++t) worker(&jobs[t]);
+    free(th);
+    free(jobs);
+    return rc < 0 && started == 0 ? -1 : 0;
+}
+
+/*
+ * uplo 0: C[i][j] for j <= i (lower, diagonal included); uplo 1: j >= i
+ * (upper); uplo 2: every entry, each computed on its own (never mirrored),
+ * so that symmetry of the result is a real check.  Entries outside the
+ * selected set are not written.  Returns 0, or -1 on bad arguments.
+ */
+int oracle_syrk_modp(int64_t n, int64_t k, uint32_t p, const uint32_t *A, int64_t lda,
+                     uint32_t *C, int64_t ldc, int uplo, int nthreads) {
+    if (n < 0 || k < 0 || p < 2 || lda < (k > 1 ? k : 1) || ldc < (n > 1 ? n : 1)) return -1;
+    if (uplo < 0 || uplo > 2) return -1;
+    if (n == 0) return 0;
+    job_t j;
+    memset(&j, 0, sizeof j);
+    j.kind = uplo == 0 ? JOB_LOWER : (uplo == 1 ? JOB_UPPER : JOB_FULL);
+    j.n = n;
+    j.k = k;
+    j.p = p;
+    j.A = A;
+    j.lda = lda;
+    j.C = C;
+    j.ldc = ldc;
+    return run(j, nthreads);
+}
+
+/*
+ * Full rows of A·Aᵀ mod p for a sample of row indices: out[t][c] for
+ * c < n is entry (rows[t], c).  out is nrows × ldo.  Used to check large
+ * products one sampled row at a time.
+ */
+int oracle_syrk_rows(int64_t n, int64_t k, uint32_t p, const uint32_t *A, int64_t lda,
+                     const int64_t *rows, int64_t nrows, uint32_t *out, int64_t ldo, int nthreads) {
+    if (n < 0 || k < 0 || p < 2 || lda < (k > 1 ? k : 1) || ldo < (n > 1 ? n : 1) || nrows < 0)
+        return -1;
+    for (int64_t t = 0; t < nrows; ++t)
+        if (rows[t] < 0 || rows[t] >= n) return -1;
+    if (n == 0 || nrows == 0) return 0;
+    job_t j;
+    memset(&j, 0, sizeof j);
+    j.kind = JOB_ROWS;
+    j.n = n;
+    j.k = k;
+    j.p = p;
+    j.A = A;
+    j.lda = lda;
+    j.C = out;
+    j.ldc = ldo;
+    j.rows = rows;
+    j.nrows = nrows;
+    return run(j, nthreads);
+}
