@@ -1,0 +1,151 @@
+/*
+ * ffsyrk -- C = A·Aᵀ over a prime field F_p on one GB300 GPU (sm_103a).
+ *
+ * Implements Algorithm 2 ("syrk") of Dumas, Pernet and Sedoglavic, "On Fast
+ * Multiplication of a Matrix by its Transpose" (arXiv 2001.04109, Section 3):
+ * per recursion level 4 block pre-additions (two of them times a
+ * skew-orthogonal Y), 3 recursive products (P1, P2, P5), 2 general products
+ * (P3, P4) and the post-additions U1..U5, down to classical leaves.  All
+ * arithmetic is exact integer arithmetic mod p; the result is bit-exact.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are row-major.  A is n×k with leading dimension lda ≥ max(1,k);
+ *   C is n×n with ldc ≥ max(1,n).  Any lda/ldc is accepted (no alignment
+ *   requirement).  Entries of A may be any uint32; they are reduced mod p.
+ * - A and C are DEVICE pointers owned by the caller.  The library never
+ *   frees or retains them beyond the call.
+ * - uplo = FFSYRK_LOWER writes C[i][j] = (A·Aᵀ)[i][j] mod p for j ≤ i
+ *   (canonical, in [0, p)); FFSYRK_UPPER writes the same values at C[j][i].
+ *   The other strict triangle of C is never read or written.
+ * - n = 0 is a no-op; k = 0 writes zeros to the selected triangle.
+ * - p must be an odd prime with 3 ≤ p < 2^24 (FFSYRK_ERR_NOT_PRIME for a
+ *   composite, FFSYRK_ERR_UNSUPPORTED_P for 2 or p ≥ 2^24).
+ * - Work is enqueued asynchronously on `stream` (NULL = legacy default
+ *   stream).  Argument errors are returned synchronously before anything is
+ *   enqueued.  A device-side failure (a bounded wait that ran out) is
+ *   recorded in the plan and reported by ffsyrk_sync_status() or by the
+ *   next call with the same plan as FFSYRK_ERR_TIMEOUT.
+ * - The calling thread's current CUDA device is the device used.
+ */
+#ifndef FFSYRK_H
+#define FFSYRK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so users need no CUDA header. */
+struct CUstream_st;
+typedef struct CUstream_st *ffsyrk_stream_t;
+
+typedef enum {
+    FFSYRK_SUCCESS = 0,
+    FFSYRK_ERR_INVALID_ARG = 1,   /* bad size, stride, pointer or option    */
+    FFSYRK_ERR_NOT_PRIME = 2,     /* p is composite                          */
+    FFSYRK_ERR_UNSUPPORTED_P = 3, /* p = 2 or p ≥ 2^24                       */
+    FFSYRK_ERR_ALLOC = 4,         /* device or host workspace allocation     */
+    FFSYRK_ERR_CUDA = 5,          /* a CUDA runtime call failed              */
+    FFSYRK_ERR_TIMEOUT = 6,       /* a device-side bounded wait ran out      */
+    FFSYRK_ERR_ARCH = 7,          /* the device is not sm_103 (GB300)        */
+    FFSYRK_ERR_TOO_LARGE = 8      /* shape exceeds the plan or a hard limit  */
+} ffsyrk_status_t;
+
+typedef enum { FFSYRK_LOWER = 0, FFSYRK_UPPER = 1 } ffsyrk_uplo_t;
+
+/* Which kernel computes the leaf products (the 3^L syrk leaves and the
+ * general products of every level). */
+typedef enum {
+    FFSYRK_LEAF_AUTO = 0,    /* the tensor-core leaf                          */
+    FFSYRK_LEAF_TC_BF16 = 1, /* tcgen05.mma kind::f16 on exact 8-bit digits,
+                                FP32 TMEM accumulators, reduction per K-chunk */
+    FFSYRK_LEAF_I64 = 2      /* CUDA-core 32×32→64-bit multiply-add leaf      */
+} ffsyrk_leaf_t;
+
+#define FFSYRK_LEVELS_AUTO (-1)
+
+/* Planning options.  Fill with ffsyrk_options_default() and change what you
+ * need; a NULL options pointer means the defaults. */
+typedef struct {
+    int32_t leaf;   /* ffsyrk_leaf_t (default FFSYRK_LEAF_AUTO)                 */
+    int32_t levels; /* FFSYRK_LEVELS_AUTO (default): chosen from the shape;
+                       0 = classical SYRK from the same leaves (no Algorithm 2
+                       level); L >= 1 = L levels of Algorithm 2, L <= 6        */
+    int32_t reserved[6]; /* must be zero                                       */
+} ffsyrk_options_t;
+
+/* The defaults: automatic leaf and recursion depth. */
+void ffsyrk_options_default(ffsyrk_options_t *opts);
+
+/* Opaque plan: the field constants (p, Y), the digit scheme, the recursion
+ * depth and the device workspace for problems up to max_n × max_k.  Owned by
+ * the caller; release with ffsyrk_plan_destroy().  A plan belongs to the
+ * device that was current when it was made; it is not thread-safe (use one
+ * plan per host thread, or serialise calls). */
+typedef struct ffsyrk_plan_st *ffsyrk_plan_t;
+
+/* Make a plan for p and problems with n ≤ max_n, k ≤ max_k.  Validates p
+ * (Miller-Rabin), builds Y (a square root of −1 when p ≡ 1 mod 4, else
+ * Y = I ⊗ [[a,b],[−b,a]] with a² + b² ≡ −1: Section 3.1, Prop. 3.2, Prop. 3.3,
+ * Algorithm 3), chooses digits and chunk lengths, and allocates the
+ * workspace (cudaMalloc).  On failure *plan is set to NULL. */
+ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int64_t max_k,
+                            const ffsyrk_options_t *opts);
+
+/* Free the plan's workspace.  Synchronises the device work it enqueued.
+ * NULL is accepted. */
+ffsyrk_status_t ffsyrk_plan_destroy(ffsyrk_plan_t plan);
+
+/* C = A·Aᵀ mod p (triangle `uplo`) with an existing plan; p must equal the
+ * plan's p and n ≤ max_n, k ≤ max_k. */
+ffsyrk_status_t ffsyrk_with_plan(ffsyrk_plan_t plan, ffsyrk_uplo_t uplo, int64_t n, int64_t k,
+                                 uint32_t p, const uint32_t *A, int64_t lda, uint32_t *C,
+                                 int64_t ldc, ffsyrk_stream_t stream);
+
+/* C = A·Aᵀ mod p with default options, through an internal per-device plan
+ * cache keyed by (p, shape).  Thread-safe. */
+ffsyrk_status_t ffsyrk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p, const uint32_t *A,
+                       int64_t lda, uint32_t *C, int64_t ldc, ffsyrk_stream_t stream);
+
+/* `count` independent products C_t = A_t·A_tᵀ mod p of uneven sizes n[t] × k[t],
+ * all with the same p and uplo.  n, k, lda, ldc are HOST arrays of `count`
+ * values; A and C are HOST arrays of `count` DEVICE pointers.  Problems with
+ * n[t] = 0 are skipped.  Workspace comes from an internal per-device cache. */
+ffsyrk_status_t ffsyrk_batched(ffsyrk_uplo_t uplo, int64_t count, const int64_t *n,
+                               const int64_t *k, uint32_t p, const uint32_t *const *A,
+                               const int64_t *lda, uint32_t *const *C, const int64_t *ldc,
+                               ffsyrk_stream_t stream);
+
+/* Wait for the plan's enqueued work on `stream` and report any device-side
+ * failure recorded since the last call (then clear it). */
+ffsyrk_status_t ffsyrk_sync_status(ffsyrk_plan_t plan, ffsyrk_stream_t stream);
+
+/* What a plan chose, for tests and reports. */
+typedef struct {
+    uint32_t p;
+    int32_t y_form;      /* 0: scalar Y = i·I; 1: Y = I ⊗ [[a,b],[−b,a]]   */
+    uint32_t y_a;        /* i (scalar form) or a                          */
+    uint32_t y_b;        /* b (2×2 form), else 0                          */
+    int32_t y_cost;      /* y of Thm 4.1: 1, 2 or 3                       */
+    int32_t leaf;        /* ffsyrk_leaf_t actually used                   */
+    int32_t levels;      /* recursion levels L for max_n × max_k          */
+    int32_t digits;      /* D, signed base-256 digits per residue          */
+    int32_t chunk_k[9];  /* K-chunk per digit pair (i*3+j), TC leaf       */
+    int64_t workspace_bytes;
+} ffsyrk_plan_info_t;
+
+ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t plan, ffsyrk_plan_info_t *info);
+
+/* Human-readable name of a status code (static storage). */
+const char *ffsyrk_status_string(ffsyrk_status_t status);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int32_t ffsyrk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFSYRK_H */

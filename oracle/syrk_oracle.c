@@ -9,7 +9,8 @@
  *
  *     C[i][j] = ( Σ_{l<k} (A[i][l] mod p) · (A[j][l] mod p) ) mod p.
  *
- * Every entry of A may be any uint32; it is reduced mod p first.  Each
+ * Every entry of A may be any uint32; A is reduced mod p first, entry by
+ * entry, into a private copy (the input is never modified).  Each
  * product is < p² < 2^48 (p < 2^24), so a uint64 running sum is reduced
  * every 2^15 terms (2^15 · 2^48 = 2^63 < 2^64) and can never wrap.
  * Work is split over POSIX threads by output rows; the arithmetic of each
@@ -22,13 +23,14 @@
 
 #define ORACLE_REDUCE_EVERY 32768
 
-/* One entry: the dot product of rows i and j of A, mod p. */
+/* One entry: the dot product of rows i and j of the reduced A, mod p.
+ * Both rows already hold residues in [0, p). */
 static uint32_t dot_mod_p(const uint32_t *ri, const uint32_t *rj, int64_t k, uint64_t p) {
     uint64_t acc = 0;
     int64_t since = 0;
     for (int64_t l = 0; l < k; ++l) {
-        uint64_t a = (uint64_t)ri[l] % p;
-        uint64_t b = (uint64_t)rj[l] % p;
+        uint64_t a = ri[l];
+        uint64_t b = rj[l];
         acc += a * b;
         if (++since == ORACLE_REDUCE_EVERY) {
             acc %= p;
@@ -77,7 +79,21 @@ static void *worker(void *arg) {
     return NULL;
 }
 
+/* A mod p, entry by entry, into a fresh n×k array (freed by the caller). */
+static uint32_t *reduce_copy(int64_t n, int64_t k, uint64_t p, const uint32_t *A, int64_t lda) {
+    size_t cnt = (size_t)(n > 0 ? n : 1) * (size_t)(k > 0 ? k : 1);
+    uint32_t *R = (uint32_t *)malloc(cnt * sizeof(uint32_t));
+    if (!R) return NULL;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t l = 0; l < k; ++l) R[i * k + l] = (uint32_t)((uint64_t)A[i * lda + l] % p);
+    return R;
+}
+
 static int run(job_t proto, int nthreads) {
+    uint32_t *R = reduce_copy(proto.n, proto.k, proto.p, proto.A, proto.lda);
+    if (!R) return -1;
+    proto.A = R;
+    proto.lda = proto.k > 0 ? proto.k : 1;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 1024) nthreads = 1024;
     pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
@@ -85,6 +101,7 @@ static int run(job_t proto, int nthreads) {
     if (!th || !jobs) {
         free(th);
         free(jobs);
+        free(R);
         return -1;
     }
     int started = 0, rc = 0;
@@ -103,6 +120,7 @@ static int run(job_t proto, int nthreads) {
     for (int t = started; t < nthreads; ++t) worker(&jobs[t]);
     free(th);
     free(jobs);
+    free(R);
     return rc < 0 && started == 0 ? -1 : 0;
 }
 

@@ -1,0 +1,1004 @@
+// C-ABI entry points and the host planner of ffsyrk.
+//
+// The planner turns one call C = A·Aᵀ mod p into a fixed sequence of kernel
+// launches following Algorithm 2 of arXiv 2001.04109 (Section 3) with L
+// levels:
+//   depth d = 0..L−1 : one pre-addition launch over the 3^d nodes of depth d
+//                      (S1..S4, the digit split of the 4 general-product
+//                      operands, and of the 3 leaf operands at d = L−1);
+//   leaves           : one grouped launch over every tile of every product —
+//                      2·3^d general products P3 = X22·S4ᵀ, P4 = S1·S2ᵀ per
+//                      depth and the 3^L leaf syrk products;
+//   depth d = L−1..0 : one post-addition launch over the nodes of depth d.
+// L = 0 is the classical comparator: digit split of A, then one lower-tile
+// syrk launch straight into C.  Odd sizes use virtual zero padding,
+// A·Aᵀ = [A 0]·[A 0]ᵀ (Section 3.1), plus zero rows that only add zero rows
+// and columns to C, which are never written.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/ffsyrk.h"
+#include "ffsyrk_internal.h"
+#include "field_host.h"
+
+using namespace fsk;
+
+namespace {
+
+constexpr int64_t kAlign = 1024;
+inline int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+inline int64_t pow3(int d) {
+    int64_t r = 1;
+    while (d-- > 0) r *= 3;
+    return r;
+}
+
+MulConst make_mul(uint32_t w, uint32_t p) {
+    MulConst c;
+    c.w = w % p;
+    c.w_sh = (uint32_t)(((uint64_t)c.w << 32) / p);
+    return c;
+}
+
+DigitScheme make_digits(uint32_t p) {
+    DigitScheme ds{};
+    const int64_t H = (p - 1) / 2;
+    int D = 1;
+    int top = 0;
+    for (D = 1; D <= kMaxDigits; ++D) {
+        int dh[kMaxDigits], dl[kMaxDigits];
+        host::split_digits(H, D, dh);
+        host::split_digits(-H, D, dl);
+        top = std::max(std::abs(dh[D - 1]), std::abs(dl[D - 1]));
+        if (top <= 256) break;
+    }
+    ds.D = D;
+    for (int t = 0; t < D; ++t) ds.max_digit[t] = (t == D - 1) ? std::max(top, 1) : 128;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            int64_t kc = (int64_t(1) << 24) / ((int64_t)ds.max_digit[i] * ds.max_digit[j]);
+            ds.chunk_kb[i][j] = (int)std::max<int64_t>(1, kc / 64);
+            uint64_t w = 1;
+            for (int e = 0; e < i + j; ++e) w = w * 256 % p;
+            ds.weight[i][j] = make_mul((uint32_t)w, p);
+        }
+    ds.offset = (uint32_t)(((uint64_t(1) << 24) + p - 1) / p * p);
+    return ds;
+}
+
+// ---- geometry of one call ----
+struct Geometry {
+    int L = 0;
+    int64_t n = 0, k = 0, np = 0, kp = 0;
+    int64_t h[kMaxLevels + 1] = {}, w[kMaxLevels + 1] = {};
+};
+
+Geometry make_geometry(int64_t n, int64_t k, int L) {
+    Geometry g;
+    g.L = L;
+    g.n = n;
+    g.k = k;
+    if (L == 0) {
+        g.np = n;
+        g.kp = k;
+    } else {
+        g.np = rup(std::max<int64_t>(n, 1), int64_t(1) << L);
+        // w_L even at every depth (the interleaved 2×2 Y pairs columns)
+        g.kp = rup(std::max<int64_t>(k, 1), int64_t(1) << (L + 1));
+    }
+    for (int d = 0; d <= L; ++d) {
+        g.h[d] = g.np >> d;
+        g.w[d] = g.kp >> d;
+    }
+    return g;
+}
+
+struct Layout {
+    Geometry g;
+    int leaf = FFSYRK_LEAF_TC_BF16;
+    int narenas = 0;
+    Arena arena[kMaxLevels + 1];          // index j: K = w_j (j = 0 only for L = 0)
+    int64_t arena_off[kMaxLevels + 1] = {};
+    int64_t s3_off[kMaxLevels + 1] = {};  // S3 node buffers of depth d (1 ≤ d ≤ L−1)
+    int64_t r_off[kMaxLevels + 1] = {};   // node results of depth d (1 ≤ d ≤ L)
+    int64_t g_off[kMaxLevels + 1] = {};   // P3/P4 of depth d (0 ≤ d ≤ L−1)
+    int64_t data_bytes = 0;
+};
+
+int64_t arena_nops(const Geometry &g, int j) {
+    if (g.L == 0) return 1;
+    return 4 * pow3(j - 1) + (j == g.L ? pow3(g.L) : 0);
+}
+
+Layout make_layout(const Geometry &g, int leaf, int D) {
+    Layout lay;
+    lay.g = g;
+    lay.leaf = leaf;
+    const bool tc = leaf == FFSYRK_LEAF_TC_BF16;
+    int64_t off = 0;
+    auto take = [&](int64_t bytes) {
+        int64_t o = off;
+        off += rup(std::max<int64_t>(bytes, 0), kAlign);
+        return o;
+    };
+    const int j0 = g.L == 0 ? 0 : 1;
+    lay.narenas = g.L == 0 ? 1 : g.L;
+    for (int j = j0; j <= (g.L == 0 ? 0 : g.L); ++j) {
+        Arena &a = lay.arena[j];
+        a.kind = tc ? ARENA_BF16 : ARENA_U32;
+        a.planes = tc ? D : 1;
+        a.rpad = rup(std::max<int64_t>(g.h[j], 1), 256);
+        a.kpad = rup(std::max<int64_t>(g.w[j], 1), 64);
+        a.rows = arena_nops(g, j) * a.planes * a.rpad;
+        lay.arena_off[j] = take(a.bytes());
+    }
+    for (int d = 1; d <= g.L - 1; ++d) lay.s3_off[d] = take(pow3(d - 1) * g.h[d] * g.w[d] * 4);
+    for (int d = 1; d <= g.L; ++d) lay.r_off[d] = take(pow3(d) * g.h[d] * g.h[d] * 4);
+    for (int d = 0; d <= g.L - 1; ++d)
+        lay.g_off[d] = take(2 * pow3(d) * g.h[d + 1] * g.h[d + 1] * 4);
+    lay.data_bytes = off;
+    return lay;
+}
+
+// ---- descriptors of one call ----
+struct Descs {
+    std::vector<PrepNode> prep[kMaxLevels];
+    std::vector<PostNode> post[kMaxLevels];
+    std::vector<LeafProd> prods;
+    std::vector<LeafTile> tiles;
+    std::vector<DigitizeJob> digit;
+    int64_t digit_max_work = 0;
+    // blob offsets (bytes) inside the descriptor region
+    int64_t prep_off[kMaxLevels] = {}, post_off[kMaxLevels] = {};
+    int64_t prods_off = 0, tiles_off = 0, tmap_off = 0, aptr_off = 0, akpad_off = 0, digit_off = 0;
+    int64_t bytes = 0;
+};
+
+int64_t desc_capacity(const Geometry &g, int leaf) {
+    // generous bound for the descriptor blob of any shape ≤ g
+    int64_t b = 0;
+    for (int d = 0; d < g.L; ++d) b += pow3(d) * (sizeof(PrepNode) + sizeof(PostNode)) + 2 * 256;
+    int64_t nprods = 1;
+    int64_t ntiles = 0;
+    const int64_t tm = leaf == FFSYRK_LEAF_TC_BF16 ? 128 : 64, tn = leaf == FFSYRK_LEAF_TC_BF16 ? 256 : 64;
+    if (g.L == 0) {
+        ntiles = ((g.n + tm - 1) / tm) * ((g.n + tn - 1) / tn);
+    } else {
+        for (int d = 0; d < g.L; ++d) {
+            int64_t h = g.h[d + 1];
+            ntiles += 2 * pow3(d) * ((h + tm - 1) / tm) * ((h + tn - 1) / tn);
+            nprods += 2 * pow3(d);
+        }
+        int64_t h = g.h[g.L];
+        ntiles += pow3(g.L) * ((h + tm - 1) / tm) * ((h + tn - 1) / tn);
+        nprods += pow3(g.L);
+    }
+    b += nprods * sizeof(LeafProd) + ntiles * sizeof(LeafTile);
+    b += (kMaxLevels + 1) * (128 + 16) + 8 * 256 + sizeof(DigitizeJob);
+    return rup(b, kAlign);
+}
+
+// TMA descriptor encoding through the driver entry point (no -lcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+}  // namespace
+
+namespace fsk {
+bool encode_arena_tmap(const Arena &a, void *out) {
+    EncodeTiledFn fn = get_encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)a.kpad, (cuuint64_t)a.rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(a.kpad * 2)};
+    cuuint32_t box[2] = {64, 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(reinterpret_cast<CUtensorMap *>(out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    a.base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+}  // namespace fsk
+
+struct ffsyrk_plan_st {
+    int device = 0;
+    int sms = 0;
+    uint32_t p = 0;
+    ModP mp{};
+    host::YChoice ych{};
+    YConst yc{};
+    DigitScheme ds{};
+    int leaf = FFSYRK_LEAF_TC_BF16;
+    int levels_opt = FFSYRK_LEVELS_AUTO;
+    int64_t max_n = 0, max_k = 0;
+    int L_max = 0;  // levels used at the max shape
+    // device workspace: data region then descriptor region
+    char *ws = nullptr;
+    int64_t ws_bytes = 0, data_cap = 0, desc_cap = 0;
+    char *desc_host = nullptr;  // pinned staging for the descriptor blob
+    cudaEvent_t desc_done = nullptr;
+    bool desc_pending = false;
+    unsigned int *err_host = nullptr, *err_dev = nullptr;  // mapped host word
+    // last call, to skip re-planning when nothing changed
+    bool have_last = false;
+    std::tuple<int64_t, int64_t, const uint32_t *, int64_t, uint32_t *, int64_t, int, int> last_key;
+    Layout lay;
+    Descs desc;
+    Geometry last_geom_for_zero;
+    bool zeroed_for_last = false;
+};
+
+namespace {
+
+int choose_levels(const ffsyrk_plan_st *pl, int64_t n, int64_t k) {
+    if (pl->levels_opt >= 0) return pl->levels_opt;
+    // Automatic depth: recurse while the halves stay large enough that the
+    // saved products outweigh the extra block additions on this GPU.
+    int L = 0;
+    int64_t nn = n, kk = k;
+    while (L < 4 && nn >= 8192 && kk >= 2048) {
+        nn /= 2;
+        kk /= 2;
+        ++L;
+    }
+    return L;
+}
+
+ffsyrk_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? FFSYRK_SUCCESS : FFSYRK_ERR_CUDA; }
+
+void tri_tiles(std::vector<LeafTile> &out, int prod, int64_t rows, int64_t cols, int tri,
+               int64_t tm, int64_t tn, int cost) {
+    const int64_t TM = (rows + tm - 1) / tm, TN = (cols + tn - 1) / tn;
+    for (int64_t a = 0; a < TM; ++a)
+        for (int64_t b = 0; b < TN; ++b) {
+            const int64_t r0 = a * tm, r1 = std::min(rows, r0 + tm) - 1;
+            const int64_t c0 = b * tn, c1 = std::min(cols, c0 + tn) - 1;
+            if (tri == 1 && r1 < c0) continue;  // no entry with c ≤ r
+            if (tri == 2 && c1 < r0) continue;  // no entry with c ≥ r
+            out.push_back(LeafTile{prod, (int32_t)a, (int32_t)b, cost});
+        }
+}
+
+// Build every descriptor of one call into pl->desc and the staging blob.
+ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int64_t lda,
+                            uint32_t *C, int64_t ldc) {
+    Layout &lay = pl->lay;
+    const Geometry &g = lay.g;
+    Descs &D = pl->desc;
+    D = Descs();
+    char *ws = pl->ws;
+    const bool tc = lay.leaf == FFSYRK_LEAF_TC_BF16;
+    const int64_t TM = tc ? leaf_tc_bm() : leaf_i64_tile();
+    const int64_t TN = tc ? leaf_tc_bn() : leaf_i64_tile();
+    for (int j = 0; j <= kMaxLevels; ++j)
+        if (lay.arena[j].rows > 0) lay.arena[j].base = ws + lay.arena_off[j];
+
+    auto operand = [&](int j, int64_t o) {
+        const Arena &a = lay.arena[j];
+        OperandDst d;
+        d.arena = a.base;
+        d.row0 = o * a.planes * a.rpad;
+        d.kpad = a.kpad;
+        d.rpad = a.rpad;
+        return d;
+    };
+    auto rbuf = [&](int d, int64_t t) {
+        return reinterpret_cast<uint32_t *>(ws + lay.r_off[d]) + t * g.h[d] * g.h[d];
+    };
+    auto gbuf = [&](int d, int64_t t, int q) {
+        const int64_t h = g.h[d + 1];
+        return reinterpret_cast<uint32_t *>(ws + lay.g_off[d]) + (2 * t + q) * h * h;
+    };
+    int cost_mult = tc ? pl->ds.D * pl->ds.D : 1;
+
+    if (g.L == 0) {
+        LeafProd pr{};
+        pr.arena = 0;
+        pr.tri = uplo == FFSYRK_UPPER ? 2 : 1;
+        pr.a_row0 = pr.b_row0 = 0;
+        pr.rows = pr.cols = g.n;
+        pr.kblocks = (int32_t)(lay.arena[0].kpad / 64);
+        pr.out = C;
+        pr.ldo = ldc;
+        D.prods.push_back(pr);
+        tri_tiles(D.tiles, 0, g.n, g.n, pr.tri, TM, TN, pr.kblocks * cost_mult);
+        const Arena &a0 = lay.arena[0];
+        D.digit.push_back(DigitizeJob{MatView{A, lda, g.n, g.k}, g.n,
+                                      OperandDst{a0.base, 0, a0.kpad, a0.rpad}});
+        D.digit_max_work = g.n * (a0.kpad / 2);
+    } else {
+        // node views, depth by depth
+        std::vector<MatView> views{MatView{A, lda, g.n, g.k}};
+        for (int d = 0; d < g.L; ++d) {
+            const int64_t h = g.h[d + 1], w = g.w[d + 1];
+            std::vector<MatView> next;
+            for (int64_t t = 0; t < (int64_t)views.size(); ++t) {
+                const MatView &X = views[t];
+                PrepNode nd{};
+                nd.X = X;
+                for (int q = 0; q < 4; ++q) nd.gemm[q] = operand(d + 1, 4 * t + q);
+                if (d == g.L - 1) {
+                    for (int q = 0; q < 3; ++q)
+                        nd.leaf[q] = operand(g.L, 4 * pow3(g.L - 1) + 3 * t + q);
+                    nd.s3 = nullptr;
+                    nd.s3_ld = 0;
+                } else {
+                    nd.s3 = reinterpret_cast<uint32_t *>(ws + lay.s3_off[d + 1]) + t * h * w;
+                    nd.s3_ld = w;
+                    MatView x11{X.ptr, X.ld, std::min(X.vr, h), std::min(X.vc, w)};
+                    MatView x12{X.ptr + w, X.ld, std::min(X.vr, h),
+                                std::max<int64_t>(0, std::min(X.vc - w, w))};
+                    MatView s3{nd.s3, w, h, w};
+                    next.push_back(x11);
+                    next.push_back(x12);
+                    next.push_back(s3);
+                }
+                D.prep[d].push_back(nd);
+                // the two general products of this node
+                for (int q = 0; q < 2; ++q) {
+                    LeafProd pr{};
+                    pr.arena = d + 1;
+                    pr.tri = 0;
+                    pr.a_row0 = operand(d + 1, 4 * t + 2 * q).row0;
+                    pr.b_row0 = operand(d + 1, 4 * t + 2 * q + 1).row0;
+                    pr.rows = pr.cols = h;
+                    pr.kblocks = (int32_t)(lay.arena[d + 1].kpad / 64);
+                    pr.out = gbuf(d, t, q);
+                    pr.ldo = h;
+                    D.prods.push_back(pr);
+                    tri_tiles(D.tiles, (int)D.prods.size() - 1, h, h, 0, TM, TN,
+                              pr.kblocks * cost_mult);
+                }
+            }
+            views.swap(next);
+        }
+        // the 3^L leaf syrk products
+        const int64_t hL = g.h[g.L];
+        for (int64_t t = 0; t < pow3(g.L); ++t) {
+            LeafProd pr{};
+            pr.arena = g.L;
+            pr.tri = 1;
+            pr.a_row0 = pr.b_row0 = operand(g.L, 4 * pow3(g.L - 1) + t).row0;
+            pr.rows = pr.cols = hL;
+            pr.kblocks = (int32_t)(lay.arena[g.L].kpad / 64);
+            pr.out = rbuf(g.L, t);
+            pr.ldo = hL;
+            D.prods.push_back(pr);
+            tri_tiles(D.tiles, (int)D.prods.size() - 1, hL, hL, 1, TM, TN, pr.kblocks * cost_mult);
+        }
+        // post-additions, node results of depth d from depth d+1
+        for (int d = g.L - 1; d >= 0; --d) {
+            const int64_t h = g.h[d + 1];
+            for (int64_t t = 0; t < pow3(d); ++t) {
+                PostNode pn{};
+                pn.P1 = rbuf(d + 1, 3 * t);
+                pn.P2 = rbuf(d + 1, 3 * t + 1);
+                pn.P5 = rbuf(d + 1, 3 * t + 2);
+                pn.ldr = h;
+                pn.P3 = gbuf(d, t, 0);
+                pn.P4 = gbuf(d, t, 1);
+                pn.ldg = h;
+                if (d == 0) {
+                    pn.out = C;
+                    pn.ldo = ldc;
+                    pn.vn = g.n;
+                    pn.upper = uplo == FFSYRK_UPPER;
+                } else {
+                    pn.out = rbuf(d, t);
+                    pn.ldo = g.h[d];
+                    pn.vn = g.h[d];
+                    pn.upper = 0;
+                }
+                D.post[d].push_back(pn);
+            }
+        }
+    }
+    // longest tiles first, then round-robin over persistent CTAs
+    std::stable_sort(D.tiles.begin(), D.tiles.end(),
+                     [](const LeafTile &a, const LeafTile &b) { return a.cost > b.cost; });
+
+    // pack the blob
+    int64_t off = 0;
+    auto slot = [&](int64_t bytes, int64_t align) {
+        off = rup(off, align);
+        int64_t o = off;
+        off += bytes;
+        return o;
+    };
+    for (int d = 0; d < g.L; ++d) {
+        D.prep_off[d] = slot((int64_t)D.prep[d].size() * sizeof(PrepNode), 256);
+        D.post_off[d] = slot((int64_t)D.post[d].size() * sizeof(PostNode), 256);
+    }
+    D.prods_off = slot((int64_t)D.prods.size() * sizeof(LeafProd), 256);
+    D.tiles_off = slot((int64_t)D.tiles.size() * sizeof(LeafTile), 256);
+    D.tmap_off = slot((kMaxLevels + 1) * 128, 128);
+    D.aptr_off = slot((kMaxLevels + 1) * sizeof(void *), 64);
+    D.akpad_off = slot((kMaxLevels + 1) * sizeof(int64_t), 64);
+    D.digit_off = slot((int64_t)D.digit.size() * sizeof(DigitizeJob), 64);
+    D.bytes = rup(off, 256);
+    if (D.bytes > pl->desc_cap) return FFSYRK_ERR_TOO_LARGE;
+
+    char *hb = pl->desc_host;
+    memset(hb, 0, (size_t)D.bytes);
+    for (int d = 0; d < g.L; ++d) {
+        memcpy(hb + D.prep_off[d], D.prep[d].data(), D.prep[d].size() * sizeof(PrepNode));
+        memcpy(hb + D.post_off[d], D.post[d].data(), D.post[d].size() * sizeof(PostNode));
+    }
+    memcpy(hb + D.prods_off, D.prods.data(), D.prods.size() * sizeof(LeafProd));
+    memcpy(hb + D.tiles_off, D.tiles.data(), D.tiles.size() * sizeof(LeafTile));
+    memcpy(hb + D.digit_off, D.digit.data(), D.digit.size() * sizeof(DigitizeJob));
+    for (int j = 0; j <= kMaxLevels; ++j) {
+        const Arena &a = lay.arena[j];
+        if (a.rows == 0) continue;
+        reinterpret_cast<void **>(hb + D.aptr_off)[j] = a.base;
+        reinterpret_cast<int64_t *>(hb + D.akpad_off)[j] = a.kpad;
+        if (tc && !encode_arena_tmap(a, hb + D.tmap_off + 128 * j)) return FFSYRK_ERR_CUDA;
+    }
+    return FFSYRK_SUCCESS;
+}
+
+ffsyrk_status_t validate_p(uint32_t p) {
+    if (p < 3 || p >= (1u << 24)) return FFSYRK_ERR_UNSUPPORTED_P;
+    if (!host::is_prime(p)) return FFSYRK_ERR_NOT_PRIME;
+    return FFSYRK_SUCCESS;
+}
+
+int64_t workspace_need(const ffsyrk_plan_st *pl, int64_t n, int64_t k, int L, int64_t *desc) {
+    Geometry g = make_geometry(n, k, L);
+    Layout lay = make_layout(g, pl->leaf, pl->ds.D);
+    *desc = desc_capacity(g, pl->leaf);
+    return lay.data_bytes;
+}
+
+ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, const uint32_t *A,
+                        int64_t lda, uint32_t *C, int64_t ldc, cudaStream_t st) {
+    cudaError_t e;
+    if (n == 0) return FFSYRK_SUCCESS;
+    if (k == 0) return cuda_status(launch_zero_tri(C, n, ldc, uplo == FFSYRK_UPPER, st));
+    const int L = choose_levels(pl, n, k);
+    auto key = std::make_tuple(n, k, A, lda, C, ldc, uplo, L);
+    if (!pl->have_last || key != pl->last_key) {
+        Geometry g = make_geometry(n, k, L);
+        Layout lay = make_layout(g, pl->leaf, pl->ds.D);
+        if (lay.data_bytes > pl->data_cap) return FFSYRK_ERR_TOO_LARGE;
+        // the staging blob may still be in flight from the previous upload
+        if (pl->desc_pending) {
+            cudaEventSynchronize(pl->desc_done);
+            pl->desc_pending = false;
+        }
+        pl->lay = lay;
+        ffsyrk_status_t s = build_descs(pl, uplo, A, lda, C, ldc);
+        if (s != FFSYRK_SUCCESS) {
+            pl->have_last = false;
+            return s;
+        }
+        char *dd = pl->ws + pl->data_cap;
+        e = cudaMemcpyAsync(dd, pl->desc_host, (size_t)pl->desc.bytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+        cudaEventRecord(pl->desc_done, st);
+        pl->desc_pending = true;
+        pl->last_key = key;
+        pl->have_last = true;
+    }
+    const Layout &lay = pl->lay;
+    const Geometry &g = lay.g;
+    const Descs &D = pl->desc;
+    char *dd = pl->ws + pl->data_cap;
+    const int kind = lay.leaf == FFSYRK_LEAF_TC_BF16 ? ARENA_BF16 : ARENA_U32;
+    if (g.L == 0) {
+        e = launch_digitize(reinterpret_cast<const DigitizeJob *>(dd + D.digit_off), 1,
+                            D.digit_max_work, pl->mp, pl->ds, kind, st);
+        if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+    } else {
+        for (int d = 0; d < g.L; ++d) {
+            e = launch_prep(reinterpret_cast<const PrepNode *>(dd + D.prep_off[d]),
+                            (int)D.prep[d].size(), g.h[d + 1], g.w[d + 1], lay.arena[d + 1].kpad,
+                            pl->mp, pl->yc, pl->ds, kind, st);
+            if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+        }
+    }
+    if (lay.leaf == FFSYRK_LEAF_TC_BF16) {
+        TcLaunch tl{};
+        tl.prods = reinterpret_cast<const LeafProd *>(dd + D.prods_off);
+        tl.tiles = reinterpret_cast<const LeafTile *>(dd + D.tiles_off);
+        tl.ntiles = (int)D.tiles.size();
+        tl.tmaps = dd + D.tmap_off;
+        tl.mp = pl->mp;
+        tl.ds = pl->ds;
+        tl.err = pl->err_dev;
+        tl.tile_ctr = nullptr;
+        e = launch_leaf_tc(tl, pl->sms, st);
+    } else {
+        e = launch_leaf_i64_arrays(reinterpret_cast<const LeafProd *>(dd + D.prods_off),
+                                   reinterpret_cast<const LeafTile *>(dd + D.tiles_off),
+                                   (int)D.tiles.size(),
+                                   reinterpret_cast<const uint32_t *const *>(dd + D.aptr_off),
+                                   reinterpret_cast<const int64_t *>(dd + D.akpad_off), pl->mp, st);
+    }
+    if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+    for (int d = g.L - 1; d >= 0; --d) {
+        e = launch_post(reinterpret_cast<const PostNode *>(dd + D.post_off[d]),
+                        (int)D.post[d].size(), g.h[d + 1], pl->mp, st);
+        if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+    }
+    return FFSYRK_SUCCESS;
+}
+
+void destroy_plan(ffsyrk_plan_st *pl) {
+    if (!pl) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != pl->device) cudaSetDevice(pl->device);
+    if (pl->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(pl->ws);
+    }
+    if (pl->desc_done) cudaEventDestroy(pl->desc_done);
+    if (pl->desc_host) cudaFreeHost(pl->desc_host);
+    if (pl->err_host) cudaFreeHost(pl->err_host);
+    if (cur != pl->device) cudaSetDevice(cur);
+    delete pl;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ffsyrk_status_string(ffsyrk_status_t s) {
+    switch (s) {
+        case FFSYRK_SUCCESS: return "FFSYRK_SUCCESS";
+        case FFSYRK_ERR_INVALID_ARG: return "FFSYRK_ERR_INVALID_ARG: invalid argument";
+        case FFSYRK_ERR_NOT_PRIME: return "FFSYRK_ERR_NOT_PRIME: p is not prime";
+        case FFSYRK_ERR_UNSUPPORTED_P: return "FFSYRK_ERR_UNSUPPORTED_P: p must be an odd prime below 2^24";
+        case FFSYRK_ERR_ALLOC: return "FFSYRK_ERR_ALLOC: workspace allocation failed";
+        case FFSYRK_ERR_CUDA: return "FFSYRK_ERR_CUDA: a CUDA call failed";
+        case FFSYRK_ERR_TIMEOUT: return "FFSYRK_ERR_TIMEOUT: a device-side bounded wait ran out";
+        case FFSYRK_ERR_ARCH: return "FFSYRK_ERR_ARCH: the device is not a GB300 (sm_103)";
+        case FFSYRK_ERR_TOO_LARGE: return "FFSYRK_ERR_TOO_LARGE: shape exceeds the plan";
+    }
+    return "FFSYRK: unknown status";
+}
+
+int32_t ffsyrk_version(void) { return 100; }
+
+void ffsyrk_options_default(ffsyrk_options_t *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->leaf = FFSYRK_LEAF_AUTO;
+    o->levels = FFSYRK_LEVELS_AUTO;
+}
+
+ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int64_t max_k,
+                            const ffsyrk_options_t *opts) {
+    if (!plan) return FFSYRK_ERR_INVALID_ARG;
+    *plan = nullptr;
+    ffsyrk_status_t s = validate_p(p);
+    if (s != FFSYRK_SUCCESS) return s;
+    if (max_n < 0 || max_k < 0 || max_n > (int64_t(1) << 20) || max_k > (int64_t(1) << 24))
+        return FFSYRK_ERR_INVALID_ARG;
+    ffsyrk_options_t o;
+    ffsyrk_options_default(&o);
+    if (opts) o = *opts;
+    if (o.leaf < FFSYRK_LEAF_AUTO || o.leaf > FFSYRK_LEAF_I64) return FFSYRK_ERR_INVALID_ARG;
+    if (o.levels < FFSYRK_LEVELS_AUTO || o.levels > kMaxLevels) return FFSYRK_ERR_INVALID_ARG;
+    for (int i = 0; i < 6; ++i)
+        if (o.reserved[i] != 0) return FFSYRK_ERR_INVALID_ARG;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFSYRK_ERR_CUDA;
+    int major = 0, minor = 0, sms = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (major != 10 || minor != 3) return FFSYRK_ERR_ARCH;
+
+    ffsyrk_plan_st *pl = new (std::nothrow) ffsyrk_plan_st();
+    if (!pl) return FFSYRK_ERR_ALLOC;
+    pl->device = dev;
+    pl->sms = sms;
+    pl->p = p;
+    pl->mp.p = p;
+    pl->mp.half = (p - 1) / 2;
+    pl->mp.barrett = (uint32_t)((uint64_t(1) << 32) / p);
+    pl->ych = host::choose_y(p);
+    pl->yc.form = pl->ych.form;
+    pl->yc.a = make_mul((uint32_t)pl->ych.a, p);
+    pl->yc.b = make_mul((uint32_t)pl->ych.b, p);
+    pl->ds = make_digits(p);
+    pl->leaf = (o.leaf == FFSYRK_LEAF_AUTO) ? FFSYRK_LEAF_TC_BF16 : o.leaf;
+    pl->levels_opt = o.levels;
+    pl->max_n = max_n;
+    pl->max_k = max_k;
+    pl->L_max = choose_levels(pl, max_n, max_k);
+
+    // capacity: the largest layout over the depths this plan may use
+    int64_t data = 0, desc = 0;
+    {
+        int Ls[2] = {pl->L_max, pl->L_max};
+        for (int L : Ls) {
+            int64_t dc = 0;
+            int64_t db = workspace_need(pl, std::max<int64_t>(max_n, 1), std::max<int64_t>(max_k, 1), L, &dc);
+            data = std::max(data, db);
+            desc = std::max(desc, dc);
+        }
+    }
+    pl->data_cap = data;
+    pl->desc_cap = desc;
+    pl->ws_bytes = data + desc;
+    cudaError_t e = cudaMalloc(&pl->ws, (size_t)pl->ws_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        destroy_plan(pl);
+        return FFSYRK_ERR_ALLOC;
+    }
+    e = cudaMemset(pl->ws, 0, (size_t)pl->ws_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&pl->desc_host, (size_t)desc);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->desc_done, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(reinterpret_cast<void **>(&pl->err_host), sizeof(unsigned int) * 4,
+                          cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        memset(pl->err_host, 0, sizeof(unsigned int) * 4);
+        e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&pl->err_dev), pl->err_host, 0);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        destroy_plan(pl);
+        return FFSYRK_ERR_CUDA;
+    }
+    *plan = pl;
+    return FFSYRK_SUCCESS;
+}
+
+ffsyrk_status_t ffsyrk_plan_destroy(ffsyrk_plan_t plan) {
+    destroy_plan(plan);
+    return FFSYRK_SUCCESS;
+}
+
+ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t pl, ffsyrk_plan_info_t *info) {
+    if (!pl || !info) return FFSYRK_ERR_INVALID_ARG;
+    memset(info, 0, sizeof *info);
+    info->p = pl->p;
+    info->y_form = pl->ych.form;
+    info->y_a = (uint32_t)pl->ych.a;
+    info->y_b = (uint32_t)pl->ych.b;
+    info->y_cost = pl->ych.cost;
+    info->leaf = pl->leaf;
+    info->levels = pl->L_max;
+    info->digits = pl->ds.D;
+    for (int i = 0; i < pl->ds.D; ++i)
+        for (int j = 0; j < pl->ds.D; ++j) info->chunk_k[i * 3 + j] = pl->ds.chunk_kb[i][j] * 64;
+    info->workspace_bytes = pl->ws_bytes;
+    return FFSYRK_SUCCESS;
+}
+
+ffsyrk_status_t ffsyrk_with_plan(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n, int64_t k,
+                                 uint32_t p, const uint32_t *A, int64_t lda, uint32_t *C,
+                                 int64_t ldc, ffsyrk_stream_t stream) {
+    if (!pl) return FFSYRK_ERR_INVALID_ARG;
+    if (p != pl->p) return FFSYRK_ERR_INVALID_ARG;
+    if (uplo != FFSYRK_LOWER && uplo != FFSYRK_UPPER) return FFSYRK_ERR_INVALID_ARG;
+    if (n < 0 || k < 0) return FFSYRK_ERR_INVALID_ARG;
+    if (n > pl->max_n || k > pl->max_k) return FFSYRK_ERR_TOO_LARGE;
+    if (lda < std::max<int64_t>(1, k) || ldc < std::max<int64_t>(1, n)) return FFSYRK_ERR_INVALID_ARG;
+    if (n > 0 && (C == nullptr || (k > 0 && A == nullptr))) return FFSYRK_ERR_INVALID_ARG;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != pl->device) return FFSYRK_ERR_INVALID_ARG;
+    if (pl->err_host[0] != 0) return FFSYRK_ERR_TIMEOUT;
+    return enqueue(pl, uplo, n, k, A, lda, C, ldc, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ffsyrk_status_t ffsyrk_sync_status(ffsyrk_plan_t pl, ffsyrk_stream_t stream) {
+    if (!pl) return FFSYRK_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+    unsigned int w = __atomic_exchange_n(&pl->err_host[0], 0u, __ATOMIC_SEQ_CST);
+    return w ? FFSYRK_ERR_TIMEOUT : FFSYRK_SUCCESS;
+}
+
+}  // extern "C"
+
+// ---- the plan cache behind ffsyrk() ----
+namespace {
+struct CacheEntry {
+    ffsyrk_plan_t plan;
+    uint64_t last_use;
+};
+std::mutex g_cache_mu;
+std::map<std::tuple<int, uint32_t, int64_t, int64_t>, CacheEntry> g_cache;
+uint64_t g_clock = 0;
+constexpr size_t kCacheMax = 8;
+}  // namespace
+
+extern "C" ffsyrk_status_t ffsyrk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
+                                  const uint32_t *A, int64_t lda, uint32_t *C, int64_t ldc,
+                                  ffsyrk_stream_t stream) {
+    ffsyrk_status_t s = validate_p(p);
+    if (s != FFSYRK_SUCCESS) return s;
+    if (n < 0 || k < 0) return FFSYRK_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFSYRK_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto key = std::make_tuple(dev, p, n, k);
+    auto it = g_cache.find(key);
+    if (it == g_cache.end()) {
+        if (g_cache.size() >= kCacheMax) {
+            auto victim = g_cache.begin();
+            for (auto jt = g_cache.begin(); jt != g_cache.end(); ++jt)
+                if (jt->second.last_use < victim->second.last_use) victim = jt;
+            ffsyrk_plan_destroy(victim->second.plan);
+            g_cache.erase(victim);
+        }
+        ffsyrk_plan_t pl = nullptr;
+        s = ffsyrk_plan(&pl, p, n, k, nullptr);
+        if (s != FFSYRK_SUCCESS) return s;
+        it = g_cache.emplace(key, CacheEntry{pl, 0}).first;
+    }
+    it->second.last_use = ++g_clock;
+    return ffsyrk_with_plan(it->second.plan, uplo, n, k, p, A, lda, C, ldc, stream);
+}
+
+// ---- batched: many independent problems in one grouped launch ----
+namespace {
+struct BatchState {
+    int device = 0, sms = 0;
+    uint32_t p = 0;
+    ModP mp{};
+    DigitScheme ds{};
+    int leaf = FFSYRK_LEAF_TC_BF16;
+    char *ws = nullptr;
+    int64_t cap = 0;
+    char *hblob = nullptr;
+    int64_t hcap = 0;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+    unsigned int *err_host = nullptr, *err_dev = nullptr;
+};
+std::mutex g_batch_mu;
+std::map<std::pair<int, uint32_t>, BatchState *> g_batch;
+
+ffsyrk_status_t batch_state(int dev, uint32_t p, BatchState **out) {
+    auto key = std::make_pair(dev, p);
+    auto it = g_batch.find(key);
+    if (it != g_batch.end()) {
+        *out = it->second;
+        return FFSYRK_SUCCESS;
+    }
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) return FFSYRK_ERR_ARCH;
+    BatchState *b = new (std::nothrow) BatchState();
+    if (!b) return FFSYRK_ERR_ALLOC;
+    b->device = dev;
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    b->p = p;
+    b->mp.p = p;
+    b->mp.half = (p - 1) / 2;
+    b->mp.barrett = (uint32_t)((uint64_t(1) << 32) / p);
+    b->ds = make_digits(p);
+    if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void **>(&b->err_host), 16, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&b->err_dev), b->err_host, 0) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return FFSYRK_ERR_CUDA;
+    }
+    memset(b->err_host, 0, 16);
+    g_batch[key] = b;
+    *out = b;
+    return FFSYRK_SUCCESS;
+}
+}  // namespace
+
+extern "C" ffsyrk_status_t ffsyrk_batched(ffsyrk_uplo_t uplo, int64_t count, const int64_t *n,
+                                          const int64_t *k, uint32_t p, const uint32_t *const *A,
+                                          const int64_t *lda, uint32_t *const *C,
+                                          const int64_t *ldc, ffsyrk_stream_t stream) {
+    ffsyrk_status_t s = validate_p(p);
+    if (s != FFSYRK_SUCCESS) return s;
+    if (uplo != FFSYRK_LOWER && uplo != FFSYRK_UPPER) return FFSYRK_ERR_INVALID_ARG;
+    if (count < 0) return FFSYRK_ERR_INVALID_ARG;
+    if (count == 0) return FFSYRK_SUCCESS;
+    if (!n || !k || !A || !lda || !C || !ldc) return FFSYRK_ERR_INVALID_ARG;
+    for (int64_t t = 0; t < count; ++t) {
+        if (n[t] < 0 || k[t] < 0 || n[t] > (int64_t(1) << 20) || k[t] > (int64_t(1) << 24))
+            return FFSYRK_ERR_INVALID_ARG;
+        if (lda[t] < std::max<int64_t>(1, k[t]) || ldc[t] < std::max<int64_t>(1, n[t]))
+            return FFSYRK_ERR_INVALID_ARG;
+        if (n[t] > 0 && (!C[t] || (k[t] > 0 && !A[t]))) return FFSYRK_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFSYRK_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    BatchState *b = nullptr;
+    s = batch_state(dev, p, &b);
+    if (s != FFSYRK_SUCCESS) return s;
+    if (b->err_host[0] != 0) {
+        b->err_host[0] = 0;
+        return FFSYRK_ERR_TIMEOUT;
+    }
+    const bool tc = b->leaf == FFSYRK_LEAF_TC_BF16;
+    const int D = tc ? b->ds.D : 1;
+    const int64_t TM = tc ? leaf_tc_bm() : leaf_i64_tile(), TN = tc ? leaf_tc_bn() : leaf_i64_tile();
+    // problems with k = 0 only need their triangle zeroed
+    for (int64_t t = 0; t < count; ++t)
+        if (n[t] > 0 && k[t] == 0) {
+            cudaError_t e = launch_zero_tri(C[t], n[t], ldc[t], uplo == FFSYRK_UPPER, st);
+            if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+        }
+    // one arena per padded K (multiple of 64); operands stacked in it
+    std::map<int64_t, int> cls;  // kpad -> arena index
+    std::vector<Arena> arenas;
+    std::vector<int64_t> row0(count, -1);
+    for (int64_t t = 0; t < count; ++t) {
+        if (n[t] == 0 || k[t] == 0) continue;
+        const int64_t kp = rup(k[t], 64);
+        auto it = cls.find(kp);
+        if (it == cls.end()) {
+            it = cls.emplace(kp, (int)arenas.size()).first;
+            Arena a;
+            a.kind = tc ? ARENA_BF16 : ARENA_U32;
+            a.planes = D;
+            a.kpad = kp;
+            a.rows = 0;
+            a.rpad = 0;
+            arenas.push_back(a);
+        }
+        Arena &a = arenas[it->second];
+        row0[t] = a.rows;
+        a.rows += D * rup(n[t], 128);
+    }
+    if (arenas.empty()) return FFSYRK_SUCCESS;
+    std::vector<int64_t> aoff(arenas.size());
+    int64_t off = 0;
+    for (size_t j = 0; j < arenas.size(); ++j) {
+        arenas[j].rows += 256;  // TMA boxes of the last operand stay inside the map
+        aoff[j] = off;
+        off += rup(arenas[j].bytes(), kAlign);
+    }
+    std::vector<LeafProd> prods;
+    std::vector<LeafTile> tiles;
+    std::vector<DigitizeJob> jobs;
+    int64_t max_work = 0;
+    std::vector<int64_t> prod_arena;
+    for (int64_t t = 0; t < count; ++t) {
+        if (row0[t] < 0) continue;
+        const int j = cls[rup(k[t], 64)];
+        LeafProd pr{};
+        pr.arena = j;
+        pr.tri = uplo == FFSYRK_UPPER ? 2 : 1;
+        pr.a_row0 = pr.b_row0 = row0[t];
+        pr.rows = pr.cols = n[t];
+        pr.kblocks = (int32_t)(arenas[j].kpad / 64);
+        pr.out = C[t];
+        pr.ldo = ldc[t];
+        prods.push_back(pr);
+        tri_tiles(tiles, (int)prods.size() - 1, n[t], n[t], pr.tri, TM, TN,
+                  pr.kblocks * (tc ? b->ds.D * b->ds.D : 1));
+        DigitizeJob jb{};
+        jb.X = MatView{A[t], lda[t], n[t], k[t]};
+        jb.rows = n[t];
+        jb.dst = OperandDst{nullptr, row0[t], arenas[j].kpad, rup(n[t], 128)};
+        jobs.push_back(jb);
+        prod_arena.push_back(j);
+        max_work = std::max(max_work, n[t] * (arenas[j].kpad / 2));
+    }
+    std::stable_sort(tiles.begin(), tiles.end(),
+                     [](const LeafTile &x, const LeafTile &y) { return x.cost > y.cost; });
+    // blob layout after the arenas
+    int64_t boff = 0;
+    auto slot = [&](int64_t bytes, int64_t align) {
+        boff = rup(boff, align);
+        int64_t o = boff;
+        boff += bytes;
+        return o;
+    };
+    const int64_t prods_off = slot((int64_t)prods.size() * sizeof(LeafProd), 256);
+    const int64_t tiles_off = slot((int64_t)tiles.size() * sizeof(LeafTile), 256);
+    const int64_t jobs_off = slot((int64_t)jobs.size() * sizeof(DigitizeJob), 256);
+    const int64_t tmap_off = slot((int64_t)arenas.size() * 128, 128);
+    const int64_t aptr_off = slot((int64_t)arenas.size() * sizeof(void *), 64);
+    const int64_t akpad_off = slot((int64_t)arenas.size() * sizeof(int64_t), 64);
+    const int64_t blob = rup(boff, 256);
+    const int64_t need = off + blob;
+    if (b->pending) {
+        cudaEventSynchronize(b->done);
+        b->pending = false;
+    }
+    if (need > b->cap) {
+        // grow: everything enqueued before may still use the old workspace
+        if (b->ws) {
+            cudaDeviceSynchronize();
+            cudaFree(b->ws);
+            b->ws = nullptr;
+            b->cap = 0;
+        }
+        int64_t cap = std::max<int64_t>(need, need + need / 4);
+        if (cudaMalloc(&b->ws, (size_t)cap) != cudaSuccess) {
+            cudaGetLastError();
+            return FFSYRK_ERR_ALLOC;
+        }
+        b->cap = cap;
+    }
+    if (blob > b->hcap) {
+        if (b->hblob) cudaFreeHost(b->hblob);
+        b->hblob = nullptr;
+        b->hcap = 0;
+        if (cudaMallocHost(&b->hblob, (size_t)blob) != cudaSuccess) {
+            cudaGetLastError();
+            return FFSYRK_ERR_ALLOC;
+        }
+        b->hcap = blob;
+    }
+    for (size_t j = 0; j < arenas.size(); ++j) arenas[j].base = b->ws + aoff[j];
+    for (size_t q = 0; q < jobs.size(); ++q) jobs[q].dst.arena = arenas[prod_arena[q]].base;
+    char *hb = b->hblob;
+    memset(hb, 0, (size_t)blob);
+    memcpy(hb + prods_off, prods.data(), prods.size() * sizeof(LeafProd));
+    memcpy(hb + tiles_off, tiles.data(), tiles.size() * sizeof(LeafTile));
+    memcpy(hb + jobs_off, jobs.data(), jobs.size() * sizeof(DigitizeJob));
+    for (size_t j = 0; j < arenas.size(); ++j) {
+        reinterpret_cast<void **>(hb + aptr_off)[j] = arenas[j].base;
+        reinterpret_cast<int64_t *>(hb + akpad_off)[j] = arenas[j].kpad;
+        if (tc && !encode_arena_tmap(arenas[j], hb + tmap_off + 128 * j)) return FFSYRK_ERR_CUDA;
+    }
+    char *dd = b->ws + off;
+    cudaError_t e = cudaMemcpyAsync(dd, hb, (size_t)blob, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+    cudaEventRecord(b->done, st);
+    b->pending = true;
+    const int kind = tc ? ARENA_BF16 : ARENA_U32;
+    for (size_t q0 = 0; q0 < jobs.size(); q0 += 65535) {
+        const int nj = (int)std::min<size_t>(65535, jobs.size() - q0);
+        e = launch_digitize(reinterpret_cast<const DigitizeJob *>(dd + jobs_off) + q0, nj, max_work,
+                            b->mp, b->ds, kind, st);
+        if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+    }
+    if (tc) {
+        TcLaunch tl{};
+        tl.prods = reinterpret_cast<const LeafProd *>(dd + prods_off);
+        tl.tiles = reinterpret_cast<const LeafTile *>(dd + tiles_off);
+        tl.ntiles = (int)tiles.size();
+        tl.tmaps = dd + tmap_off;
+        tl.mp = b->mp;
+        tl.ds = b->ds;
+        tl.err = b->err_dev;
+        tl.tile_ctr = nullptr;
+        e = launch_leaf_tc(tl, b->sms, st);
+    } else {
+        e = launch_leaf_i64_arrays(reinterpret_cast<const LeafProd *>(dd + prods_off),
+                                   reinterpret_cast<const LeafTile *>(dd + tiles_off),
+                                   (int)tiles.size(),
+                                   reinterpret_cast<const uint32_t *const *>(dd + aptr_off),
+                                   reinterpret_cast<const int64_t *>(dd + akpad_off), b->mp, st);
+    }
+    return e == cudaSuccess ? FFSYRK_SUCCESS : FFSYRK_ERR_CUDA;
+}

@@ -1,0 +1,164 @@
+// Internal declarations shared by the ffsyrk translation units.
+//
+// Data layout in HBM (one call of Algorithm 2 with L levels, n×k padded to
+// n_pad×k_pad so that every level splits evenly):
+//   * node matrices (uint32 residues in [0,p)): depth 0 is the user's A
+//     (read with virtual zero padding); X11 and X12 children are strided views
+//     of their parent; only S3 children are materialised;
+//   * operand arenas, one per leaf K length: arena j (1 ≤ j ≤ L) holds the
+//     general-product operands of depth j−1 (X22, S4, S1, S2 per node) and,
+//     for j = L, the 3^L syrk-leaf operands.  Each operand is D digit planes
+//     of R_pad×K_pad elements, plane after plane (bf16 digits for the tensor
+//     leaf; one plane of uint32 residues for the int64 leaf);
+//   * product buffers: leaf syrk results and per-depth node results (lower
+//     triangle used), P3/P4 per node (full), all uint32 residues.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace fsk {
+
+constexpr int kMaxLevels = 6;
+constexpr int kMaxDigits = 3;
+
+// Barrett-style reduction constants for p < 2^24.
+struct ModP {
+    uint32_t p;
+    uint32_t half;     // (p−1)/2: residues above it are negative in signed form
+    uint32_t barrett;  // floor(2^32 / p)
+};
+
+// Multiplication by a constant w < p with Shoup's precomputed quotient
+// w_sh = floor(w·2^32 / p).
+struct MulConst {
+    uint32_t w;
+    uint32_t w_sh;
+};
+
+// The skew-orthogonal Y (Section 3.1): form 0 is i·I; form 1 is the
+// interleaved I ⊗ [[a, b], [−b, a]].
+struct YConst {
+    int form;
+    MulConst a;  // i, or a
+    MulConst b;  // b (form 1)
+};
+
+// Signed base-256 digits of the symmetric residue and the per-pair
+// chunk lengths that keep every FP32 partial sum an exact integer.
+struct DigitScheme {
+    int D;
+    int max_digit[kMaxDigits];                 // bound of |digit t|
+    int chunk_kb[kMaxDigits][kMaxDigits];      // K-chunk per pair, in 64-wide k-blocks
+    MulConst weight[kMaxDigits][kMaxDigits];   // 256^(i+j) mod p
+    uint32_t offset;                           // a multiple of p ≥ 2^24
+};
+
+// A uint32 matrix view with virtual zero padding beyond (vr, vc).
+struct MatView {
+    const uint32_t *ptr;
+    int64_t ld;
+    int64_t vr, vc;
+};
+
+// Element types of operand arenas.
+enum ArenaKind { ARENA_BF16 = 0, ARENA_U32 = 1 };
+
+struct Arena {
+    void *base = nullptr;   // [rows][kpad] elements
+    int64_t rows = 0;       // total rows (all operands, all digit planes)
+    int64_t kpad = 0;       // padded leaf K (multiple of 64)
+    int64_t rpad = 0;       // rows per digit plane of one operand
+    int planes = 1;         // digit planes per operand
+    int kind = ARENA_BF16;
+    int64_t bytes() const { return rows * kpad * (kind == ARENA_BF16 ? 2 : 4); }
+};
+
+// Destination of one derived operand written by a pre-addition kernel.
+struct OperandDst {
+    void *arena;       // nullptr = not written
+    int64_t row0;      // first row of digit plane 0
+    int64_t kpad;      // row length in elements
+    int64_t rpad;      // rows per digit plane
+};
+
+// One node of a recursion depth for the pre-addition kernel.
+struct PrepNode {
+    MatView X;                  // the node's (padded h×w) matrix
+    OperandDst gemm[4];         // X22, S4 (P3 = X22·S4ᵀ) and S1, S2 (P4 = S1·S2ᵀ)
+    OperandDst leaf[3];         // X11, X12, S3 as leaf operands (last level)
+    uint32_t *s3;               // S3 as uint32 for the next depth (else nullptr)
+    int64_t s3_ld;
+};
+
+// One matrix to digit-split (classical path; one per problem when batched).
+struct DigitizeJob {
+    MatView X;
+    int64_t rows;
+    OperandDst dst;
+};
+
+// One post-addition node: combines the five products into the node result.
+struct PostNode {
+    const uint32_t *P1, *P2, *P5;  // lower h×h (ld = ldr)
+    const uint32_t *P3, *P4;       // full h×h (ld = ldg)
+    int64_t ldr, ldg;
+    uint32_t *out;                 // 2h×2h result
+    int64_t ldo;
+    int64_t vn;                    // rows/cols of `out` that exist (root: n)
+    int upper;                     // write the upper triangle (transposed)
+};
+
+// One leaf product out = X·Zᵀ mod p (rows × cols) on arena operands.
+struct LeafProd {
+    int32_t arena;
+    int32_t tri;          // entries written: 0 all; 1 lower (c ≤ r); 2 upper (c ≥ r)
+    int64_t a_row0, b_row0;
+    int64_t rows, cols;   // valid output extent
+    int32_t kblocks;      // K_pad / 64
+    int32_t pad_;
+    uint32_t *out;
+    int64_t ldo;
+};
+
+struct LeafTile {
+    int32_t prod;
+    int32_t tm, tn;
+    int32_t cost;
+};
+
+// ---- launchers (each returns cudaGetLastError() of its launch) ----
+cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_t w,
+                        int64_t kpad, ModP mp, YConst y, DigitScheme ds, int arena_kind,
+                        cudaStream_t st);
+// max_work: the largest rows·kpad/2 over the jobs
+cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_work, ModP mp,
+                            DigitScheme ds, int arena_kind, cudaStream_t st);
+cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP mp,
+                        cudaStream_t st);
+cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st);
+cudaError_t launch_leaf_i64_arrays(const LeafProd *prods_dev, const LeafTile *tiles_dev,
+                                   int ntiles, const uint32_t *const *arenas_dev,
+                                   const int64_t *kpad_dev, ModP mp, cudaStream_t st);
+
+// The tensor-core leaf.  tmaps_dev holds one CUtensorMap (128 B) per arena.
+struct TcLaunch {
+    const LeafProd *prods;
+    const LeafTile *tiles;
+    int ntiles;
+    const void *tmaps;        // device array of CUtensorMap, 64-B aligned
+    ModP mp;
+    DigitScheme ds;
+    unsigned int *err;        // device-visible error word (bounded waits)
+    unsigned int *tile_ctr;   // device work counter (zeroed before launch)
+};
+cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st);
+int leaf_tc_bm();
+int leaf_tc_bn();
+int leaf_i64_tile();
+
+// Build the TMA descriptor of a bf16 arena (box 64 × 128 rows, 128B swizzle).
+bool encode_arena_tmap(const Arena &a, void *tmap_out /* 128 B */);
+
+}  // namespace fsk

@@ -1,0 +1,196 @@
+"""ctypes binding of libffsyrk.so (see include/ffsyrk.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Matrices are torch tensors on the current CUDA device holding
+uint32 bit patterns (dtype torch.int32 or torch.uint32), row-major with unit
+column stride.  If the library is missing this module raises on first use;
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libffsyrk.so")
+
+SUCCESS, ERR_INVALID_ARG, ERR_NOT_PRIME, ERR_UNSUPPORTED_P, ERR_ALLOC, ERR_CUDA, ERR_TIMEOUT, \
+    ERR_ARCH, ERR_TOO_LARGE = range(9)
+LOWER, UPPER = 0, 1
+LEAF_AUTO, LEAF_TC_BF16, LEAF_I64 = 0, 1, 2
+LEVELS_AUTO = -1
+
+_LEAVES = {None: LEAF_AUTO, "auto": LEAF_AUTO, "tc": LEAF_TC_BF16, "bf16": LEAF_TC_BF16,
+           "i64": LEAF_I64}
+
+#: every entry point include/ffsyrk.h declares
+EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan",
+           "ffsyrk", "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
+           "ffsyrk_status_string", "ffsyrk_version"]
+
+
+class FfsyrkError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)}")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("leaf", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_uint32), ("y_form", ctypes.c_int32), ("y_a", ctypes.c_uint32),
+                ("y_b", ctypes.c_uint32), ("y_cost", ctypes.c_int32), ("leaf", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("digits", ctypes.c_int32),
+                ("chunk_k", ctypes.c_int32 * 9), ("workspace_bytes", ctypes.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    """Load libffsyrk.so (raises FileNotFoundError if it was never built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise FileNotFoundError(
+                    f"{LIB_PATH} is missing: build it with paper_2001_04109_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            i64, u32, vp, i32 = ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int32
+            P = ctypes.POINTER
+            L.ffsyrk_options_default.argtypes = [P(Options)]
+            L.ffsyrk_options_default.restype = None
+            L.ffsyrk_plan.argtypes = [P(vp), u32, i64, i64, P(Options)]
+            L.ffsyrk_plan_destroy.argtypes = [vp]
+            L.ffsyrk_with_plan.argtypes = [vp, i32, i64, i64, u32, vp, i64, vp, i64, vp]
+            L.ffsyrk.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
+            L.ffsyrk_batched.argtypes = [i32, i64, P(i64), P(i64), u32, P(vp), P(i64), P(vp),
+                                         P(i64), vp]
+            L.ffsyrk_sync_status.argtypes = [vp, vp]
+            L.ffsyrk_plan_get_info.argtypes = [vp, P(PlanInfo)]
+            L.ffsyrk_status_string.argtypes = [i32]
+            L.ffsyrk_status_string.restype = ctypes.c_char_p
+            L.ffsyrk_version.restype = i32
+            for name in ["ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan", "ffsyrk",
+                         "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info"]:
+                getattr(L, name).restype = i32
+            _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return lib().ffsyrk_status_string(code).decode()
+    except FileNotFoundError:
+        return f"status {code}"
+
+
+def _check(code: int, where: str) -> None:
+    if code != SUCCESS:
+        raise FfsyrkError(code, where)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _mat_args(X: torch.Tensor, name: str):
+    if X.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    if X.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        raise TypeError(f"{name} must hold uint32 bit patterns (torch.int32 or torch.uint32)")
+    if X.numel() > 0 and X.stride(1) != 1:
+        raise ValueError(f"{name} must have unit column stride")
+    ld = max(X.stride(0), X.shape[1], 1) if X.shape[0] > 1 else max(X.shape[1], 1)
+    return X.data_ptr(), ld
+
+
+def make_options(leaf=None, levels=None) -> Options:
+    o = Options()
+    lib().ffsyrk_options_default(ctypes.byref(o))
+    o.leaf = _LEAVES[leaf] if not isinstance(leaf, int) else leaf
+    o.levels = LEVELS_AUTO if levels is None else int(levels)
+    return o
+
+
+class Plan:
+    """An ffsyrk plan: p, Y, digits, depth and workspace for n ≤ max_n, k ≤ max_k."""
+
+    def __init__(self, p: int, max_n: int, max_k: int, leaf=None, levels=None):
+        self.p = int(p)
+        self._h = ctypes.c_void_p()
+        o = make_options(leaf, levels)
+        _check(lib().ffsyrk_plan(ctypes.byref(self._h), self.p, int(max_n), int(max_k),
+                                 ctypes.byref(o)), "ffsyrk_plan")
+
+    def info(self) -> dict:
+        i = PlanInfo()
+        _check(lib().ffsyrk_plan_get_info(self._h, ctypes.byref(i)), "ffsyrk_plan_get_info")
+        return {"p": i.p, "y_form": i.y_form, "y_a": i.y_a, "y_b": i.y_b, "y_cost": i.y_cost,
+                "leaf": i.leaf, "levels": i.levels, "digits": i.digits,
+                "chunk_k": list(i.chunk_k), "workspace_bytes": i.workspace_bytes}
+
+    def __call__(self, A: torch.Tensor, C: torch.Tensor | None = None, uplo: str = "lower",
+                 stream=None) -> torch.Tensor:
+        n, k = A.shape
+        if C is None:
+            C = torch.zeros((n, n), dtype=torch.int32, device=A.device)
+        pa, lda = _mat_args(A, "A")
+        pc, ldc = _mat_args(C, "C")
+        _check(lib().ffsyrk_with_plan(self._h, UPPER if uplo == "upper" else LOWER, n, k, self.p,
+                                      pa, lda, pc, ldc, _stream_handle(stream)), "ffsyrk_with_plan")
+        return C
+
+    def sync_status(self, stream=None) -> None:
+        _check(lib().ffsyrk_sync_status(self._h, _stream_handle(stream)), "ffsyrk_sync_status")
+
+    def close(self) -> None:
+        if self._h:
+            lib().ffsyrk_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def syrk(A: torch.Tensor, p: int, uplo: str = "lower", C: torch.Tensor | None = None,
+         stream=None) -> torch.Tensor:
+    """C = A·Aᵀ mod p (triangle ``uplo``) through the library's plan cache."""
+    n, k = A.shape
+    if C is None:
+        C = torch.zeros((n, n), dtype=torch.int32, device=A.device)
+    pa, lda = _mat_args(A, "A")
+    pc, ldc = _mat_args(C, "C")
+    _check(lib().ffsyrk(UPPER if uplo == "upper" else LOWER, n, k, int(p), pa, lda, pc, ldc,
+                        _stream_handle(stream)), "ffsyrk")
+    return C
+
+
+def batched(As: list[torch.Tensor], p: int, Cs: list[torch.Tensor] | None = None,
+            uplo: str = "lower", stream=None) -> list[torch.Tensor]:
+    """C_t = A_t·A_tᵀ mod p for uneven problems, in one library call."""
+    count = len(As)
+    if Cs is None:
+        Cs = [torch.zeros((a.shape[0], a.shape[0]), dtype=torch.int32, device=a.device) for a in As]
+    I64 = ctypes.c_int64 * count
+    VP = ctypes.c_void_p * count
+    ns, ks, ldas, ldcs, pas, pcs = I64(), I64(), I64(), I64(), VP(), VP()
+    for t, (a, c) in enumerate(zip(As, Cs)):
+        ns[t], ks[t] = a.shape
+        pas[t], ldas[t] = _mat_args(a, "A")
+        pcs[t], ldcs[t] = _mat_args(c, "C")
+    _check(lib().ffsyrk_batched(UPPER if uplo == "upper" else LOWER, count, ns, ks, int(p), pas,
+                                ldas, pcs, ldcs, _stream_handle(stream)), "ffsyrk_batched")
+    return Cs

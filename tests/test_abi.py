@@ -1,0 +1,83 @@
+"""The C-ABI library builds, loads and exports every declared entry point (CPU only).
+
+No compute call is made here (there is no GPU): only argument validation
+paths that return before touching the device, and pure host queries.
+"""
+import os
+import re
+
+import pytest
+
+import __graft_entry__
+from paper_2001_04109_gb300 import ffsyrk
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    return ffsyrk.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "ffsyrk.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ffsyrk\w*)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "ffsyrk" in names and "ffsyrk_batched" in names and "ffsyrk_plan" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(ffsyrk.EXPORTS)
+
+
+def test_status_strings_and_version(lib):
+    for code in range(9):
+        s = ffsyrk.status_string(code)
+        assert s.startswith("FFSYRK_")
+    assert lib.ffsyrk_version() >= 100
+
+
+@pytest.mark.parametrize("p,code", [(4, ffsyrk.ERR_NOT_PRIME), (65535, ffsyrk.ERR_NOT_PRIME),
+                                    (2, ffsyrk.ERR_UNSUPPORTED_P), (1 << 24, ffsyrk.ERR_UNSUPPORTED_P),
+                                    (16777259, ffsyrk.ERR_UNSUPPORTED_P), (0, ffsyrk.ERR_UNSUPPORTED_P)])
+def test_bad_primes_rejected_before_any_device_work(lib, p, code):
+    import ctypes
+    h = ctypes.c_void_p(123)
+    assert lib.ffsyrk_plan(ctypes.byref(h), p, 10, 10, None) == code
+    assert h.value is None
+    assert lib.ffsyrk(0, 4, 4, p, None, 4, None, 4, None) == code
+
+
+def test_bad_arguments_rejected(lib):
+    import ctypes
+    assert lib.ffsyrk(0, -1, 4, 65521, None, 4, None, 4, None) == ffsyrk.ERR_INVALID_ARG
+    assert lib.ffsyrk_with_plan(None, 0, 4, 4, 65521, None, 4, None, 4, None) == ffsyrk.ERR_INVALID_ARG
+    assert lib.ffsyrk_plan(None, 65521, 4, 4, None) == ffsyrk.ERR_INVALID_ARG
+    o = ffsyrk.Options()
+    lib.ffsyrk_options_default(ctypes.byref(o))
+    assert o.leaf == ffsyrk.LEAF_AUTO and o.levels == ffsyrk.LEVELS_AUTO
+    o.levels = 99
+    h = ctypes.c_void_p()
+    assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
+    o.levels = 1
+    o.reserved[2] = 5
+    assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
+    # batched argument checks happen before any device call
+    I64 = ctypes.c_int64 * 1
+    VP = ctypes.c_void_p * 1
+    assert lib.ffsyrk_batched(0, 1, I64(-3), I64(4), 65521, VP(), I64(4), VP(), I64(4), None) == \
+        ffsyrk.ERR_INVALID_ARG
+    assert lib.ffsyrk_batched(0, 0, None, None, 65521, None, None, None, None, None) == ffsyrk.SUCCESS
+    assert lib.ffsyrk_batched(0, 1, I64(4), I64(4), 65521, VP(None), I64(4), VP(None), I64(4), None) == \
+        ffsyrk.ERR_INVALID_ARG
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(ffsyrk, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(ffsyrk, "_lib", None)
+    with pytest.raises(FileNotFoundError):
+        ffsyrk.lib()
