@@ -139,6 +139,28 @@ typedef struct {
 
 ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t plan, ffsyrk_plan_info_t *info);
 
+/* Device timing of a plan's calls, for benchmarks and tracing.  While
+ * enabled, every call records CUDA events on its stream before the first
+ * launch, between the stage groups (pre-additions/digit split, leaf
+ * products, post-additions) and after the last launch.  Enabling allocates
+ * four events (cudaEventCreate). */
+ffsyrk_status_t ffsyrk_plan_set_timing(ffsyrk_plan_t plan, int32_t enable);
+
+typedef struct {
+    float prep_ms;            /* pre-additions and digit split (Algorithm 2, S1..S4) */
+    float leaf_ms;            /* the grouped leaf-product launch (P1..P5 leaves)      */
+    float post_ms;            /* post-additions (U1..U5)                              */
+    float total_ms;
+    int32_t launches;         /* kernel launches of the call                          */
+    int32_t leaf_launches;
+    double field_macs;        /* useful multiply-adds mod p of the leaf products      */
+    double tensor_macs;       /* digit-pair multiply-adds issued for them (D²×)       */
+} ffsyrk_timing_t;
+
+/* Timing of the most recent call with timing enabled: waits for its last
+ * event.  FFSYRK_ERR_INVALID_ARG if timing is off or no call was made. */
+ffsyrk_status_t ffsyrk_plan_get_timing(ffsyrk_plan_t plan, ffsyrk_timing_t *timing);
+
 /* Human-readable name of a status code (static storage). */
 const char *ffsyrk_status_string(ffsyrk_status_t status);
 

@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <new>
@@ -248,8 +249,12 @@ struct ffsyrk_plan_st {
     std::tuple<int64_t, int64_t, const uint32_t *, int64_t, uint32_t *, int64_t, int, int> last_key;
     Layout lay;
     Descs desc;
-    Geometry last_geom_for_zero;
-    bool zeroed_for_last = false;
+    // optional per-stage timing
+    bool timing = false;
+    bool timed_call = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int last_launches = 0, last_leaf_launches = 0;
+    double last_field_macs = 0, last_tensor_macs = 0;
 };
 
 namespace {
@@ -322,6 +327,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         pr.a_row0 = pr.b_row0 = 0;
         pr.rows = pr.cols = g.n;
         pr.kblocks = (int32_t)(lay.arena[0].kpad / 64);
+        pr.plane_rows = lay.arena[0].rpad;
         pr.out = C;
         pr.ldo = ldc;
         D.prods.push_back(pr);
@@ -367,6 +373,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
                     pr.b_row0 = operand(d + 1, 4 * t + 2 * q + 1).row0;
                     pr.rows = pr.cols = h;
                     pr.kblocks = (int32_t)(lay.arena[d + 1].kpad / 64);
+                    pr.plane_rows = lay.arena[d + 1].rpad;
                     pr.out = gbuf(d, t, q);
                     pr.ldo = h;
                     D.prods.push_back(pr);
@@ -385,6 +392,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
             pr.a_row0 = pr.b_row0 = operand(g.L, 4 * pow3(g.L - 1) + t).row0;
             pr.rows = pr.cols = hL;
             pr.kblocks = (int32_t)(lay.arena[g.L].kpad / 64);
+            pr.plane_rows = lay.arena[g.L].rpad;
             pr.out = rbuf(g.L, t);
             pr.ldo = hL;
             D.prods.push_back(pr);
@@ -509,6 +517,27 @@ ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, cons
     const Descs &D = pl->desc;
     char *dd = pl->ws + pl->data_cap;
     const int kind = lay.leaf == FFSYRK_LEAF_TC_BF16 ? ARENA_BF16 : ARENA_U32;
+    if (pl->timing) cudaEventRecord(pl->ev[0], st);
+    pl->last_launches = g.L == 0 ? 2 : 2 * g.L + 1;
+    pl->last_leaf_launches = 1;
+    {
+        double f = 0;
+        for (const LeafProd &pr : D.prods) {
+            const double K = (double)(pr.kblocks) * 64.0;
+            f += (pr.tri == 0 ? (double)pr.rows * pr.cols : (double)pr.rows * (pr.rows + 1) / 2) * K;
+        }
+        pl->last_tensor_macs = f * (lay.leaf == FFSYRK_LEAF_TC_BF16 ? pl->ds.D * pl->ds.D : 1);
+        // useful work counts the unpadded K of every product
+        double u = 0;
+        if (g.L == 0) {
+            u = (double)g.n * (g.n + 1) / 2 * (double)g.k;
+        } else {
+            for (int d = 0; d < g.L; ++d)
+                u += 2.0 * std::pow(3.0, d) * (double)g.h[d + 1] * g.h[d + 1] * (double)g.w[d + 1];
+            u += std::pow(3.0, g.L) * (double)g.h[g.L] * (g.h[g.L] + 1) / 2 * (double)g.w[g.L];
+        }
+        pl->last_field_macs = u;
+    }
     if (g.L == 0) {
         e = launch_digitize(reinterpret_cast<const DigitizeJob *>(dd + D.digit_off), 1,
                             D.digit_max_work, pl->mp, pl->ds, kind, st);
@@ -521,6 +550,7 @@ ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, cons
             if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
         }
     }
+    if (pl->timing) cudaEventRecord(pl->ev[1], st);
     if (lay.leaf == FFSYRK_LEAF_TC_BF16) {
         TcLaunch tl{};
         tl.prods = reinterpret_cast<const LeafProd *>(dd + D.prods_off);
@@ -540,10 +570,15 @@ ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, cons
                                    reinterpret_cast<const int64_t *>(dd + D.akpad_off), pl->mp, st);
     }
     if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+    if (pl->timing) cudaEventRecord(pl->ev[2], st);
     for (int d = g.L - 1; d >= 0; --d) {
         e = launch_post(reinterpret_cast<const PostNode *>(dd + D.post_off[d]),
                         (int)D.post[d].size(), g.h[d + 1], pl->mp, st);
         if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+    }
+    if (pl->timing) {
+        cudaEventRecord(pl->ev[3], st);
+        pl->timed_call = true;
     }
     return FFSYRK_SUCCESS;
 }
@@ -558,6 +593,8 @@ void destroy_plan(ffsyrk_plan_st *pl) {
         cudaFree(pl->ws);
     }
     if (pl->desc_done) cudaEventDestroy(pl->desc_done);
+    for (cudaEvent_t &ev : pl->ev)
+        if (ev) cudaEventDestroy(ev);
     if (pl->desc_host) cudaFreeHost(pl->desc_host);
     if (pl->err_host) cudaFreeHost(pl->err_host);
     if (cur != pl->device) cudaSetDevice(cur);
@@ -712,6 +749,36 @@ ffsyrk_status_t ffsyrk_with_plan(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n
     if (cur != pl->device) return FFSYRK_ERR_INVALID_ARG;
     if (pl->err_host[0] != 0) return FFSYRK_ERR_TIMEOUT;
     return enqueue(pl, uplo, n, k, A, lda, C, ldc, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ffsyrk_status_t ffsyrk_plan_set_timing(ffsyrk_plan_t pl, int32_t enable) {
+    if (!pl) return FFSYRK_ERR_INVALID_ARG;
+    if (enable && !pl->ev[0]) {
+        for (cudaEvent_t &ev : pl->ev)
+            if (cudaEventCreate(&ev) != cudaSuccess) return FFSYRK_ERR_CUDA;
+    }
+    pl->timing = enable != 0;
+    pl->timed_call = false;
+    return FFSYRK_SUCCESS;
+}
+
+ffsyrk_status_t ffsyrk_plan_get_timing(ffsyrk_plan_t pl, ffsyrk_timing_t *t) {
+    if (!pl || !t || !pl->timing || !pl->timed_call) return FFSYRK_ERR_INVALID_ARG;
+    if (cudaEventSynchronize(pl->ev[3]) != cudaSuccess) return FFSYRK_ERR_CUDA;
+    float a = 0, b = 0, c = 0, d = 0;
+    cudaEventElapsedTime(&a, pl->ev[0], pl->ev[1]);
+    cudaEventElapsedTime(&b, pl->ev[1], pl->ev[2]);
+    cudaEventElapsedTime(&c, pl->ev[2], pl->ev[3]);
+    cudaEventElapsedTime(&d, pl->ev[0], pl->ev[3]);
+    t->prep_ms = a;
+    t->leaf_ms = b;
+    t->post_ms = c;
+    t->total_ms = d;
+    t->launches = pl->last_launches;
+    t->leaf_launches = pl->last_leaf_launches;
+    t->field_macs = pl->last_field_macs;
+    t->tensor_macs = pl->last_tensor_macs;
+    return FFSYRK_SUCCESS;
 }
 
 ffsyrk_status_t ffsyrk_sync_status(ffsyrk_plan_t pl, ffsyrk_stream_t stream) {
@@ -898,6 +965,7 @@ extern "C" ffsyrk_status_t ffsyrk_batched(ffsyrk_uplo_t uplo, int64_t count, con
         pr.a_row0 = pr.b_row0 = row0[t];
         pr.rows = pr.cols = n[t];
         pr.kblocks = (int32_t)(arenas[j].kpad / 64);
+        pr.plane_rows = rup(n[t], 128);
         pr.out = C[t];
         pr.ldo = ldc[t];
         prods.push_back(pr);

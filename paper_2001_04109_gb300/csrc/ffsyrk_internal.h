@@ -118,6 +118,7 @@ struct LeafProd {
     int64_t rows, cols;   // valid output extent
     int32_t kblocks;      // K_pad / 64
     int32_t pad_;
+    int64_t plane_rows;   // arena rows between consecutive digit planes of an operand
     uint32_t *out;
     int64_t ldo;
 };

@@ -29,7 +29,8 @@ _LEAVES = {None: LEAF_AUTO, "auto": LEAF_AUTO, "tc": LEAF_TC_BF16, "bf16": LEAF_
 #: every entry point include/ffsyrk.h declares
 EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan",
            "ffsyrk", "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
-           "ffsyrk_status_string", "ffsyrk_version"]
+           "ffsyrk_plan_set_timing", "ffsyrk_plan_get_timing", "ffsyrk_status_string",
+           "ffsyrk_version"]
 
 
 class FfsyrkError(RuntimeError):
@@ -48,6 +49,13 @@ class PlanInfo(ctypes.Structure):
                 ("y_b", ctypes.c_uint32), ("y_cost", ctypes.c_int32), ("leaf", ctypes.c_int32),
                 ("levels", ctypes.c_int32), ("digits", ctypes.c_int32),
                 ("chunk_k", ctypes.c_int32 * 9), ("workspace_bytes", ctypes.c_int64)]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("prep_ms", ctypes.c_float), ("leaf_ms", ctypes.c_float),
+                ("post_ms", ctypes.c_float), ("total_ms", ctypes.c_float),
+                ("launches", ctypes.c_int32), ("leaf_launches", ctypes.c_int32),
+                ("field_macs", ctypes.c_double), ("tensor_macs", ctypes.c_double)]
 
 
 _lib = None
@@ -75,11 +83,14 @@ def lib() -> ctypes.CDLL:
                                          P(i64), vp]
             L.ffsyrk_sync_status.argtypes = [vp, vp]
             L.ffsyrk_plan_get_info.argtypes = [vp, P(PlanInfo)]
+            L.ffsyrk_plan_set_timing.argtypes = [vp, i32]
+            L.ffsyrk_plan_get_timing.argtypes = [vp, P(Timing)]
             L.ffsyrk_status_string.argtypes = [i32]
             L.ffsyrk_status_string.restype = ctypes.c_char_p
             L.ffsyrk_version.restype = i32
             for name in ["ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan", "ffsyrk",
-                         "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info"]:
+                         "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
+                         "ffsyrk_plan_set_timing", "ffsyrk_plan_get_timing"]:
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -149,6 +160,14 @@ class Plan:
         _check(lib().ffsyrk_with_plan(self._h, UPPER if uplo == "upper" else LOWER, n, k, self.p,
                                       pa, lda, pc, ldc, _stream_handle(stream)), "ffsyrk_with_plan")
         return C
+
+    def set_timing(self, enable: bool = True) -> None:
+        _check(lib().ffsyrk_plan_set_timing(self._h, 1 if enable else 0), "ffsyrk_plan_set_timing")
+
+    def timing(self) -> dict:
+        t = Timing()
+        _check(lib().ffsyrk_plan_get_timing(self._h, ctypes.byref(t)), "ffsyrk_plan_get_timing")
+        return {f: getattr(t, f) for f, _ in Timing._fields_}
 
     def sync_status(self, stream=None) -> None:
         _check(lib().ffsyrk_sync_status(self._h, _stream_handle(stream)), "ffsyrk_sync_status")

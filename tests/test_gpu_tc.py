@@ -1,0 +1,68 @@
+"""Tensor-core leaf: a single tile first, then exactness at the FP32 bound (marked gpu).
+
+The leaf accumulates bf16 digit products in FP32 over K-chunks sized so that
+|partial sum| ≤ 2^24.  These inputs put every digit at its largest magnitude
+with one sign, so every chunk sum lands exactly on ±2^24: any loss of
+integer precision in the tensor-core accumulation would show up here.
+"""
+import numpy as np
+import pytest
+import torch
+
+from parity_util import check_against_oracle, gpu_syrk, residues
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def test_single_tile_classical():
+    p = 65521
+    A = residues(128, 64, p, seed=1)
+    C, info = gpu_syrk(A, p, leaf="tc", levels=0)
+    assert info["leaf"] == 1
+    check_against_oracle(A, p, C)
+
+
+@pytest.mark.parametrize("n,k", [(128, 128), (256, 64), (300, 200), (129, 1000)])
+def test_small_classical(n, k):
+    p = 65521
+    A = residues(n, k, p, seed=n + k)
+    C, _ = gpu_syrk(A, p, leaf="tc", levels=0)
+    check_against_oracle(A, p, C)
+
+
+# (p, symmetric residue whose signed base-256 digits are all at their bound)
+BOUND_CASES = [(65521, 32640), (131071, 65408), (8388593, 4161408)]
+
+
+@pytest.mark.parametrize("p,s", BOUND_CASES)
+@pytest.mark.parametrize("levels", [0, 1])
+def test_exact_at_fp32_bound(p, s, levels):
+    n, k = 300, 4096 + 64
+    x = s % p
+    A = torch.full((n, k), x, dtype=torch.int32)
+    C, info = gpu_syrk(A, p, leaf="tc", levels=levels)
+    check_against_oracle(A, p, C)
+    # mixed signs: rows alternate s and −s, columns alternate too
+    sign = np.where((np.arange(n)[:, None] + np.arange(k)[None, :]) % 2 == 0, 1, -1)
+    B = torch.from_numpy(((sign * s) % p).astype(np.int32))
+    C, _ = gpu_syrk(B, p, leaf="tc", levels=levels)
+    check_against_oracle(B, p, C)
+
+
+def test_chunks_match_plan_info():
+    from paper_2001_04109_gb300 import ffsyrk
+    for p, D in [(65521, 2), (131071, 2), (8388593, 3), (251, 1)]:
+        plan = ffsyrk.Plan(p, 8, 8, leaf="tc", levels=0)
+        info = plan.info()
+        plan.close()
+        assert info["digits"] == D
+        ck = info["chunk_k"]
+        for i in range(D):
+            for j in range(D):
+                assert ck[i * 3 + j] % 64 == 0 and ck[i * 3 + j] >= 256
