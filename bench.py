@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Benchmark of C = lower(A·Aᵀ) mod p on GB300 (arXiv 2001.04109, Algorithm 2).
+
+One "step" is one library call ffsyrk_with_plan on device-resident input:
+digit split / pre-additions, every leaf product and the post-additions.  The
+metric is the effective rate n²·k / t (the paper's effective-Gfops
+definition with n³ → n²·k, counted once per output entry pair).
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle (the
+schoolbook definition) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A·Aᵀ mod p effective ops/s (n²k/t), fast vs classical SYRK on 1 GB300, bit-exact"
+UNIT = "ops/s"
+
+WORKLOADS = {
+    # name: (n, k, p, description)
+    "square4096": (4096, 4096, 65521,
+                   "fast recursive A·Aᵀ mod p, A 4096×4096 uint32 uniform in [0,p), p=65521"),
+    "small256": (256, 256, 65521, "classical A·Aᵀ mod p, A 256×256, p=65521"),
+    "tall": (16384, 4096, 131071, "fast A·Aᵀ mod p, A 16384×4096, p=131071 (2×2 Y)"),
+    "wide": (4096, 16384, 131071, "fast A·Aᵀ mod p, A 4096×16384, p=131071 (2×2 Y)"),
+    "odd": (16383, 4097, 131071, "fast A·Aᵀ mod p, A 16383×4097, p=131071 (2×2 Y, padding)"),
+    "square8192": (8192, 8192, 65521, "fast A·Aᵀ mod p, A 8192×8192, p=65521"),
+    "square16384": (16384, 16384, 65521, "fast A·Aᵀ mod p, A 16384×16384, p=65521"),
+    "large": (32768, 32768, 8388593, "fast A·Aᵀ mod p, A 32768×32768, p=8388593 (D=3)"),
+}
+DEFAULT_WORKLOAD = "square4096"
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def kernel_traffic(kernel_file: str, workload: str):
+    """dram bytes per launch recorded under profiles/ for this kernel source, else None."""
+    src = os.path.join(ROOT, "paper_2001_04109_gb300", "csrc", kernel_file)
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    prof = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(prof):
+        return None
+    for name in sorted(os.listdir(prof)):
+        if not name.endswith((".txt", ".md")):
+            continue
+        text = open(os.path.join(prof, name)).read()
+        m_src = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", text)
+        m_wl = re.search(r"workload:\s*(\S+)", text)
+        m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+        m_k = re.search(r"kernel_file:\s*(\S+)", text)
+        if m_src and m_tr and m_k and m_wl and m_src.group(1) == h and m_k.group(1) == kernel_file \
+                and m_wl.group(1) == workload:
+            return float(m_tr.group(1))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(A_np, p, budget_s: float):
+    """Time the schoolbook oracle on a bounded row sample; effective n²k/s of the full product."""
+    import numpy as np
+
+    import oracle
+    n, k = A_np.shape
+    threads = oracle.default_threads()
+    rows_total = n
+    # calibrate on a few rows, then size the sample to the budget
+    r0 = max(1, min(n, threads))
+    t0 = time.perf_counter()
+    oracle.syrk_rows(A_np, p, np.arange(r0), threads=threads)
+    t_cal = max(time.perf_counter() - t0, 1e-6)
+    per_row = t_cal / r0
+    r = int(max(r0, min(rows_total, budget_s / per_row)))
+    rows = np.linspace(0, n - 1, r).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.syrk_rows(A_np, p, rows, threads=threads)
+    dt = time.perf_counter() - t0
+    # a full row is n dot products; the lower product needs n(n+1)/2 of them
+    t_full = dt / (r * n) * (n * (n + 1) / 2)
+    return {"value": n * n * k / t_full, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{r} full rows of A·Aᵀ mod p ({r * n} entries, {dt:.1f} s), "
+                      f"scaled to the {n}×{n} lower triangle"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    from paper_2001_04109_gb300 import inputs
+    n, k, p, desc = WORKLOADS[args.workload]
+    A = inputs.uniform_residues(n, k, p, seed=2).numpy().view(np.uint32)
+    vals = []
+    base = None
+    for s in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(A, p, budget_s=args.ref_budget)
+        if s >= args.warmup:
+            vals.append(r["value"])
+            base = r
+    v = statistics.median(vals)
+    ms = n * n * k / v * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": args.workload, "description": desc,
+                                            "n": n, "k": k, "p": p},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_plan(plan, A, C, steps, warmup, flush, stream, timing=True):
+    """Device time per call (CUDA events on the launching stream), L2 flushed between calls."""
+    import torch
+    for _ in range(warmup):
+        plan(A, C, stream=stream)
+    torch.cuda.synchronize()
+    plan.set_timing(timing)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    stage = []
+    for s in range(steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        plan(A, C, stream=stream)
+        ev[s][1].record(stream)
+        if timing:
+            stage.append(plan.timing())
+    torch.cuda.synchronize()
+    plan.set_timing(False)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return ms, stage
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2001_04109_gb300 import ffsyrk, inputs
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    n, k, p, desc = WORKLOADS[args.workload]
+    levels = args.levels
+    if levels is None and args.workload == "small256":
+        levels = 0
+    stream = torch.cuda.current_stream()
+    A_host = inputs.uniform_residues(n, k, p, seed=2)
+    A = A_host.cuda()
+    C = torch.zeros((n, n), dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    plan = ffsyrk.Plan(p, n, k, leaf=args.leaf, levels=levels)
+    info = plan.info()
+    sampler = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ms, stage = time_plan(plan, A, C, args.steps, args.warmup, flush, stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = sum(ms) / len(ms)
+    if ws > 1:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = ws * n * n * k / (step_ms * 1e-3)
+    leaf_ms = statistics.mean(s["leaf_ms"] for s in stage)
+    tmacs = stage[-1]["field_macs"] * info["digits"] ** 2
+    launches = stage[-1]["launches"]
+
+    # roofline of the dominant kernel (the grouped tensor-core leaf launch)
+    peaks, peak_src = measured_peaks()
+    long_step = step_ms > 100.0
+    peak = peaks["bf16_tflops_sustained" if long_step else "bf16_tflops"]
+    achieved = 2.0 * tmacs / (leaf_ms * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "traffic": kernel_traffic("kern_leaf_tc.cu", args.workload),
+                "kernel": "k_leaf_tc (tcgen05 kind::f16, bf16 digits, fp32 TMEM)",
+                "peak_source": f"{peak_src} {'sustained' if long_step else 'burst'} bf16 dense",
+                "algorithmic_flops_per_launch": 2.0 * tmacs,
+                "leaf_ms": leaf_ms,
+                "stage_ms": {"prep": statistics.mean(s["prep_ms"] for s in stage),
+                             "leaf": leaf_ms,
+                             "post": statistics.mean(s["post_ms"] for s in stage)}}
+
+    # bit-exactness on sampled rows against the oracle (not timed)
+    parity = None
+    if not args.no_check and rank == 0:
+        import oracle
+        rows = np.unique(np.linspace(0, n - 1, 8).astype(np.int64))
+        want = oracle.syrk_rows(A_host.numpy(), p, rows)
+        got = C.cpu().numpy().view(np.uint32)[rows]
+        ok = all(np.array_equal(got[t, : r + 1], want[t, : r + 1]) for t, r in enumerate(rows))
+        parity = {"rows_checked": int(len(rows)), "bit_exact": bool(ok)}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        A_pin = A_host.pin_memory()
+        C_pin = torch.empty((n, n), dtype=torch.int32).pin_memory()
+        A_dev = torch.empty_like(A)
+        C_dev = torch.zeros_like(C)
+        for _ in range(max(1, args.warmup)):
+            A_dev.copy_(A_pin, non_blocking=True)
+            plan(A_dev, C_dev, stream=stream)
+            C_pin.copy_(C_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            A_dev.copy_(A_pin, non_blocking=True)
+            plan(A_dev, C_dev, stream=stream)
+            C_pin.copy_(C_dev, non_blocking=True)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        e_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        e2e = {"value": ws * n * n * k / (e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": n * k * 4, "d2h_bytes_per_step": n * n * 4,
+               "ms_per_step": e_ms}
+
+    # comparators: classical SYRK from the same leaves; the int64 CUDA-core leaf
+    compare = {}
+    if not args.no_compare:
+        for name, leaf, lv in [("classical_tc", "tc", 0), ("fast_i64", "i64", levels),
+                               ("classical_i64", "i64", 0)]:
+            if name.endswith("i64") and n * n * k > 2 ** 40:
+                continue
+            pl = ffsyrk.Plan(p, n, k, leaf=leaf, levels=lv)
+            st = max(2, min(args.steps, 5))
+            cms, cstage = time_plan(pl, A, C, st, 2, flush, stream)
+            cm = sum(cms) / len(cms)
+            compare[name] = {"value": n * n * k / (cm * 1e-3), "ms_per_step": cm,
+                             "levels": pl.info()["levels"],
+                             "leaf_ms": statistics.mean(s["leaf_ms"] for s in cstage)}
+            pl.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_oracle_rate(A_host.numpy().view(np.uint32), p, budget_s=args.cpu_budget)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u32", "data": "synthetic",
+                "config": {"workload": args.workload, "description": desc, "n": n, "k": k,
+                           "p": p, "levels": info["levels"], "digits": info["digits"],
+                           "leaf": {1: "tc_bf16", 2: "i64"}[info["leaf"]],
+                           "y_form": "scalar" if info["y_form"] == 0 else "2x2",
+                           "l2": "flushed between steps (512 MiB write)",
+                           "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "e2e": e2e, "gpu_launches": launches * args.steps, "roofline": roofline,
+                "cpu_baseline": cpu, "clocks": clocks, "parity": parity, "compare": compare}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--levels", type=int, default=None)
+    ap.add_argument("--leaf", choices=["tc", "i64"], default="tc")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--ref-budget", type=float, default=6.0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        # each step one bounded oracle sample; the whole run stays within a few minutes
+        args.ref_budget = min(args.ref_budget, 150.0 / (args.steps + args.warmup))
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
