@@ -119,6 +119,38 @@ ffsyrk_status_t ffsyrk_batched(ffsyrk_uplo_t uplo, int64_t count, const int64_t 
                                const int64_t *lda, uint32_t *const *C, const int64_t *ldc,
                                ffsyrk_stream_t stream);
 
+/* C = A·Aᵀ mod p (triangle `uplo`) without allocating any memory.
+ *
+ * The paper has no counterpart: this is a deployment variant of the
+ * classical path (levels = 0, tensor-core leaf).  It is for callers that
+ * must not allocate device memory at call time: applications whose pool
+ * allocator owns all device memory, processes under a fixed memory budget,
+ * or latency-critical code where cudaMalloc/cudaFree (which can synchronise
+ * the device) are not acceptable.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine; its scratch is one array compiled into the library
+ * (64 MiB of digit planes + 1 MiB of launch descriptors) that every GPU which
+ * loads the library holds until the process exits.
+ *
+ * Limits: the digit planes of A must fit, i.e.
+ * D · roundup(n,256) · roundup(k,64) · 2 bytes ≤ 64 MiB, where D is the digit
+ * count of p (2 for p < 2^17, 3 above; e.g. n = k = 4096 with D = 2); larger
+ * shapes return FFSYRK_ERR_TOO_LARGE before anything is enqueued.
+ *
+ * Set-up: the first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.
+ *
+ * Sharing: all calls on a device share the one array and every call
+ * overwrites it, so calls whose GPU work overlaps (different streams, or
+ * threads without ordering between them) race and may produce wrong
+ * results.  Calls on one stream are ordered and safe.  A device-side bounded
+ * wait that runs out is not reported by this entry point.
+ *
+ * Arguments, layout and results are those of ffsyrk(). */
+ffsyrk_status_t ffsyrk_noalloc(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
+                               const uint32_t *A, int64_t lda, uint32_t *C, int64_t ldc,
+                               ffsyrk_stream_t stream);
+
 /* Wait for the plan's enqueued work on `stream` and report any device-side
  * failure recorded since the last call (then clear it). */
 ffsyrk_status_t ffsyrk_sync_status(ffsyrk_plan_t plan, ffsyrk_stream_t stream);

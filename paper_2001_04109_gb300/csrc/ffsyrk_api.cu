@@ -210,6 +210,8 @@ EncodeTiledFn get_encode_fn() {
 }  // namespace
 
 namespace fsk {
+DigitScheme digit_scheme_for(uint32_t p) { return make_digits(p); }
+
 bool encode_arena_tmap(const Arena &a, void *out) {
     EncodeTiledFn fn = get_encode_fn();
     if (!fn) return false;

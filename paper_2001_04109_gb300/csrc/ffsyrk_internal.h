@@ -159,6 +159,9 @@ int leaf_tc_bm();
 int leaf_tc_bn();
 int leaf_i64_tile();
 
+// The signed base-256 digit scheme and chunk lengths the planner uses for p.
+DigitScheme digit_scheme_for(uint32_t p);
+
 // Build the TMA descriptor of a bf16 arena (box 64 × 128 rows, 128B swizzle).
 bool encode_arena_tmap(const Arena &a, void *tmap_out /* 128 B */);
 

@@ -30,7 +30,7 @@ _LEAVES = {None: LEAF_AUTO, "auto": LEAF_AUTO, "tc": LEAF_TC_BF16, "bf16": LEAF_
 EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan",
            "ffsyrk", "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
            "ffsyrk_plan_set_timing", "ffsyrk_plan_get_timing", "ffsyrk_status_string",
-           "ffsyrk_version"]
+           "ffsyrk_version", "ffsyrk_noalloc"]
 
 
 class FfsyrkError(RuntimeError):
@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_plan_destroy.argtypes = [vp]
             L.ffsyrk_with_plan.argtypes = [vp, i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
+            L.ffsyrk_noalloc.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk_batched.argtypes = [i32, i64, P(i64), P(i64), u32, P(vp), P(i64), P(vp),
                                          P(i64), vp]
             L.ffsyrk_sync_status.argtypes = [vp, vp]
@@ -89,6 +90,7 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_status_string.restype = ctypes.c_char_p
             L.ffsyrk_version.restype = i32
             for name in ["ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan", "ffsyrk",
+                         "ffsyrk_noalloc",
                          "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
                          "ffsyrk_plan_set_timing", "ffsyrk_plan_get_timing"]:
                 getattr(L, name).restype = i32
