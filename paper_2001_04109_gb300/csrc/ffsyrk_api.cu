@@ -156,7 +156,7 @@ struct Descs {
     std::vector<LeafProd> prods;
     std::vector<LeafTile> tiles;
     std::vector<DigitizeJob> digit;
-    int64_t digit_max_work = 0;
+    int64_t digit_max_rows = 0, digit_max_kpad = 0;
     // blob offsets (bytes) inside the descriptor region
     int64_t prep_off[kMaxLevels] = {}, post_off[kMaxLevels] = {};
     int64_t prods_off = 0, tiles_off = 0, tmap_off = 0, aptr_off = 0, akpad_off = 0, digit_off = 0;
@@ -277,17 +277,22 @@ int choose_levels(const ffsyrk_plan_st *pl, int64_t n, int64_t k) {
 
 ffsyrk_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? FFSYRK_SUCCESS : FFSYRK_ERR_CUDA; }
 
+// Tiles of one product in bands of kBand tile rows, column by column inside
+// a band: the CTAs of one wave then share a few row and column panels,
+// which stay in L2.
+constexpr int64_t kBand = 8;
 void tri_tiles(std::vector<LeafTile> &out, int prod, int64_t rows, int64_t cols, int tri,
                int64_t tm, int64_t tn, int cost) {
     const int64_t TM = (rows + tm - 1) / tm, TN = (cols + tn - 1) / tn;
-    for (int64_t a = 0; a < TM; ++a)
-        for (int64_t b = 0; b < TN; ++b) {
-            const int64_t r0 = a * tm, r1 = std::min(rows, r0 + tm) - 1;
-            const int64_t c0 = b * tn, c1 = std::min(cols, c0 + tn) - 1;
-            if (tri == 1 && r1 < c0) continue;  // no entry with c ≤ r
-            if (tri == 2 && c1 < r0) continue;  // no entry with c ≥ r
-            out.push_back(LeafTile{prod, (int32_t)a, (int32_t)b, cost});
-        }
+    for (int64_t band = 0; band < TM; band += kBand)
+        for (int64_t b = 0; b < TN; ++b)
+            for (int64_t a = band; a < std::min(TM, band + kBand); ++a) {
+                const int64_t r0 = a * tm, r1 = std::min(rows, r0 + tm) - 1;
+                const int64_t c0 = b * tn, c1 = std::min(cols, c0 + tn) - 1;
+                if (tri == 1 && r1 < c0) continue;  // no entry with c ≤ r
+                if (tri == 2 && c1 < r0) continue;  // no entry with c ≥ r
+                out.push_back(LeafTile{prod, (int32_t)a, (int32_t)b, cost});
+            }
 }
 
 // Build every descriptor of one call into pl->desc and the staging blob.
@@ -337,7 +342,8 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         const Arena &a0 = lay.arena[0];
         D.digit.push_back(DigitizeJob{MatView{A, lda, g.n, g.k}, g.n,
                                       OperandDst{a0.base, 0, a0.kpad, a0.rpad}});
-        D.digit_max_work = g.n * (a0.kpad / 2);
+        D.digit_max_rows = g.n;
+        D.digit_max_kpad = a0.kpad;
     } else {
         // node views, depth by depth
         std::vector<MatView> views{MatView{A, lda, g.n, g.k}};
@@ -542,13 +548,13 @@ ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, cons
     }
     if (g.L == 0) {
         e = launch_digitize(reinterpret_cast<const DigitizeJob *>(dd + D.digit_off), 1,
-                            D.digit_max_work, pl->mp, pl->ds, kind, st);
+                            D.digit_max_rows, D.digit_max_kpad, pl->mp, pl->ds, kind, st);
         if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
     } else {
         for (int d = 0; d < g.L; ++d) {
             e = launch_prep(reinterpret_cast<const PrepNode *>(dd + D.prep_off[d]),
                             (int)D.prep[d].size(), g.h[d + 1], g.w[d + 1], lay.arena[d + 1].kpad,
-                            pl->mp, pl->yc, pl->ds, kind, st);
+                            pl->mp, pl->yc, pl->ds, kind, /*reduce_input=*/true, st);
             if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
         }
     }
@@ -956,7 +962,7 @@ extern "C" ffsyrk_status_t ffsyrk_batched(ffsyrk_uplo_t uplo, int64_t count, con
     std::vector<LeafProd> prods;
     std::vector<LeafTile> tiles;
     std::vector<DigitizeJob> jobs;
-    int64_t max_work = 0;
+    int64_t max_rows = 0, max_kpad = 0;
     std::vector<int64_t> prod_arena;
     for (int64_t t = 0; t < count; ++t) {
         if (row0[t] < 0) continue;
@@ -979,7 +985,8 @@ extern "C" ffsyrk_status_t ffsyrk_batched(ffsyrk_uplo_t uplo, int64_t count, con
         jb.dst = OperandDst{nullptr, row0[t], arenas[j].kpad, rup(n[t], 128)};
         jobs.push_back(jb);
         prod_arena.push_back(j);
-        max_work = std::max(max_work, n[t] * (arenas[j].kpad / 2));
+        max_rows = std::max(max_rows, n[t]);
+        max_kpad = std::max(max_kpad, arenas[j].kpad);
     }
     std::stable_sort(tiles.begin(), tiles.end(),
                      [](const LeafTile &x, const LeafTile &y) { return x.cost > y.cost; });
@@ -1048,8 +1055,8 @@ extern "C" ffsyrk_status_t ffsyrk_batched(ffsyrk_uplo_t uplo, int64_t count, con
     const int kind = tc ? ARENA_BF16 : ARENA_U32;
     for (size_t q0 = 0; q0 < jobs.size(); q0 += 65535) {
         const int nj = (int)std::min<size_t>(65535, jobs.size() - q0);
-        e = launch_digitize(reinterpret_cast<const DigitizeJob *>(dd + jobs_off) + q0, nj, max_work,
-                            b->mp, b->ds, kind, st);
+        e = launch_digitize(reinterpret_cast<const DigitizeJob *>(dd + jobs_off) + q0, nj, max_rows,
+                            max_kpad, b->mp, b->ds, kind, st);
         if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
     }
     if (tc) {

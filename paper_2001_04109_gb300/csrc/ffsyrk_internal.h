@@ -130,12 +130,14 @@ struct LeafTile {
 };
 
 // ---- launchers (each returns cudaGetLastError() of its launch) ----
+// reduce_input: some node views may hold values ≥ p (views of the caller's A)
 cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_t w,
                         int64_t kpad, ModP mp, YConst y, DigitScheme ds, int arena_kind,
-                        cudaStream_t st);
-// max_work: the largest rows·kpad/2 over the jobs
-cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_work, ModP mp,
-                            DigitScheme ds, int arena_kind, cudaStream_t st);
+                        bool reduce_input, cudaStream_t st);
+// max_rows, max_kpad: the largest rows and padded K over the jobs (njobs ≤ 65535)
+cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_rows,
+                            int64_t max_kpad, ModP mp, DigitScheme ds, int arena_kind,
+                            cudaStream_t st);
 cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP mp,
                         cudaStream_t st);
 cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st);

@@ -166,8 +166,8 @@ extern "C" ffsyrk_status_t ffsyrk_noalloc(ffsyrk_uplo_t uplo, int64_t n, int64_t
     if (cudaMemcpyAsync(hdr, g_stage, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return FFSYRK_ERR_CUDA;
 
-    cudaError_t e = launch_digitize(reinterpret_cast<const DigitizeJob *>(hdr + kJobOff), 1,
-                                    n * (kpad / 2), mp, ds, ARENA_BF16, st);
+    cudaError_t e = launch_digitize(reinterpret_cast<const DigitizeJob *>(hdr + kJobOff), 1, n,
+                                    kpad, mp, ds, ARENA_BF16, st);
     if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
     TcLaunch tl{};
     tl.prods = reinterpret_cast<const LeafProd *>(hdr + kProdOff);

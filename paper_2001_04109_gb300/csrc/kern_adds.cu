@@ -3,11 +3,14 @@
 //  * prep: the 4 pre-additions S1 = (A21 − A11)·Y, S2 = A22 − A21·Y,
 //    S3 = S1 − A22, S4 = S3 + A12 of every node of one recursion depth, fused
 //    with the signed base-256 digit split that feeds the leaf products.
+//  * digitize: the digit split alone, for the classical path's operands.
 //  * post: the post-additions Low(U1) = Low(P1 + P5), Low(U3) = Low(P1 + P2),
 //    Up(U1) = Low(U1)ᵀ, U2 = U1 + P4, U4 = U2 + P3, Low(U5) = Low(U2 + P4ᵀ),
 //    written straight into the node's result [[U3, ·], [U4, U5]].
-// Both are HBM-bound streaming kernels: coalesced along rows, with the two
-// transposed reads of the post-additions staged through shared memory.
+// All are HBM-bound streaming kernels, coalesced along rows; the two
+// transposed reads of the post-additions are staged through shared memory.
+// The prep and digit kernels are instantiated per digit count, operand type
+// and Y form, so the per-element work is straight-line integer code.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -42,43 +45,54 @@ __device__ __forceinline__ uint32_t ld_view(const MatView &v, int64_t r, int64_t
     return (r < v.vr && c < v.vc) ? __ldg(v.ptr + r * v.ld + c) : 0u;
 }
 
-// Write the residue pair (v0, v1) at (r, 2·cp) of an operand destination.
+// Float bits of the small integer d (|d| < 2^22) without a conversion
+// instruction: 1.5·2^23 + d is exact in FP32, so subtracting 1.5·2^23 leaves
+// exactly d.  For |d| ≤ 256 the low 16 bits are zero, i.e. the high half is
+// the exact bf16 encoding of d.
+__device__ __forceinline__ uint32_t small_int_f32_bits(int d) {
+    return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f);
+}
+__device__ __forceinline__ int sbyte(int s) {
+    int d;
+    asm("bfe.s32 %0, %1, 0, 8;" : "=r"(d) : "r"(s));
+    return d;
+}
+
+// Store the residue pair (v0, v1) at (row r, column c) of an operand.
+template <int D, bool U32>
 __device__ __forceinline__ void put_pair(const OperandDst &d, int64_t r, int64_t c, uint32_t v0,
-                                         uint32_t v1, const ModP &m, const DigitScheme &ds,
-                                         int kind) {
+                                         uint32_t v1, uint32_t half, uint32_t p) {
     if (d.arena == nullptr) return;
-    if (kind == ARENA_U32) {
-        uint2 *dst = reinterpret_cast<uint2 *>(static_cast<uint32_t *>(d.arena) +
-                                               (d.row0 + r) * d.kpad + c);
-        *dst = make_uint2(v0, v1);
+    if (U32) {
+        *reinterpret_cast<uint2 *>(static_cast<uint32_t *>(d.arena) + (d.row0 + r) * d.kpad + c) =
+            make_uint2(v0, v1);
         return;
     }
-    int s0 = v0 > m.half ? (int)v0 - (int)m.p : (int)v0;
-    int s1 = v1 > m.half ? (int)v1 - (int)m.p : (int)v1;
-    __nv_bfloat16 *base = static_cast<__nv_bfloat16 *>(d.arena);
+    int s0 = v0 > half ? (int)v0 - (int)p : (int)v0;  // symmetric residue
+    int s1 = v1 > half ? (int)v1 - (int)p : (int)v1;
+    uint32_t *base = static_cast<uint32_t *>(d.arena);  // bf16 pairs
 #pragma unroll
-    for (int t = 0; t < kMaxDigits; ++t) {
-        if (t >= ds.D) break;
+    for (int t = 0; t < D; ++t) {
         int d0, d1;
-        if (t == ds.D - 1) {
+        if (t == D - 1) {
             d0 = s0;
             d1 = s1;
         } else {
-            d0 = (int)(int8_t)(s0 & 0xFF);
-            d1 = (int)(int8_t)(s1 & 0xFF);
+            d0 = sbyte(s0);
+            d1 = sbyte(s1);
             s0 = (s0 - d0) >> 8;
             s1 = (s1 - d1) >> 8;
         }
-        __nv_bfloat162 pr;
-        pr.x = __int2bfloat16_rn(d0);
-        pr.y = __int2bfloat16_rn(d1);
-        *reinterpret_cast<__nv_bfloat162 *>(base + (d.row0 + t * d.rpad + r) * d.kpad + c) = pr;
+        const uint32_t packed =
+            __byte_perm(small_int_f32_bits(d0), small_int_f32_bits(d1), 0x7632);
+        base[((d.row0 + t * d.rpad + r) * d.kpad + c) >> 1] = packed;
     }
 }
 
+template <int YF>
 __device__ __forceinline__ void ymul(const YConst &y, uint32_t t0, uint32_t t1, uint32_t &o0,
                                      uint32_t &o1, uint32_t p) {
-    if (y.form == 0) {
+    if (YF == 0) {
         o0 = mulc(t0, y.a, p);
         o1 = mulc(t1, y.a, p);
     } else {
@@ -88,176 +102,205 @@ __device__ __forceinline__ void ymul(const YConst &y, uint32_t t0, uint32_t t1, 
     }
 }
 
+constexpr int PREP_THREADS = 128;  // column pairs per block
+constexpr int PREP_ROWS = 4;       // rows per thread (independent loads in flight)
+
 // Columns [w, kpad) of every written operand are zero (K padding of the
 // leaf products); rows [h, rpad) are never read into a stored result.
-__global__ void __launch_bounds__(256) k_prep(const PrepNode *__restrict__ nodes, int nnodes,
-                                              int64_t h, int64_t w, int64_t kpad, ModP m,
-                                              YConst y, DigitScheme ds, int kind) {
-    const int64_t wp = kpad / 2;  // column pairs written per operand row
-    const int64_t per_node = h * wp;
-    const int64_t total = per_node * nnodes;
-    const uint32_t p = m.p;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int node = (int)(idx / per_node);
-        const int64_t rem = idx - node * per_node;
-        const int64_t r = rem / wp;
-        const int64_t c = (rem - r * wp) * 2;
-        const PrepNode &nd = nodes[node];
-        const bool inside = c < w;
-        uint32_t a11[2] = {0, 0}, a12[2] = {0, 0}, a21[2] = {0, 0}, a22[2] = {0, 0};
-        if (inside) {
+// Grid: x = column-pair blocks, y = row blocks (strided), z = node.
+// RED: reduce the loaded values mod p (only the caller's A can hold values ≥ p).
+template <int D, bool U32, int YF, bool RED>
+__global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restrict__ nodes,
+                                                       int64_t h, int64_t w, int64_t kpad, ModP m,
+                                                       YConst y) {
+    const int64_t c = 2 * ((int64_t)blockIdx.x * PREP_THREADS + threadIdx.x);
+    if (c >= kpad) return;
+    const PrepNode &nd = nodes[blockIdx.z];
+    const uint32_t p = m.p, half = m.half;
+    const bool inside = c < w;
+    const int64_t nrb = (h + PREP_ROWS - 1) / PREP_ROWS;
+    for (int64_t rb = blockIdx.y; rb < nrb; rb += gridDim.y) {
+        uint32_t a[PREP_ROWS][4][2];  // quadrant 0..3 = A11, A12, A21, A22
+#pragma unroll
+        for (int i = 0; i < PREP_ROWS; ++i) {
+            const int64_t r = rb * PREP_ROWS + i;
+            const bool ok = inside && r < h;
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-                a11[e] = red(ld_view(nd.X, r, c + e), m);
-                a12[e] = red(ld_view(nd.X, r, w + c + e), m);
-                a21[e] = red(ld_view(nd.X, h + r, c + e), m);
-                a22[e] = red(ld_view(nd.X, h + r, w + c + e), m);
+                a[i][0][e] = ok ? ld_view(nd.X, r, c + e) : 0u;
+                a[i][1][e] = ok ? ld_view(nd.X, r, w + c + e) : 0u;
+                a[i][2][e] = ok ? ld_view(nd.X, h + r, c + e) : 0u;
+                a[i][3][e] = ok ? ld_view(nd.X, h + r, w + c + e) : 0u;
             }
         }
-        uint32_t t0 = subm(a21[0], a11[0], p), t1 = subm(a21[1], a11[1], p);
-        uint32_t s1[2], s2[2], s3[2], s4[2], u[2];
-        ymul(y, t0, t1, s1[0], s1[1], p);          // S1 = (A21 − A11)·Y
-        ymul(y, a21[0], a21[1], u[0], u[1], p);
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            s2[e] = subm(a22[e], u[e], p);          // S2 = A22 − A21·Y
-            s3[e] = subm(s1[e], a22[e], p);         // S3 = S1 − A22
-            s4[e] = addm(s3[e], a12[e], p);         // S4 = S3 + A12
+        for (int i = 0; i < PREP_ROWS; ++i) {
+            const int64_t r = rb * PREP_ROWS + i;
+            if (r >= h) break;
+            uint32_t x11[2], x12[2], x21[2], x22[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                x11[e] = RED ? red(a[i][0][e], m) : a[i][0][e];
+                x12[e] = RED ? red(a[i][1][e], m) : a[i][1][e];
+                x21[e] = RED ? red(a[i][2][e], m) : a[i][2][e];
+                x22[e] = RED ? red(a[i][3][e], m) : a[i][3][e];
+            }
+            uint32_t t0 = subm(x21[0], x11[0], p), t1 = subm(x21[1], x11[1], p);
+            uint32_t s1[2], s2[2], s3[2], s4[2], u[2];
+            ymul<YF>(y, t0, t1, s1[0], s1[1], p);       // S1 = (A21 − A11)·Y
+            ymul<YF>(y, x21[0], x21[1], u[0], u[1], p);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                s2[e] = subm(x22[e], u[e], p);          // S2 = A22 − A21·Y
+                s3[e] = subm(s1[e], x22[e], p);         // S3 = S1 − A22
+                s4[e] = addm(s3[e], x12[e], p);         // S4 = S3 + A12
+            }
+            put_pair<D, U32>(nd.gemm[0], r, c, x22[0], x22[1], half, p);
+            put_pair<D, U32>(nd.gemm[1], r, c, s4[0], s4[1], half, p);
+            put_pair<D, U32>(nd.gemm[2], r, c, s1[0], s1[1], half, p);
+            put_pair<D, U32>(nd.gemm[3], r, c, s2[0], s2[1], half, p);
+            put_pair<D, U32>(nd.leaf[0], r, c, x11[0], x11[1], half, p);
+            put_pair<D, U32>(nd.leaf[1], r, c, x12[0], x12[1], half, p);
+            put_pair<D, U32>(nd.leaf[2], r, c, s3[0], s3[1], half, p);
+            if (nd.s3 != nullptr && inside)
+                *reinterpret_cast<uint2 *>(nd.s3 + r * nd.s3_ld + c) = make_uint2(s3[0], s3[1]);
         }
-        put_pair(nd.gemm[0], r, c, a22[0], a22[1], m, ds, kind);
-        put_pair(nd.gemm[1], r, c, s4[0], s4[1], m, ds, kind);
-        put_pair(nd.gemm[2], r, c, s1[0], s1[1], m, ds, kind);
-        put_pair(nd.gemm[3], r, c, s2[0], s2[1], m, ds, kind);
-        put_pair(nd.leaf[0], r, c, a11[0], a11[1], m, ds, kind);
-        put_pair(nd.leaf[1], r, c, a12[0], a12[1], m, ds, kind);
-        put_pair(nd.leaf[2], r, c, s3[0], s3[1], m, ds, kind);
-        if (nd.s3 != nullptr && inside)
-            *reinterpret_cast<uint2 *>(nd.s3 + r * nd.s3_ld + c) = make_uint2(s3[0], s3[1]);
     }
 }
 
-// Digit split of a whole matrix (the classical path's only operand).
 // Digit split of whole matrices (the classical path's operands): rows
 // [0, rows) × columns [0, kpad) of each destination, zero beyond the view.
-// blockIdx.y selects the matrix.
-__global__ void __launch_bounds__(256) k_digitize(const DigitizeJob *__restrict__ jobs, ModP m,
-                                                  DigitScheme ds, int kind) {
-    const DigitizeJob jb = jobs[blockIdx.y];
-    const int64_t cp = jb.dst.kpad / 2;
-    const int64_t total = jb.rows * cp;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = idx / cp;
-        const int64_t c = (idx - r * cp) * 2;
-        uint32_t v0 = red(ld_view(jb.X, r, c), m);
-        uint32_t v1 = red(ld_view(jb.X, r, c + 1), m);
-        put_pair(jb.dst, r, c, v0, v1, m, ds, kind);
+// Grid: x = column-pair blocks, y = row blocks (strided), z = matrix.
+constexpr int DIG_ROWS = 8;
+template <int D, bool U32>
+__global__ void __launch_bounds__(PREP_THREADS) k_digitize(const DigitizeJob *__restrict__ jobs,
+                                                           ModP m) {
+    const DigitizeJob &jb = jobs[blockIdx.z];
+    const int64_t c = 2 * ((int64_t)blockIdx.x * PREP_THREADS + threadIdx.x);
+    if (c >= jb.dst.kpad) return;
+    const int64_t nrb = (jb.rows + DIG_ROWS - 1) / DIG_ROWS;
+    for (int64_t rb = blockIdx.y; rb < nrb; rb += gridDim.y) {
+        uint32_t v[DIG_ROWS][2];
+#pragma unroll
+        for (int i = 0; i < DIG_ROWS; ++i) {
+            const int64_t r = rb * DIG_ROWS + i;
+            v[i][0] = r < jb.rows ? ld_view(jb.X, r, c) : 0u;
+            v[i][1] = r < jb.rows ? ld_view(jb.X, r, c + 1) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < DIG_ROWS; ++i) {
+            const int64_t r = rb * DIG_ROWS + i;
+            if (r >= jb.rows) break;
+            put_pair<D, U32>(jb.dst, r, c, red(v[i][0], m), red(v[i][1], m), m.half, m.p);
+        }
     }
 }
 
-// Lower-triangular tile index → (I, J), I ≥ J.
-__device__ __forceinline__ void tri_tile(int64_t idx, int64_t &I, int64_t &J) {
-    int64_t i = (int64_t)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
-    while (i * (i + 1) / 2 > idx) --i;
-    while ((i + 1) * (i + 2) / 2 <= idx) ++i;
-    I = i;
-    J = idx - i * (i + 1) / 2;
-}
+constexpr int PT = 32;  // post-addition tile: 32×32, 256 threads, 4 rows each
 
-constexpr int PT = 32;  // post-addition tile
-
+// Grid: x = tile column J, y = tile row I, z = 3·node + quadrant, where the
+// quadrants of the node's 2h×2h result are 0: C11 = Low(U3), 1: C21 = U4,
+// 2: C22 = Low(U5).  Tiles above the diagonal of quadrants 0 and 2 exit.
+// Every quadrant first issues all of its loads, then combines.
 __global__ void __launch_bounds__(256) k_post(const PostNode *__restrict__ nodes, int64_t h,
                                               ModP m) {
     __shared__ uint32_t sa[PT][PT + 1];
-    __shared__ uint32_t sb[PT][PT + 1];
     __shared__ uint32_t so[PT][PT + 1];
-    const PostNode &nd = nodes[blockIdx.y];
-    const int64_t T = (h + PT - 1) / PT;
-    const int64_t ntri = T * (T + 1) / 2;
-    int64_t t = blockIdx.x;
-    int quad;  // 0: C11 = Low(U3); 1: C21 = U4; 2: C22 = Low(U5)
-    int64_t I, J;
-    if (t < ntri) {
-        quad = 0;
-        tri_tile(t, I, J);
-    } else if (t < ntri + T * T) {
-        quad = 1;
-        t -= ntri;
-        I = t / T;
-        J = t - I * T;
-    } else {
-        quad = 2;
-        t -= ntri + T * T;
-        if (t >= ntri) return;
-        tri_tile(t, I, J);
-    }
+    const PostNode &nd = nodes[blockIdx.z / 3];
+    const int quad = blockIdx.z % 3;
+    const int64_t I = blockIdx.y, J = blockIdx.x;
+    if (quad != 1 && J > I) return;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const uint32_t p = m.p;
-    // transposed sources: tile (J, I) of P1 + P5 (quad 1) or of P4 (quad 2)
-    const bool need_t = (quad == 1 && I <= J) || (quad == 2);
-    if (need_t) {
-        for (int q = 0; q < PT; q += 8) {
-            int64_t rr = J * PT + ty + q, cc = I * PT + tx;
-            uint32_t va = 0, vb = 0;
-            if (rr < h && cc < h) {
-                if (quad == 1) {
-                    va = __ldg(nd.P1 + rr * nd.ldr + cc);
-                    vb = __ldg(nd.P5 + rr * nd.ldr + cc);
-                } else {
-                    va = __ldg(nd.P4 + rr * nd.ldg + cc);
-                }
+    constexpr int NR = PT / 8;
+    const int64_t j = J * PT + tx;
+    uint32_t vals[NR];
+    if (quad == 0) {
+        uint32_t x[NR], z[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            const int64_t i = I * PT + ty + 8 * q;
+            const bool ok = i < h && j < h && j <= i;
+            x[q] = ok ? __ldg(nd.P1 + i * nd.ldr + j) : 0u;
+            z[q] = ok ? __ldg(nd.P2 + i * nd.ldr + j) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < NR; ++q) vals[q] = addm(x[q], z[q], p);  // Low(U3) = Low(P1 + P2)
+    } else if (quad == 1) {
+        // Up(U1) = Low(U1)ᵀ: tile (J, I) of P1 + P5 through shared memory
+        if (I <= J) {
+            uint32_t t1[NR], t5[NR];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                const int64_t rr = J * PT + ty + 8 * q, cc = I * PT + tx;
+                const bool ok = rr < h && cc < h;
+                t1[q] = ok ? __ldg(nd.P1 + rr * nd.ldr + cc) : 0u;
+                t5[q] = ok ? __ldg(nd.P5 + rr * nd.ldr + cc) : 0u;
             }
-            sa[ty + q][tx] = va;
-            sb[ty + q][tx] = vb;
+#pragma unroll
+            for (int q = 0; q < NR; ++q) sa[ty + 8 * q][tx] = t1[q] + t5[q];
+            __syncthreads();
+        }
+        uint32_t u1[NR], g3[NR], g4[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            const int ly = ty + 8 * q;
+            const int64_t i = I * PT + ly;
+            const bool ok = i < h && j < h;
+            const bool lowr = ok && i >= j;
+            const uint32_t a1 = lowr ? __ldg(nd.P1 + i * nd.ldr + j) : 0u;
+            const uint32_t a5 = lowr ? __ldg(nd.P5 + i * nd.ldr + j) : 0u;
+            u1[q] = lowr ? a1 + a5 : (ok ? sa[tx][ly] : 0u);
+            g3[q] = ok ? __ldg(nd.P3 + i * nd.ldg + j) : 0u;
+            g4[q] = ok ? __ldg(nd.P4 + i * nd.ldg + j) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < NR; ++q) vals[q] = red(u1[q] + g4[q] + g3[q], m);  // U4 = U1 + P4 + P3
+    } else {
+        // P4ᵀ: tile (J, I) of P4 through shared memory
+        {
+            uint32_t t4[NR];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                const int64_t rr = J * PT + ty + 8 * q, cc = I * PT + tx;
+                t4[q] = (rr < h && cc < h) ? __ldg(nd.P4 + rr * nd.ldg + cc) : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < NR; ++q) sa[ty + 8 * q][tx] = t4[q];
+        }
+        uint32_t a1[NR], a5[NR], g4[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            const int64_t i = I * PT + ty + 8 * q;
+            const bool ok = i < h && j < h && j <= i;
+            a1[q] = ok ? __ldg(nd.P1 + i * nd.ldr + j) : 0u;
+            a5[q] = ok ? __ldg(nd.P5 + i * nd.ldr + j) : 0u;
+            g4[q] = ok ? __ldg(nd.P4 + i * nd.ldg + j) : 0u;
         }
         __syncthreads();
-    }
-    int64_t r0, c0;  // output tile origin in the node's 2h×2h result
-    if (quad == 0) {
-        r0 = I * PT;
-        c0 = J * PT;
-    } else if (quad == 1) {
-        r0 = h + I * PT;
-        c0 = J * PT;
-    } else {
-        r0 = h + I * PT;
-        c0 = h + J * PT;
-    }
-    for (int q = 0; q < PT; q += 8) {
-        const int ly = ty + q;
-        const int64_t i = I * PT + ly, j = J * PT + tx;
-        uint32_t val = 0;
-        if (i < h && j < h) {
-            if (quad == 0) {
-                if (j <= i) val = addm(__ldg(nd.P1 + i * nd.ldr + j), __ldg(nd.P2 + i * nd.ldr + j), p);
-            } else if (quad == 1) {
-                uint32_t u1;
-                if (i >= j)
-                    u1 = __ldg(nd.P1 + i * nd.ldr + j) + __ldg(nd.P5 + i * nd.ldr + j);
-                else
-                    u1 = sa[tx][ly] + sb[tx][ly];  // Up(U1) = Low(U1)ᵀ
-                val = red(u1 + __ldg(nd.P4 + i * nd.ldg + j) + __ldg(nd.P3 + i * nd.ldg + j), m);
-            } else if (j <= i) {
-                val = red(__ldg(nd.P1 + i * nd.ldr + j) + __ldg(nd.P5 + i * nd.ldr + j) +
-                              __ldg(nd.P4 + i * nd.ldg + j) + sa[tx][ly],
-                          m);
-            }
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            const int ly = ty + 8 * q;
+            vals[q] = red(a1[q] + a5[q] + g4[q] + sa[tx][ly], m);  // Low(U5) = Low(U1 + P4 + P4ᵀ)
         }
-        so[ly][tx] = val;
     }
+    const int64_t r0 = (quad == 0 ? 0 : h) + I * PT, c0 = (quad == 2 ? h : 0) + J * PT;
     if (!nd.upper) {
-        for (int q = 0; q < PT; q += 8) {
-            const int ly = ty + q;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            const int ly = ty + 8 * q;
             const int64_t R = r0 + ly, Cc = c0 + tx;
             const bool inside = (I * PT + ly < h) && (J * PT + tx < h);
-            if (inside && R < nd.vn && Cc < nd.vn && Cc <= R) nd.out[R * nd.ldo + Cc] = so[ly][tx];
+            if (inside && R < nd.vn && Cc < nd.vn && Cc <= R) nd.out[R * nd.ldo + Cc] = vals[q];
         }
     } else {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) so[ty + 8 * q][tx] = vals[q];
         __syncthreads();
         // element (R, Cc) of the lower result goes to out[Cc][R]
-        for (int q = 0; q < PT; q += 8) {
-            const int lc = ty + q;  // column within the tile
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            const int lc = ty + 8 * q;  // column within the tile
             const int64_t R = r0 + tx, Cc = c0 + lc;
             const bool inside = (I * PT + tx < h) && (J * PT + lc < h);
             if (inside && R < nd.vn && Cc < nd.vn && Cc <= R) nd.out[Cc * nd.ldo + R] = so[tx][lc];
@@ -265,62 +308,89 @@ __global__ void __launch_bounds__(256) k_post(const PostNode *__restrict__ nodes
     }
 }
 
-__global__ void k_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper) {
-    const int64_t total = n * n;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = idx / n, c = idx - r * n;
+// Zero row r0 + blockIdx.y of the selected triangle of C.
+__global__ void k_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, int64_t r0) {
+    const int64_t r = r0 + blockIdx.y;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x)
         if (upper ? c >= r : c <= r) C[r * ldc + c] = 0;
-    }
 }
 
-int grid_for(int64_t work, int threads) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t blocks = (work + threads - 1) / threads;
-    int64_t cap = (int64_t)sms * 16;  // grid-stride beyond 16 blocks per SM
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    return (int)blocks;
+template <int D, bool U32, int YF, bool RED>
+cudaError_t launch_prep_t(dim3 grid, cudaStream_t st, const PrepNode *nodes, int64_t h, int64_t w,
+                          int64_t kpad, ModP mp, YConst y) {
+    k_prep<D, U32, YF, RED><<<grid, PREP_THREADS, 0, st>>>(nodes, h, w, kpad, mp, y);
+    return cudaGetLastError();
+}
+
+template <int D, bool U32>
+cudaError_t launch_prep_d(dim3 grid, cudaStream_t st, const PrepNode *nodes, int64_t h, int64_t w,
+                          int64_t kpad, ModP mp, YConst y, bool reduce) {
+    if (y.form == 0)
+        return reduce ? launch_prep_t<D, U32, 0, true>(grid, st, nodes, h, w, kpad, mp, y)
+                      : launch_prep_t<D, U32, 0, false>(grid, st, nodes, h, w, kpad, mp, y);
+    return reduce ? launch_prep_t<D, U32, 1, true>(grid, st, nodes, h, w, kpad, mp, y)
+                  : launch_prep_t<D, U32, 1, false>(grid, st, nodes, h, w, kpad, mp, y);
 }
 
 }  // namespace
 
 cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_t w,
                         int64_t kpad, ModP mp, YConst y, DigitScheme ds, int arena_kind,
-                        cudaStream_t st) {
-    int64_t work = h * (kpad / 2) * nnodes;
-    if (work == 0) return cudaSuccess;
-    k_prep<<<grid_for(work, 256), 256, 0, st>>>(nodes_dev, nnodes, h, w, kpad, mp, y, ds,
-                                                arena_kind);
-    return cudaGetLastError();
+                        bool reduce_input, cudaStream_t st) {
+    if (h == 0 || kpad == 0 || nnodes == 0) return cudaSuccess;
+    const int64_t gx = (kpad / 2 + PREP_THREADS - 1) / PREP_THREADS;
+    const int64_t gy = std::min<int64_t>((h + PREP_ROWS - 1) / PREP_ROWS, 65535);
+    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nnodes);
+    if (arena_kind == ARENA_U32)
+        return launch_prep_d<1, true>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+    switch (ds.D) {
+        case 1: return launch_prep_d<1, false>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+        case 2: return launch_prep_d<2, false>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+        case 3: return launch_prep_d<3, false>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+    }
+    return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_work, ModP mp,
-                            DigitScheme ds, int arena_kind, cudaStream_t st) {
-    if (njobs == 0 || max_work == 0) return cudaSuccess;
-    int gx = grid_for(max_work, 256);
-    if (njobs > 1) gx = (int)std::min<int64_t>(gx, std::max<int64_t>(1, (max_work + 1023) / 1024));
-    dim3 grid((unsigned)gx, (unsigned)njobs);
-    k_digitize<<<grid, 256, 0, st>>>(jobs_dev, mp, ds, arena_kind);
+cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_rows,
+                            int64_t max_kpad, ModP mp, DigitScheme ds, int arena_kind,
+                            cudaStream_t st) {
+    if (njobs == 0 || max_rows == 0 || max_kpad == 0) return cudaSuccess;
+    const int64_t gx = (max_kpad / 2 + PREP_THREADS - 1) / PREP_THREADS;
+    const int64_t gy = std::min<int64_t>((max_rows + DIG_ROWS - 1) / DIG_ROWS, 65535);
+    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)njobs);
+    if (arena_kind == ARENA_U32) {
+        k_digitize<1, true><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, mp);
+    } else {
+        switch (ds.D) {
+            case 1: k_digitize<1, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, mp); break;
+            case 2: k_digitize<2, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, mp); break;
+            case 3: k_digitize<3, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, mp); break;
+            default: return cudaErrorInvalidValue;
+        }
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP mp,
                         cudaStream_t st) {
     if (h == 0 || nnodes == 0) return cudaSuccess;
-    int64_t T = (h + PT - 1) / PT;
-    int64_t tiles = 2 * T * T + T;  // two triangles + one square
-    dim3 grid((unsigned)tiles, (unsigned)nnodes);
+    const int64_t T = (h + PT - 1) / PT;
+    if (T > 65535 || 3 * (int64_t)nnodes > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)T, (unsigned)T, (unsigned)(3 * nnodes));
     k_post<<<grid, 256, 0, st>>>(nodes_dev, h, mp);
     return cudaGetLastError();
 }
 
 cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    k_zero_tri<<<grid_for(n * n, 256), 256, 0, st>>>(C, n, ldc, upper);
-    return cudaGetLastError();
+    for (int64_t r0 = 0; r0 < n; r0 += 65535) {
+        const int64_t rows = std::min<int64_t>(65535, n - r0);
+        dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 1024), (unsigned)rows);
+        k_zero_tri<<<grid, 256, 0, st>>>(C, n, ldc, upper, r0);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace fsk

@@ -162,11 +162,17 @@ __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// The (tile, digit pair, K-chunk) sequence every role walks in the same order.
+// The (tile, K-span, digit pair, K-chunk) sequence every role walks in the
+// same order.  K is cut into spans of SPAN_KB k-blocks; inside a span every
+// digit pair (i, j) runs over it in chunks of at most chunk_kb[i][j].  Taking
+// all pairs of one span before moving on reuses each operand's span D times
+// while it is still in L2.
+constexpr int SPAN_KB = 16;  // 1024 k-elements
 struct UnitIter {
     int D;
-    int i, j;       // digit pair
-    int kb0, nkb;   // k-block range of this chunk
+    int i, j;          // digit pair
+    int kb0, nkb;      // k-block range of this unit
+    int span0, span1;  // current span [span0, span1)
     int kblocks;
     const DigitScheme *ds;
     __device__ void start(const DigitScheme &s, int kbl) {
@@ -175,23 +181,32 @@ struct UnitIter {
         kblocks = kbl;
         i = 0;
         j = 0;
+        span0 = 0;
+        span1 = kbl < SPAN_KB ? kbl : SPAN_KB;
         kb0 = 0;
         set_len();
     }
     __device__ void set_len() {
-        int c = ds->chunk_kb[i][j];
-        nkb = kblocks - kb0 < c ? kblocks - kb0 : c;
+        const int c = ds->chunk_kb[i][j];
+        nkb = span1 - kb0 < c ? span1 - kb0 : c;
     }
     // advance; false when the tile is done
     __device__ bool next() {
         kb0 += nkb;
-        if (kb0 >= kblocks) {
-            kb0 = 0;
-            if (++j == D) {
-                j = 0;
-                if (++i == D) return false;
+        if (kb0 < span1) {
+            set_len();
+            return true;
+        }
+        if (++j == D) {
+            j = 0;
+            if (++i == D) {
+                i = 0;
+                span0 = span1;
+                if (span0 >= kblocks) return false;
+                span1 = kblocks - span0 < SPAN_KB ? kblocks : span0 + SPAN_KB;
             }
         }
+        kb0 = span0;
         set_len();
         return true;
     }
