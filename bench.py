@@ -244,7 +244,7 @@ def run_ours(args):
     C = torch.zeros((n, n), dtype=torch.int32, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
-    plan = ffsyrk.Plan(p, n, k, leaf=args.leaf, levels=levels)
+    plan = ffsyrk.Plan(p, n, k, leaf=args.leaf, levels=levels, tile_ctas=args.tile_ctas)
     info = plan.info()
     sampler = ClockSampler(local)
     if ws > 1:
@@ -348,6 +348,7 @@ def run_ours(args):
                 "config": {"workload": args.workload, "description": desc, "n": n, "k": k,
                            "p": p, "levels": info["levels"], "digits": info["digits"],
                            "leaf": {1: "tc_bf16", 2: "i64"}[info["leaf"]],
+                           "tile_ctas": info["tile_ctas"],
                            "y_form": "scalar" if info["y_form"] == 0 else "2x2",
                            "l2": "flushed between steps (512 MiB write)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -369,6 +370,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--levels", type=int, default=None)
     ap.add_argument("--leaf", choices=["tc", "i64"], default="tc")
+    ap.add_argument("--tile-ctas", type=int, choices=[0, 1, 2], default=0,
+                    help="tensor-core leaf tiles: 0 auto, 1 one SM, 2 SM pairs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")

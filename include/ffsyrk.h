@@ -74,7 +74,10 @@ typedef struct {
     int32_t levels; /* FFSYRK_LEVELS_AUTO (default): chosen from the shape;
                        0 = classical SYRK from the same leaves (no Algorithm 2
                        level); L >= 1 = L levels of Algorithm 2, L <= 6        */
-    int32_t reserved[6]; /* must be zero                                       */
+    int32_t tile_ctas; /* tensor-core leaf tiles: 0 = choose from the shape;
+                          1 = 128×256 tiles on one SM; 2 = 256×256 tiles on a
+                          pair of SMs (tcgen05 cta_group::2)                    */
+    int32_t reserved[5]; /* must be zero                                       */
 } ffsyrk_options_t;
 
 /* The defaults: automatic leaf and recursion depth. */
@@ -167,6 +170,7 @@ typedef struct {
     int32_t digits;      /* D, signed base-256 digits per residue          */
     int32_t chunk_k[9];  /* K-chunk per digit pair (i*3+j), TC leaf       */
     int64_t workspace_bytes;
+    int32_t tile_ctas;   /* 1 or 2: SMs per tensor-core leaf tile at max_n  */
 } ffsyrk_plan_info_t;
 
 ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t plan, ffsyrk_plan_info_t *info);

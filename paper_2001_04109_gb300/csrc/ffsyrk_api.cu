@@ -105,6 +105,7 @@ Geometry make_geometry(int64_t n, int64_t k, int L) {
 struct Layout {
     Geometry g;
     int leaf = FFSYRK_LEAF_TC_BF16;
+    int ctas = 1;  // tensor-core leaf tiles: 1 = one SM, 2 = a pair of SMs
     int narenas = 0;
     Arena arena[kMaxLevels + 1];          // index j: K = w_j (j = 0 only for L = 0)
     int64_t arena_off[kMaxLevels + 1] = {};
@@ -237,6 +238,7 @@ struct ffsyrk_plan_st {
     DigitScheme ds{};
     int leaf = FFSYRK_LEAF_TC_BF16;
     int levels_opt = FFSYRK_LEVELS_AUTO;
+    int ctas_opt = 0;
     int64_t max_n = 0, max_k = 0;
     int L_max = 0;  // levels used at the max shape
     // device workspace: data region then descriptor region
@@ -275,6 +277,16 @@ int choose_levels(const ffsyrk_plan_st *pl, int64_t n, int64_t k) {
     return L;
 }
 
+// SMs per tensor-core tile.  Measured on GB300 the CTA-pair tiles were 5-15%
+// slower than one-SM tiles on every shape tried (the pair's shared barriers
+// add latency while neither shared memory nor L2 is the limit), so one-SM
+// tiles are the default and pairs are an explicit option.
+int choose_ctas(const ffsyrk_plan_st *pl, const Geometry &g) {
+    (void)g;
+    if (pl->ctas_opt == 1 || pl->ctas_opt == 2) return pl->ctas_opt;
+    return 1;
+}
+
 ffsyrk_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? FFSYRK_SUCCESS : FFSYRK_ERR_CUDA; }
 
 // Tiles of one product in bands of kBand tile rows, column by column inside
@@ -304,8 +316,9 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     D = Descs();
     char *ws = pl->ws;
     const bool tc = lay.leaf == FFSYRK_LEAF_TC_BF16;
-    const int64_t TM = tc ? leaf_tc_bm() : leaf_i64_tile();
-    const int64_t TN = tc ? leaf_tc_bn() : leaf_i64_tile();
+    const bool pair = tc && lay.ctas == 2;
+    const int64_t TM = tc ? (pair ? leaf_tc2_bm() : leaf_tc_bm()) : leaf_i64_tile();
+    const int64_t TN = tc ? (pair ? leaf_tc2_bn() : leaf_tc_bn()) : leaf_i64_tile();
     for (int j = 0; j <= kMaxLevels; ++j)
         if (lay.arena[j].rows > 0) lay.arena[j].base = ws + lay.arena_off[j];
 
@@ -500,6 +513,7 @@ ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, cons
     if (!pl->have_last || key != pl->last_key) {
         Geometry g = make_geometry(n, k, L);
         Layout lay = make_layout(g, pl->leaf, pl->ds.D);
+        lay.ctas = choose_ctas(pl, g);
         if (lay.data_bytes > pl->data_cap) return FFSYRK_ERR_TOO_LARGE;
         // the staging blob may still be in flight from the previous upload
         if (pl->desc_pending) {
@@ -569,7 +583,7 @@ ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, cons
         tl.ds = pl->ds;
         tl.err = pl->err_dev;
         tl.tile_ctr = nullptr;
-        e = launch_leaf_tc(tl, pl->sms, st);
+        e = lay.ctas == 2 ? launch_leaf_tc2(tl, pl->sms, st) : launch_leaf_tc(tl, pl->sms, st);
     } else {
         e = launch_leaf_i64_arrays(reinterpret_cast<const LeafProd *>(dd + D.prods_off),
                                    reinterpret_cast<const LeafTile *>(dd + D.tiles_off),
@@ -650,7 +664,8 @@ ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
     if (opts) o = *opts;
     if (o.leaf < FFSYRK_LEAF_AUTO || o.leaf > FFSYRK_LEAF_I64) return FFSYRK_ERR_INVALID_ARG;
     if (o.levels < FFSYRK_LEVELS_AUTO || o.levels > kMaxLevels) return FFSYRK_ERR_INVALID_ARG;
-    for (int i = 0; i < 6; ++i)
+    if (o.tile_ctas < 0 || o.tile_ctas > 2) return FFSYRK_ERR_INVALID_ARG;
+    for (int i = 0; i < 5; ++i)
         if (o.reserved[i] != 0) return FFSYRK_ERR_INVALID_ARG;
 
     int dev = 0;
@@ -676,6 +691,7 @@ ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
     pl->ds = make_digits(p);
     pl->leaf = (o.leaf == FFSYRK_LEAF_AUTO) ? FFSYRK_LEAF_TC_BF16 : o.leaf;
     pl->levels_opt = o.levels;
+    pl->ctas_opt = o.tile_ctas;
     pl->max_n = max_n;
     pl->max_k = max_k;
     pl->L_max = choose_levels(pl, max_n, max_k);
@@ -739,6 +755,9 @@ ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t pl, ffsyrk_plan_info_t *info)
     for (int i = 0; i < pl->ds.D; ++i)
         for (int j = 0; j < pl->ds.D; ++j) info->chunk_k[i * 3 + j] = pl->ds.chunk_kb[i][j] * 64;
     info->workspace_bytes = pl->ws_bytes;
+    info->tile_ctas = pl->leaf == FFSYRK_LEAF_TC_BF16
+                          ? choose_ctas(pl, make_geometry(pl->max_n, pl->max_k, pl->L_max))
+                          : 1;
     return FFSYRK_SUCCESS;
 }
 

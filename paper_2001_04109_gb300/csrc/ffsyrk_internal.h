@@ -159,6 +159,10 @@ struct TcLaunch {
 cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st);
 int leaf_tc_bm();
 int leaf_tc_bn();
+// the same leaf on 256×256 tiles computed by a pair of CTAs (cta_group::2)
+cudaError_t launch_leaf_tc2(const TcLaunch &L, int num_sms, cudaStream_t st);
+int leaf_tc2_bm();
+int leaf_tc2_bn();
 int leaf_i64_tile();
 
 // The signed base-256 digit scheme and chunk lengths the planner uses for p.

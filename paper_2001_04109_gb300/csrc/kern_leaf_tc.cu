@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 
 #include "ffsyrk_internal.h"
+#include "tc_common.cuh"
 
 namespace fsk {
 namespace {
@@ -45,172 +46,9 @@ constexpr int NUM_THREADS = 32 * (EPI_WARPS + 2);  // no other warps: every warp
 constexpr int EPI_COLS = BN / (EPI_WARPS / 4);  // columns per epilogue thread (128)
 constexpr int LD_COLS = 16;  // TMEM columns per tcgen05.ld (128 residues + 16 loads fit 168 regs)
 constexpr int TMEM_COLS = 512;
-constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
-constexpr unsigned int ERR_WAIT = 1u;
 
-// instruction descriptor: D = f32, A = B = bf16, both K-major, N = 256, M = 128
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ uint32_t su32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t gtimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(su32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for the phase of `bar` with the given parity.  Returns false
-// (after recording the error) if it ran out or another role gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          unsigned int *err) {
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = gtimer();
-    uint32_t it = 0;
-    while (true) {
-        if (mbar_try(bar, parity)) return true;
-        if ((++it & 255u) == 0) {
-            if (*abort_flag) return false;
-            if (gtimer() - t0 > WAIT_LIMIT_NS) {
-                *abort_flag = 1;
-                if (err) atomicOr(err, ERR_WAIT);
-                return false;
-            }
-        }
-    }
-}
-// Bounded wait used while shutting down: ignores the abort flag so that
-// copies and MMAs already in flight can finish before the CTA exits.
-__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
-    const uint64_t t0 = gtimer();
-    while (!mbar_try(bar, parity))
-        if (gtimer() - t0 > WAIT_LIMIT_NS / 4) return;
-}
-
-__device__ __forceinline__ void tma_load(void *dst, const void *tmap, uint64_t *bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
-        "l"(tmap), "r"(su32(bar)), "r"(x), "r"(y)
-        : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)1 << 16;              // leading byte offset (unused with swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
-    d |= (uint64_t)1 << 46;              // version
-    d |= (uint64_t)2 << 61;              // SWIZZLE_128B
-    return d;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(IDESC), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     su32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-// 32 lanes × 16 consecutive 32-bit columns: thread t of the warp gets lane
-// (base lane + t), columns [col, col + 16).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-          "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// The (tile, K-span, digit pair, K-chunk) sequence every role walks in the
-// same order.  K is cut into spans of SPAN_KB k-blocks; inside a span every
-// digit pair (i, j) runs over it in chunks of at most chunk_kb[i][j].  Taking
-// all pairs of one span before moving on reuses each operand's span D times
-// while it is still in L2.
-constexpr int SPAN_KB = 16;  // 1024 k-elements
-struct UnitIter {
-    int D;
-    int i, j;          // digit pair
-    int kb0, nkb;      // k-block range of this unit
-    int span0, span1;  // current span [span0, span1)
-    int kblocks;
-    const DigitScheme *ds;
-    __device__ void start(const DigitScheme &s, int kbl) {
-        ds = &s;
-        D = s.D;
-        kblocks = kbl;
-        i = 0;
-        j = 0;
-        span0 = 0;
-        span1 = kbl < SPAN_KB ? kbl : SPAN_KB;
-        kb0 = 0;
-        set_len();
-    }
-    __device__ void set_len() {
-        const int c = ds->chunk_kb[i][j];
-        nkb = span1 - kb0 < c ? span1 - kb0 : c;
-    }
-    // advance; false when the tile is done
-    __device__ bool next() {
-        kb0 += nkb;
-        if (kb0 < span1) {
-            set_len();
-            return true;
-        }
-        if (++j == D) {
-            j = 0;
-            if (++i == D) {
-                i = 0;
-                span0 = span1;
-                if (span0 >= kblocks) return false;
-                span1 = kblocks - span0 < SPAN_KB ? kblocks : span0 + SPAN_KB;
-            }
-        }
-        kb0 = span0;
-        set_len();
-        return true;
-    }
-};
+constexpr uint32_t IDESC = tc::idesc_bf16(BM, BN);
+using namespace tc;
 
 __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__restrict__ prods,
                                                              const LeafTile *__restrict__ tiles,
@@ -321,7 +159,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
                         const uint32_t sb = sa + A_BYTES;
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk)
-                            mma_bf16(tmem_d, sdesc(sa + kk * 32), sdesc(sb + kk * 32),
+                            mma_bf16(tmem_d, sdesc(sa + kk * 32), sdesc(sb + kk * 32), IDESC,
                                      (kb > 0 || kk > 0) ? 1u : 0u);
                         mma_commit(&empty_bar[s]);
                     }

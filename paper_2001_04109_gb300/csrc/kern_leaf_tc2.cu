@@ -1,0 +1,333 @@
+// Tensor-core leaf on CTA pairs: out = X·Zᵀ mod p with tcgen05.mma.cta_group::2.
+//
+// Same arithmetic as the one-CTA leaf (exact signed base-256 digits in bf16,
+// FP32 accumulation over K-chunks bounded by 2^24, delayed reduction mod p
+// in the epilogue), on 256×256 output tiles computed by a cluster of two
+// CTAs on two SMs.  CTA r of the pair stages rows [128r, 128r + 128) of the
+// X tile and rows [128r, 128r + 128) of the Z tile (the tile's columns); one
+// 256×256×16 MMA issued by the even CTA reads both CTAs' shared memory, and
+// each CTA's tensor memory receives its own 128 rows × 256 columns.  Per SM
+// and per k-block this stages 32 KB instead of the 48 KB a one-CTA 128×256
+// tile needs for the same multiply-adds, which relieves shared memory.
+//
+// Synchronisation across the pair:
+//   full[s]   lives in the even CTA; its producer expects both CTAs' bytes,
+//             and both CTAs' TMA loads (cta_group::2) complete on it;
+//   empty[s]  in both CTAs, signalled by a multicast MMA commit;
+//   accf[b]   in both CTAs, signalled by a multicast MMA commit;
+//   acce[b]   in the even CTA, 16 arrivals: every epilogue warp of both CTAs.
+// Every wait is bounded (mbar_wait); the pair meets at cluster barriers after
+// initialising its barriers and before releasing tensor memory.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "ffsyrk_internal.h"
+#include "tc_common.cuh"
+
+namespace fsk {
+namespace {
+
+using namespace tc;
+
+constexpr int BM = 256, BN = 256, BK = 64;  // pair tile
+constexpr int ROWS = 128;                    // rows of X and of Z staged per CTA
+constexpr int STAGES = 6;
+constexpr int A_BYTES = ROWS * BK * 2;              // 16 KB
+constexpr int B_BYTES = ROWS * BK * 2;              // 16 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;      // 32 KB per CTA
+constexpr int EPI_WARPS = 8;
+constexpr int PRODUCER_WARP = 8, MMA_WARP = 9;
+constexpr int NUM_THREADS = 32 * (EPI_WARPS + 2);
+constexpr int EPI_COLS = BN / (EPI_WARPS / 4);      // 128 columns per epilogue thread
+constexpr int LD_COLS = 16;
+constexpr int TMEM_COLS = 512;
+constexpr uint32_t IDESC = idesc_bf16(BM, BN);
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void arrive_remote(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+                 : "memory");
+}
+// TMA load into this CTA's shared memory, completing on a barrier that may
+// live in the peer CTA (cluster address).
+__device__ __forceinline__ void tma_load_pair(void *dst, const void *tmap, uint32_t bar_cluster,
+                                              int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
+        "l"(tmap), "r"(bar_cluster), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void mma_pair(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+        : "memory");
+}
+// Arrive on the barrier at this offset in every CTA of `mask` once all
+// previously issued MMAs of this thread have completed.
+__device__ __forceinline__ void commit_pair(uint64_t *bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(su32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
+    k_leaf_tc2(const LeafProd *__restrict__ prods, const LeafTile *__restrict__ tiles, int ntiles,
+               const CUtensorMap *__restrict__ tmaps, ModP m,
+               const __grid_constant__ DigitScheme ds, unsigned int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
+    __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], drain_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf_bar[b], 1);
+            mbar_init(&acce_bar[b], 2 * EPI_WARPS);
+        }
+        mbar_init(&drain_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == MMA_WARP) {
+        // both CTAs of the pair allocate the same columns together
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(&tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        fence_before();
+    }
+    __syncthreads();
+    cluster_sync();  // the peer's barriers are initialised before any remote use
+    fence_after();
+    const uint32_t tmem_base = tmem_slot;
+
+    if (warp == PRODUCER_WARP) {
+        // ---------------- TMA producer (both CTAs) ----------------
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok; t += npairs) {
+                const LeafTile tl = tiles[t];
+                const LeafProd pr = prods[tl.prod];
+                const CUtensorMap *tm = tmaps + pr.arena;
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tm)
+                             : "memory");
+                UnitIter u;
+                u.start(ds, pr.kblocks);
+                do {
+                    const int ya = (int)(pr.a_row0 + (int64_t)u.i * pr.plane_rows +
+                                         (int64_t)tl.tm * BM + rank * ROWS);
+                    const int yb = (int)(pr.b_row0 + (int64_t)u.j * pr.plane_rows +
+                                         (int64_t)tl.tn * BN + rank * ROWS);
+                    for (int kb = u.kb0; kb < u.kb0 + u.nkb; ++kb, ++it) {
+                        const int s = it % STAGES;
+                        const uint32_t ph = (it / STAGES) & 1u;
+                        if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag, err)) {
+                            ok = false;
+                            break;
+                        }
+                        unsigned char *sa = smem + s * STAGE_BYTES;
+                        unsigned char *sb = sa + A_BYTES;
+                        const uint32_t fb = mapa_rank(su32(&full_bar[s]), 0);
+                        if (rank == 0) mbar_expect_tx(&full_bar[s], 2 * STAGE_BYTES);
+                        tma_load_pair(sa, tm, fb, kb * BK, ya);
+                        tma_load_pair(sb, tm, fb, kb * BK, yb);
+                    }
+                } while (ok && u.next());
+            }
+            if (!ok && rank == 0) {
+                const uint32_t first = it > STAGES ? it - STAGES : 0;
+                for (uint32_t q = first; q < it; ++q) mbar_drain(&full_bar[q % STAGES], (q / STAGES) & 1u);
+            }
+        }
+    } else if (warp == MMA_WARP) {
+        // ---------------- MMA issuer (even CTA only) ----------------
+        if (lane == 0 && rank == 0) {
+            uint32_t it = 0, unit = 0;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok; t += npairs) {
+                const LeafProd pr = prods[tiles[t].prod];
+                UnitIter u;
+                u.start(ds, pr.kblocks);
+                do {
+                    const uint32_t b = unit & 1u;
+                    if (!mbar_wait(&acce_bar[b], ((unit >> 1) & 1u) ^ 1u, &abort_flag, err)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t tmem_d = tmem_base + b * BN;
+                    for (int kb = 0; kb < u.nkb; ++kb, ++it) {
+                        const int s = it % STAGES;
+                        if (!mbar_wait(&full_bar[s], (it / STAGES) & 1u, &abort_flag, err)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint32_t sa = su32(smem + s * STAGE_BYTES);
+                        const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            mma_pair(tmem_d, sdesc(sa + kk * 32), sdesc(sb + kk * 32),
+                                     (kb > 0 || kk > 0) ? 1u : 0u);
+                        commit_pair(&empty_bar[s], 0x3);
+                    }
+                    if (!ok) break;
+                    commit_pair(&accf_bar[b], 0x3);
+                    ++unit;
+                } while (u.next());
+            }
+            commit_pair(&drain_bar, 0x1);
+            mbar_drain(&drain_bar, 0);
+        }
+    } else if (warp < EPI_WARPS) {
+        // ---------------- epilogue (both CTAs) ----------------
+        const uint32_t p = m.p, twop = 2 * m.p, off = ds.offset;
+        const int quad = warp & 3, colq = warp >> 2;
+        const uint32_t acce_leader[2] = {mapa_rank(su32(&acce_bar[0]), 0),
+                                         mapa_rank(su32(&acce_bar[1]), 0)};
+        uint32_t unit = 0;
+        bool ok = true;
+        for (int t = pair; t < ntiles && ok; t += npairs) {
+            const LeafTile tl = tiles[t];
+            const LeafProd pr = prods[tl.prod];
+            uint32_t acc[EPI_COLS];
+#pragma unroll
+            for (int e = 0; e < EPI_COLS; ++e) acc[e] = 0;
+            UnitIter u;
+            u.start(ds, pr.kblocks);
+            do {
+                const uint32_t b = unit & 1u;
+                const bool got = mbar_wait(&accf_bar[b], (unit >> 1) & 1u, &abort_flag, err);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t w = ds.weight[u.i][u.j].w, wsh = ds.weight[u.i][u.j].w_sh;
+                const uint32_t taddr =
+                    tmem_base + b * BN + ((uint32_t)(quad * 32) << 16) + colq * EPI_COLS;
+#pragma unroll
+                for (int cc = 0; cc < EPI_COLS / LD_COLS; ++cc) {
+                    uint32_t v[LD_COLS];
+                    tmem_ld16(taddr + cc * LD_COLS, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < LD_COLS; ++e) {
+                        const int xi = __float2int_rn(__uint_as_float(v[e]));
+                        const uint32_t a = (uint32_t)(xi + (int)off);
+                        const uint32_t q = __umulhi(a, wsh);
+                        const uint32_t r = a * w - q * p;  // [0, 2p)
+                        const uint32_t s = acc[cc * LD_COLS + e] + r;
+                        acc[cc * LD_COLS + e] = min(s, s - twop);
+                    }
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) arrive_remote(acce_leader[b]);
+                ++unit;
+            } while (u.next());
+            if (!ok) break;
+            const int64_t r = (int64_t)tl.tm * BM + rank * ROWS + quad * 32 + lane;
+            const int64_t c0 = (int64_t)tl.tn * BN + colq * EPI_COLS;
+            if (r < pr.rows) {
+                uint32_t *orow = pr.out + r * pr.ldo;
+                const bool all_cols = c0 + EPI_COLS <= pr.cols;
+                const bool tri_ok = pr.tri == 0 || (pr.tri == 1 && c0 + EPI_COLS - 1 <= r) ||
+                                    (pr.tri == 2 && c0 >= r);
+                const bool aligned = ((reinterpret_cast<uintptr_t>(orow + c0) & 15u) == 0);
+                if (all_cols && tri_ok && aligned) {
+#pragma unroll
+                    for (int e = 0; e < EPI_COLS; e += 4) {
+                        uint4 v4;
+                        v4.x = acc[e] >= p ? acc[e] - p : acc[e];
+                        v4.y = acc[e + 1] >= p ? acc[e + 1] - p : acc[e + 1];
+                        v4.z = acc[e + 2] >= p ? acc[e + 2] - p : acc[e + 2];
+                        v4.w = acc[e + 3] >= p ? acc[e + 3] - p : acc[e + 3];
+                        *reinterpret_cast<uint4 *>(orow + c0 + e) = v4;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < EPI_COLS; ++e) {
+                        const int64_t c = c0 + e;
+                        const bool keep = c < pr.cols && (pr.tri == 0 || (pr.tri == 1 && c <= r) ||
+                                                          (pr.tri == 2 && c >= r));
+                        if (keep) orow[c] = acc[e] >= p ? acc[e] - p : acc[e];
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    cluster_sync();  // no CTA leaves while its peer may still signal it
+    if (warp == MMA_WARP) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+int leaf_tc2_bm() { return BM; }
+int leaf_tc2_bn() { return BN; }
+
+cudaError_t launch_leaf_tc2(const TcLaunch &L, int num_sms, cudaStream_t st) {
+    if (L.ntiles == 0) return cudaSuccess;
+    const int smem = STAGES * STAGE_BYTES + 1024;
+    static int max_pairs = 0;
+    if (max_pairs == 0) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_leaf_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * (num_sms / 2), 1, 1);
+        cfg.blockDim = dim3(NUM_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        int clusters = 0;
+        e = cudaOccupancyMaxActiveClusters(&clusters, k_leaf_tc2, &cfg);
+        if (e != cudaSuccess || clusters <= 0) {
+            cudaGetLastError();
+            clusters = num_sms / 2;
+        }
+        max_pairs = clusters;
+    }
+    const int pairs = L.ntiles < max_pairs ? L.ntiles : max_pairs;
+    k_leaf_tc2<<<2 * pairs, NUM_THREADS, smem, st>>>(
+        L.prods, L.tiles, L.ntiles, reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp, L.ds,
+        L.err);
+    return cudaGetLastError();
+}
+
+}  // namespace fsk

@@ -41,14 +41,15 @@ class FfsyrkError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int32), ("levels", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("tile_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("p", ctypes.c_uint32), ("y_form", ctypes.c_int32), ("y_a", ctypes.c_uint32),
                 ("y_b", ctypes.c_uint32), ("y_cost", ctypes.c_int32), ("leaf", ctypes.c_int32),
                 ("levels", ctypes.c_int32), ("digits", ctypes.c_int32),
-                ("chunk_k", ctypes.c_int32 * 9), ("workspace_bytes", ctypes.c_int64)]
+                ("chunk_k", ctypes.c_int32 * 9), ("workspace_bytes", ctypes.c_int64),
+                ("tile_ctas", ctypes.c_int32)]
 
 
 class Timing(ctypes.Structure):
@@ -127,21 +128,22 @@ def _mat_args(X: torch.Tensor, name: str):
     return X.data_ptr(), ld
 
 
-def make_options(leaf=None, levels=None) -> Options:
+def make_options(leaf=None, levels=None, tile_ctas=None) -> Options:
     o = Options()
     lib().ffsyrk_options_default(ctypes.byref(o))
     o.leaf = _LEAVES[leaf] if not isinstance(leaf, int) else leaf
     o.levels = LEVELS_AUTO if levels is None else int(levels)
+    o.tile_ctas = 0 if tile_ctas is None else int(tile_ctas)
     return o
 
 
 class Plan:
     """An ffsyrk plan: p, Y, digits, depth and workspace for n ≤ max_n, k ≤ max_k."""
 
-    def __init__(self, p: int, max_n: int, max_k: int, leaf=None, levels=None):
+    def __init__(self, p: int, max_n: int, max_k: int, leaf=None, levels=None, tile_ctas=None):
         self.p = int(p)
         self._h = ctypes.c_void_p()
-        o = make_options(leaf, levels)
+        o = make_options(leaf, levels, tile_ctas)
         _check(lib().ffsyrk_plan(ctypes.byref(self._h), self.p, int(max_n), int(max_k),
                                  ctypes.byref(o)), "ffsyrk_plan")
 
@@ -150,7 +152,8 @@ class Plan:
         _check(lib().ffsyrk_plan_get_info(self._h, ctypes.byref(i)), "ffsyrk_plan_get_info")
         return {"p": i.p, "y_form": i.y_form, "y_a": i.y_a, "y_b": i.y_b, "y_cost": i.y_cost,
                 "leaf": i.leaf, "levels": i.levels, "digits": i.digits,
-                "chunk_k": list(i.chunk_k), "workspace_bytes": i.workspace_bytes}
+                "chunk_k": list(i.chunk_k), "workspace_bytes": i.workspace_bytes,
+                "tile_ctas": i.tile_ctas}
 
     def __call__(self, A: torch.Tensor, C: torch.Tensor | None = None, uplo: str = "lower",
                  stream=None) -> torch.Tensor:

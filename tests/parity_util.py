@@ -9,7 +9,7 @@ SENTINEL = -559038737  # 0xDEADBEEF as int32: marks entries that must stay untou
 
 
 def gpu_syrk(A_host: torch.Tensor, p: int, leaf=None, levels=None, uplo="lower", lda_pad=0,
-             ldc_pad=0):
+             ldc_pad=0, tile_ctas=None):
     """Run the library on a host int32 matrix; returns (C as uint32 numpy, plan info)."""
     n, k = A_host.shape
     dev = torch.device("cuda")
@@ -18,7 +18,7 @@ def gpu_syrk(A_host: torch.Tensor, p: int, leaf=None, levels=None, uplo="lower",
     A = Abig[:, :k]
     Cbig = torch.full((n, n + ldc_pad), SENTINEL, dtype=torch.int32, device=dev)
     C = Cbig[:, :n]
-    plan = ffsyrk.Plan(p, max(n, 1), max(k, 1), leaf=leaf, levels=levels)
+    plan = ffsyrk.Plan(p, max(n, 1), max(k, 1), leaf=leaf, levels=levels, tile_ctas=tile_ctas)
     plan(A, C, uplo=uplo)
     plan.sync_status()
     info = plan.info()
