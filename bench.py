@@ -42,6 +42,9 @@ WORKLOADS = {
     "large": (32768, 32768, 8388593, "fast A·Aᵀ mod p, A 32768×32768, p=8388593 (D=3)"),
 }
 DEFAULT_WORKLOAD = "square4096"
+# 2048 independent problems, n and k each log-uniform in [32, 2048] (seed 5), p = 65521
+BATCH = {"count": 2048, "lo": 32, "hi": 2048, "seed": 5, "p": 65521,
+         "description": "batched A·Aᵀ mod p: 2048 problems, n, k log-uniform in [32, 2048], p=65521"}
 
 
 def measured_peaks():
@@ -175,6 +178,27 @@ def run_reference(args):
     import numpy as np
 
     from paper_2001_04109_gb300 import inputs
+    if args.workload == "batched":
+        shapes = inputs.batch_shapes(BATCH["count"], BATCH["lo"], BATCH["hi"], BATCH["seed"])
+        vals, base = [], None
+        for s in range(args.warmup + args.steps):
+            r = cpu_batched_rate(shapes, BATCH["p"], args.ref_budget)
+            if s >= args.warmup:
+                vals.append(r["value"])
+                base = r
+        v = statistics.median(vals)
+        ops = float(sum(n * n * k for n, k in shapes))
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ops / v * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic", "config": {"workload": "batched",
+                                                "description": BATCH["description"]},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"],
+                                 "kind": "oracle", "sample": base["sample"]},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     n, k, p, desc = WORKLOADS[args.workload]
     A = inputs.uniform_residues(n, k, p, seed=2).numpy().view(np.uint32)
     vals = []
@@ -199,25 +223,35 @@ def run_reference(args):
 
 
 def time_plan(plan, A, C, steps, warmup, flush, stream, timing=True):
-    """Device time per call (CUDA events on the launching stream), L2 flushed between calls."""
+    """Device time per call (CUDA events on the launching stream), L2 flushed between calls.
+
+    The timed calls run exactly as a user's repeated calls do (the library
+    replays its captured launch graph).  With ``timing``, a second pass of the
+    same length records the library's per-stage events (direct launches) for
+    the stage split and the leaf kernel's own duration.
+    """
     import torch
     for _ in range(warmup):
         plan(A, C, stream=stream)
     torch.cuda.synchronize()
-    plan.set_timing(timing)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
-    stage = []
     for s in range(steps):
         flush.zero_()
         ev[s][0].record(stream)
         plan(A, C, stream=stream)
         ev[s][1].record(stream)
-        if timing:
-            stage.append(plan.timing())
     torch.cuda.synchronize()
-    plan.set_timing(False)
     ms = [a.elapsed_time(b) for a, b in ev]
+    stage = []
+    if timing:
+        plan.set_timing(True)
+        for s in range(steps):
+            flush.zero_()
+            plan(A, C, stream=stream)
+            stage.append(plan.timing())
+        torch.cuda.synchronize()
+        plan.set_timing(False)
     return ms, stage
 
 
@@ -361,13 +395,177 @@ def run_ours(args):
     return 0
 
 
+def batch_problem(t, shapes, p, device):
+    from paper_2001_04109_gb300 import inputs
+    n, k = shapes[t]
+    return inputs.uniform_residues(n, k, p, seed=BATCH["seed"] * 100000 + t, device=device)
+
+
+def run_batched(args):
+    """One step = one ffsyrk_batched call over all 2048 problems (device-resident)."""
+    import ctypes
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2001_04109_gb300 import ffsyrk, inputs
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    p = BATCH["p"]
+    shapes = inputs.batch_shapes(BATCH["count"], BATCH["lo"], BATCH["hi"], BATCH["seed"])
+    count = len(shapes)
+    # all problems live in one contiguous input and one contiguous output buffer
+    a_off = np.cumsum([0] + [n * k for n, k in shapes])
+    c_off = np.cumsum([0] + [n * n for n, _ in shapes])
+    A_all = torch.empty(int(a_off[-1]), dtype=torch.int32, device="cuda")
+    C_all = torch.zeros(int(c_off[-1]), dtype=torch.int32, device="cuda")
+    As = [A_all[a_off[t]:a_off[t + 1]].view(n, k) for t, (n, k) in enumerate(shapes)]
+    Cs = [C_all[c_off[t]:c_off[t + 1]].view(n, n) for t, (n, _) in enumerate(shapes)]
+    for t in range(count):
+        As[t].copy_(batch_problem(t, shapes, p, "cuda"))
+    ops = float(sum(n * n * k for n, k in shapes))
+    field_macs = float(sum(n * (n + 1) // 2 * k for n, k in shapes))
+    I64 = ctypes.c_int64 * count
+    VP = ctypes.c_void_p * count
+    ns, ks = I64(*[n for n, _ in shapes]), I64(*[k for _, k in shapes])
+    pas, ldas = VP(*[a.data_ptr() for a in As]), I64(*[max(1, k) for _, k in shapes])
+    pcs, ldcs = VP(*[c.data_ptr() for c in Cs]), I64(*[max(1, n) for n, _ in shapes])
+    lib = ffsyrk.lib()
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    def call():
+        rc = lib.ffsyrk_batched(0, count, ns, ks, p, pas, ldas, pcs, ldcs, sh)
+        if rc != ffsyrk.SUCCESS:
+            raise ffsyrk.FfsyrkError(rc, "ffsyrk_batched")
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    host_ms = []
+    for s_ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev[s_][0].record(stream)
+        call()
+        ev[s_][1].record(stream)
+        torch.cuda.synchronize()
+        host_ms.append((time.perf_counter() - t0) * 1e3)
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    step_ms = sum(ms) / len(ms)
+    if ws > 1:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = ws * ops / (step_ms * 1e-3)
+    info = ffsyrk.Plan(p, 8, 8, leaf="tc", levels=0).info()
+    D = info["digits"]
+    peaks, peak_src = measured_peaks()
+    achieved = 2.0 * D * D * field_macs / (step_ms * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"],
+                "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
+                "traffic": None,
+                "kernel": "whole step (digit split + persistent grouped leaf launch)",
+                "peak_source": f"{peak_src} burst bf16 dense",
+                "algorithmic_flops_per_launch": 2.0 * D * D * field_macs}
+    parity = None
+    if not args.no_check and rank == 0:
+        import oracle
+        ok = True
+        picks = sorted(set([0, count - 1] + list(np.linspace(1, count - 2, 6).astype(int))))
+        for t in picks:
+            A_h = batch_problem(t, shapes, p, "cpu")
+            want = oracle.syrk(A_h.numpy(), p, "lower")
+            got = np.tril(Cs[t].cpu().numpy().view(np.uint32))
+            ok &= bool(np.array_equal(got, want))
+        parity = {"problems_checked": len(picks), "bit_exact": ok}
+    e2e = None
+    if not args.no_e2e:
+        A_pin = A_all.cpu().pin_memory()
+        C_pin = torch.empty_like(C_all, device="cpu").pin_memory()
+        evs = []
+        for it in range(1 + args.steps):
+            flush.zero_()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            A_all.copy_(A_pin, non_blocking=True)
+            call()
+            C_pin.copy_(C_all, non_blocking=True)
+            b_.record(stream)
+            if it > 0:
+                evs.append((a_, b_))
+        torch.cuda.synchronize()
+        e_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        e2e = {"value": ws * ops / (e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(4 * n * k for n, k in shapes)),
+               "d2h_bytes_per_step": int(sum(4 * n * n for n, _ in shapes)), "ms_per_step": e_ms}
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_batched_rate(shapes, p, args.cpu_budget)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u32", "data": "synthetic",
+                "config": {"workload": "batched", "description": BATCH["description"],
+                           "count": count, "sum_n2k": ops, "p": p, "levels": 0,
+                           "leaf": "tc_bf16", "scheduling": "device work queue, graph replay",
+                           "l2": "flushed between steps (512 MiB write)",
+                           "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "latency_ms": {"device_per_call": step_ms, "host_call_to_done": statistics.median(host_ms)},
+                "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roofline,
+                "cpu_baseline": cpu, "clocks": clocks, "parity": parity}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def cpu_batched_rate(shapes, p, budget_s):
+    """The oracle on whole problems of the batch (spread over the size range) within a budget."""
+    import oracle
+    order = sorted(range(len(shapes)), key=lambda t: shapes[t][0] * shapes[t][0] * shapes[t][1])
+    picks = order[:: max(1, len(order) // 64)]
+    done_ops, t_used, used = 0.0, 0.0, 0
+    for t in picks:
+        n, k = shapes[t]
+        A = batch_problem(t, shapes, p, "cpu").numpy()
+        t0 = time.perf_counter()
+        oracle.syrk(A, p, "lower")
+        t_used += time.perf_counter() - t0
+        done_ops += n * n * k
+        used += 1
+        if t_used > budget_s:
+            break
+    return {"value": done_ops / t_used, "unit": UNIT, "cores": oracle.default_threads(),
+            "kind": "oracle", "sample": f"{used} whole problems of the batch spread over the size "
+                                        f"range ({t_used:.1f} s)"}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--levels", type=int, default=None)
     ap.add_argument("--leaf", choices=["tc", "i64"], default="tc")
     ap.add_argument("--tile-ctas", type=int, choices=[0, 1, 2], default=0,
@@ -384,6 +582,8 @@ def main():
         # each step one bounded oracle sample; the whole run stays within a few minutes
         args.ref_budget = min(args.ref_budget, 150.0 / (args.steps + args.warmup))
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

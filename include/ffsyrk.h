@@ -77,7 +77,14 @@ typedef struct {
     int32_t tile_ctas; /* tensor-core leaf tiles: 0 = choose from the shape;
                           1 = 128×256 tiles on one SM; 2 = 256×256 tiles on a
                           pair of SMs (tcgen05 cta_group::2)                    */
-    int32_t reserved[5]; /* must be zero                                       */
+    int32_t autotune;  /* 1 (with levels = FFSYRK_LEVELS_AUTO and tile_ctas = 0):
+                          ffsyrk_plan times every candidate depth and tile
+                          variant at max_n × max_k on synthetic data in its own
+                          workspace and keeps the fastest.  Results are cached
+                          per process and, if the environment variable
+                          FFSYRK_TUNE_CACHE names a file, in that file.
+                          0: depth from the built-in cost model.            */
+    int32_t reserved[4]; /* must be zero                                       */
 } ffsyrk_options_t;
 
 /* The defaults: automatic leaf and recursion depth. */
@@ -171,6 +178,8 @@ typedef struct {
     int32_t chunk_k[9];  /* K-chunk per digit pair (i*3+j), TC leaf       */
     int64_t workspace_bytes;
     int32_t tile_ctas;   /* 1 or 2: SMs per tensor-core leaf tile at max_n  */
+    int32_t autotuned;   /* 1 if levels/tile_ctas came from the autotuner    */
+    float tuned_ms;      /* the winning candidate's time per call, or 0      */
 } ffsyrk_plan_info_t;
 
 ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t plan, ffsyrk_plan_info_t *info);
@@ -196,6 +205,20 @@ typedef struct {
 /* Timing of the most recent call with timing enabled: waits for its last
  * event.  FFSYRK_ERR_INVALID_ARG if timing is off or no call was made. */
 ffsyrk_status_t ffsyrk_plan_get_timing(ffsyrk_plan_t plan, ffsyrk_timing_t *timing);
+
+/* Introspection of the tensor-core leaf's exact-accumulation schedule for p
+ * and a leaf K of 64·kblocks (for tests and tools; needs no GPU).
+ * Writes up to `cap` segments as 5 int32 each: digit i, digit j, first
+ * k-block, k-block count, 1 if the segment opens a new FP32 accumulator
+ * (unit).  Returns the number of segments, or −1 for a bad p or argument.
+ * Every unit holds one weight class i + j and satisfies
+ * Σ 64·count·bound(i)·bound(j) ≤ 2^24 with the bounds of
+ * ffsyrk_digit_bounds(). */
+int32_t ffsyrk_leaf_schedule(uint32_t p, int32_t kblocks, int32_t *out, int32_t cap);
+
+/* The signed base-256 digit count D of p and the bound on |digit t| for
+ * t < D (written to max_digit[0..D−1]).  Returns D, or −1. */
+int32_t ffsyrk_digit_bounds(uint32_t p, int32_t *max_digit);
 
 /* Human-readable name of a status code (static storage). */
 const char *ffsyrk_status_string(ffsyrk_status_t status);

@@ -97,6 +97,7 @@ struct DigitizeJob {
     MatView X;
     int64_t rows;
     OperandDst dst;
+    int64_t block0;  // first block of this job in a flattened launch (prefix sum)
 };
 
 // One post-addition node: combines the five products into the node result.
@@ -117,11 +118,31 @@ struct LeafProd {
     int64_t a_row0, b_row0;
     int64_t rows, cols;   // valid output extent
     int32_t kblocks;      // K_pad / 64
-    int32_t pad_;
+    int32_t nseg;         // segments of the K schedule (see LeafSeg)
     int64_t plane_rows;   // arena rows between consecutive digit planes of an operand
     uint32_t *out;
     int64_t ldo;
+    int64_t seg0;         // first segment in the launch's segment table
 };
+
+// One step of a tile's K schedule: digit pair (i, j) over k-blocks
+// [kb0, kb0 + nkb).  `first` opens a unit: a run of segments of one weight
+// class 256^(i+j) accumulated in one FP32 tensor-memory buffer and drained
+// once by the epilogue.  Built on the host (build_segments) so the kernels
+// carry only an index.
+struct LeafSeg {
+    int32_t kb0;
+    uint16_t nkb;
+    uint8_t ij;     // i << 4 | j
+    uint8_t first;
+};
+// The schedule for one product with `kblocks` k-blocks: spans of 16
+// k-blocks; inside a span the weight classes e = i + j in order, the pairs
+// of a class in order; a unit grows while its worst-case |sum|
+// Σ 64·nkb·max|d_i|·max|d_j| stays ≤ 2^24 and never crosses a class.
+void build_segments(const DigitScheme &ds, int kblocks, std::vector<LeafSeg> &out);
+// The same into a caller's buffer of `cap` entries: the count, or −1 if it does not fit.
+int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int cap);
 
 struct LeafTile {
     int32_t prod;
@@ -138,6 +159,12 @@ cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_
 cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_rows,
                             int64_t max_kpad, ModP mp, DigitScheme ds, int arena_kind,
                             cudaStream_t st);
+// Digit split of many matrices in one flattened launch: exactly the blocks
+// the jobs need (jobs[t].block0 = blocks of jobs 0..t−1; total_blocks in all).
+cudaError_t launch_digitize_flat(const DigitizeJob *jobs_dev, int njobs, int64_t total_blocks,
+                                 ModP mp, DigitScheme ds, int arena_kind, cudaStream_t st);
+// blocks one job needs in launch_digitize_flat
+int64_t digitize_flat_blocks(int64_t rows, int64_t kpad);
 cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP mp,
                         cudaStream_t st);
 cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st);
@@ -149,6 +176,7 @@ cudaError_t launch_leaf_i64_arrays(const LeafProd *prods_dev, const LeafTile *ti
 struct TcLaunch {
     const LeafProd *prods;
     const LeafTile *tiles;
+    const LeafSeg *segs;
     int ntiles;
     const void *tmaps;        // device array of CUtensorMap, 64-B aligned
     ModP mp;

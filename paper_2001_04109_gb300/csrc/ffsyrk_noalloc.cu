@@ -57,7 +57,9 @@ constexpr size_t kErrOff = 0;      // device-side error word of the leaf kernel
 constexpr size_t kTmapOff = 256;   // one CUtensorMap (128 B, 64-B aligned)
 constexpr size_t kJobOff = 512;    // one DigitizeJob
 constexpr size_t kProdOff = 1024;  // one LeafProd
-constexpr size_t kTileOff = 2048;  // the tile list
+constexpr size_t kSegOff = 2048;   // the K schedule (LeafSeg table)
+constexpr size_t kMaxSegs = 8192;
+constexpr size_t kTileOff = kSegOff + kMaxSegs * sizeof(LeafSeg);  // the tile list
 constexpr size_t kMaxTiles = (kHeaderBytes - kTileOff) / sizeof(LeafTile);
 
 // First call on a device (with that device current): resolve the array's
@@ -134,7 +136,8 @@ extern "C" ffsyrk_status_t ffsyrk_noalloc(ffsyrk_uplo_t uplo, int64_t n, int64_t
     a.kpad = kpad;
     a.rows = ds.D * rpad;
 
-    // build the header on the host: error word zero, tensor map, job, product, tiles
+    // build the header on the host: error word zero, tensor map, job, product,
+    // K schedule, tiles
     memset(g_stage, 0, kTileOff);
     if (!encode_arena_tmap(a, g_stage + kTmapOff)) return FFSYRK_ERR_CUDA;
     DigitizeJob job{};
@@ -151,6 +154,11 @@ extern "C" ffsyrk_status_t ffsyrk_noalloc(ffsyrk_uplo_t uplo, int64_t n, int64_t
     pr.plane_rows = rpad;
     pr.out = C;
     pr.ldo = ldc;
+    const int nseg = build_segments_into(ds, pr.kblocks,
+                                         reinterpret_cast<LeafSeg *>(g_stage + kSegOff), (int)kMaxSegs);
+    if (nseg < 0) return FFSYRK_ERR_TOO_LARGE;
+    pr.seg0 = 0;
+    pr.nseg = nseg;
     memcpy(g_stage + kProdOff, &pr, sizeof pr);
     int64_t nt = 0;
     LeafTile *tiles = reinterpret_cast<LeafTile *>(g_stage + kTileOff);
@@ -172,6 +180,7 @@ extern "C" ffsyrk_status_t ffsyrk_noalloc(ffsyrk_uplo_t uplo, int64_t n, int64_t
     TcLaunch tl{};
     tl.prods = reinterpret_cast<const LeafProd *>(hdr + kProdOff);
     tl.tiles = reinterpret_cast<const LeafTile *>(hdr + kTileOff);
+    tl.segs = reinterpret_cast<const LeafSeg *>(hdr + kSegOff);
     tl.ntiles = (int)nt;
     tl.tmaps = hdr + kTmapOff;
     tl.mp = mp;

@@ -196,6 +196,40 @@ __global__ void __launch_bounds__(PREP_THREADS) k_digitize(const DigitizeJob *__
     }
 }
 
+// The same digit split over a flattened block list: block b belongs to the
+// job t with block0[t] ≤ b < block0[t+1] (binary search), then to one row
+// block and one column block of that job.
+template <int D, bool U32>
+__global__ void __launch_bounds__(PREP_THREADS) k_digitize_flat(const DigitizeJob *__restrict__ jobs,
+                                                                int njobs, ModP m) {
+    const int64_t b = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].block0 <= b) lo = mid; else hi = mid - 1;
+    }
+    const DigitizeJob &jb = jobs[lo];
+    const int64_t gx = (jb.dst.kpad / 2 + PREP_THREADS - 1) / PREP_THREADS;
+    const int64_t local = b - jb.block0;
+    const int64_t rb = local / gx, cb = local - rb * gx;
+    if (rb * DIG_ROWS >= jb.rows) return;
+    const int64_t c = 2 * (cb * PREP_THREADS + threadIdx.x);
+    if (c >= jb.dst.kpad) return;
+    uint32_t v[DIG_ROWS][2];
+#pragma unroll
+    for (int i = 0; i < DIG_ROWS; ++i) {
+        const int64_t r = rb * DIG_ROWS + i;
+        v[i][0] = r < jb.rows ? ld_view(jb.X, r, c) : 0u;
+        v[i][1] = r < jb.rows ? ld_view(jb.X, r, c + 1) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < DIG_ROWS; ++i) {
+        const int64_t r = rb * DIG_ROWS + i;
+        if (r >= jb.rows) break;
+        put_pair<D, U32>(jb.dst, r, c, red(v[i][0], m), red(v[i][1], m), m.half, m.p);
+    }
+}
+
 constexpr int PT = 32;  // post-addition tile: 32×32, 256 threads, 4 rows each
 
 // Grid: x = tile column J, y = tile row I, z = 3·node + quadrant, where the
@@ -366,6 +400,31 @@ cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_
             case 1: k_digitize<1, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, mp); break;
             case 2: k_digitize<2, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, mp); break;
             case 3: k_digitize<3, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, mp); break;
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaGetLastError();
+}
+
+int64_t digitize_flat_blocks(int64_t rows, int64_t kpad) {
+    return ((rows + DIG_ROWS - 1) / DIG_ROWS) * ((kpad / 2 + PREP_THREADS - 1) / PREP_THREADS);
+}
+
+cudaError_t launch_digitize_flat(const DigitizeJob *jobs_dev, int njobs, int64_t total_blocks,
+                                 ModP mp, DigitScheme ds, int arena_kind, cudaStream_t st) {
+    if (njobs == 0 || total_blocks == 0) return cudaSuccess;
+    const int64_t gx = std::min<int64_t>(total_blocks, 65535);
+    const int64_t gy = (total_blocks + gx - 1) / gx;
+    if (gy > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)gx, (unsigned)gy);
+    // blocks past the last job's range find its job and return on the row check
+    if (arena_kind == ARENA_U32) {
+        k_digitize_flat<1, true><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, njobs, mp);
+    } else {
+        switch (ds.D) {
+            case 1: k_digitize_flat<1, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
+            case 2: k_digitize_flat<2, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
+            case 3: k_digitize_flat<3, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
             default: return cudaErrorInvalidValue;
         }
     }

@@ -14,7 +14,10 @@
 // residue held in registers (delayed modular reduction: one reduction per
 // chunk instead of per product).
 //
-// Pipeline (one CTA per SM, persistent over a longest-first tile list):
+// Pipeline (one CTA per SM, persistent: tiles are taken from a device work
+// queue -- an atomic counter over a longest-first tile list -- by the
+// producer warp and handed to the MMA and epilogue warps through a small
+// shared-memory ring):
 //   warp 8  : TMA producer, 4 stages of a 128×64 X-tile and a 256×64 Z-tile,
 //             128-byte swizzle;
 //   warp 9  : MMA issuer (one thread), 128×256×16 MMAs into one of two TMEM
@@ -45,6 +48,7 @@ constexpr int PRODUCER_WARP = 8, MMA_WARP = 9;
 constexpr int NUM_THREADS = 32 * (EPI_WARPS + 2);  // no other warps: every warp has exactly one role
 constexpr int EPI_COLS = BN / (EPI_WARPS / 4);  // columns per epilogue thread (128)
 constexpr int LD_COLS = 16;  // TMEM columns per tcgen05.ld (128 residues + 16 loads fit 168 regs)
+constexpr int RING = 4;      // tiles handed from the producer to the MMA and epilogue warps
 constexpr int TMEM_COLS = 512;
 
 constexpr uint32_t IDESC = tc::idesc_bf16(BM, BN);
@@ -52,14 +56,18 @@ using namespace tc;
 
 __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__restrict__ prods,
                                                              const LeafTile *__restrict__ tiles,
+                                                             const LeafSeg *__restrict__ segs,
                                                              int ntiles,
                                                              const CUtensorMap *__restrict__ tmaps,
                                                              ModP m,
                                                              const __grid_constant__ DigitScheme ds,
-                                                             unsigned int *err) {
+                                                             unsigned int *err,
+                                                             unsigned int *tile_ctr) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
     __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], drain_bar;
+    __shared__ __align__(8) uint64_t ring_full[RING], ring_empty[RING];
+    __shared__ int tile_ring[RING];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
 
@@ -77,6 +85,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
             mbar_init(&acce_bar[b], EPI_WARPS);
         }
         mbar_init(&drain_bar, 1);
+        for (int q = 0; q < RING; ++q) {
+            mbar_init(&ring_full[q], 1);
+            mbar_init(&ring_empty[q], 1 + EPI_WARPS);
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -97,19 +109,30 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (uint32_t seq = 0; ok; ++seq) {
+                // next tile from the device work queue (or round-robin), handed
+                // to the MMA and epilogue warps through the shared ring
+                const int slot = seq % RING;
+                if (!mbar_wait(&ring_empty[slot], ((seq / RING) & 1u) ^ 1u, &abort_flag, err)) {
+                    ok = false;
+                    break;
+                }
+                const int t = tile_ctr ? (int)atomicAdd(tile_ctr, 1u)
+                                       : (int)(blockIdx.x + seq * gridDim.x);
+                tile_ring[slot] = t < ntiles ? t : -1;
+                mbar_arrive(&ring_full[slot]);
+                if (t >= ntiles) break;
                 const LeafTile tl = tiles[t];
                 const LeafProd pr = prods[tl.prod];
                 const CUtensorMap *tm = tmaps + pr.arena;
                 // the descriptor was written by a host copy before this launch
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tm)
                              : "memory");
-                UnitIter u;
-                u.start(ds, pr.kblocks);
-                do {
-                    const int ya = (int)(pr.a_row0 + (int64_t)u.i * pr.plane_rows + (int64_t)tl.tm * BM);
-                    const int yb = (int)(pr.b_row0 + (int64_t)u.j * pr.plane_rows + (int64_t)tl.tn * BN);
-                    for (int kb = u.kb0; kb < u.kb0 + u.nkb; ++kb, ++it) {
+                for (int sx = 0; sx < pr.nseg && ok; ++sx) {
+                    const LeafSeg sg = segs[pr.seg0 + sx];
+                    const int ya = (int)(pr.a_row0 + (int64_t)(sg.ij >> 4) * pr.plane_rows + (int64_t)tl.tm * BM);
+                    const int yb = (int)(pr.b_row0 + (int64_t)(sg.ij & 15) * pr.plane_rows + (int64_t)tl.tn * BN);
+                    for (int kb = sg.kb0; kb < sg.kb0 + sg.nkb; ++kb, ++it) {
                         const int s = it % STAGES;
                         const uint32_t ph = (it / STAGES) & 1u;
                         if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag, err)) {
@@ -123,7 +146,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
                         tma_load(sb, tm, &full_bar[s], kb * BK, yb);
                         tma_load(sb + B_BYTES / 2, tm, &full_bar[s], kb * BK, yb + BM);
                     }
-                } while (ok && u.next());
+                }
             }
             if (!ok) {
                 // let the copies already issued land before the CTA exits
@@ -136,19 +159,35 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
         if (lane == 0) {
             uint32_t it = 0, unit = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (uint32_t seq = 0; ok; ++seq) {
+                const int slot = seq % RING;
+                if (!mbar_wait(&ring_full[slot], (seq / RING) & 1u, &abort_flag, err)) {
+                    ok = false;
+                    break;
+                }
+                const int t = tile_ring[slot];
+                mbar_arrive(&ring_empty[slot]);
+                if (t < 0) break;
                 const LeafProd pr = prods[tiles[t].prod];
-                UnitIter u;
-                u.start(ds, pr.kblocks);
-                do {
-                    const uint32_t b = unit & 1u;
-                    if (!mbar_wait(&acce_bar[b], ((unit >> 1) & 1u) ^ 1u, &abort_flag, err)) {
-                        ok = false;
-                        break;
+                bool open = false;  // a unit's accumulator is being filled
+                uint32_t b = 0, tmem_d = 0;
+                for (int sx = 0; sx < pr.nseg; ++sx) {
+                    const LeafSeg sg = segs[pr.seg0 + sx];
+                    if (sg.first) {
+                        if (open) {
+                            mma_commit(&accf_bar[b]);
+                            ++unit;
+                        }
+                        b = unit & 1u;
+                        if (!mbar_wait(&acce_bar[b], ((unit >> 1) & 1u) ^ 1u, &abort_flag, err)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        tmem_d = tmem_base + b * BN;
+                        open = true;
                     }
-                    fence_after();
-                    const uint32_t tmem_d = tmem_base + b * BN;
-                    for (int kb = 0; kb < u.nkb; ++kb, ++it) {
+                    for (int kb = 0; kb < sg.nkb; ++kb, ++it) {
                         const int s = it % STAGES;
                         if (!mbar_wait(&full_bar[s], (it / STAGES) & 1u, &abort_flag, err)) {
                             ok = false;
@@ -160,13 +199,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk)
                             mma_bf16(tmem_d, sdesc(sa + kk * 32), sdesc(sb + kk * 32), IDESC,
-                                     (kb > 0 || kk > 0) ? 1u : 0u);
+                                     (sg.first && kb == 0 && kk == 0) ? 0u : 1u);
                         mma_commit(&empty_bar[s]);
                     }
                     if (!ok) break;
+                }
+                if (!ok) break;
+                if (open) {
                     mma_commit(&accf_bar[b]);
                     ++unit;
-                } while (u.next());
+                }
             }
             // every MMA issued so far has completed once this barrier fires
             mma_commit(&drain_bar);
@@ -178,15 +220,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
         const int quad = warp & 3, colq = warp >> 2;
         uint32_t unit = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (uint32_t seq = 0; ok; ++seq) {
+            const int slot = seq % RING;
+            const bool gotr = mbar_wait(&ring_full[slot], (seq / RING) & 1u, &abort_flag, err);
+            if (!__all_sync(0xffffffffu, gotr)) break;
+            const int t = tile_ring[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ring_empty[slot]);
+            if (t < 0) break;
             const LeafTile tl = tiles[t];
             const LeafProd pr = prods[tl.prod];
             uint32_t acc[EPI_COLS];
 #pragma unroll
             for (int e = 0; e < EPI_COLS; ++e) acc[e] = 0;
-            UnitIter u;
-            u.start(ds, pr.kblocks);
-            do {
+            int lo = 0, hi = 0;  // 16-column chunks of this warp that hold stored entries
+            live_chunks(pr, (int64_t)tl.tm * BM + quad * 32, (int64_t)tl.tn * BN + colq * EPI_COLS,
+                        EPI_COLS / LD_COLS, lo, hi);
+            for (int sx = 0; sx < pr.nseg; ++sx) {
+                const LeafSeg sg = segs[pr.seg0 + sx];
+                if (!sg.first) continue;  // one drain per unit
                 const uint32_t b = unit & 1u;
                 // warp-uniform outcome: tcgen05.ld below is .sync.aligned
                 const bool got = mbar_wait(&accf_bar[b], (unit >> 1) & 1u, &abort_flag, err);
@@ -195,11 +247,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
                     break;
                 }
                 fence_after();
-                const uint32_t w = ds.weight[u.i][u.j].w, wsh = ds.weight[u.i][u.j].w_sh;
+                const MulConst wt = ds.weight[sg.ij >> 4][sg.ij & 15];
+                const uint32_t w = wt.w, wsh = wt.w_sh;
                 const uint32_t taddr =
                     tmem_base + b * BN + ((uint32_t)(quad * 32) << 16) + colq * EPI_COLS;
 #pragma unroll
                 for (int cc = 0; cc < EPI_COLS / LD_COLS; ++cc) {
+                    if (cc < lo || cc >= hi) continue;
                     uint32_t v[LD_COLS];
                     tmem_ld16(taddr + cc * LD_COLS, v);
                     tmem_wait_ld();
@@ -218,7 +272,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acce_bar[b]);
                 ++unit;
-            } while (u.next());
+            }
             if (!ok) break;
             // store the tile's residues
             const int64_t r = (int64_t)tl.tm * BM + quad * 32 + lane;
@@ -275,9 +329,9 @@ cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st) {
         attr_done = true;
     }
     const int grid = L.ntiles < num_sms ? L.ntiles : num_sms;
-    k_leaf_tc<<<grid, NUM_THREADS, smem, st>>>(L.prods, L.tiles, L.ntiles,
+    k_leaf_tc<<<grid, NUM_THREADS, smem, st>>>(L.prods, L.tiles, L.segs, L.ntiles,
                                                reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp,
-                                               L.ds, L.err);
+                                               L.ds, L.err, L.tile_ctr);
     return cudaGetLastError();
 }
 

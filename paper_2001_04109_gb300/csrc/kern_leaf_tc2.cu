@@ -89,8 +89,9 @@ __device__ __forceinline__ void commit_pair(uint64_t *bar, uint16_t mask) {
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
-    k_leaf_tc2(const LeafProd *__restrict__ prods, const LeafTile *__restrict__ tiles, int ntiles,
-               const CUtensorMap *__restrict__ tmaps, ModP m,
+    k_leaf_tc2(const LeafProd *__restrict__ prods, const LeafTile *__restrict__ tiles,
+               const LeafSeg *__restrict__ segs, int ntiles, const CUtensorMap *__restrict__ tmaps,
+               ModP m,
                const __grid_constant__ DigitScheme ds, unsigned int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
@@ -142,14 +143,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
                 const CUtensorMap *tm = tmaps + pr.arena;
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tm)
                              : "memory");
-                UnitIter u;
-                u.start(ds, pr.kblocks);
-                do {
-                    const int ya = (int)(pr.a_row0 + (int64_t)u.i * pr.plane_rows +
+                for (int sx = 0; sx < pr.nseg && ok; ++sx) {
+                    const LeafSeg sg = segs[pr.seg0 + sx];
+                    const int ya = (int)(pr.a_row0 + (int64_t)(sg.ij >> 4) * pr.plane_rows +
                                          (int64_t)tl.tm * BM + rank * ROWS);
-                    const int yb = (int)(pr.b_row0 + (int64_t)u.j * pr.plane_rows +
+                    const int yb = (int)(pr.b_row0 + (int64_t)(sg.ij & 15) * pr.plane_rows +
                                          (int64_t)tl.tn * BN + rank * ROWS);
-                    for (int kb = u.kb0; kb < u.kb0 + u.nkb; ++kb, ++it) {
+                    for (int kb = sg.kb0; kb < sg.kb0 + sg.nkb; ++kb, ++it) {
                         const int s = it % STAGES;
                         const uint32_t ph = (it / STAGES) & 1u;
                         if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag, err)) {
@@ -163,7 +163,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
                         tma_load_pair(sa, tm, fb, kb * BK, ya);
                         tma_load_pair(sb, tm, fb, kb * BK, yb);
                     }
-                } while (ok && u.next());
+                }
             }
             if (!ok && rank == 0) {
                 const uint32_t first = it > STAGES ? it - STAGES : 0;
@@ -177,17 +177,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
             bool ok = true;
             for (int t = pair; t < ntiles && ok; t += npairs) {
                 const LeafProd pr = prods[tiles[t].prod];
-                UnitIter u;
-                u.start(ds, pr.kblocks);
-                do {
-                    const uint32_t b = unit & 1u;
-                    if (!mbar_wait(&acce_bar[b], ((unit >> 1) & 1u) ^ 1u, &abort_flag, err)) {
-                        ok = false;
-                        break;
+                bool open = false;  // a unit's accumulator is being filled
+                uint32_t b = 0, tmem_d = 0;
+                for (int sx = 0; sx < pr.nseg; ++sx) {
+                    const LeafSeg sg = segs[pr.seg0 + sx];
+                    if (sg.first) {
+                        if (open) {
+                            commit_pair(&accf_bar[b], 0x3);
+                            ++unit;
+                        }
+                        b = unit & 1u;
+                        if (!mbar_wait(&acce_bar[b], ((unit >> 1) & 1u) ^ 1u, &abort_flag, err)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        tmem_d = tmem_base + b * BN;
+                        open = true;
                     }
-                    fence_after();
-                    const uint32_t tmem_d = tmem_base + b * BN;
-                    for (int kb = 0; kb < u.nkb; ++kb, ++it) {
+                    for (int kb = 0; kb < sg.nkb; ++kb, ++it) {
                         const int s = it % STAGES;
                         if (!mbar_wait(&full_bar[s], (it / STAGES) & 1u, &abort_flag, err)) {
                             ok = false;
@@ -199,13 +207,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk)
                             mma_pair(tmem_d, sdesc(sa + kk * 32), sdesc(sb + kk * 32),
-                                     (kb > 0 || kk > 0) ? 1u : 0u);
+                                     (sg.first && kb == 0 && kk == 0) ? 0u : 1u);
                         commit_pair(&empty_bar[s], 0x3);
                     }
                     if (!ok) break;
+                }
+                if (!ok) break;
+                if (open) {
                     commit_pair(&accf_bar[b], 0x3);
                     ++unit;
-                } while (u.next());
+                }
             }
             commit_pair(&drain_bar, 0x1);
             mbar_drain(&drain_bar, 0);
@@ -224,9 +235,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
             uint32_t acc[EPI_COLS];
 #pragma unroll
             for (int e = 0; e < EPI_COLS; ++e) acc[e] = 0;
-            UnitIter u;
-            u.start(ds, pr.kblocks);
-            do {
+            int lo = 0, hi = 0;  // 16-column chunks of this warp that hold stored entries
+            live_chunks(pr, (int64_t)tl.tm * BM + rank * ROWS + quad * 32, (int64_t)tl.tn * BN + colq * EPI_COLS,
+                        EPI_COLS / LD_COLS, lo, hi);
+            for (int sx = 0; sx < pr.nseg; ++sx) {
+                const LeafSeg sg = segs[pr.seg0 + sx];
+                if (!sg.first) continue;  // one drain per unit
                 const uint32_t b = unit & 1u;
                 const bool got = mbar_wait(&accf_bar[b], (unit >> 1) & 1u, &abort_flag, err);
                 if (!__all_sync(0xffffffffu, got)) {
@@ -234,11 +248,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
                     break;
                 }
                 fence_after();
-                const uint32_t w = ds.weight[u.i][u.j].w, wsh = ds.weight[u.i][u.j].w_sh;
+                const MulConst wt = ds.weight[sg.ij >> 4][sg.ij & 15];
+                const uint32_t w = wt.w, wsh = wt.w_sh;
                 const uint32_t taddr =
                     tmem_base + b * BN + ((uint32_t)(quad * 32) << 16) + colq * EPI_COLS;
 #pragma unroll
                 for (int cc = 0; cc < EPI_COLS / LD_COLS; ++cc) {
+                    if (cc < lo || cc >= hi) continue;
                     uint32_t v[LD_COLS];
                     tmem_ld16(taddr + cc * LD_COLS, v);
                     tmem_wait_ld();
@@ -256,7 +272,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
                 __syncwarp();
                 if (lane == 0) arrive_remote(acce_leader[b]);
                 ++unit;
-            } while (u.next());
+            }
             if (!ok) break;
             const int64_t r = (int64_t)tl.tm * BM + rank * ROWS + quad * 32 + lane;
             const int64_t c0 = (int64_t)tl.tn * BN + colq * EPI_COLS;
@@ -325,7 +341,7 @@ cudaError_t launch_leaf_tc2(const TcLaunch &L, int num_sms, cudaStream_t st) {
     }
     const int pairs = L.ntiles < max_pairs ? L.ntiles : max_pairs;
     k_leaf_tc2<<<2 * pairs, NUM_THREADS, smem, st>>>(
-        L.prods, L.tiles, L.ntiles, reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp, L.ds,
+        L.prods, L.tiles, L.segs, L.ntiles, reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp, L.ds,
         L.err);
     return cudaGetLastError();
 }

@@ -124,56 +124,24 @@ __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// The (tile, K-span, digit pair, K-chunk) sequence every role walks in the
-// same order.  K is cut into spans of SPAN_KB k-blocks; inside a span every
-// digit pair (i, j) runs over it in chunks of at most chunk_kb[i][j].  Taking
-// all pairs of one span before moving on reuses each operand's span D times
-// while it is still in L2.
-constexpr int SPAN_KB = 16;  // 1024 k-elements
-struct UnitIter {
-    int D;
-    int i, j;          // digit pair
-    int kb0, nkb;      // k-block range of this unit
-    int span0, span1;  // current span [span0, span1)
-    int kblocks;
-    const DigitScheme *ds;
-    __device__ void start(const DigitScheme &s, int kbl) {
-        ds = &s;
-        D = s.D;
-        kblocks = kbl;
-        i = 0;
-        j = 0;
-        span0 = 0;
-        span1 = kbl < SPAN_KB ? kbl : SPAN_KB;
-        kb0 = 0;
-        set_len();
+// 16-column chunks [lo, hi) of an epilogue warp's 32 rows × (nch·16) columns
+// that hold stored entries: rows below `rows`, columns below `cols`, and for
+// a triangular product only chunks that reach the stored side of the
+// diagonal.  Warp-uniform; chunks outside are neither loaded nor reduced.
+__device__ __forceinline__ void live_chunks(const LeafProd &pr, int64_t rbase, int64_t cbase,
+                                            int nch, int &lo, int &hi) {
+    lo = 0;
+    hi = 0;
+    if (rbase >= pr.rows || cbase >= pr.cols) return;
+    int64_t cmax = pr.cols;                                       // exclusive
+    if (pr.tri == 1 && rbase + 32 < cmax) cmax = rbase + 32;      // c ≤ r
+    int64_t h = (cmax - cbase + 15) / 16;
+    hi = (int)(h < 0 ? 0 : (h > nch ? nch : h));
+    if (pr.tri == 2 && rbase > cbase) {                           // c ≥ r
+        int64_t l = (rbase - cbase) / 16;
+        lo = (int)(l > nch ? nch : l);
     }
-    __device__ void set_len() {
-        const int c = ds->chunk_kb[i][j];
-        nkb = span1 - kb0 < c ? span1 - kb0 : c;
-    }
-    // advance; false when the tile is done
-    __device__ bool next() {
-        kb0 += nkb;
-        if (kb0 < span1) {
-            set_len();
-            return true;
-        }
-        if (++j == D) {
-            j = 0;
-            if (++i == D) {
-                i = 0;
-                span0 = span1;
-                if (span0 >= kblocks) return false;
-                span1 = kblocks - span0 < SPAN_KB ? kblocks : span0 + SPAN_KB;
-            }
-        }
-        kb0 = span0;
-        set_len();
-        return true;
-    }
-};
-
+}
 
 // Instruction descriptor of tcgen05.mma kind::f16: D = f32, A = B = bf16,
 // both K-major, shape M×N.

@@ -30,7 +30,7 @@ _LEAVES = {None: LEAF_AUTO, "auto": LEAF_AUTO, "tc": LEAF_TC_BF16, "bf16": LEAF_
 EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan",
            "ffsyrk", "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
            "ffsyrk_plan_set_timing", "ffsyrk_plan_get_timing", "ffsyrk_status_string",
-           "ffsyrk_version", "ffsyrk_noalloc"]
+           "ffsyrk_version", "ffsyrk_noalloc", "ffsyrk_leaf_schedule", "ffsyrk_digit_bounds"]
 
 
 class FfsyrkError(RuntimeError):
@@ -41,7 +41,8 @@ class FfsyrkError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int32), ("levels", ctypes.c_int32),
-                ("tile_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("tile_ctas", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -49,7 +50,8 @@ class PlanInfo(ctypes.Structure):
                 ("y_b", ctypes.c_uint32), ("y_cost", ctypes.c_int32), ("leaf", ctypes.c_int32),
                 ("levels", ctypes.c_int32), ("digits", ctypes.c_int32),
                 ("chunk_k", ctypes.c_int32 * 9), ("workspace_bytes", ctypes.c_int64),
-                ("tile_ctas", ctypes.c_int32)]
+                ("tile_ctas", ctypes.c_int32), ("autotuned", ctypes.c_int32),
+                ("tuned_ms", ctypes.c_float)]
 
 
 class Timing(ctypes.Structure):
@@ -90,6 +92,10 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_status_string.argtypes = [i32]
             L.ffsyrk_status_string.restype = ctypes.c_char_p
             L.ffsyrk_version.restype = i32
+            L.ffsyrk_leaf_schedule.argtypes = [u32, i32, P(i32), i32]
+            L.ffsyrk_leaf_schedule.restype = i32
+            L.ffsyrk_digit_bounds.argtypes = [u32, P(i32)]
+            L.ffsyrk_digit_bounds.restype = i32
             for name in ["ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan", "ffsyrk",
                          "ffsyrk_noalloc",
                          "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
@@ -128,22 +134,24 @@ def _mat_args(X: torch.Tensor, name: str):
     return X.data_ptr(), ld
 
 
-def make_options(leaf=None, levels=None, tile_ctas=None) -> Options:
+def make_options(leaf=None, levels=None, tile_ctas=None, autotune=False) -> Options:
     o = Options()
     lib().ffsyrk_options_default(ctypes.byref(o))
     o.leaf = _LEAVES[leaf] if not isinstance(leaf, int) else leaf
     o.levels = LEVELS_AUTO if levels is None else int(levels)
     o.tile_ctas = 0 if tile_ctas is None else int(tile_ctas)
+    o.autotune = 1 if autotune else 0
     return o
 
 
 class Plan:
     """An ffsyrk plan: p, Y, digits, depth and workspace for n ≤ max_n, k ≤ max_k."""
 
-    def __init__(self, p: int, max_n: int, max_k: int, leaf=None, levels=None, tile_ctas=None):
+    def __init__(self, p: int, max_n: int, max_k: int, leaf=None, levels=None, tile_ctas=None,
+                 autotune=False):
         self.p = int(p)
         self._h = ctypes.c_void_p()
-        o = make_options(leaf, levels, tile_ctas)
+        o = make_options(leaf, levels, tile_ctas, autotune)
         _check(lib().ffsyrk_plan(ctypes.byref(self._h), self.p, int(max_n), int(max_k),
                                  ctypes.byref(o)), "ffsyrk_plan")
 
@@ -153,7 +161,7 @@ class Plan:
         return {"p": i.p, "y_form": i.y_form, "y_a": i.y_a, "y_b": i.y_b, "y_cost": i.y_cost,
                 "leaf": i.leaf, "levels": i.levels, "digits": i.digits,
                 "chunk_k": list(i.chunk_k), "workspace_bytes": i.workspace_bytes,
-                "tile_ctas": i.tile_ctas}
+                "tile_ctas": i.tile_ctas, "autotuned": i.autotuned, "tuned_ms": i.tuned_ms}
 
     def __call__(self, A: torch.Tensor, C: torch.Tensor | None = None, uplo: str = "lower",
                  stream=None) -> torch.Tensor:
@@ -187,6 +195,26 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def leaf_schedule(p: int, kblocks: int) -> list[tuple[int, int, int, int, bool]]:
+    """The leaf's K schedule for p: (i, j, first k-block, k-blocks, opens a unit)."""
+    n = lib().ffsyrk_leaf_schedule(int(p), int(kblocks), None, 0)
+    if n < 0:
+        raise ValueError("bad p or kblocks")
+    buf = (ctypes.c_int32 * (5 * max(n, 1)))()
+    lib().ffsyrk_leaf_schedule(int(p), int(kblocks), buf, n)
+    return [(buf[5 * q], buf[5 * q + 1], buf[5 * q + 2], buf[5 * q + 3], bool(buf[5 * q + 4]))
+            for q in range(n)]
+
+
+def digit_bounds(p: int) -> list[int]:
+    """Bounds on |digit t| of the signed base-256 split of residues mod p."""
+    out = (ctypes.c_int32 * 3)()
+    D = lib().ffsyrk_digit_bounds(int(p), out)
+    if D < 0:
+        raise ValueError("bad p")
+    return [out[t] for t in range(D)]
 
 
 def syrk(A: torch.Tensor, p: int, uplo: str = "lower", C: torch.Tensor | None = None,

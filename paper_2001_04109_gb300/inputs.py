@@ -45,7 +45,7 @@ def splitmix64(z: torch.Tensor) -> torch.Tensor:
 
 def splitmix64_int(x: int) -> int:
     """Scalar SplitMix64 on Python integers (for seeds and counters)."""
-    z = (x + 0x9E3779B97F4A7C15) & _M64
+    z = (int(x) + 0x9E3779B97F4A7C15) & _M64
     z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
     z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
     return z ^ (z >> 31)

@@ -81,3 +81,16 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(ffsyrk, "_lib", None)
     with pytest.raises(FileNotFoundError):
         ffsyrk.lib()
+
+
+def test_autotune_option_validated(lib):
+    import ctypes
+    o = ffsyrk.Options()
+    lib.ffsyrk_options_default(ctypes.byref(o))
+    assert o.autotune == 0 and o.tile_ctas == 0
+    o.autotune = 2
+    h = ctypes.c_void_p()
+    assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
+    o.autotune = 0
+    o.tile_ctas = 3
+    assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG

@@ -1,0 +1,75 @@
+"""The tensor-core leaf's exact-accumulation schedule (CPU only, no GPU needed).
+
+These pin, independently of the kernels, the property that makes the bf16
+digit leaf exact: every FP32 accumulator (a "unit") sums at most 2^24 in
+magnitude, holds a single weight class 256^(i+j), and every (digit pair,
+k-block) is accumulated exactly once.  The digit bounds themselves are
+checked by brute force over all symmetric residues of small primes and at
+the extremes of the large ones.
+"""
+import pytest
+
+import __graft_entry__
+from paper_2001_04109_gb300 import ffsyrk
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+
+
+def balanced_digits(s, D):
+    out = []
+    for _ in range(D - 1):
+        lo = ((s + 128) % 256) - 128
+        out.append(lo)
+        s = (s - lo) // 256
+    out.append(s)
+    return out
+
+
+@pytest.mark.parametrize("p", [3, 251, 257, 65521, 131071, 131041, 8388593, 16777213])
+def test_digit_bounds_cover_every_residue(p):
+    bounds = ffsyrk.digit_bounds(p)
+    D = len(bounds)
+    h = (p - 1) // 2
+    samples = range(-h, h + 1) if p < 300000 else list(range(-h, -h + 70000)) + list(range(h - 70000, h + 1))
+    seen = [0] * D
+    for s in samples:
+        d = balanced_digits(s, D)
+        assert sum(dt * 256 ** t for t, dt in enumerate(d)) == s
+        for t in range(D):
+            assert abs(d[t]) <= bounds[t] <= 256
+            seen[t] = max(seen[t], abs(d[t]))
+    assert seen == bounds  # tight
+
+
+@pytest.mark.parametrize("p", [251, 65521, 131071, 8388593])
+@pytest.mark.parametrize("kblocks", [1, 3, 4, 5, 16, 17, 33, 64, 513])
+def test_schedule_units_exact_and_complete(p, kblocks):
+    bounds = ffsyrk.digit_bounds(p)
+    D = len(bounds)
+    segs = ffsyrk.leaf_schedule(p, kblocks)
+    assert segs and segs[0][4]
+    covered = {}
+    unit_sum, unit_class = 0, None
+    for i, j, kb0, nkb, first in segs:
+        assert nkb >= 1 and 0 <= kb0 and kb0 + nkb <= kblocks
+        if first:
+            unit_sum, unit_class = 0, i + j
+        assert i + j == unit_class                  # one weight per accumulator
+        unit_sum += 64 * nkb * bounds[i] * bounds[j]
+        assert unit_sum <= 1 << 24                  # every FP32 partial sum exact
+        for kb in range(kb0, kb0 + nkb):
+            covered[(i, j, kb)] = covered.get((i, j, kb), 0) + 1
+    assert set(covered) == {(i, j, kb) for i in range(D) for j in range(D) for kb in range(kblocks)}
+    assert all(c == 1 for c in covered.values())
+
+
+def test_same_weight_pairs_share_a_unit_for_short_k():
+    # p = 65521: pairs (0,1) and (1,0) both weigh 256; with 4 k-blocks they fit one unit
+    segs = ffsyrk.leaf_schedule(65521, 4)
+    units = sum(1 for s in segs if s[4])
+    assert units == 3
+    segs = ffsyrk.leaf_schedule(8388593, 4)
+    assert sum(1 for s in segs if s[4]) == 5   # one unit per weight class, D = 3
