@@ -206,6 +206,15 @@ typedef struct {
  * event.  FFSYRK_ERR_INVALID_ARG if timing is off or no call was made. */
 ffsyrk_status_t ffsyrk_plan_get_timing(ffsyrk_plan_t plan, ffsyrk_timing_t *timing);
 
+/* Failure-detection self-test (the paper has no counterpart): enqueue on
+ * `stream` a kernel whose bounded device-side wait runs out after limit_ns
+ * nanoseconds (≤ 10 s) on a barrier that nothing signals.  It records the
+ * timeout in the plan exactly as a stalled leaf kernel would, and returns
+ * normally: the next ffsyrk_sync_status() reports FFSYRK_ERR_TIMEOUT (and
+ * clears it) and the plan and context remain usable. */
+ffsyrk_status_t ffsyrk_plan_selftest_timeout(ffsyrk_plan_t plan, int64_t limit_ns,
+                                             ffsyrk_stream_t stream);
+
 /* Introspection of the tensor-core leaf's exact-accumulation schedule for p
  * and a leaf K of 64·kblocks (for tests and tools; needs no GPU).
  * Writes up to `cap` segments as 5 int32 each: digit i, digit j, first

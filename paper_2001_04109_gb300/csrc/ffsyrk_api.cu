@@ -94,9 +94,11 @@ Geometry make_geometry(int64_t n, int64_t k, int L) {
         g.np = n;
         g.kp = k;
     } else {
-        g.np = rup(std::max<int64_t>(n, 1), int64_t(1) << L);
-        // w_L even at every depth (the interleaved 2×2 Y pairs columns)
-        g.kp = rup(std::max<int64_t>(k, 1), int64_t(1) << (L + 1));
+        // every block height a multiple of 4 (16-byte rows in the product buffers)
+        g.np = rup(std::max<int64_t>(n, 1), int64_t(1) << (L + 2));
+        // every block width a multiple of 4: the interleaved 2×2 Y pairs
+        // columns, and the pre-addition kernel moves 4 columns at a time
+        g.kp = rup(std::max<int64_t>(k, 1), int64_t(1) << (L + 2));
     }
     for (int d = 0; d <= L; ++d) {
         g.h[d] = g.np >> d;
@@ -1101,6 +1103,18 @@ ffsyrk_status_t ffsyrk_plan_get_timing(ffsyrk_plan_t pl, ffsyrk_timing_t *t) {
     t->field_macs = pl->last_field_macs;
     t->tensor_macs = pl->last_tensor_macs;
     return FFSYRK_SUCCESS;
+}
+
+ffsyrk_status_t ffsyrk_plan_selftest_timeout(ffsyrk_plan_t pl, int64_t limit_ns,
+                                             ffsyrk_stream_t stream) {
+    if (!pl || limit_ns < 0 || limit_ns > 10000000000ll) return FFSYRK_ERR_INVALID_ARG;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != pl->device) return FFSYRK_ERR_INVALID_ARG;
+    return launch_wait_selftest(pl->err_dev, (unsigned long long)limit_ns,
+                                reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? FFSYRK_SUCCESS
+               : FFSYRK_ERR_CUDA;
 }
 
 int32_t ffsyrk_leaf_schedule(uint32_t p, int32_t kblocks, int32_t *out, int32_t cap) {

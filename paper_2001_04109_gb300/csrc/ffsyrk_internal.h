@@ -196,6 +196,9 @@ int leaf_i64_tile();
 // The signed base-256 digit scheme and chunk lengths the planner uses for p.
 DigitScheme digit_scheme_for(uint32_t p);
 
+// A kernel whose bounded wait runs out (after limit_ns) and records it in err.
+cudaError_t launch_wait_selftest(unsigned int *err, unsigned long long limit_ns, cudaStream_t st);
+
 // Build the TMA descriptor of a bf16 arena (box 64 × 128 rows, 128B swizzle).
 bool encode_arena_tmap(const Arena &a, void *tmap_out /* 128 B */);
 

@@ -58,37 +58,6 @@ __device__ __forceinline__ int sbyte(int s) {
     return d;
 }
 
-// Store the residue pair (v0, v1) at (row r, column c) of an operand.
-template <int D, bool U32>
-__device__ __forceinline__ void put_pair(const OperandDst &d, int64_t r, int64_t c, uint32_t v0,
-                                         uint32_t v1, uint32_t half, uint32_t p) {
-    if (d.arena == nullptr) return;
-    if (U32) {
-        *reinterpret_cast<uint2 *>(static_cast<uint32_t *>(d.arena) + (d.row0 + r) * d.kpad + c) =
-            make_uint2(v0, v1);
-        return;
-    }
-    int s0 = v0 > half ? (int)v0 - (int)p : (int)v0;  // symmetric residue
-    int s1 = v1 > half ? (int)v1 - (int)p : (int)v1;
-    uint32_t *base = static_cast<uint32_t *>(d.arena);  // bf16 pairs
-#pragma unroll
-    for (int t = 0; t < D; ++t) {
-        int d0, d1;
-        if (t == D - 1) {
-            d0 = s0;
-            d1 = s1;
-        } else {
-            d0 = sbyte(s0);
-            d1 = sbyte(s1);
-            s0 = (s0 - d0) >> 8;
-            s1 = (s1 - d1) >> 8;
-        }
-        const uint32_t packed =
-            __byte_perm(small_int_f32_bits(d0), small_int_f32_bits(d1), 0x7632);
-        base[((d.row0 + t * d.rpad + r) * d.kpad + c) >> 1] = packed;
-    }
-}
-
 template <int YF>
 __device__ __forceinline__ void ymul(const YConst &y, uint32_t t0, uint32_t t1, uint32_t &o0,
                                      uint32_t &o1, uint32_t p) {
@@ -102,68 +71,185 @@ __device__ __forceinline__ void ymul(const YConst &y, uint32_t t0, uint32_t t1, 
     }
 }
 
-constexpr int PREP_THREADS = 128;  // column pairs per block
+constexpr int PREP_THREADS = 128;  // threads per block, 4 columns each
 constexpr int PREP_ROWS = 4;       // rows per thread (independent loads in flight)
+
+// Four consecutive entries (row r, columns c..c+3) of a view, zero outside;
+// one 16-byte load when aligned and fully inside.
+__device__ __forceinline__ void ld_view4(const MatView &v, bool vec_ok, int64_t r, int64_t c,
+                                         uint32_t (&x)[4]) {
+    if (r < v.vr && c + 4 <= v.vc && vec_ok) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(v.ptr + r * v.ld + c));
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[e] = ld_view(v, r, c + e);
+    }
+}
+
+// Store four residues at (row r, columns c..c+3): one 8-byte store per digit
+// plane (bf16) or one 16-byte store (uint32).
+template <int D, bool U32>
+__device__ __forceinline__ void put4(const OperandDst &d, int64_t r, int64_t c, const uint32_t (&v)[4],
+                                     uint32_t half, uint32_t p) {
+    if (d.arena == nullptr) return;
+    if constexpr (U32) {
+        *reinterpret_cast<uint4 *>(static_cast<uint32_t *>(d.arena) + (d.row0 + r) * d.kpad + c) =
+            make_uint4(v[0], v[1], v[2], v[3]);
+    } else {
+        int sv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sv[e] = v[e] > half ? (int)v[e] - (int)p : (int)v[e];
+        uint32_t *base = static_cast<uint32_t *>(d.arena);
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+            uint32_t w[2];
+#pragma unroll
+            for (int e = 0; e < 4; e += 2) {
+                int d0, d1;
+                if (t == D - 1) {
+                    d0 = sv[e];
+                    d1 = sv[e + 1];
+                } else {
+                    d0 = sbyte(sv[e]);
+                    d1 = sbyte(sv[e + 1]);
+                    sv[e] = (sv[e] - d0) >> 8;
+                    sv[e + 1] = (sv[e + 1] - d1) >> 8;
+                }
+                w[e / 2] = __byte_perm(small_int_f32_bits(d0), small_int_f32_bits(d1), 0x7632);
+            }
+            *reinterpret_cast<uint2 *>(base + (((d.row0 + t * d.rpad + r) * d.kpad + c) >> 1)) =
+                make_uint2(w[0], w[1]);
+        }
+    }
+}
 
 // Columns [w, kpad) of every written operand are zero (K padding of the
 // leaf products); rows [h, rpad) are never read into a stored result.
-// Grid: x = column-pair blocks, y = row blocks (strided), z = node.
-// RED: reduce the loaded values mod p (only the caller's A can hold values ≥ p).
+// Grid: x = 4-column blocks, y = row blocks (strided), z = node.
+// RED: reduce the loaded values mod p (views of the caller's A can hold values ≥ p).
 template <int D, bool U32, int YF, bool RED>
 __global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restrict__ nodes,
                                                        int64_t h, int64_t w, int64_t kpad, ModP m,
                                                        YConst y) {
-    const int64_t c = 2 * ((int64_t)blockIdx.x * PREP_THREADS + threadIdx.x);
+    const int64_t c = 4 * ((int64_t)blockIdx.x * PREP_THREADS + threadIdx.x);
     if (c >= kpad) return;
     const PrepNode &nd = nodes[blockIdx.z];
     const uint32_t p = m.p, half = m.half;
     const bool inside = c < w;
+    // quadrant column offsets 0 and w keep 16-byte alignment when w % 4 == 0
+    const bool vec_ok = ((reinterpret_cast<uintptr_t>(nd.X.ptr) & 15u) == 0) &&
+                        ((nd.X.ld & 3) == 0) && ((w & 3) == 0);
     const int64_t nrb = (h + PREP_ROWS - 1) / PREP_ROWS;
     for (int64_t rb = blockIdx.y; rb < nrb; rb += gridDim.y) {
-        uint32_t a[PREP_ROWS][4][2];  // quadrant 0..3 = A11, A12, A21, A22
+        uint32_t a[PREP_ROWS][4][4];  // [row][quadrant A11, A12, A21, A22][column]
 #pragma unroll
         for (int i = 0; i < PREP_ROWS; ++i) {
             const int64_t r = rb * PREP_ROWS + i;
             const bool ok = inside && r < h;
+            if (ok) {
+                ld_view4(nd.X, vec_ok, r, c, a[i][0]);
+                ld_view4(nd.X, vec_ok, r, w + c, a[i][1]);
+                ld_view4(nd.X, vec_ok, h + r, c, a[i][2]);
+                ld_view4(nd.X, vec_ok, h + r, w + c, a[i][3]);
+            } else {
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                a[i][0][e] = ok ? ld_view(nd.X, r, c + e) : 0u;
-                a[i][1][e] = ok ? ld_view(nd.X, r, w + c + e) : 0u;
-                a[i][2][e] = ok ? ld_view(nd.X, h + r, c + e) : 0u;
-                a[i][3][e] = ok ? ld_view(nd.X, h + r, w + c + e) : 0u;
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) a[i][q][e] = 0u;
             }
         }
 #pragma unroll
         for (int i = 0; i < PREP_ROWS; ++i) {
             const int64_t r = rb * PREP_ROWS + i;
             if (r >= h) break;
-            uint32_t x11[2], x12[2], x21[2], x22[2];
+            uint32_t x11[4], x12[4], x21[4], x22[4], s1[4], s2[4], s3[4], s4[4], u[4];
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
+            for (int e = 0; e < 4; ++e) {
                 x11[e] = RED ? red(a[i][0][e], m) : a[i][0][e];
                 x12[e] = RED ? red(a[i][1][e], m) : a[i][1][e];
                 x21[e] = RED ? red(a[i][2][e], m) : a[i][2][e];
                 x22[e] = RED ? red(a[i][3][e], m) : a[i][3][e];
             }
-            uint32_t t0 = subm(x21[0], x11[0], p), t1 = subm(x21[1], x11[1], p);
-            uint32_t s1[2], s2[2], s3[2], s4[2], u[2];
-            ymul<YF>(y, t0, t1, s1[0], s1[1], p);       // S1 = (A21 − A11)·Y
-            ymul<YF>(y, x21[0], x21[1], u[0], u[1], p);
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                s2[e] = subm(x22[e], u[e], p);          // S2 = A22 − A21·Y
-                s3[e] = subm(s1[e], x22[e], p);         // S3 = S1 − A22
-                s4[e] = addm(s3[e], x12[e], p);         // S4 = S3 + A12
+            for (int e = 0; e < 4; e += 2) {
+                ymul<YF>(y, subm(x21[e], x11[e], p), subm(x21[e + 1], x11[e + 1], p), s1[e],
+                         s1[e + 1], p);                         // S1 = (A21 − A11)·Y
+                ymul<YF>(y, x21[e], x21[e + 1], u[e], u[e + 1], p);
             }
-            put_pair<D, U32>(nd.gemm[0], r, c, x22[0], x22[1], half, p);
-            put_pair<D, U32>(nd.gemm[1], r, c, s4[0], s4[1], half, p);
-            put_pair<D, U32>(nd.gemm[2], r, c, s1[0], s1[1], half, p);
-            put_pair<D, U32>(nd.gemm[3], r, c, s2[0], s2[1], half, p);
-            put_pair<D, U32>(nd.leaf[0], r, c, x11[0], x11[1], half, p);
-            put_pair<D, U32>(nd.leaf[1], r, c, x12[0], x12[1], half, p);
-            put_pair<D, U32>(nd.leaf[2], r, c, s3[0], s3[1], half, p);
-            if (nd.s3 != nullptr && inside)
-                *reinterpret_cast<uint2 *>(nd.s3 + r * nd.s3_ld + c) = make_uint2(s3[0], s3[1]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                s2[e] = subm(x22[e], u[e], p);                  // S2 = A22 − A21·Y
+                s3[e] = subm(s1[e], x22[e], p);                 // S3 = S1 − A22
+                s4[e] = addm(s3[e], x12[e], p);                 // S4 = S3 + A12
+            }
+            put4<D, U32>(nd.gemm[0], r, c, x22, half, p);
+            put4<D, U32>(nd.gemm[1], r, c, s4, half, p);
+            put4<D, U32>(nd.gemm[2], r, c, s1, half, p);
+            put4<D, U32>(nd.gemm[3], r, c, s2, half, p);
+            put4<D, U32>(nd.leaf[0], r, c, x11, half, p);
+            put4<D, U32>(nd.leaf[1], r, c, x12, half, p);
+            put4<D, U32>(nd.leaf[2], r, c, s3, half, p);
+            if (nd.s3 != nullptr && inside) {
+                uint32_t *dst = nd.s3 + r * nd.s3_ld + c;
+                if (((reinterpret_cast<uintptr_t>(dst)) & 15u) == 0)
+                    *reinterpret_cast<uint4 *>(dst) = make_uint4(s3[0], s3[1], s3[2], s3[3]);
+                else
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) dst[e] = s3[e];
+            }
+        }
+    }
+}
+
+// Eight consecutive entries (row r, columns c..c+7) of a view, zero outside;
+// one 16-byte load pair when the view is 16-byte aligned and fully inside.
+__device__ __forceinline__ void ld_view8(const MatView &v, bool vec_ok, int64_t r, int64_t c,
+                                         uint32_t (&x)[8]) {
+    if (r < v.vr && c + 8 <= v.vc && vec_ok) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(v.ptr + r * v.ld + c);
+        const uint4 a = __ldg(q), b = __ldg(q + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = ld_view(v, r, c + e);
+    }
+}
+
+// Store eight residues at (row r, columns c..c+7) of an operand: one
+// 16-byte store per digit plane (bf16) or two (uint32).
+template <int D, bool U32>
+__device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, const uint32_t (&v)[8],
+                                     uint32_t half, uint32_t p) {
+    if constexpr (U32) {
+        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(d.arena) + (d.row0 + r) * d.kpad + c);
+        dst[0] = make_uint4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_uint4(v[4], v[5], v[6], v[7]);
+    } else {
+        int sv[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sv[e] = v[e] > half ? (int)v[e] - (int)p : (int)v[e];
+        uint32_t *base = static_cast<uint32_t *>(d.arena);
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                int d0, d1;
+                if (t == D - 1) {
+                    d0 = sv[e];
+                    d1 = sv[e + 1];
+                } else {
+                    d0 = sbyte(sv[e]);
+                    d1 = sbyte(sv[e + 1]);
+                    sv[e] = (sv[e] - d0) >> 8;
+                    sv[e + 1] = (sv[e + 1] - d1) >> 8;
+                }
+                w[e / 2] = __byte_perm(small_int_f32_bits(d0), small_int_f32_bits(d1), 0x7632);
+            }
+            *reinterpret_cast<uint4 *>(base + (((d.row0 + t * d.rpad + r) * d.kpad + c) >> 1)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -171,27 +257,28 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restric
 // Digit split of whole matrices (the classical path's operands): rows
 // [0, rows) × columns [0, kpad) of each destination, zero beyond the view.
 // Grid: x = column-pair blocks, y = row blocks (strided), z = matrix.
-constexpr int DIG_ROWS = 8;
+constexpr int DIG_ROWS = 4;   // rows per thread
+constexpr int DIG_COLS = 8;   // columns per thread
+constexpr int DIG_THREADS = 128;
 template <int D, bool U32>
-__global__ void __launch_bounds__(PREP_THREADS) k_digitize(const DigitizeJob *__restrict__ jobs,
-                                                           ModP m) {
+__global__ void __launch_bounds__(DIG_THREADS) k_digitize(const DigitizeJob *__restrict__ jobs,
+                                                          ModP m) {
     const DigitizeJob &jb = jobs[blockIdx.z];
-    const int64_t c = 2 * ((int64_t)blockIdx.x * PREP_THREADS + threadIdx.x);
+    const int64_t c = DIG_COLS * ((int64_t)blockIdx.x * DIG_THREADS + threadIdx.x);
     if (c >= jb.dst.kpad) return;
+    const bool vec_ok = ((reinterpret_cast<uintptr_t>(jb.X.ptr) & 15u) == 0) && ((jb.X.ld & 3) == 0);
     const int64_t nrb = (jb.rows + DIG_ROWS - 1) / DIG_ROWS;
     for (int64_t rb = blockIdx.y; rb < nrb; rb += gridDim.y) {
-        uint32_t v[DIG_ROWS][2];
+        uint32_t v[DIG_ROWS][8];
 #pragma unroll
-        for (int i = 0; i < DIG_ROWS; ++i) {
-            const int64_t r = rb * DIG_ROWS + i;
-            v[i][0] = r < jb.rows ? ld_view(jb.X, r, c) : 0u;
-            v[i][1] = r < jb.rows ? ld_view(jb.X, r, c + 1) : 0u;
-        }
+        for (int i = 0; i < DIG_ROWS; ++i) ld_view8(jb.X, vec_ok, rb * DIG_ROWS + i, c, v[i]);
 #pragma unroll
         for (int i = 0; i < DIG_ROWS; ++i) {
             const int64_t r = rb * DIG_ROWS + i;
             if (r >= jb.rows) break;
-            put_pair<D, U32>(jb.dst, r, c, red(v[i][0], m), red(v[i][1], m), m.half, m.p);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[i][e] = red(v[i][e], m);
+            put8<D, U32>(jb.dst, r, c, v[i], m.half, m.p);
         }
     }
 }
@@ -200,7 +287,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_digitize(const DigitizeJob *__
 // job t with block0[t] ≤ b < block0[t+1] (binary search), then to one row
 // block and one column block of that job.
 template <int D, bool U32>
-__global__ void __launch_bounds__(PREP_THREADS) k_digitize_flat(const DigitizeJob *__restrict__ jobs,
+__global__ void __launch_bounds__(DIG_THREADS) k_digitize_flat(const DigitizeJob *__restrict__ jobs,
                                                                 int njobs, ModP m) {
     const int64_t b = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
     int lo = 0, hi = njobs - 1;
@@ -209,134 +296,149 @@ __global__ void __launch_bounds__(PREP_THREADS) k_digitize_flat(const DigitizeJo
         if (jobs[mid].block0 <= b) lo = mid; else hi = mid - 1;
     }
     const DigitizeJob &jb = jobs[lo];
-    const int64_t gx = (jb.dst.kpad / 2 + PREP_THREADS - 1) / PREP_THREADS;
+    const int64_t gx = (jb.dst.kpad / DIG_COLS + DIG_THREADS - 1) / DIG_THREADS;
     const int64_t local = b - jb.block0;
     const int64_t rb = local / gx, cb = local - rb * gx;
     if (rb * DIG_ROWS >= jb.rows) return;
-    const int64_t c = 2 * (cb * PREP_THREADS + threadIdx.x);
+    const int64_t c = DIG_COLS * (cb * DIG_THREADS + threadIdx.x);
     if (c >= jb.dst.kpad) return;
-    uint32_t v[DIG_ROWS][2];
+    const bool vec_ok = ((reinterpret_cast<uintptr_t>(jb.X.ptr) & 15u) == 0) && ((jb.X.ld & 3) == 0);
+    uint32_t v[DIG_ROWS][8];
 #pragma unroll
-    for (int i = 0; i < DIG_ROWS; ++i) {
-        const int64_t r = rb * DIG_ROWS + i;
-        v[i][0] = r < jb.rows ? ld_view(jb.X, r, c) : 0u;
-        v[i][1] = r < jb.rows ? ld_view(jb.X, r, c + 1) : 0u;
-    }
+    for (int i = 0; i < DIG_ROWS; ++i) ld_view8(jb.X, vec_ok, rb * DIG_ROWS + i, c, v[i]);
 #pragma unroll
     for (int i = 0; i < DIG_ROWS; ++i) {
         const int64_t r = rb * DIG_ROWS + i;
         if (r >= jb.rows) break;
-        put_pair<D, U32>(jb.dst, r, c, red(v[i][0], m), red(v[i][1], m), m.half, m.p);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[i][e] = red(v[i][e], m);
+        put8<D, U32>(jb.dst, r, c, v[i], m.half, m.p);
     }
 }
 
-constexpr int PT = 32;  // post-addition tile: 32×32, 256 threads, 4 rows each
+constexpr int PR = 32;   // post-addition tile rows
+constexpr int PC = 128;  // post-addition tile columns (4 per thread)
 
-// Grid: x = tile column J, y = tile row I, z = 3·node + quadrant, where the
-// quadrants of the node's 2h×2h result are 0: C11 = Low(U3), 1: C21 = U4,
-// 2: C22 = Low(U5).  Tiles above the diagonal of quadrants 0 and 2 exit.
-// Every quadrant first issues all of its loads, then combines.
+__device__ __forceinline__ void ld4(const uint32_t *base, int64_t ld, int64_t i, int64_t j, int64_t h,
+                                    uint32_t (&x)[4]) {
+    // row i, columns j..j+3 of an h×h buffer whose row stride is a multiple of 4
+    if (i < h && j + 4 <= h) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(base + i * ld + j));
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[e] = (i < h && j + e < h) ? __ldg(base + i * ld + j + e) : 0u;
+    }
+}
+
+// Grid: x = tile column J (128 columns), y = tile row I (32 rows),
+// z = 3·node + quadrant, where the quadrants of the node's 2h×2h result are
+// 0: C11 = Low(U3), 1: C21 = U4, 2: C22 = Low(U5).  Tiles wholly above the
+// diagonal of quadrants 0 and 2 exit.  The transposed operands -- Up(U1) in
+// quadrant 1 and P4ᵀ in quadrant 2 -- come from the 128×32 tile (J, I) staged
+// through shared memory.  Product buffers have row strides that are
+// multiples of 4 (16-byte loads).
 __global__ void __launch_bounds__(256) k_post(const PostNode *__restrict__ nodes, int64_t h,
                                               ModP m) {
-    __shared__ uint32_t sa[PT][PT + 1];
-    __shared__ uint32_t so[PT][PT + 1];
+    __shared__ uint32_t st[PC][PR + 1];
+    __shared__ uint32_t so[PR][PC + 1];
     const PostNode &nd = nodes[blockIdx.z / 3];
     const int quad = blockIdx.z % 3;
     const int64_t I = blockIdx.y, J = blockIdx.x;
-    if (quad != 1 && J > I) return;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t i0 = I * PR, j0 = J * PC;
+    if (quad != 1 && j0 > i0 + PR - 1) return;  // wholly above the diagonal
+    const int tid = threadIdx.x;
+    const int tx = tid & 31, ty = tid >> 5;     // 4 columns 4·tx.., rows ty + 8q
     const uint32_t p = m.p;
-    constexpr int NR = PT / 8;
-    const int64_t j = J * PT + tx;
-    uint32_t vals[NR];
-    if (quad == 0) {
-        uint32_t x[NR], z[NR];
+    const int64_t j = j0 + 4 * tx;
+    // the diagonal of the quadrant crosses or lies below this tile
+    const bool need_t = (quad == 1 && j0 + PC - 1 > i0) || quad == 2;
+    if (need_t) {
+        // tile (J, I): rows j0.., columns i0.. (32 wide: 8 threads × 4 per row)
 #pragma unroll
-        for (int q = 0; q < NR; ++q) {
-            const int64_t i = I * PT + ty + 8 * q;
-            const bool ok = i < h && j < h && j <= i;
-            x[q] = ok ? __ldg(nd.P1 + i * nd.ldr + j) : 0u;
-            z[q] = ok ? __ldg(nd.P2 + i * nd.ldr + j) : 0u;
-        }
+        for (int q = 0; q < PC / 32; ++q) {
+            const int lr = (tid >> 3) + 32 * q, lc = 4 * (tid & 7);
+            uint32_t a[4], b[4];
+            if (quad == 1) {
+                ld4(nd.P1, nd.ldr, j0 + lr, i0 + lc, h, a);
+                ld4(nd.P5, nd.ldr, j0 + lr, i0 + lc, h, b);
 #pragma unroll
-        for (int q = 0; q < NR; ++q) vals[q] = addm(x[q], z[q], p);  // Low(U3) = Low(P1 + P2)
-    } else if (quad == 1) {
-        // Up(U1) = Low(U1)ᵀ: tile (J, I) of P1 + P5 through shared memory
-        if (I <= J) {
-            uint32_t t1[NR], t5[NR];
+                for (int e = 0; e < 4; ++e) st[lr][lc + e] = a[e] + b[e];  // < 2p
+            } else {
+                ld4(nd.P4, nd.ldg, j0 + lr, i0 + lc, h, a);
 #pragma unroll
-            for (int q = 0; q < NR; ++q) {
-                const int64_t rr = J * PT + ty + 8 * q, cc = I * PT + tx;
-                const bool ok = rr < h && cc < h;
-                t1[q] = ok ? __ldg(nd.P1 + rr * nd.ldr + cc) : 0u;
-                t5[q] = ok ? __ldg(nd.P5 + rr * nd.ldr + cc) : 0u;
+                for (int e = 0; e < 4; ++e) st[lr][lc + e] = a[e];
             }
-#pragma unroll
-            for (int q = 0; q < NR; ++q) sa[ty + 8 * q][tx] = t1[q] + t5[q];
-            __syncthreads();
-        }
-        uint32_t u1[NR], g3[NR], g4[NR];
-#pragma unroll
-        for (int q = 0; q < NR; ++q) {
-            const int ly = ty + 8 * q;
-            const int64_t i = I * PT + ly;
-            const bool ok = i < h && j < h;
-            const bool lowr = ok && i >= j;
-            const uint32_t a1 = lowr ? __ldg(nd.P1 + i * nd.ldr + j) : 0u;
-            const uint32_t a5 = lowr ? __ldg(nd.P5 + i * nd.ldr + j) : 0u;
-            u1[q] = lowr ? a1 + a5 : (ok ? sa[tx][ly] : 0u);
-            g3[q] = ok ? __ldg(nd.P3 + i * nd.ldg + j) : 0u;
-            g4[q] = ok ? __ldg(nd.P4 + i * nd.ldg + j) : 0u;
-        }
-#pragma unroll
-        for (int q = 0; q < NR; ++q) vals[q] = red(u1[q] + g4[q] + g3[q], m);  // U4 = U1 + P4 + P3
-    } else {
-        // P4ᵀ: tile (J, I) of P4 through shared memory
-        {
-            uint32_t t4[NR];
-#pragma unroll
-            for (int q = 0; q < NR; ++q) {
-                const int64_t rr = J * PT + ty + 8 * q, cc = I * PT + tx;
-                t4[q] = (rr < h && cc < h) ? __ldg(nd.P4 + rr * nd.ldg + cc) : 0u;
-            }
-#pragma unroll
-            for (int q = 0; q < NR; ++q) sa[ty + 8 * q][tx] = t4[q];
-        }
-        uint32_t a1[NR], a5[NR], g4[NR];
-#pragma unroll
-        for (int q = 0; q < NR; ++q) {
-            const int64_t i = I * PT + ty + 8 * q;
-            const bool ok = i < h && j < h && j <= i;
-            a1[q] = ok ? __ldg(nd.P1 + i * nd.ldr + j) : 0u;
-            a5[q] = ok ? __ldg(nd.P5 + i * nd.ldr + j) : 0u;
-            g4[q] = ok ? __ldg(nd.P4 + i * nd.ldg + j) : 0u;
         }
         __syncthreads();
+    }
+    uint32_t vals[PR / 8][4];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) {
-            const int ly = ty + 8 * q;
-            vals[q] = red(a1[q] + a5[q] + g4[q] + sa[tx][ly], m);  // Low(U5) = Low(U1 + P4 + P4ᵀ)
+    for (int q = 0; q < PR / 8; ++q) {
+        const int ly = ty + 8 * q;
+        const int64_t i = i0 + ly;
+        uint32_t x[4], z[4], g[4];
+        if (quad == 0) {
+            ld4(nd.P1, nd.ldr, i, j, h, x);
+            ld4(nd.P2, nd.ldr, i, j, h, z);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) vals[q][e] = addm(x[e], z[e], p);  // Low(U3) = Low(P1 + P2)
+        } else if (quad == 1) {
+            ld4(nd.P1, nd.ldr, i, j, h, x);
+            ld4(nd.P5, nd.ldr, i, j, h, z);
+            uint32_t g3[4];
+            ld4(nd.P3, nd.ldg, i, j, h, g3);
+            ld4(nd.P4, nd.ldg, i, j, h, g);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int64_t jj = j + e;
+                // Up(U1) = Low(U1)ᵀ above the diagonal
+                const uint32_t u1 = jj <= i ? x[e] + z[e] : (need_t ? st[jj - j0][ly] : 0u);
+                vals[q][e] = red(u1 + g[e] + g3[e], m);  // U4 = U1 + P4 + P3
+            }
+        } else {
+            ld4(nd.P1, nd.ldr, i, j, h, x);
+            ld4(nd.P5, nd.ldr, i, j, h, z);
+            ld4(nd.P4, nd.ldg, i, j, h, g);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)  // Low(U5) = Low(U1 + P4 + P4ᵀ)
+                vals[q][e] = red(x[e] + z[e] + g[e] + st[j + e - j0][ly], m);
         }
     }
-    const int64_t r0 = (quad == 0 ? 0 : h) + I * PT, c0 = (quad == 2 ? h : 0) + J * PT;
+    const int64_t r0 = (quad == 0 ? 0 : h) + i0, c0 = (quad == 2 ? h : 0) + j0;
     if (!nd.upper) {
 #pragma unroll
-        for (int q = 0; q < NR; ++q) {
+        for (int q = 0; q < PR / 8; ++q) {
             const int ly = ty + 8 * q;
-            const int64_t R = r0 + ly, Cc = c0 + tx;
-            const bool inside = (I * PT + ly < h) && (J * PT + tx < h);
-            if (inside && R < nd.vn && Cc < nd.vn && Cc <= R) nd.out[R * nd.ldo + Cc] = vals[q];
+            const int64_t R = r0 + ly;
+            if (i0 + ly >= h || R >= nd.vn) continue;
+            uint32_t *orow = nd.out + R * nd.ldo;
+            const int64_t Cc = c0 + 4 * tx;
+            const bool full = (j + 4 <= h) && (Cc + 3 < nd.vn) && (Cc + 3 <= R) &&
+                              ((reinterpret_cast<uintptr_t>(orow + Cc) & 15u) == 0);
+            if (full) {
+                *reinterpret_cast<uint4 *>(orow + Cc) =
+                    make_uint4(vals[q][0], vals[q][1], vals[q][2], vals[q][3]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (j + e < h && Cc + e < nd.vn && Cc + e <= R) orow[Cc + e] = vals[q][e];
+            }
         }
     } else {
+        __syncthreads();  // st may still be read above
 #pragma unroll
-        for (int q = 0; q < NR; ++q) so[ty + 8 * q][tx] = vals[q];
+        for (int q = 0; q < PR / 8; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) so[ty + 8 * q][4 * tx + e] = vals[q][e];
         __syncthreads();
-        // element (R, Cc) of the lower result goes to out[Cc][R]
+        // element (R, Cc) of the lower result goes to out[Cc][R]: 128 output
+        // rows (columns of the tile), 32 consecutive entries each
 #pragma unroll
-        for (int q = 0; q < NR; ++q) {
-            const int lc = ty + 8 * q;  // column within the tile
-            const int64_t R = r0 + tx, Cc = c0 + lc;
-            const bool inside = (I * PT + tx < h) && (J * PT + lc < h);
+        for (int q = 0; q < PC / 8; ++q) {
+            const int lc = ty + 8 * q;  // tile column
+            const int64_t Cc = c0 + lc, R = r0 + tx;
+            const bool inside = (i0 + tx < h) && (j0 + lc < h);
             if (inside && R < nd.vn && Cc < nd.vn && Cc <= R) nd.out[Cc * nd.ldo + R] = so[tx][lc];
         }
     }
@@ -373,7 +475,7 @@ cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_
                         int64_t kpad, ModP mp, YConst y, DigitScheme ds, int arena_kind,
                         bool reduce_input, cudaStream_t st) {
     if (h == 0 || kpad == 0 || nnodes == 0) return cudaSuccess;
-    const int64_t gx = (kpad / 2 + PREP_THREADS - 1) / PREP_THREADS;
+    const int64_t gx = (kpad / 4 + PREP_THREADS - 1) / PREP_THREADS;
     const int64_t gy = std::min<int64_t>((h + PREP_ROWS - 1) / PREP_ROWS, 65535);
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nnodes);
     if (arena_kind == ARENA_U32)
@@ -390,16 +492,16 @@ cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_
                             int64_t max_kpad, ModP mp, DigitScheme ds, int arena_kind,
                             cudaStream_t st) {
     if (njobs == 0 || max_rows == 0 || max_kpad == 0) return cudaSuccess;
-    const int64_t gx = (max_kpad / 2 + PREP_THREADS - 1) / PREP_THREADS;
+    const int64_t gx = (max_kpad / DIG_COLS + DIG_THREADS - 1) / DIG_THREADS;
     const int64_t gy = std::min<int64_t>((max_rows + DIG_ROWS - 1) / DIG_ROWS, 65535);
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)njobs);
     if (arena_kind == ARENA_U32) {
-        k_digitize<1, true><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, mp);
+        k_digitize<1, true><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp);
     } else {
         switch (ds.D) {
-            case 1: k_digitize<1, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, mp); break;
-            case 2: k_digitize<2, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, mp); break;
-            case 3: k_digitize<3, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, mp); break;
+            case 1: k_digitize<1, false><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
+            case 2: k_digitize<2, false><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
+            case 3: k_digitize<3, false><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
             default: return cudaErrorInvalidValue;
         }
     }
@@ -407,7 +509,7 @@ cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_
 }
 
 int64_t digitize_flat_blocks(int64_t rows, int64_t kpad) {
-    return ((rows + DIG_ROWS - 1) / DIG_ROWS) * ((kpad / 2 + PREP_THREADS - 1) / PREP_THREADS);
+    return ((rows + DIG_ROWS - 1) / DIG_ROWS) * ((kpad / DIG_COLS + DIG_THREADS - 1) / DIG_THREADS);
 }
 
 cudaError_t launch_digitize_flat(const DigitizeJob *jobs_dev, int njobs, int64_t total_blocks,
@@ -419,12 +521,12 @@ cudaError_t launch_digitize_flat(const DigitizeJob *jobs_dev, int njobs, int64_t
     dim3 grid((unsigned)gx, (unsigned)gy);
     // blocks past the last job's range find its job and return on the row check
     if (arena_kind == ARENA_U32) {
-        k_digitize_flat<1, true><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, njobs, mp);
+        k_digitize_flat<1, true><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp);
     } else {
         switch (ds.D) {
-            case 1: k_digitize_flat<1, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
-            case 2: k_digitize_flat<2, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
-            case 3: k_digitize_flat<3, false><<<grid, PREP_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
+            case 1: k_digitize_flat<1, false><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
+            case 2: k_digitize_flat<2, false><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
+            case 3: k_digitize_flat<3, false><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
             default: return cudaErrorInvalidValue;
         }
     }
@@ -434,9 +536,9 @@ cudaError_t launch_digitize_flat(const DigitizeJob *jobs_dev, int njobs, int64_t
 cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP mp,
                         cudaStream_t st) {
     if (h == 0 || nnodes == 0) return cudaSuccess;
-    const int64_t T = (h + PT - 1) / PT;
-    if (T > 65535 || 3 * (int64_t)nnodes > 65535) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)T, (unsigned)T, (unsigned)(3 * nnodes));
+    const int64_t TI = (h + PR - 1) / PR, TJ = (h + PC - 1) / PC;
+    if (TI > 65535 || TJ > 65535 || 3 * (int64_t)nnodes > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)TJ, (unsigned)TI, (unsigned)(3 * nnodes));
     k_post<<<grid, 256, 0, st>>>(nodes_dev, h, mp);
     return cudaGetLastError();
 }

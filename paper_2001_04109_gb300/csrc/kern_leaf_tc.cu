@@ -314,7 +314,34 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
     }
 }
 
+// Failure-detection self-test: one thread waits on an mbarrier that nothing
+// ever signals, gives up after limit_ns and records the timeout in the error
+// word -- the same path every bounded wait of the leaf takes -- and the
+// kernel returns normally, so the context stays usable.
+__global__ void k_wait_selftest(unsigned int *err, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t t0 = gtimer();
+        while (!mbar_try(&bar, 0)) {
+            if (gtimer() - t0 > limit_ns) {
+                atomicOr(err, ERR_WAIT);
+                break;
+            }
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(unsigned int *err, unsigned long long limit_ns, cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(err, limit_ns);
+    return cudaGetLastError();
+}
 
 int leaf_tc_bm() { return BM; }
 int leaf_tc_bn() { return BN; }

@@ -30,7 +30,8 @@ _LEAVES = {None: LEAF_AUTO, "auto": LEAF_AUTO, "tc": LEAF_TC_BF16, "bf16": LEAF_
 EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan",
            "ffsyrk", "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
            "ffsyrk_plan_set_timing", "ffsyrk_plan_get_timing", "ffsyrk_status_string",
-           "ffsyrk_version", "ffsyrk_noalloc", "ffsyrk_leaf_schedule", "ffsyrk_digit_bounds"]
+           "ffsyrk_version", "ffsyrk_noalloc", "ffsyrk_leaf_schedule", "ffsyrk_digit_bounds",
+           "ffsyrk_plan_selftest_timeout"]
 
 
 class FfsyrkError(RuntimeError):
@@ -92,6 +93,8 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_status_string.argtypes = [i32]
             L.ffsyrk_status_string.restype = ctypes.c_char_p
             L.ffsyrk_version.restype = i32
+            L.ffsyrk_plan_selftest_timeout.argtypes = [vp, i64, vp]
+            L.ffsyrk_plan_selftest_timeout.restype = i32
             L.ffsyrk_leaf_schedule.argtypes = [u32, i32, P(i32), i32]
             L.ffsyrk_leaf_schedule.restype = i32
             L.ffsyrk_digit_bounds.argtypes = [u32, P(i32)]
@@ -181,6 +184,10 @@ class Plan:
         t = Timing()
         _check(lib().ffsyrk_plan_get_timing(self._h, ctypes.byref(t)), "ffsyrk_plan_get_timing")
         return {f: getattr(t, f) for f, _ in Timing._fields_}
+
+    def selftest_timeout(self, limit_ns: int, stream=None) -> None:
+        _check(lib().ffsyrk_plan_selftest_timeout(self._h, int(limit_ns), _stream_handle(stream)),
+               "ffsyrk_plan_selftest_timeout")
 
     def sync_status(self, stream=None) -> None:
         _check(lib().ffsyrk_sync_status(self._h, _stream_handle(stream)), "ffsyrk_sync_status")
