@@ -200,6 +200,13 @@ typedef struct {
     int32_t leaf_launches;
     double field_macs;        /* useful multiply-adds mod p of the leaf products      */
     double tensor_macs;       /* digit-pair multiply-adds issued for them (D²×)       */
+    int32_t leaf_tiles;       /* output tiles of the leaf launch                      */
+    int32_t leaf_entries;     /* work entries handed to its CTAs                      */
+    int32_t split_tiles;      /* tiles whose K schedule several CTAs share (a launch
+                                 with few, long tiles: each CTA takes an equal share
+                                 of the K units and the last to finish a tile adds
+                                 the others' partial residues)                        */
+    int32_t reserved;
 } ffsyrk_timing_t;
 
 /* Timing of the most recent call with timing enabled: waits for its last

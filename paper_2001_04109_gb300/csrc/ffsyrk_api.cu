@@ -163,18 +163,25 @@ struct Descs {
     std::vector<LeafTile> tiles;
     std::vector<DigitizeJob> digit;
     std::vector<LeafSeg> segs;
+    // tail split of the 1-CTA tensor-core leaf (empty: whole tiles only)
+    std::vector<LeafPiece> pieces;
+    std::vector<int32_t> entries;
+    int nslots = 0;
     int64_t digit_max_rows = 0, digit_max_kpad = 0;
     // blob offsets (bytes) inside the descriptor region
     int64_t prep_off[kMaxLevels] = {}, post_off[kMaxLevels] = {};
     int64_t prods_off = 0, tiles_off = 0, tmap_off = 0, aptr_off = 0, akpad_off = 0, digit_off = 0;
-    int64_t ctr_off = 0, segs_off = 0;
+    int64_t ctr_off = 0, segs_off = 0, pieces_off = 0, entries_off = 0;
+    int64_t ctr_bytes = 16;  // work counter + 8 counters per split tile, zeroed every call
     int64_t bytes = 0;
 };
 
-int64_t desc_capacity(const Geometry &g, int leaf) {
-    // generous bound for the descriptor blob of any shape ≤ g
-    int64_t b = 0;
-    for (int d = 0; d < g.L; ++d) b += pow3(d) * (sizeof(PrepNode) + sizeof(PostNode)) + 2 * 256;
+// Upper bounds used to size a plan: CTAs of one launch, and leaf tiles of
+// one call at geometry g.
+constexpr int64_t kMaxCtas = 256;
+
+// Leaf tiles (bound) and products of one call at geometry g.
+int64_t leaf_tiles_bound(const Geometry &g, int leaf, int64_t *nprods_out = nullptr) {
     int64_t nprods = 1;
     int64_t ntiles = 0;
     const int64_t tm = leaf == FFSYRK_LEAF_TC_BF16 ? 128 : 64, tn = leaf == FFSYRK_LEAF_TC_BF16 ? 256 : 64;
@@ -190,7 +197,20 @@ int64_t desc_capacity(const Geometry &g, int leaf) {
         ntiles += pow3(g.L) * ((h + tm - 1) / tm) * ((h + tn - 1) / tn);
         nprods += pow3(g.L);
     }
+    if (nprods_out) *nprods_out = nprods;
+    return ntiles;
+}
+
+int64_t desc_capacity(const Geometry &g, int leaf) {
+    // generous bound for the descriptor blob of any shape ≤ g
+    int64_t b = 0;
+    for (int d = 0; d < g.L; ++d) b += pow3(d) * (sizeof(PrepNode) + sizeof(PostNode)) + 2 * 256;
+    int64_t nprods = 1;
+    const int64_t ntiles = leaf_tiles_bound(g, leaf, &nprods);
     b += nprods * sizeof(LeafProd) + ntiles * sizeof(LeafTile);
+    // tail split: items ≤ tiles + 2 CTAs' shares, entries ≤ tiles + CTAs + 1, counters
+    b += (ntiles + 2 * kMaxCtas) * (int64_t)(sizeof(LeafTile) + sizeof(LeafPiece)) +
+         (ntiles + kMaxCtas + 2) * 4 + 2 * kMaxCtas * 32 + 4 * 256;
     b += (kMaxLevels + 1) * (128 + 16) + 10 * 256 + sizeof(DigitizeJob);
     // segment tables: at most L + 1 distinct K per call, ≤ 40 segments per 16 k-blocks
     b += (int64_t)(g.L + 1) * ((g.kp / 64 + 16) / 16 + 1) * 40 * (int64_t)sizeof(LeafSeg);
@@ -313,6 +333,8 @@ struct ffsyrk_plan_st {
     char *ws = nullptr;
     int64_t ws_bytes = 0, data_cap = 0, desc_cap = 0;
     char *desc_host = nullptr;  // pinned staging for the descriptor blob
+    uint32_t *part = nullptr;   // partial-result slots of split tiles
+    int part_slots = 0;
     cudaEvent_t desc_done = nullptr;
     bool desc_pending = false;
     unsigned int *err_host = nullptr, *err_dev = nullptr;  // mapped host word
@@ -326,6 +348,7 @@ struct ffsyrk_plan_st {
     bool timed_call = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int last_launches = 0, last_leaf_launches = 0;
+    int last_leaf_tiles = 0, last_leaf_entries = 0, last_split_tiles = 0;
     double last_field_macs = 0, last_tensor_macs = 0;
     // the launch sequence of the last call, captured once and replayed
     cudaStream_t cap_stream = nullptr;
@@ -385,6 +408,102 @@ void tri_tiles(std::vector<LeafTile> &out, int prod, int64_t rows, int64_t cols,
                 if (tri == 2 && c1 < r0) continue;  // no entry with c ≥ r
                 out.push_back(LeafTile{prod, (int32_t)a, (int32_t)b, cost});
             }
+}
+
+// Split of small launches over the 1-CTA leaf's CTAs.  With at most half
+// as many tiles as CTAs most SMs would idle, so when the tiles are long
+// (≥ kSplitMinKb k-blocks of MMAs each) they are cut at unit boundaries into
+// S shares of equal estimated time (stream-K style), each share handed out
+// as one work entry; a tile cut in several pieces is finished by whichever
+// CTA completes its last piece (see LeafPiece).  Measured on GB300:
+// A 2048×8192 (72 tiles of 512 k-blocks) 0.215 → 0.159 ms; short tiles lose
+// to the per-piece overhead (A 512×512: 0.044 → 0.056 ms), and launches of a
+// wave or more lose because every SM is busy already and the leaf is bound
+// by L2 bandwidth (A 4096×4096, 272 tiles: 0.191 → 0.211 ms).
+constexpr double kUnitCost = 2.0;   // epilogue drain of one unit, in k-blocks
+constexpr double kSplitMinKb = 256;  // mean k-blocks per tile worth splitting
+
+void split_tail(Descs &D, int S, int slot_cap) {
+    D.pieces.clear();
+    D.entries.clear();
+    D.nslots = 0;
+    const int T = (int)D.tiles.size();
+    if (T == 0 || S < 2 || 2 * T > S) return;
+    const int R = T;
+    const int DP = 0;
+    struct Unit {
+        int tile, sx0, sx1;
+        double cost;
+    };
+    std::vector<Unit> units;
+    double total = 0;
+    for (int i = DP; i < T; ++i) {
+        const LeafProd &pr = D.prods[D.tiles[i].prod];
+        int start = 0;
+        double c = 0;
+        for (int sx = 0; sx <= pr.nseg; ++sx) {
+            const bool boundary = sx == pr.nseg || (sx > start && D.segs[pr.seg0 + sx].first);
+            if (boundary && sx > start) {
+                units.push_back(Unit{i, start, sx, c + kUnitCost});
+                total += c + kUnitCost;
+                start = sx;
+                c = 0;
+            }
+            if (sx < pr.nseg) c += D.segs[pr.seg0 + sx].nkb;
+        }
+    }
+    const int nshares = (int)std::min<size_t>((size_t)S, units.size());
+    if (nshares < 2 || total - kUnitCost * (double)units.size() < kSplitMinKb * T) return;
+    const double target = total / nshares;
+    struct Piece {
+        int share, tile, sx0, sx1;
+    };
+    std::vector<Piece> ps;
+    double cum = 0;
+    for (const Unit &u : units) {
+        const int sh = std::min(nshares - 1, (int)((cum + u.cost / 2) / target));
+        cum += u.cost;
+        if (!ps.empty() && ps.back().share == sh && ps.back().tile == u.tile)
+            ps.back().sx1 = u.sx1;
+        else
+            ps.push_back(Piece{sh, u.tile, u.sx0, u.sx1});
+    }
+    // pieces per tile (a tile's pieces are consecutive) and their slots
+    std::vector<int> npieces(T, 0);
+    for (const Piece &q : ps) ++npieces[q.tile];
+    int slots = 0;
+    for (int i = DP; i < T; ++i)
+        if (npieces[i] > 1) slots += npieces[i];
+    if (slots > slot_cap) return;
+    std::vector<LeafTile> items(D.tiles.begin(), D.tiles.begin() + DP);
+    for (int i = 0; i < DP; ++i) {
+        D.pieces.push_back(LeafPiece{0, D.prods[D.tiles[i].prod].nseg, -1, 0, 1});
+        D.entries.push_back(i);
+    }
+    std::vector<int> slot0(T, -1), seen(T, 0);
+    int next = 0;
+    for (int i = DP; i < T; ++i)
+        if (npieces[i] > 1) {
+            slot0[i] = next;
+            next += npieces[i];
+        }
+    int cur = -1;
+    for (const Piece &q : ps) {
+        while (cur < q.share) {
+            ++cur;
+            D.entries.push_back((int32_t)items.size());  // shares without units stay empty
+        }
+        items.push_back(D.tiles[q.tile]);
+        D.pieces.push_back(LeafPiece{q.sx0, q.sx1, slot0[q.tile], (int16_t)seen[q.tile]++,
+                                     (int16_t)npieces[q.tile]});
+    }
+    while (cur < nshares - 1) {
+        ++cur;
+        D.entries.push_back((int32_t)items.size());
+    }
+    D.entries.push_back((int32_t)items.size());
+    D.tiles.swap(items);
+    D.nslots = slots;
 }
 
 // Build every descriptor of one call into pl->desc and the staging blob.
@@ -530,6 +649,8 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     // longest tiles first, then round-robin over persistent CTAs
     std::stable_sort(D.tiles.begin(), D.tiles.end(),
                      [](const LeafTile &a, const LeafTile &b) { return a.cost > b.cost; });
+    if (tc && !pair) split_tail(D, pl->sms, pl->part_slots);
+    D.ctr_bytes = 16 + (int64_t)D.nslots * 8 * 4;
 
     // pack the blob
     int64_t off = 0;
@@ -549,8 +670,10 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     D.aptr_off = slot((kMaxLevels + 1) * sizeof(void *), 64);
     D.akpad_off = slot((kMaxLevels + 1) * sizeof(int64_t), 64);
     D.digit_off = slot((int64_t)D.digit.size() * sizeof(DigitizeJob), 64);
-    D.ctr_off = slot(16, 16);  // the leaf kernel's tile counter (zeroed every call)
+    D.ctr_off = slot(D.ctr_bytes, 16);  // the leaf kernel's counters (zeroed every call)
     D.segs_off = slot((int64_t)D.segs.size() * sizeof(LeafSeg), 64);
+    D.pieces_off = slot((int64_t)D.pieces.size() * sizeof(LeafPiece), 64);
+    D.entries_off = slot((int64_t)D.entries.size() * sizeof(int32_t), 64);
     D.bytes = rup(off, 256);
     if (D.bytes > pl->desc_cap) return FFSYRK_ERR_TOO_LARGE;
 
@@ -564,6 +687,8 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     memcpy(hb + D.tiles_off, D.tiles.data(), D.tiles.size() * sizeof(LeafTile));
     memcpy(hb + D.digit_off, D.digit.data(), D.digit.size() * sizeof(DigitizeJob));
     memcpy(hb + D.segs_off, D.segs.data(), D.segs.size() * sizeof(LeafSeg));
+    memcpy(hb + D.pieces_off, D.pieces.data(), D.pieces.size() * sizeof(LeafPiece));
+    memcpy(hb + D.entries_off, D.entries.data(), D.entries.size() * sizeof(int32_t));
     for (int j = 0; j <= kMaxLevels; ++j) {
         const Arena &a = lay.arena[j];
         if (a.rows == 0) continue;
@@ -625,7 +750,14 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
             tl.tile_ctr = nullptr;
             e = launch_leaf_tc2(tl, pl->sms, st);
         } else {
-            e = cudaMemsetAsync(tl.tile_ctr, 0, sizeof(unsigned int), st);
+            if (!D.entries.empty()) {
+                tl.pieces = reinterpret_cast<const LeafPiece *>(dd + D.pieces_off);
+                tl.entries = reinterpret_cast<const int32_t *>(dd + D.entries_off);
+                tl.nentries = (int)D.entries.size() - 1;
+                tl.part = pl->part;
+                tl.part_ctr = reinterpret_cast<unsigned int *>(dd + D.ctr_off + 16);
+            }
+            e = cudaMemsetAsync(tl.tile_ctr, 0, (size_t)D.ctr_bytes, st);
             if (e == cudaSuccess) e = launch_leaf_tc(tl, pl->sms, st);
         }
     } else {
@@ -700,6 +832,14 @@ void record_work(ffsyrk_plan_st *pl) {
     const Descs &D = pl->desc;
     pl->last_launches = g.L == 0 ? 2 : 2 * g.L + 1;
     pl->last_leaf_launches = 1;
+    int split = 0, whole = 0;
+    for (const LeafPiece &q : D.pieces) {
+        if (q.slot0 >= 0 && q.j == 0) ++split;
+        if (q.slot0 < 0) ++whole;
+    }
+    pl->last_leaf_tiles = D.pieces.empty() ? (int)D.tiles.size() : whole + split;
+    pl->last_leaf_entries = D.entries.empty() ? (int)D.tiles.size() : (int)D.entries.size() - 1;
+    pl->last_split_tiles = split;
     double f = 0;
     for (const LeafProd &pr : D.prods) {
         const double K = (double)(pr.kblocks) * 64.0;
@@ -766,6 +906,7 @@ void destroy_plan(ffsyrk_plan_st *pl) {
         cudaDeviceSynchronize();
         cudaFree(pl->ws);
     }
+    if (pl->part) cudaFree(pl->part);
     drop_graph(pl);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     if (pl->desc_done) cudaEventDestroy(pl->desc_done);
@@ -1003,6 +1144,20 @@ ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
         destroy_plan(pl);
         return FFSYRK_ERR_ALLOC;
     }
+    if (pl->leaf == FFSYRK_LEAF_TC_BF16) {
+        // partial-result slots of the tail split: at most two per CTA, and no
+        // more than the units of all tiles at the largest shape
+        const Geometry g0 = make_geometry(std::max<int64_t>(max_n, 1), std::max<int64_t>(max_k, 1), 0);
+        const int64_t units = leaf_tiles_bound(g0, pl->leaf) *
+                              ((g0.kp / 64 + 15) / 16 + 1) * pl->ds.D * pl->ds.D;
+        pl->part_slots = (int)std::min<int64_t>(std::min<int64_t>(2 * sms, 2 * kMaxCtas), units);
+        const size_t bytes = (size_t)pl->part_slots * leaf_tc_bm() * leaf_tc_bn() * 4;
+        if (cudaMalloc(&pl->part, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            destroy_plan(pl);
+            return FFSYRK_ERR_ALLOC;
+        }
+    }
     e = cudaMemset(pl->ws, 0, (size_t)pl->ws_bytes);
     if (e == cudaSuccess) e = cudaMallocHost(&pl->desc_host, (size_t)desc);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->desc_done, cudaEventDisableTiming);
@@ -1102,6 +1257,10 @@ ffsyrk_status_t ffsyrk_plan_get_timing(ffsyrk_plan_t pl, ffsyrk_timing_t *t) {
     t->leaf_launches = pl->last_leaf_launches;
     t->field_macs = pl->last_field_macs;
     t->tensor_macs = pl->last_tensor_macs;
+    t->leaf_tiles = pl->last_leaf_tiles;
+    t->leaf_entries = pl->last_leaf_entries;
+    t->split_tiles = pl->last_split_tiles;
+    t->reserved = 0;
     return FFSYRK_SUCCESS;
 }
 

@@ -150,6 +150,20 @@ struct LeafTile {
     int32_t cost;
 };
 
+// Part of a tile's K schedule, for tiles shared by several CTAs (the tail of
+// a launch is split so that every CTA ends at about the same time).  A piece
+// covers segments [sx0, sx1) of its product, starting and ending on unit
+// boundaries.  A tile split in npieces pieces owns partial-result slots
+// slot0 .. slot0 + npieces − 1 and one counter per epilogue warp at
+// 8·slot0 + warp; piece j writes its residues to slot slot0 + j, and for each
+// warp's rows the piece that finishes them last adds the others' and stores
+// them.  slot0 < 0: the piece is the whole tile (stored directly).
+struct LeafPiece {
+    int32_t sx0, sx1;
+    int32_t slot0;
+    int16_t j, npieces;
+};
+
 // ---- launchers (each returns cudaGetLastError() of its launch) ----
 // reduce_input: some node views may hold values ≥ p (views of the caller's A)
 cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_t w,
@@ -183,6 +197,13 @@ struct TcLaunch {
     DigitScheme ds;
     unsigned int *err;        // device-visible error word (bounded waits)
     unsigned int *tile_ctr;   // device work counter (zeroed before launch)
+    // optional work split (1-CTA leaf only): pieces[i] describes tiles[i];
+    // entries[e] .. entries[e+1] are the items one CTA takes together
+    const LeafPiece *pieces;  // nullptr: every item is a whole tile
+    const int32_t *entries;   // nullptr: entry e is item e
+    int nentries;
+    uint32_t *part;           // partial-result slots, BM·BN residues each
+    unsigned int *part_ctr;   // 8 per split tile, zero before the first launch
 };
 cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st);
 int leaf_tc_bm();

@@ -62,7 +62,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
                                                              ModP m,
                                                              const __grid_constant__ DigitScheme ds,
                                                              unsigned int *err,
-                                                             unsigned int *tile_ctr) {
+                                                             unsigned int *tile_ctr,
+                                                             const LeafPiece *__restrict__ pieces,
+                                                             const int32_t *__restrict__ entries,
+                                                             int nentries, uint32_t *part,
+                                                             unsigned int *part_ctr) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
     __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], drain_bar;
@@ -107,46 +111,53 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
     if (warp == PRODUCER_WARP) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            uint32_t it = 0;
+            uint32_t it = 0, seq = 0;
             bool ok = true;
-            for (uint32_t seq = 0; ok; ++seq) {
-                // next tile from the device work queue (or round-robin), handed
-                // to the MMA and epilogue warps through the shared ring
-                const int slot = seq % RING;
-                if (!mbar_wait(&ring_empty[slot], ((seq / RING) & 1u) ^ 1u, &abort_flag, err)) {
-                    ok = false;
-                    break;
-                }
-                const int t = tile_ctr ? (int)atomicAdd(tile_ctr, 1u)
-                                       : (int)(blockIdx.x + seq * gridDim.x);
-                tile_ring[slot] = t < ntiles ? t : -1;
-                mbar_arrive(&ring_full[slot]);
-                if (t >= ntiles) break;
-                const LeafTile tl = tiles[t];
-                const LeafProd pr = prods[tl.prod];
-                const CUtensorMap *tm = tmaps + pr.arena;
-                // the descriptor was written by a host copy before this launch
-                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tm)
-                             : "memory");
-                for (int sx = 0; sx < pr.nseg && ok; ++sx) {
-                    const LeafSeg sg = segs[pr.seg0 + sx];
-                    const int ya = (int)(pr.a_row0 + (int64_t)(sg.ij >> 4) * pr.plane_rows + (int64_t)tl.tm * BM);
-                    const int yb = (int)(pr.b_row0 + (int64_t)(sg.ij & 15) * pr.plane_rows + (int64_t)tl.tn * BN);
-                    for (int kb = sg.kb0; kb < sg.kb0 + sg.nkb; ++kb, ++it) {
-                        const int s = it % STAGES;
-                        const uint32_t ph = (it / STAGES) & 1u;
-                        if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag, err)) {
-                            ok = false;
-                            break;
+            for (uint32_t round = 0; ok; ++round) {
+                // next entry from the device work queue (or round-robin); its
+                // items go to the MMA and epilogue warps through the shared
+                // ring, followed by -1 once the queue is empty
+                const int e = tile_ctr ? (int)atomicAdd(tile_ctr, 1u) : (int)(blockIdx.x + round * gridDim.x);
+                const bool done = e >= nentries;
+                const int i0 = done ? 0 : (entries ? entries[e] : e);
+                const int i1 = done ? 1 : (entries ? entries[e + 1] : e + 1);
+                for (int t = i0; t < i1 && ok; ++t, ++seq) {
+                    const int slot = seq % RING;
+                    if (!mbar_wait(&ring_empty[slot], ((seq / RING) & 1u) ^ 1u, &abort_flag, err)) {
+                        ok = false;
+                        break;
+                    }
+                    tile_ring[slot] = done ? -1 : t;
+                    mbar_arrive(&ring_full[slot]);
+                    if (done) break;
+                    const LeafTile tl = tiles[t];
+                    const LeafProd pr = prods[tl.prod];
+                    const int sx0 = pieces ? pieces[t].sx0 : 0, sx1 = pieces ? pieces[t].sx1 : pr.nseg;
+                    const CUtensorMap *tm = tmaps + pr.arena;
+                    // the descriptor was written by a host copy before this launch
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tm)
+                                 : "memory");
+                    for (int sx = sx0; sx < sx1 && ok; ++sx) {
+                        const LeafSeg sg = segs[pr.seg0 + sx];
+                        const int ya = (int)(pr.a_row0 + (int64_t)(sg.ij >> 4) * pr.plane_rows + (int64_t)tl.tm * BM);
+                        const int yb = (int)(pr.b_row0 + (int64_t)(sg.ij & 15) * pr.plane_rows + (int64_t)tl.tn * BN);
+                        for (int kb = sg.kb0; kb < sg.kb0 + sg.nkb; ++kb, ++it) {
+                            const int s = it % STAGES;
+                            const uint32_t ph = (it / STAGES) & 1u;
+                            if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag, err)) {
+                                ok = false;
+                                break;
+                            }
+                            unsigned char *sa = smem + s * STAGE_BYTES;
+                            unsigned char *sb = sa + A_BYTES;
+                            mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+                            tma_load(sa, tm, &full_bar[s], kb * BK, ya);
+                            tma_load(sb, tm, &full_bar[s], kb * BK, yb);
+                            tma_load(sb + B_BYTES / 2, tm, &full_bar[s], kb * BK, yb + BM);
                         }
-                        unsigned char *sa = smem + s * STAGE_BYTES;
-                        unsigned char *sb = sa + A_BYTES;
-                        mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-                        tma_load(sa, tm, &full_bar[s], kb * BK, ya);
-                        tma_load(sb, tm, &full_bar[s], kb * BK, yb);
-                        tma_load(sb + B_BYTES / 2, tm, &full_bar[s], kb * BK, yb + BM);
                     }
                 }
+                if (done) break;
             }
             if (!ok) {
                 // let the copies already issued land before the CTA exits
@@ -169,9 +180,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
                 mbar_arrive(&ring_empty[slot]);
                 if (t < 0) break;
                 const LeafProd pr = prods[tiles[t].prod];
+                const int sx0 = pieces ? pieces[t].sx0 : 0, sx1 = pieces ? pieces[t].sx1 : pr.nseg;
                 bool open = false;  // a unit's accumulator is being filled
                 uint32_t b = 0, tmem_d = 0;
-                for (int sx = 0; sx < pr.nseg; ++sx) {
+                for (int sx = sx0; sx < sx1; ++sx) {
                     const LeafSeg sg = segs[pr.seg0 + sx];
                     if (sg.first) {
                         if (open) {
@@ -236,7 +248,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
             int lo = 0, hi = 0;  // 16-column chunks of this warp that hold stored entries
             live_chunks(pr, (int64_t)tl.tm * BM + quad * 32, (int64_t)tl.tn * BN + colq * EPI_COLS,
                         EPI_COLS / LD_COLS, lo, hi);
-            for (int sx = 0; sx < pr.nseg; ++sx) {
+            const int sx0 = pieces ? pieces[t].sx0 : 0, sx1 = pieces ? pieces[t].sx1 : pr.nseg;
+            for (int sx = sx0; sx < sx1; ++sx) {
                 const LeafSeg sg = segs[pr.seg0 + sx];
                 if (!sg.first) continue;  // one drain per unit
                 const uint32_t b = unit & 1u;
@@ -274,6 +287,47 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
                 ++unit;
             }
             if (!ok) break;
+            const LeafPiece pc = pieces ? pieces[t] : LeafPiece{0, 0, -1, 0, 1};
+            if (pc.slot0 >= 0) {
+                // a piece of a shared tile: publish its residues; the piece
+                // that finishes last adds the others' and stores the tile
+                uint32_t *mine = part + ((int64_t)(pc.slot0 + pc.j) * (BM * BN)) + threadIdx.x * EPI_COLS;
+#pragma unroll
+                for (int e = 0; e < EPI_COLS; e += 4) {
+                    uint4 v4;
+                    v4.x = acc[e] >= p ? acc[e] - p : acc[e];
+                    v4.y = acc[e + 1] >= p ? acc[e + 1] - p : acc[e + 1];
+                    v4.z = acc[e + 2] >= p ? acc[e + 2] - p : acc[e + 2];
+                    v4.w = acc[e + 3] >= p ? acc[e + 3] - p : acc[e + 3];
+                    *reinterpret_cast<uint4 *>(mine + e) = v4;
+                }
+                // per warp: its 32 rows × 128 columns are combined by the
+                // CTA whose warp finishes them last (no cross-warp barrier)
+                __threadfence();
+                __syncwarp();
+                unsigned int prev = 0;
+                if (lane == 0) prev = atomicAdd(&part_ctr[pc.slot0 * EPI_WARPS + warp], 1u);
+                prev = __shfl_sync(0xffffffffu, prev, 0);
+                if (prev != (unsigned)(pc.npieces - 1)) continue;
+                __threadfence();
+#pragma unroll 1
+                for (int q = 0; q < pc.npieces; ++q) {
+                    if (q == pc.j) continue;
+                    const uint32_t *other = part + ((int64_t)(pc.slot0 + q) * (BM * BN)) + threadIdx.x * EPI_COLS;
+#pragma unroll
+                    for (int e = 0; e < EPI_COLS; e += 4) {
+                        const uint4 o = __ldcg(reinterpret_cast<const uint4 *>(other + e));
+                        // acc < 2p and o < p: the sum stays below 2p after one conditional subtract
+                        uint32_t s0 = acc[e] + o.x, s1 = acc[e + 1] + o.y, s2 = acc[e + 2] + o.z,
+                                 s3 = acc[e + 3] + o.w;
+                        acc[e] = min(s0, s0 - twop);
+                        acc[e + 1] = min(s1, s1 - twop);
+                        acc[e + 2] = min(s2, s2 - twop);
+                        acc[e + 3] = min(s3, s3 - twop);
+                    }
+                }
+                if (lane == 0) part_ctr[pc.slot0 * EPI_WARPS + warp] = 0;  // ready for the next launch
+            }
             // store the tile's residues
             const int64_t r = (int64_t)tl.tm * BM + quad * 32 + lane;
             const int64_t c0 = (int64_t)tl.tn * BN + colq * EPI_COLS;
@@ -355,10 +409,12 @@ cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    const int grid = L.ntiles < num_sms ? L.ntiles : num_sms;
+    const int nwork = L.entries ? L.nentries : L.ntiles;
+    const int grid = nwork < num_sms ? nwork : num_sms;
     k_leaf_tc<<<grid, NUM_THREADS, smem, st>>>(L.prods, L.tiles, L.segs, L.ntiles,
                                                reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp,
-                                               L.ds, L.err, L.tile_ctr);
+                                               L.ds, L.err, L.tile_ctr, L.pieces, L.entries,
+                                               L.entries ? L.nentries : L.ntiles, L.part, L.part_ctr);
     return cudaGetLastError();
 }
 

@@ -59,7 +59,9 @@ class Timing(ctypes.Structure):
     _fields_ = [("prep_ms", ctypes.c_float), ("leaf_ms", ctypes.c_float),
                 ("post_ms", ctypes.c_float), ("total_ms", ctypes.c_float),
                 ("launches", ctypes.c_int32), ("leaf_launches", ctypes.c_int32),
-                ("field_macs", ctypes.c_double), ("tensor_macs", ctypes.c_double)]
+                ("field_macs", ctypes.c_double), ("tensor_macs", ctypes.c_double),
+                ("leaf_tiles", ctypes.c_int32), ("leaf_entries", ctypes.c_int32),
+                ("split_tiles", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
