@@ -232,9 +232,17 @@ ffsyrk_status_t ffsyrk_plan_selftest_timeout(ffsyrk_plan_t plan, int64_t limit_n
  * ffsyrk_digit_bounds(). */
 int32_t ffsyrk_leaf_schedule(uint32_t p, int32_t kblocks, int32_t *out, int32_t cap);
 
-/* The signed base-256 digit count D of p and the bound on |digit t| for
- * t < D (written to max_digit[0..D−1]).  Returns D, or −1. */
+/* The signed digit count D of p and the bound on |digit t| for t < D
+ * (written to max_digit[0..D−1]), for the digit base ffsyrk_digit_base(p).
+ * Returns D, or −1. */
 int32_t ffsyrk_digit_bounds(uint32_t p, int32_t *max_digit);
+
+/* The base of the signed digits the tensor-core leaf splits residues into:
+ * 256, except for two-digit primes above 2^16, where a balanced base b ≈ √p
+ * keeps both digits within b/2 ≤ 256 (for p = 131071: 362).  Digits are
+ * d_0 = s − b·round(s/b), d_1 = round(s/b) of the signed residue s.
+ * Returns the base, or −1 for an unsupported p. */
+int32_t ffsyrk_digit_base(uint32_t p);
 
 /* Human-readable name of a status code (static storage). */
 const char *ffsyrk_status_string(ffsyrk_status_t status);

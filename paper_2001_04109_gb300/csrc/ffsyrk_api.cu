@@ -65,13 +65,23 @@ DigitScheme make_digits(uint32_t p) {
         if (top <= 256) break;
     }
     ds.D = D;
+    ds.base = 256;
     for (int t = 0; t < D; ++t) ds.max_digit[t] = (t == D - 1) ? std::max(top, 1) : 128;
+    if (D == 2 && top > 128) {
+        // balanced base: the smallest even b whose rounded quotient of the
+        // largest |s| is at most b/2; then |d0| ≤ b/2 and |d1| ≤ round(H/b)
+        int64_t b = 2;
+        while ((H + b / 2) / b > b / 2) b += 2;
+        ds.base = (int)b;
+        ds.max_digit[0] = (int)(b / 2);
+        ds.max_digit[1] = (int)((H + b / 2) / b);
+    }
     for (int i = 0; i < D; ++i)
         for (int j = 0; j < D; ++j) {
             int64_t kc = (int64_t(1) << 24) / ((int64_t)ds.max_digit[i] * ds.max_digit[j]);
             ds.chunk_kb[i][j] = (int)std::max<int64_t>(1, kc / 64);
             uint64_t w = 1;
-            for (int e = 0; e < i + j; ++e) w = w * 256 % p;
+            for (int e = 0; e < i + j; ++e) w = w * (uint64_t)ds.base % p;
             ds.weight[i][j] = make_mul((uint32_t)w, p);
         }
     ds.offset = (uint32_t)(((uint64_t(1) << 24) + p - 1) / p * p);
@@ -243,12 +253,21 @@ namespace fsk {
 DigitScheme digit_scheme_for(uint32_t p) { return make_digits(p); }
 
 int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int cap) {
-    constexpr int kSpan = 16;
     constexpr int64_t kBound = int64_t(1) << 24;
     const int D = ds.D;
+    // span: at most 16 k-blocks and no longer than the shortest chunk, so
+    // that every pair takes one unit per span where its bound allows; the
+    // spans of one K are balanced (a ragged K such as 65 k-blocks becomes
+    // spans of 13 rather than 16, 16, 16, 16, 1: no pair gets a unit of one
+    // k-block, which would drain the accumulator after almost no MMA work)
+    int span = 16;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) span = std::min(span, std::max(1, ds.chunk_kb[i][j]));
+    const int nspans = kblocks > 0 ? (kblocks + span - 1) / span : 0;
     int count = 0;
-    for (int s0 = 0; s0 < kblocks; s0 += kSpan) {
-        const int s1 = std::min(kblocks, s0 + kSpan);
+    for (int sp = 0, s0 = 0; sp < nspans; ++sp) {
+        const int len = kblocks / nspans + (sp < kblocks % nspans ? 1 : 0);
+        const int s1 = s0 + len;
         for (int e = 0; e <= 2 * (D - 1); ++e) {
             int64_t used = 0;
             bool open = false;
@@ -272,6 +291,7 @@ int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int ca
                 }
             }
         }
+        s0 = s1;
     }
     return count;
 }
@@ -1105,14 +1125,13 @@ ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
     pl->device = dev;
     pl->sms = sms;
     pl->p = p;
-    pl->mp.p = p;
-    pl->mp.half = (p - 1) / 2;
-    pl->mp.barrett = (uint32_t)((uint64_t(1) << 32) / p);
+
     pl->ych = host::choose_y(p);
     pl->yc.form = pl->ych.form;
     pl->yc.a = make_mul((uint32_t)pl->ych.a, p);
     pl->yc.b = make_mul((uint32_t)pl->ych.b, p);
     pl->ds = make_digits(p);
+    pl->mp = make_modp(p, pl->ds);
     pl->leaf = (o.leaf == FFSYRK_LEAF_AUTO) ? FFSYRK_LEAF_TC_BF16 : o.leaf;
     pl->levels_opt = o.levels;
     pl->ctas_opt = o.tile_ctas;
@@ -1299,6 +1318,11 @@ int32_t ffsyrk_digit_bounds(uint32_t p, int32_t *max_digit) {
     return ds.D;
 }
 
+int32_t ffsyrk_digit_base(uint32_t p) {
+    if (validate_p(p) != FFSYRK_SUCCESS) return -1;
+    return make_digits(p).base;
+}
+
 ffsyrk_status_t ffsyrk_sync_status(ffsyrk_plan_t pl, ffsyrk_stream_t stream) {
     if (!pl) return FFSYRK_ERR_INVALID_ARG;
     cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
@@ -1453,10 +1477,8 @@ ffsyrk_status_t batch_state(int dev, uint32_t p, BatchState **out) {
     b->device = dev;
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     b->p = p;
-    b->mp.p = p;
-    b->mp.half = (p - 1) / 2;
-    b->mp.barrett = (uint32_t)((uint64_t(1) << 32) / p);
     b->ds = make_digits(p);
+    b->mp = make_modp(p, b->ds);
     if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess ||
         cudaHostAlloc(reinterpret_cast<void **>(&b->err_host), 16, cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer(reinterpret_cast<void **>(&b->err_dev), b->err_host, 0) != cudaSuccess) {

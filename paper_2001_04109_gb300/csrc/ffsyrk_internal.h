@@ -28,6 +28,8 @@ struct ModP {
     uint32_t p;
     uint32_t half;     // (p−1)/2: residues above it are negative in signed form
     uint32_t barrett;  // floor(2^32 / p)
+    uint32_t dbase;    // digit base of the tensor-core operands (see DigitScheme)
+    float dinv;        // 1 / dbase
 };
 
 // Multiplication by a constant w < p with Shoup's precomputed quotient
@@ -47,13 +49,33 @@ struct YConst {
 
 // Signed base-256 digits of the symmetric residue and the per-pair
 // chunk lengths that keep every FP32 partial sum an exact integer.
+// Residues in signed form s ∈ [−(p−1)/2, (p−1)/2] are written as
+// s = Σ_t d_t·base^t with D signed digits, every |d_t| ≤ 256 (exact in bf16).
+// The base is 256 (byte digits) unless D = 2 and the top byte digit would
+// exceed 128 (primes between 2^16 and 2^17): there a balanced base b ≈ √p
+// bounds both digits by b/2 ≤ 256, so that the worst digit pair, and with it
+// the shortest exact K-chunk, is no worse than the others (p = 131071:
+// base 362, digits ≤ 181, every pair 8 k-blocks per chunk instead of 4 for
+// the top pair of byte digits).
 struct DigitScheme {
     int D;
+    int base;                                  // 256, or the balanced base for D = 2
     int max_digit[kMaxDigits];                 // bound of |digit t|
     int chunk_kb[kMaxDigits][kMaxDigits];      // K-chunk per pair, in 64-wide k-blocks
-    MulConst weight[kMaxDigits][kMaxDigits];   // 256^(i+j) mod p
+    MulConst weight[kMaxDigits][kMaxDigits];   // base^(i+j) mod p
     uint32_t offset;                           // a multiple of p ≥ 2^24
 };
+
+// ModP of p with the digit base of ds.
+inline ModP make_modp(uint32_t p, const DigitScheme &ds) {
+    ModP m;
+    m.p = p;
+    m.half = (p - 1) / 2;
+    m.barrett = (uint32_t)((uint64_t(1) << 32) / p);
+    m.dbase = (uint32_t)ds.base;
+    m.dinv = 1.0f / (float)ds.base;
+    return m;
+}
 
 // A uint32 matrix view with virtual zero padding beyond (vr, vc).
 struct MatView {
@@ -136,10 +158,11 @@ struct LeafSeg {
     uint8_t ij;     // i << 4 | j
     uint8_t first;
 };
-// The schedule for one product with `kblocks` k-blocks: spans of 16
-// k-blocks; inside a span the weight classes e = i + j in order, the pairs
-// of a class in order; a unit grows while its worst-case |sum|
-// Σ 64·nkb·max|d_i|·max|d_j| stays ≤ 2^24 and never crosses a class.
+// The schedule for one product with `kblocks` k-blocks: balanced spans of
+// at most min(16, shortest chunk) k-blocks; inside a span the weight classes
+// e = i + j in order, the pairs of a class in order; a unit grows while its
+// worst-case |sum| Σ 64·nkb·max|d_i|·max|d_j| stays ≤ 2^24 and never crosses
+// a class.
 void build_segments(const DigitScheme &ds, int kblocks, std::vector<LeafSeg> &out);
 // The same into a caller's buffer of `cap` entries: the count, or −1 if it does not fit.
 int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int cap);

@@ -123,10 +123,7 @@ extern "C" ffsyrk_status_t ffsyrk_noalloc(ffsyrk_uplo_t uplo, int64_t n, int64_t
     unsigned char *hdr = ds_dev->scratch;
     unsigned char *planes = ds_dev->scratch + kHeaderBytes;
 
-    ModP mp;
-    mp.p = p;
-    mp.half = (p - 1) / 2;
-    mp.barrett = (uint32_t)((uint64_t(1) << 32) / p);
+    const ModP mp = make_modp(p, ds);
 
     Arena a;
     a.base = planes;

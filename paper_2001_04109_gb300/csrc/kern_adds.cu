@@ -57,6 +57,23 @@ __device__ __forceinline__ int sbyte(int s) {
     asm("bfe.s32 %0, %1, 0, 8;" : "=r"(d) : "r"(s));
     return d;
 }
+// Low signed digit of s in the scheme's base, leaving the rest in s.  Byte
+// digits (base 256) are the low byte read as signed; for a balanced base b
+// (two digits, |s| ≤ (p−1)/2 < 2^16, |s/b| < 182) the quotient is rounded to
+// nearest: the float quotient s·(1/b) is off by less than 182·2^-23 < 2^-15,
+// far less than the distance 1/b from a tie to any other value, so
+// |digit| ≤ b/2 holds.
+__device__ __forceinline__ int low_digit(int &s, const ModP &m) {
+    if (m.dbase == 256u) {
+        const int d = sbyte(s);
+        s = (s - d) >> 8;
+        return d;
+    }
+    const int q = __float2int_rn(__int2float_rn(s) * m.dinv);
+    const int d = s - (int)m.dbase * q;
+    s = q;
+    return d;
+}
 
 template <int YF>
 __device__ __forceinline__ void ymul(const YConst &y, uint32_t t0, uint32_t t1, uint32_t &o0,
@@ -91,7 +108,7 @@ __device__ __forceinline__ void ld_view4(const MatView &v, bool vec_ok, int64_t 
 // plane (bf16) or one 16-byte store (uint32).
 template <int D, bool U32>
 __device__ __forceinline__ void put4(const OperandDst &d, int64_t r, int64_t c, const uint32_t (&v)[4],
-                                     uint32_t half, uint32_t p) {
+                                     const ModP &m) {
     if (d.arena == nullptr) return;
     if constexpr (U32) {
         *reinterpret_cast<uint4 *>(static_cast<uint32_t *>(d.arena) + (d.row0 + r) * d.kpad + c) =
@@ -99,7 +116,7 @@ __device__ __forceinline__ void put4(const OperandDst &d, int64_t r, int64_t c, 
     } else {
         int sv[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) sv[e] = v[e] > half ? (int)v[e] - (int)p : (int)v[e];
+        for (int e = 0; e < 4; ++e) sv[e] = v[e] > m.half ? (int)v[e] - (int)m.p : (int)v[e];
         uint32_t *base = static_cast<uint32_t *>(d.arena);
 #pragma unroll
         for (int t = 0; t < D; ++t) {
@@ -111,10 +128,8 @@ __device__ __forceinline__ void put4(const OperandDst &d, int64_t r, int64_t c, 
                     d0 = sv[e];
                     d1 = sv[e + 1];
                 } else {
-                    d0 = sbyte(sv[e]);
-                    d1 = sbyte(sv[e + 1]);
-                    sv[e] = (sv[e] - d0) >> 8;
-                    sv[e + 1] = (sv[e + 1] - d1) >> 8;
+                    d0 = low_digit(sv[e], m);
+                    d1 = low_digit(sv[e + 1], m);
                 }
                 w[e / 2] = __byte_perm(small_int_f32_bits(d0), small_int_f32_bits(d1), 0x7632);
             }
@@ -183,13 +198,13 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restric
                 s3[e] = subm(s1[e], x22[e], p);                 // S3 = S1 − A22
                 s4[e] = addm(s3[e], x12[e], p);                 // S4 = S3 + A12
             }
-            put4<D, U32>(nd.gemm[0], r, c, x22, half, p);
-            put4<D, U32>(nd.gemm[1], r, c, s4, half, p);
-            put4<D, U32>(nd.gemm[2], r, c, s1, half, p);
-            put4<D, U32>(nd.gemm[3], r, c, s2, half, p);
-            put4<D, U32>(nd.leaf[0], r, c, x11, half, p);
-            put4<D, U32>(nd.leaf[1], r, c, x12, half, p);
-            put4<D, U32>(nd.leaf[2], r, c, s3, half, p);
+            put4<D, U32>(nd.gemm[0], r, c, x22, m);
+            put4<D, U32>(nd.gemm[1], r, c, s4, m);
+            put4<D, U32>(nd.gemm[2], r, c, s1, m);
+            put4<D, U32>(nd.gemm[3], r, c, s2, m);
+            put4<D, U32>(nd.leaf[0], r, c, x11, m);
+            put4<D, U32>(nd.leaf[1], r, c, x12, m);
+            put4<D, U32>(nd.leaf[2], r, c, s3, m);
             if (nd.s3 != nullptr && inside) {
                 uint32_t *dst = nd.s3 + r * nd.s3_ld + c;
                 if (((reinterpret_cast<uintptr_t>(dst)) & 15u) == 0)
@@ -221,7 +236,7 @@ __device__ __forceinline__ void ld_view8(const MatView &v, bool vec_ok, int64_t 
 // 16-byte store per digit plane (bf16) or two (uint32).
 template <int D, bool U32>
 __device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, const uint32_t (&v)[8],
-                                     uint32_t half, uint32_t p) {
+                                     const ModP &m) {
     if constexpr (U32) {
         uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(d.arena) + (d.row0 + r) * d.kpad + c);
         dst[0] = make_uint4(v[0], v[1], v[2], v[3]);
@@ -229,7 +244,7 @@ __device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, 
     } else {
         int sv[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) sv[e] = v[e] > half ? (int)v[e] - (int)p : (int)v[e];
+        for (int e = 0; e < 8; ++e) sv[e] = v[e] > m.half ? (int)v[e] - (int)m.p : (int)v[e];
         uint32_t *base = static_cast<uint32_t *>(d.arena);
 #pragma unroll
         for (int t = 0; t < D; ++t) {
@@ -241,10 +256,8 @@ __device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, 
                     d0 = sv[e];
                     d1 = sv[e + 1];
                 } else {
-                    d0 = sbyte(sv[e]);
-                    d1 = sbyte(sv[e + 1]);
-                    sv[e] = (sv[e] - d0) >> 8;
-                    sv[e + 1] = (sv[e + 1] - d1) >> 8;
+                    d0 = low_digit(sv[e], m);
+                    d1 = low_digit(sv[e + 1], m);
                 }
                 w[e / 2] = __byte_perm(small_int_f32_bits(d0), small_int_f32_bits(d1), 0x7632);
             }
@@ -278,7 +291,7 @@ __global__ void __launch_bounds__(DIG_THREADS) k_digitize(const DigitizeJob *__r
             if (r >= jb.rows) break;
 #pragma unroll
             for (int e = 0; e < 8; ++e) v[i][e] = red(v[i][e], m);
-            put8<D, U32>(jb.dst, r, c, v[i], m.half, m.p);
+            put8<D, U32>(jb.dst, r, c, v[i], m);
         }
     }
 }
@@ -312,7 +325,7 @@ __global__ void __launch_bounds__(DIG_THREADS) k_digitize_flat(const DigitizeJob
         if (r >= jb.rows) break;
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[i][e] = red(v[i][e], m);
-        put8<D, U32>(jb.dst, r, c, v[i], m.half, m.p);
+        put8<D, U32>(jb.dst, r, c, v[i], m);
     }
 }
 

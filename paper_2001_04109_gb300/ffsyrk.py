@@ -31,7 +31,7 @@ EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsy
            "ffsyrk", "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
            "ffsyrk_plan_set_timing", "ffsyrk_plan_get_timing", "ffsyrk_status_string",
            "ffsyrk_version", "ffsyrk_noalloc", "ffsyrk_leaf_schedule", "ffsyrk_digit_bounds",
-           "ffsyrk_plan_selftest_timeout"]
+           "ffsyrk_digit_base", "ffsyrk_plan_selftest_timeout"]
 
 
 class FfsyrkError(RuntimeError):
@@ -101,6 +101,8 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_leaf_schedule.restype = i32
             L.ffsyrk_digit_bounds.argtypes = [u32, P(i32)]
             L.ffsyrk_digit_bounds.restype = i32
+            L.ffsyrk_digit_base.argtypes = [u32]
+            L.ffsyrk_digit_base.restype = i32
             for name in ["ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan", "ffsyrk",
                          "ffsyrk_noalloc",
                          "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
@@ -218,12 +220,20 @@ def leaf_schedule(p: int, kblocks: int) -> list[tuple[int, int, int, int, bool]]
 
 
 def digit_bounds(p: int) -> list[int]:
-    """Bounds on |digit t| of the signed base-256 split of residues mod p."""
+    """Bounds on |digit t| of the signed digit split of residues mod p (base: digit_base)."""
     out = (ctypes.c_int32 * 3)()
     D = lib().ffsyrk_digit_bounds(int(p), out)
     if D < 0:
         raise ValueError("bad p")
     return [out[t] for t in range(D)]
+
+
+def digit_base(p: int) -> int:
+    """Base of the signed digit split of residues mod p (256, or balanced ≈ √p)."""
+    b = lib().ffsyrk_digit_base(int(p))
+    if b < 0:
+        raise ValueError("bad p")
+    return b
 
 
 def syrk(A: torch.Tensor, p: int, uplo: str = "lower", C: torch.Tensor | None = None,

@@ -18,30 +18,45 @@ def built():
     __graft_entry__.build()
 
 
-def balanced_digits(s, D):
+def balanced_digits(s, D, b):
+    """Signed digits of s in base b, each low digit in [−b/2, b/2)."""
     out = []
     for _ in range(D - 1):
-        lo = ((s + 128) % 256) - 128
+        lo = ((s + b // 2) % b) - b // 2
         out.append(lo)
-        s = (s - lo) // 256
+        s = (s - lo) // b
     out.append(s)
     return out
 
 
-@pytest.mark.parametrize("p", [3, 251, 257, 65521, 131071, 131041, 8388593, 16777213])
+@pytest.mark.parametrize("p", [3, 251, 257, 65521, 65537, 131071, 131041, 8388593, 16777213])
 def test_digit_bounds_cover_every_residue(p):
     bounds = ffsyrk.digit_bounds(p)
+    b = ffsyrk.digit_base(p)
     D = len(bounds)
     h = (p - 1) // 2
     samples = range(-h, h + 1) if p < 300000 else list(range(-h, -h + 70000)) + list(range(h - 70000, h + 1))
     seen = [0] * D
     for s in samples:
-        d = balanced_digits(s, D)
-        assert sum(dt * 256 ** t for t, dt in enumerate(d)) == s
+        d = balanced_digits(s, D, b)
+        assert sum(dt * b ** t for t, dt in enumerate(d)) == s
         for t in range(D):
             assert abs(d[t]) <= bounds[t] <= 256
             seen[t] = max(seen[t], abs(d[t]))
     assert seen == bounds  # tight
+
+
+@pytest.mark.parametrize("p,base,bounds", [(65521, 256, [128, 128]), (131071, 362, [181, 181]),
+                                           (8388593, 256, [128, 128, 64]), (251, 256, [125])])
+def test_digit_base_balances_the_two_digit_primes_above_2_16(p, base, bounds):
+    # below 2^16 byte digits are already balanced; p = 131071 with bytes would
+    # need a top digit of 256 (chunks of 4 k-blocks for the top pair), the
+    # balanced base 362 bounds both digits by 181 (8 k-blocks for every pair)
+    assert ffsyrk.digit_base(p) == base
+    assert ffsyrk.digit_bounds(p) == bounds
+    if base != 256:
+        assert all(nkb <= 8 for *_, nkb, _ in ffsyrk.leaf_schedule(p, 64))
+        assert min(nkb for *_, nkb, first in ffsyrk.leaf_schedule(p, 64) if first) >= 4
 
 
 @pytest.mark.parametrize("p", [251, 65521, 131071, 8388593])
