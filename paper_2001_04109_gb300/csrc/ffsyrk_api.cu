@@ -85,6 +85,9 @@ DigitScheme make_digits(uint32_t p) {
             ds.weight[i][j] = make_mul((uint32_t)w, p);
         }
     ds.offset = (uint32_t)(((uint64_t(1) << 24) + p - 1) / p * p);
+    // sums start below 2p and grow by less than 2p per unit: m units fit
+    // while 2p·(m + 1) ≤ 2^32
+    ds.lazy_units = (int)std::min<uint64_t>(1u << 20, (uint64_t(1) << 32) / (2ull * p) - 1);
     return ds;
 }
 
@@ -177,6 +180,7 @@ struct Descs {
     std::vector<LeafPiece> pieces;
     std::vector<int32_t> entries;
     int nslots = 0;
+    int max_units = 0;  // most accumulator drains of any product's K schedule
     int64_t digit_max_rows = 0, digit_max_kpad = 0;
     // blob offsets (bytes) inside the descriptor region
     int64_t prep_off[kMaxLevels] = {}, post_off[kMaxLevels] = {};
@@ -251,6 +255,12 @@ EncodeTiledFn get_encode_fn() {
 
 namespace fsk {
 DigitScheme digit_scheme_for(uint32_t p) { return make_digits(p); }
+
+int count_units(const LeafSeg *segs, int nseg) {
+    int u = 0;
+    for (int i = 0; i < nseg; ++i) u += segs[i].first ? 1 : 0;
+    return u;
+}
 
 int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int cap) {
     constexpr int64_t kBound = int64_t(1) << 24;
@@ -666,6 +676,8 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         }
     }
     attach_segments(pl->ds, D.prods, D.segs);
+    for (const LeafProd &pr : D.prods)
+        D.max_units = std::max(D.max_units, count_units(D.segs.data() + pr.seg0, pr.nseg));
     // longest tiles first, then round-robin over persistent CTAs
     std::stable_sort(D.tiles.begin(), D.tiles.end(),
                      [](const LeafTile &a, const LeafTile &b) { return a.cost > b.cost; });
@@ -761,6 +773,7 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
         tl.tiles = reinterpret_cast<const LeafTile *>(dd + D.tiles_off);
         tl.segs = reinterpret_cast<const LeafSeg *>(dd + D.segs_off);
         tl.ntiles = (int)D.tiles.size();
+        tl.max_units = D.max_units;
         tl.tmaps = dd + D.tmap_off;
         tl.mp = pl->mp;
         tl.ds = pl->ds;
@@ -1394,7 +1407,7 @@ struct BatchState {
         int64_t jobs_off = 0, prods_off = 0, tiles_off = 0, tmap_off = 0, aptr_off = 0,
                 akpad_off = 0, ctr_off = 0, segs_off = 0;
         int64_t off = 0;  // arenas end, blob start
-        int njobs = 0, ntiles = 0;
+        int njobs = 0, ntiles = 0, max_units = 0;
         int64_t max_rows = 0, max_kpad = 0, digit_blocks = 0;
     } last;
     cudaStream_t cap_stream = nullptr;
@@ -1419,6 +1432,7 @@ cudaError_t batch_issue(BatchState *b, cudaStream_t st) {
         tl.tiles = reinterpret_cast<const LeafTile *>(dd + L.tiles_off);
         tl.segs = reinterpret_cast<const LeafSeg *>(dd + L.segs_off);
         tl.ntiles = L.ntiles;
+        tl.max_units = L.max_units;
         tl.tmaps = dd + L.tmap_off;
         tl.mp = b->mp;
         tl.ds = b->ds;
@@ -1616,6 +1630,8 @@ extern "C" ffsyrk_status_t ffsyrk_batched(ffsyrk_uplo_t uplo, int64_t count, con
                      [](const LeafTile &x, const LeafTile &y) { return x.cost > y.cost; });
     std::vector<LeafSeg> segs;
     attach_segments(b->ds, prods, segs);
+    int max_units = 0;
+    for (const LeafProd &pr : prods) max_units = std::max(max_units, count_units(segs.data() + pr.seg0, pr.nseg));
     // blob layout after the arenas
     int64_t boff = 0;
     auto slot = [&](int64_t bytes, int64_t align) {
@@ -1693,6 +1709,7 @@ extern "C" ffsyrk_status_t ffsyrk_batched(ffsyrk_uplo_t uplo, int64_t count, con
     L.off = off;
     L.njobs = (int)jobs.size();
     L.ntiles = (int)tiles.size();
+    L.max_units = max_units;
     L.max_rows = max_rows;
     L.max_kpad = max_kpad;
     L.digit_blocks = digit_blocks;

@@ -64,6 +64,7 @@ struct DigitScheme {
     int chunk_kb[kMaxDigits][kMaxDigits];      // K-chunk per pair, in 64-wide k-blocks
     MulConst weight[kMaxDigits][kMaxDigits];   // base^(i+j) mod p
     uint32_t offset;                           // a multiple of p ≥ 2^24
+    int lazy_units;  // units the epilogue may add (each < 2p) before its uint32 sums need a reduction
 };
 
 // ModP of p with the digit base of ds.
@@ -227,7 +228,10 @@ struct TcLaunch {
     int nentries;
     uint32_t *part;           // partial-result slots, BM·BN residues each
     unsigned int *part_ctr;   // 8 per split tile, zero before the first launch
+    int max_units;            // most units (accumulator drains) of any tile's K schedule
 };
+// Units (segments that open an accumulator) of a K schedule.
+int count_units(const LeafSeg *segs, int nseg);
 cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st);
 int leaf_tc_bm();
 int leaf_tc_bn();

@@ -179,6 +179,7 @@ extern "C" ffsyrk_status_t ffsyrk_noalloc(ffsyrk_uplo_t uplo, int64_t n, int64_t
     tl.tiles = reinterpret_cast<const LeafTile *>(hdr + kTileOff);
     tl.segs = reinterpret_cast<const LeafSeg *>(hdr + kSegOff);
     tl.ntiles = (int)nt;
+    tl.max_units = count_units(reinterpret_cast<const LeafSeg *>(g_stage + kSegOff), nseg);
     tl.tmaps = hdr + kTmapOff;
     tl.mp = mp;
     tl.ds = ds;

@@ -54,6 +54,36 @@ constexpr int TMEM_COLS = 512;
 constexpr uint32_t IDESC = tc::idesc_bf16(BM, BN);
 using namespace tc;
 
+// Running sums of the epilogue are reduced lazily: Barrett with
+// floor(2^32 / p) brings any uint32 sum into [0, 2p).
+__device__ __forceinline__ uint32_t reduce_2p(uint32_t x, uint32_t p, uint32_t barrett) {
+    return x - __umulhi(x, barrett) * p;
+}
+__device__ __forceinline__ uint32_t final_mod(uint32_t x, uint32_t p) { return x >= p ? x - p : x; }
+
+// One epilogue thread's 128 residues (sums below 2p) to a row at dst, where
+// dst + E0 is the first 16-byte aligned address: E0 leading scalar stores,
+// 16-byte stores, then the remaining scalars.
+template <int E0>
+__device__ __forceinline__ void store_row(uint32_t *dst, const uint32_t (&acc)[EPI_COLS], uint32_t p) {
+#pragma unroll
+    for (int e = 0; e < E0; ++e) dst[e] = final_mod(acc[e], p);
+    constexpr int NV = (EPI_COLS - E0) / 4;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const int e = E0 + 4 * v;
+        *reinterpret_cast<uint4 *>(dst + e) = make_uint4(final_mod(acc[e], p), final_mod(acc[e + 1], p),
+                                                         final_mod(acc[e + 2], p), final_mod(acc[e + 3], p));
+    }
+#pragma unroll
+    for (int e = E0 + 4 * NV; e < EPI_COLS; ++e) dst[e] = final_mod(acc[e], p);
+}
+
+// LAZY: no tile of the launch has more units than ds.lazy_units, so the
+// running sums may grow unreduced (one add per unit and element) and are
+// brought below 2p once, before the store; otherwise every unit's add is
+// followed by a conditional subtract that keeps them below 2p.
+template <bool LAZY>
 __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__restrict__ prods,
                                                              const LeafTile *__restrict__ tiles,
                                                              const LeafSeg *__restrict__ segs,
@@ -242,7 +272,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
             if (t < 0) break;
             const LeafTile tl = tiles[t];
             const LeafProd pr = prods[tl.prod];
-            uint32_t acc[EPI_COLS];
+            uint32_t acc[EPI_COLS];  // running sums of the tile row's residues
 #pragma unroll
             for (int e = 0; e < EPI_COLS; ++e) acc[e] = 0;
             int lo = 0, hi = 0;  // 16-column chunks of this warp that hold stored entries
@@ -277,14 +307,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
                         const uint32_t a = (uint32_t)(xi + (int)off);
                         const uint32_t q = __umulhi(a, wsh);
                         const uint32_t r = a * w - q * p;  // [0, 2p)
-                        const uint32_t s = acc[cc * LD_COLS + e] + r;
-                        acc[cc * LD_COLS + e] = min(s, s - twop);
+                        if constexpr (LAZY) {
+                            acc[cc * LD_COLS + e] += r;
+                        } else {
+                            const uint32_t s = acc[cc * LD_COLS + e] + r;
+                            acc[cc * LD_COLS + e] = min(s, s - twop);
+                        }
                     }
                 }
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acce_bar[b]);
                 ++unit;
+            }
+            if constexpr (LAZY) {
+#pragma unroll
+                for (int e = 0; e < EPI_COLS; ++e) acc[e] = reduce_2p(acc[e], p, m.barrett);
             }
             if (!ok) break;
             const LeafPiece pc = pieces ? pieces[t] : LeafPiece{0, 0, -1, 0, 1};
@@ -336,16 +374,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
                 const bool all_cols = c0 + EPI_COLS <= pr.cols;
                 const bool tri_ok = pr.tri == 0 || (pr.tri == 1 && c0 + EPI_COLS - 1 <= r) ||
                                     (pr.tri == 2 && c0 >= r);
-                const bool aligned = ((reinterpret_cast<uintptr_t>(orow + c0) & 15u) == 0);
-                if (all_cols && tri_ok && aligned) {
-#pragma unroll
-                    for (int e = 0; e < EPI_COLS; e += 4) {
-                        uint4 v4;
-                        v4.x = acc[e] >= p ? acc[e] - p : acc[e];
-                        v4.y = acc[e + 1] >= p ? acc[e + 1] - p : acc[e + 1];
-                        v4.z = acc[e + 2] >= p ? acc[e + 2] - p : acc[e + 2];
-                        v4.w = acc[e + 3] >= p ? acc[e + 3] - p : acc[e + 3];
-                        *reinterpret_cast<uint4 *>(orow + c0 + e) = v4;
+                if (all_cols && tri_ok) {
+                    // rows of an odd ldc start at any 4-byte offset
+                    uint32_t *dst = orow + c0;
+                    switch ((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u) {
+                        case 0: store_row<0>(dst, acc, p); break;
+                        case 1: store_row<3>(dst, acc, p); break;
+                        case 2: store_row<2>(dst, acc, p); break;
+                        default: store_row<1>(dst, acc, p); break;
                     }
                 } else {
 #pragma unroll
@@ -405,16 +441,19 @@ cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st) {
     const int smem = STAGES * STAGE_BYTES + 1024;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_leaf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_leaf_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     const int nwork = L.entries ? L.nentries : L.ntiles;
     const int grid = nwork < num_sms ? nwork : num_sms;
-    k_leaf_tc<<<grid, NUM_THREADS, smem, st>>>(L.prods, L.tiles, L.segs, L.ntiles,
-                                               reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp,
-                                               L.ds, L.err, L.tile_ctr, L.pieces, L.entries,
-                                               L.entries ? L.nentries : L.ntiles, L.part, L.part_ctr);
+    auto kern = L.max_units <= L.ds.lazy_units ? k_leaf_tc<true> : k_leaf_tc<false>;
+    kern<<<grid, NUM_THREADS, smem, st>>>(L.prods, L.tiles, L.segs, L.ntiles,
+                                          reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp, L.ds,
+                                          L.err, L.tile_ctr, L.pieces, L.entries,
+                                          L.entries ? L.nentries : L.ntiles, L.part, L.part_ctr);
     return cudaGetLastError();
 }
 
