@@ -57,12 +57,22 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def kernel_source_hash(kernel_file: str):
+    """sha256 (16 hex digits) of the kernel's source and the device helpers it includes."""
+    csrc = os.path.join(ROOT, "paper_2001_04109_gb300", "csrc")
+    h = hashlib.sha256()
+    try:
+        for name in (kernel_file, "tc_common.cuh"):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    except OSError:
+        return None
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(kernel_file: str, workload: str):
     """dram bytes per launch recorded under profiles/ for this kernel source, else None."""
-    src = os.path.join(ROOT, "paper_2001_04109_gb300", "csrc", kernel_file)
-    try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
+    h = kernel_source_hash(kernel_file)
+    if h is None:
         return None
     prof = os.path.join(ROOT, "profiles")
     if not os.path.isdir(prof):

@@ -1,0 +1,100 @@
+"""Full-size parity in the benchmark's launch configuration (marked gpu).
+
+Every workload the benchmark times, at its full size, with the same inputs
+(seed 2), plan options (default depth rule, one-SM tiles) and entry point:
+sampled output rows -- first and last rows, tile boundaries, rows of every
+tile band, near-diagonal entries -- against the oracle computed row by row.
+The classical path (depth 0) is checked next to the fast one where the
+benchmark compares them.  The batch of 2048 uneven problems is checked on a
+seeded sample of whole problems.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2001_04109_gb300 import ffsyrk, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def sample_rows(n, count, seed):
+    fixed = [0, 1, 127, 128, 255, 256, n // 2, n - 2, n - 1]
+    rng = np.random.default_rng(seed)
+    rows = set(r for r in fixed if 0 <= r < n)
+    rows.update(int(r) for r in rng.integers(0, n, size=count))
+    return np.array(sorted(rows), dtype=np.int64)
+
+
+def check_rows(A_host, p, C_dev, rows):
+    want = oracle.syrk_rows(A_host.numpy(), p, rows)
+    got = C_dev[torch.from_numpy(rows).cuda()].cpu().numpy().view(np.uint32)
+    for t, r in enumerate(rows):
+        bad = np.flatnonzero(got[t, : r + 1] != want[t, : r + 1])
+        assert bad.size == 0, f"row {r}: {bad.size} entries differ (first at column {bad[0]})"
+
+
+# (n, k, p, depths): the benchmark's workloads; None = the default depth rule
+WORKLOADS = [
+    (256, 256, 65521, [0]),
+    (4096, 4096, 65521, [None, 1]),
+    (8192, 8192, 65521, [0, 1]),
+    (16384, 4096, 131071, [None, 1]),
+    (4096, 16384, 131071, [None, 1]),
+    (16383, 4097, 131071, [None, 1]),
+    (16384, 16384, 65521, [None]),
+]
+
+
+@pytest.mark.parametrize("n,k,p,depths", WORKLOADS, ids=[f"{n}x{k}_p{p}" for n, k, p, _ in WORKLOADS])
+def test_workload_sampled_rows(n, k, p, depths):
+    A = inputs.uniform_residues(n, k, p, seed=2, device="cuda")  # the same matrix on any device
+    A_host = A.cpu()
+    rows = sample_rows(n, 24, seed=n + k)
+    for levels in depths:
+        C = torch.zeros((n, n), dtype=torch.int32, device="cuda")
+        plan = ffsyrk.Plan(p, n, k, levels=levels)
+        plan(A, C)
+        plan.sync_status()
+        check_rows(A_host, p, C, rows)
+        plan.close()
+        del C
+    torch.cuda.empty_cache()
+
+
+def test_large_d3_three_levels_sampled_rows():
+    # A 32768×32768 (4 GiB), p = 8388593: three digits, the depth the benchmark times
+    n = k = 32768
+    p = 8388593
+    A = inputs.uniform_residues(n, k, p, seed=2, device="cuda")
+    A_host = A.cpu()
+    C = torch.zeros((n, n), dtype=torch.int32, device="cuda")
+    plan = ffsyrk.Plan(p, n, k, levels=3)
+    plan(A, C)
+    plan.sync_status()
+    check_rows(A_host, p, C, sample_rows(n, 6, seed=7))
+    plan.close()
+    del A, C
+    torch.cuda.empty_cache()
+
+
+def test_batched_2048_uneven_sampled_problems():
+    p, seed = 65521, 5
+    shapes = inputs.batch_shapes(2048, 32, 2048, seed)
+    As = [inputs.uniform_residues(n, k, p, seed=seed * 100000 + t, device="cuda")
+          for t, (n, k) in enumerate(shapes)]
+    Cs = ffsyrk.batched(As, p)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    picks = sorted(set(int(t) for t in rng.integers(0, len(shapes), size=12)) |
+                   {int(np.argmin([n * n * k for n, k in shapes])), int(np.argmax([n for n, _ in shapes]))})
+    for t in picks:
+        n, _ = shapes[t]
+        rows = sample_rows(n, 16, seed=t)
+        check_rows(As[t].cpu(), p, Cs[t], rows)
