@@ -803,8 +803,10 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
     if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
     if (timed) cudaEventRecord(pl->ev[2], st);
     for (int d = g.L - 1; d >= 0; --d) {
+        bool upper = false;
+        for (const PostNode &pn : D.post[d]) upper = upper || pn.upper;
         e = launch_post(reinterpret_cast<const PostNode *>(dd + D.post_off[d]),
-                        (int)D.post[d].size(), g.h[d + 1], pl->mp, st);
+                        (int)D.post[d].size(), g.h[d + 1], pl->mp, st, upper);
         if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
     }
     if (timed) {

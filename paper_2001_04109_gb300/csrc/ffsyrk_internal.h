@@ -203,8 +203,10 @@ cudaError_t launch_digitize_flat(const DigitizeJob *jobs_dev, int njobs, int64_t
                                  ModP mp, DigitScheme ds, int arena_kind, cudaStream_t st);
 // blocks one job needs in launch_digitize_flat
 int64_t digitize_flat_blocks(int64_t rows, int64_t kpad);
+// upper: a node writes the upper triangle (transposed); otherwise the
+// fused one-pass kernel over lower tile pairs runs
 cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP mp,
-                        cudaStream_t st);
+                        cudaStream_t st, bool upper);
 cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st);
 cudaError_t launch_leaf_i64_arrays(const LeafProd *prods_dev, const LeafTile *tiles_dev,
                                    int ntiles, const uint32_t *const *arenas_dev,

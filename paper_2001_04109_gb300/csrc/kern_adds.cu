@@ -457,6 +457,128 @@ __global__ void __launch_bounds__(256) k_post(const PostNode *__restrict__ nodes
     }
 }
 
+// Post-additions for the lower triangle, one 64×64 tile pair per block:
+// block (I, J), J ≤ I, reads P1, P2, P5 at (I, J) and P3, P4 at (I, J) and
+// (J, I) -- every product entry exactly once -- and writes C11 = Low(U3) and
+// C22 = Low(U5) at (I, J) and C21 = U4 at (I, J) and (J, I).  The transposed
+// operands, Up(U1) = Low(U1)ᵀ for C21 above the diagonal and P4ᵀ for U5,
+// come from the same tiles through shared memory.  Grid: x = I·(I+1)/2 + J
+// over the lower tile triangle, y = node.
+constexpr int FT = 64;  // fused post tile
+__device__ __forceinline__ void ld4c(const uint32_t *base, int64_t ld, int64_t i, int64_t j, int64_t h,
+                                     uint32_t (&x)[4]) {
+    if (i < h && j < h) {  // h and j are multiples of 4
+        const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(base + i * ld + j));
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    } else {
+        x[0] = x[1] = x[2] = x[3] = 0u;
+    }
+}
+__device__ __forceinline__ void st4(uint32_t *out, int64_t ldo, int64_t cend, int64_t R, int64_t Cc,
+                                    const uint32_t (&v)[4], bool lower_only) {
+    // row R, columns Cc..Cc+3 of the result; only c < cend and (lower_only: c ≤ R)
+    uint32_t *row = out + R * ldo;
+    const bool full = Cc + 3 < cend && (!lower_only || Cc + 3 <= R) &&
+                      ((reinterpret_cast<uintptr_t>(row + Cc) & 15u) == 0);
+    if (full) {
+        *reinterpret_cast<uint4 *>(row + Cc) = make_uint4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (Cc + e < cend && (!lower_only || Cc + e <= R)) row[Cc + e] = v[e];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_post_fused(const PostNode *__restrict__ nodes, int64_t h,
+                                                    ModP m) {
+    __shared__ uint32_t sU[FT][FT + 1];   // U1 = P1 + P5 of tile (I, J), for its transpose
+    __shared__ uint32_t sP4[FT][FT + 1];  // P4 of tile (J, I), for P4ᵀ
+    const PostNode &nd = nodes[blockIdx.y];
+    // lower tile triangle: x = I(I+1)/2 + J
+    const int64_t x = blockIdx.x;
+    int64_t I = (int64_t)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
+    while ((I + 1) * (I + 2) / 2 <= x) ++I;
+    while (I * (I + 1) / 2 > x) --I;
+    const int64_t J = x - I * (I + 1) / 2;
+    const bool diag = I == J;
+    const int tid = threadIdx.x;
+    const int tr = tid >> 4, tc = 4 * (tid & 15);  // rows tr + 16q, columns tc..tc+3
+    const uint32_t p = m.p;
+    const int64_t iI = I * FT, iJ = J * FT;
+    uint32_t u1[4][4], p4[4][4], p3[4][4], c11[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = tr + 16 * q;
+        uint32_t a[4], b[4], c[4];
+        ld4c(nd.P1, nd.ldr, iI + r, iJ + tc, h, a);
+        ld4c(nd.P5, nd.ldr, iI + r, iJ + tc, h, b);
+        ld4c(nd.P2, nd.ldr, iI + r, iJ + tc, h, c);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            u1[q][e] = a[e] + b[e];  // < 2p
+            c11[q][e] = addm(a[e], c[e], p);
+            sU[r][tc + e] = u1[q][e];
+        }
+        ld4c(nd.P3, nd.ldg, iI + r, iJ + tc, h, p3[q]);
+        ld4c(nd.P4, nd.ldg, iI + r, iJ + tc, h, p4[q]);
+    }
+    uint32_t p4t[4][4], p3t[4][4];  // tile (J, I), direct layout
+    if (diag) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) sP4[tr + 16 * q][tc + e] = p4[q][e];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = tr + 16 * q;
+            ld4c(nd.P4, nd.ldg, iJ + r, iI + tc, h, p4t[q]);
+            ld4c(nd.P3, nd.ldg, iJ + r, iI + tc, h, p3t[q]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) sP4[r][tc + e] = p4t[q][e];
+        }
+    }
+    __syncthreads();
+    // quadrant row/column offsets in the 2h×2h result
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = tr + 16 * q;
+        const int64_t i = iI + r;
+        if (i >= h) continue;
+        uint32_t o21[4], o22[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int c = tc + e;
+            // U1 at (i, iJ + c): the lower half directly, the upper half of a
+            // diagonal tile from the mirrored entry
+            const uint32_t u = (!diag || c <= r) ? u1[q][e] : sU[c][r];
+            o21[e] = red(u + p4[q][e] + p3[q][e], m);          // U4 = U1 + P4 + P3
+            o22[e] = red(u + p4[q][e] + sP4[c][r], m);         // U5 = U1 + P4 + P4ᵀ
+        }
+        // the quadrants end at column h (C11, C21) and 2h (C22); the result
+        // has vn rows and columns
+        const int64_t c_lo = h < nd.vn ? h : nd.vn, c_hi = 2 * h < nd.vn ? 2 * h : nd.vn;
+        if (i < nd.vn) st4(nd.out, nd.ldo, c_lo, i, iJ + tc, c11[q], diag);     // C11 = Low(U3)
+        if (h + i < nd.vn) {
+            st4(nd.out, nd.ldo, c_lo, h + i, iJ + tc, o21, false);               // C21 = U4
+            st4(nd.out, nd.ldo, c_hi, h + i, h + iJ + tc, o22, diag);            // C22 = Low(U5)
+        }
+    }
+    if (!diag) {
+        // C21 at (J, I): Up(U1) there is the transpose of U1 at (I, J)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = tr + 16 * q;
+            const int64_t i = iJ + r;
+            if (i >= h) continue;
+            uint32_t o[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) o[e] = red(sU[tc + e][r] + p4t[q][e] + p3t[q][e], m);
+            if (h + i < nd.vn) st4(nd.out, nd.ldo, h < nd.vn ? h : nd.vn, h + i, iI + tc, o, false);
+        }
+    }
+}
+
 // Zero row r0 + blockIdx.y of the selected triangle of C.
 __global__ void k_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, int64_t r0) {
     const int64_t r = r0 + blockIdx.y;
@@ -547,8 +669,14 @@ cudaError_t launch_digitize_flat(const DigitizeJob *jobs_dev, int njobs, int64_t
 }
 
 cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP mp,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool upper) {
     if (h == 0 || nnodes == 0) return cudaSuccess;
+    if (!upper) {
+        const int64_t T = (h + FT - 1) / FT, ntri = T * (T + 1) / 2;
+        if (ntri > 0x7fffffff || nnodes > 65535) return cudaErrorInvalidValue;
+        k_post_fused<<<dim3((unsigned)ntri, (unsigned)nnodes), 256, 0, st>>>(nodes_dev, h, mp);
+        return cudaGetLastError();
+    }
     const int64_t TI = (h + PR - 1) / PR, TJ = (h + PC - 1) / PC;
     if (TI > 65535 || TJ > 65535 || 3 * (int64_t)nnodes > 65535) return cudaErrorInvalidValue;
     dim3 grid((unsigned)TJ, (unsigned)TI, (unsigned)(3 * nnodes));
