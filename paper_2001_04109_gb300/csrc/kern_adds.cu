@@ -88,8 +88,9 @@ __device__ __forceinline__ void ymul(const YConst &y, uint32_t t0, uint32_t t1, 
     }
 }
 
-constexpr int PREP_THREADS = 128;  // threads per block, 4 columns each
-constexpr int PREP_ROWS = 4;       // rows per thread (independent loads in flight)
+constexpr int PREP_THREADS = 128;  // threads per block
+constexpr int PREP_COLS = 8;       // columns per thread
+constexpr int PREP_ROWS = 2;       // rows per thread (independent loads in flight)
 
 // Four consecutive entries (row r, columns c..c+3) of a view, zero outside;
 // one 16-byte load when aligned and fully inside.
@@ -104,8 +105,89 @@ __device__ __forceinline__ void ld_view4(const MatView &v, bool vec_ok, int64_t 
     }
 }
 
+// Eight consecutive entries (row r, columns c..c+7) of a view, zero outside.
+// Inside the view they take two 16-byte loads when the row start is 16-byte
+// aligned, else three aligned 16-byte loads and a shift by the misalignment:
+// every 16-byte block read holds at least one wanted entry, so no read
+// leaves the pages the view's entries live on.
+__device__ __forceinline__ void ld_view8(const MatView &v, bool vec_ok, int64_t r, int64_t c,
+                                         uint32_t (&x)[8]) {
+    if (r < v.vr && c + 8 <= v.vc) {
+        const uint32_t *ptr = v.ptr + r * v.ld + c;
+        if (vec_ok) {
+            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(ptr));
+            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(ptr) + 1);
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+            x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+            return;
+        }
+        const int off = (int)((reinterpret_cast<uintptr_t>(ptr) >> 2) & 3u);
+        const uint4 *blk = reinterpret_cast<const uint4 *>(ptr - off);
+        const uint4 q0 = __ldg(blk), q1 = __ldg(blk + 1);
+        const uint4 q2 = off ? __ldg(blk + 2) : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t w[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+        switch (off) {
+            case 0:
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = w[e];
+                break;
+            case 1:
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = w[e + 1];
+                break;
+            case 2:
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = w[e + 2];
+                break;
+            default:
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = w[e + 3];
+                break;
+        }
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = ld_view(v, r, c + e);
+}
+
 // Store four residues at (row r, columns c..c+3): one 8-byte store per digit
 // plane (bf16) or one 16-byte store (uint32).
+// Store eight residues at (row r, columns c..c+7) of an operand: one
+// 16-byte store per digit plane (bf16) or two (uint32).
+template <int D, bool U32>
+__device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, const uint32_t (&v)[8],
+                                     const ModP &m) {
+    if (d.arena == nullptr) return;
+    if constexpr (U32) {
+        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(d.arena) + (d.row0 + r) * d.kpad + c);
+        dst[0] = make_uint4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_uint4(v[4], v[5], v[6], v[7]);
+    } else {
+        int sv[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sv[e] = v[e] > m.half ? (int)v[e] - (int)m.p : (int)v[e];
+        uint32_t *base = static_cast<uint32_t *>(d.arena);
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                int d0, d1;
+                if (t == D - 1) {
+                    d0 = sv[e];
+                    d1 = sv[e + 1];
+                } else {
+                    d0 = low_digit(sv[e], m);
+                    d1 = low_digit(sv[e + 1], m);
+                }
+                w[e / 2] = __byte_perm(small_int_f32_bits(d0), small_int_f32_bits(d1), 0x7632);
+            }
+            *reinterpret_cast<uint4 *>(base + (((d.row0 + t * d.rpad + r) * d.kpad + c) >> 1)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
 template <int D, bool U32>
 __device__ __forceinline__ void put4(const OperandDst &d, int64_t r, int64_t c, const uint32_t (&v)[4],
                                      const ModP &m) {
@@ -147,125 +229,88 @@ template <int D, bool U32, int YF, bool RED>
 __global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restrict__ nodes,
                                                        int64_t h, int64_t w, int64_t kpad, ModP m,
                                                        YConst y) {
-    const int64_t c = 4 * ((int64_t)blockIdx.x * PREP_THREADS + threadIdx.x);
+    // 8 columns per thread: two 16-byte loads per quadrant row, one 16-byte
+    // store per digit plane row
+    const int64_t c = PREP_COLS * ((int64_t)blockIdx.x * PREP_THREADS + threadIdx.x);
     if (c >= kpad) return;
     const PrepNode &nd = nodes[blockIdx.z];
-    const uint32_t p = m.p, half = m.half;
-    const bool inside = c < w;
+    const uint32_t p = m.p;
+    // w is a multiple of 4: each 4-column half lies wholly inside or outside
+    const bool in0 = c < w, in1 = c + 4 < w;
     // quadrant column offsets 0 and w keep 16-byte alignment when w % 4 == 0
     const bool vec_ok = ((reinterpret_cast<uintptr_t>(nd.X.ptr) & 15u) == 0) &&
                         ((nd.X.ld & 3) == 0) && ((w & 3) == 0);
     const int64_t nrb = (h + PREP_ROWS - 1) / PREP_ROWS;
     for (int64_t rb = blockIdx.y; rb < nrb; rb += gridDim.y) {
-        uint32_t a[PREP_ROWS][4][4];  // [row][quadrant A11, A12, A21, A22][column]
+        uint32_t a[PREP_ROWS][4][8];  // [row][quadrant A11, A12, A21, A22][column]
 #pragma unroll
         for (int i = 0; i < PREP_ROWS; ++i) {
             const int64_t r = rb * PREP_ROWS + i;
-            const bool ok = inside && r < h;
-            if (ok) {
-                ld_view4(nd.X, vec_ok, r, c, a[i][0]);
-                ld_view4(nd.X, vec_ok, r, w + c, a[i][1]);
-                ld_view4(nd.X, vec_ok, h + r, c, a[i][2]);
-                ld_view4(nd.X, vec_ok, h + r, w + c, a[i][3]);
+            if (in0 && r < h) {
+                ld_view8(nd.X, vec_ok, r, c, a[i][0]);
+                ld_view8(nd.X, vec_ok, r, w + c, a[i][1]);
+                ld_view8(nd.X, vec_ok, h + r, c, a[i][2]);
+                ld_view8(nd.X, vec_ok, h + r, w + c, a[i][3]);
+                if (!in1)  // columns past the quadrant width are K padding
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int e = 4; e < 8; ++e) a[i][q][e] = 0u;
             } else {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) a[i][q][e] = 0u;
+                    for (int e = 0; e < 8; ++e) a[i][q][e] = 0u;
             }
         }
 #pragma unroll
         for (int i = 0; i < PREP_ROWS; ++i) {
             const int64_t r = rb * PREP_ROWS + i;
             if (r >= h) break;
-            uint32_t x11[4], x12[4], x21[4], x22[4], s1[4], s2[4], s3[4], s4[4], u[4];
+            uint32_t x11[8], x12[8], x21[8], x22[8], s1[8], s2[8], s3[8], s4[8], u[8];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
+            for (int e = 0; e < 8; ++e) {
                 x11[e] = RED ? red(a[i][0][e], m) : a[i][0][e];
                 x12[e] = RED ? red(a[i][1][e], m) : a[i][1][e];
                 x21[e] = RED ? red(a[i][2][e], m) : a[i][2][e];
                 x22[e] = RED ? red(a[i][3][e], m) : a[i][3][e];
             }
 #pragma unroll
-            for (int e = 0; e < 4; e += 2) {
+            for (int e = 0; e < 8; e += 2) {
                 ymul<YF>(y, subm(x21[e], x11[e], p), subm(x21[e + 1], x11[e + 1], p), s1[e],
                          s1[e + 1], p);                         // S1 = (A21 − A11)·Y
                 ymul<YF>(y, x21[e], x21[e + 1], u[e], u[e + 1], p);
             }
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
+            for (int e = 0; e < 8; ++e) {
                 s2[e] = subm(x22[e], u[e], p);                  // S2 = A22 − A21·Y
                 s3[e] = subm(s1[e], x22[e], p);                 // S3 = S1 − A22
                 s4[e] = addm(s3[e], x12[e], p);                 // S4 = S3 + A12
             }
-            put4<D, U32>(nd.gemm[0], r, c, x22, m);
-            put4<D, U32>(nd.gemm[1], r, c, s4, m);
-            put4<D, U32>(nd.gemm[2], r, c, s1, m);
-            put4<D, U32>(nd.gemm[3], r, c, s2, m);
-            put4<D, U32>(nd.leaf[0], r, c, x11, m);
-            put4<D, U32>(nd.leaf[1], r, c, x12, m);
-            put4<D, U32>(nd.leaf[2], r, c, s3, m);
-            if (nd.s3 != nullptr && inside) {
-                uint32_t *dst = nd.s3 + r * nd.s3_ld + c;
-                if (((reinterpret_cast<uintptr_t>(dst)) & 15u) == 0)
-                    *reinterpret_cast<uint4 *>(dst) = make_uint4(s3[0], s3[1], s3[2], s3[3]);
-                else
+            put8<D, U32>(nd.gemm[0], r, c, x22, m);
+            put8<D, U32>(nd.gemm[1], r, c, s4, m);
+            put8<D, U32>(nd.gemm[2], r, c, s1, m);
+            put8<D, U32>(nd.gemm[3], r, c, s2, m);
+            put8<D, U32>(nd.leaf[0], r, c, x11, m);
+            put8<D, U32>(nd.leaf[1], r, c, x12, m);
+            put8<D, U32>(nd.leaf[2], r, c, s3, m);
+            if (nd.s3 != nullptr) {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) dst[e] = s3[e];
-            }
-        }
-    }
-}
-
-// Eight consecutive entries (row r, columns c..c+7) of a view, zero outside;
-// one 16-byte load pair when the view is 16-byte aligned and fully inside.
-__device__ __forceinline__ void ld_view8(const MatView &v, bool vec_ok, int64_t r, int64_t c,
-                                         uint32_t (&x)[8]) {
-    if (r < v.vr && c + 8 <= v.vc && vec_ok) {
-        const uint4 *q = reinterpret_cast<const uint4 *>(v.ptr + r * v.ld + c);
-        const uint4 a = __ldg(q), b = __ldg(q + 1);
-        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
-    } else {
+                for (int hf = 0; hf < 2; ++hf) {
+                    if (!(hf ? in1 : in0)) continue;
+                    uint32_t *dst = nd.s3 + r * nd.s3_ld + c + 4 * hf;
+                    const uint32_t *v = s3 + 4 * hf;
+                    if (((reinterpret_cast<uintptr_t>(dst)) & 15u) == 0)
+                        *reinterpret_cast<uint4 *>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
+                    else
 #pragma unroll
-        for (int e = 0; e < 8; ++e) x[e] = ld_view(v, r, c + e);
-    }
-}
-
-// Store eight residues at (row r, columns c..c+7) of an operand: one
-// 16-byte store per digit plane (bf16) or two (uint32).
-template <int D, bool U32>
-__device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, const uint32_t (&v)[8],
-                                     const ModP &m) {
-    if constexpr (U32) {
-        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(d.arena) + (d.row0 + r) * d.kpad + c);
-        dst[0] = make_uint4(v[0], v[1], v[2], v[3]);
-        dst[1] = make_uint4(v[4], v[5], v[6], v[7]);
-    } else {
-        int sv[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) sv[e] = v[e] > m.half ? (int)v[e] - (int)m.p : (int)v[e];
-        uint32_t *base = static_cast<uint32_t *>(d.arena);
-#pragma unroll
-        for (int t = 0; t < D; ++t) {
-            uint32_t w[4];
-#pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-                int d0, d1;
-                if (t == D - 1) {
-                    d0 = sv[e];
-                    d1 = sv[e + 1];
-                } else {
-                    d0 = low_digit(sv[e], m);
-                    d1 = low_digit(sv[e + 1], m);
+                        for (int e = 0; e < 4; ++e) dst[e] = v[e];
                 }
-                w[e / 2] = __byte_perm(small_int_f32_bits(d0), small_int_f32_bits(d1), 0x7632);
             }
-            *reinterpret_cast<uint4 *>(base + (((d.row0 + t * d.rpad + r) * d.kpad + c) >> 1)) =
-                make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
+
 
 // Digit split of whole matrices (the classical path's operands): rows
 // [0, rows) × columns [0, kpad) of each destination, zero beyond the view.
@@ -610,7 +655,7 @@ cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_
                         int64_t kpad, ModP mp, YConst y, DigitScheme ds, int arena_kind,
                         bool reduce_input, cudaStream_t st) {
     if (h == 0 || kpad == 0 || nnodes == 0) return cudaSuccess;
-    const int64_t gx = (kpad / 4 + PREP_THREADS - 1) / PREP_THREADS;
+    const int64_t gx = (kpad / PREP_COLS + PREP_THREADS - 1) / PREP_THREADS;
     const int64_t gy = std::min<int64_t>((h + PREP_ROWS - 1) / PREP_ROWS, 65535);
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nnodes);
     if (arena_kind == ARENA_U32)
