@@ -315,10 +315,14 @@ def run_ours(args):
     long_step = step_ms > 100.0
     peak = peaks["bf16_tflops_sustained" if long_step else "bf16_tflops"]
     achieved = 2.0 * tmacs / (leaf_ms * 1e-3) / 1e12
+    pair = info["leaf"] == ffsyrk.LEAF_TC_BF16 and info["tile_ctas"] == 2
+    kernel_file = "kern_leaf_tc2.cu" if pair else "kern_leaf_tc.cu"
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": kernel_traffic("kern_leaf_tc.cu", args.workload),
-                "kernel": "k_leaf_tc (tcgen05 kind::f16, bf16 digits, fp32 TMEM)",
+                "traffic": kernel_traffic(kernel_file, args.workload),
+                "kernel": ("k_leaf_tc2 (tcgen05 kind::f16 cta_group::2, 256x256 tiles on SM pairs, "
+                           "bf16 digits, fp32 TMEM)" if pair else
+                           "k_leaf_tc (tcgen05 kind::f16, 128x256 tiles, bf16 digits, fp32 TMEM)"),
                 "peak_source": f"{peak_src} {'sustained' if long_step else 'burst'} bf16 dense",
                 "algorithmic_flops_per_launch": 2.0 * tmacs,
                 "leaf_ms": leaf_ms,

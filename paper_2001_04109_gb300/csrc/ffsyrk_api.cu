@@ -410,14 +410,34 @@ int choose_levels(const ffsyrk_plan_st *pl, int64_t n, int64_t k) {
     return L;
 }
 
-// SMs per tensor-core tile.  Measured on GB300 the CTA-pair tiles were 5-15%
-// slower than one-SM tiles on every shape tried (the pair's shared barriers
-// add latency while neither shared memory nor L2 is the limit), so one-SM
-// tiles are the default and pairs are an explicit option.
+// SMs per tensor-core tile.  With every SM busy the one-SM 128×256 leaf is
+// bound by the L2 bandwidth its operand stream needs (48 KB per SM and
+// k-block); SM-pair 256×256 tiles stage 32 KB per SM for the same MMAs and
+// measured 4-6 % faster on GB300 once a launch fills the SMs (A 4096²:
+// 0.195 → 0.185 ms leaf, A 8192²: 1.23 → 1.18 ms, A 16384² one level:
+// 8.84 → 8.33 ms).  But the pairs draw more power per multiply-add: in leaf
+// launches long enough to run at the 1.4 kW cap the clock drops further
+// and they lose (A 32768², p = 8388593: 146 → 157 ms at three levels), and
+// with balanced-base digits the pair's shared accumulator hand-off slows the
+// more frequent epilogue drains (A 4096×16384, p = 131071: 0.733 → 0.763 ms).
+// So pairs are used for launches that fill the SMs, with byte digits and an
+// estimated leaf time under 40 ms; one-SM tiles otherwise (small launches can
+// then also share long tiles' K among idle SMs, split_tail).
 int choose_ctas(const ffsyrk_plan_st *pl, const Geometry &g) {
-    (void)g;
     if (pl->ctas_opt == 1 || pl->ctas_opt == 2) return pl->ctas_opt;
-    return 1;
+    if (pl->leaf != FFSYRK_LEAF_TC_BF16 || pl->ds.base != 256) return 1;
+    if (leaf_tiles_bound(g, pl->leaf) < pl->sms) return 1;
+    // digit multiply-adds of the leaf over a measured ≈ 9e14 per second
+    double macs = 0;
+    if (g.L == 0) {
+        macs = (double)g.n * (g.n + 1) / 2 * (double)g.k;
+    } else {
+        for (int d = 0; d < g.L; ++d)
+            macs += 2.0 * std::pow(3.0, d) * (double)g.h[d + 1] * g.h[d + 1] * (double)g.w[d + 1];
+        macs += std::pow(3.0, g.L) * (double)g.h[g.L] * (g.h[g.L] + 1) / 2 * (double)g.w[g.L];
+    }
+    const double est_ms = macs * pl->ds.D * pl->ds.D / 9e14 * 1e3;
+    return est_ms < 40.0 ? 2 : 1;
 }
 
 ffsyrk_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? FFSYRK_SUCCESS : FFSYRK_ERR_CUDA; }

@@ -54,31 +54,6 @@ constexpr int TMEM_COLS = 512;
 constexpr uint32_t IDESC = tc::idesc_bf16(BM, BN);
 using namespace tc;
 
-// Running sums of the epilogue are reduced lazily: Barrett with
-// floor(2^32 / p) brings any uint32 sum into [0, 2p).
-__device__ __forceinline__ uint32_t reduce_2p(uint32_t x, uint32_t p, uint32_t barrett) {
-    return x - __umulhi(x, barrett) * p;
-}
-__device__ __forceinline__ uint32_t final_mod(uint32_t x, uint32_t p) { return x >= p ? x - p : x; }
-
-// One epilogue thread's 128 residues (sums below 2p) to a row at dst, where
-// dst + E0 is the first 16-byte aligned address: E0 leading scalar stores,
-// 16-byte stores, then the remaining scalars.
-template <int E0>
-__device__ __forceinline__ void store_row(uint32_t *dst, const uint32_t (&acc)[EPI_COLS], uint32_t p) {
-#pragma unroll
-    for (int e = 0; e < E0; ++e) dst[e] = final_mod(acc[e], p);
-    constexpr int NV = (EPI_COLS - E0) / 4;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const int e = E0 + 4 * v;
-        *reinterpret_cast<uint4 *>(dst + e) = make_uint4(final_mod(acc[e], p), final_mod(acc[e + 1], p),
-                                                         final_mod(acc[e + 2], p), final_mod(acc[e + 3], p));
-    }
-#pragma unroll
-    for (int e = E0 + 4 * NV; e < EPI_COLS; ++e) dst[e] = final_mod(acc[e], p);
-}
-
 // LAZY: no tile of the launch has more units than ds.lazy_units, so the
 // running sums may grow unreduced (one add per unit and element) and are
 // brought below 2p once, before the store; otherwise every unit's add is
@@ -378,10 +353,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
                     // rows of an odd ldc start at any 4-byte offset
                     uint32_t *dst = orow + c0;
                     switch ((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u) {
-                        case 0: store_row<0>(dst, acc, p); break;
-                        case 1: store_row<3>(dst, acc, p); break;
-                        case 2: store_row<2>(dst, acc, p); break;
-                        default: store_row<1>(dst, acc, p); break;
+                        case 0: store_row<0, EPI_COLS>(dst, acc, p); break;
+                        case 1: store_row<3, EPI_COLS>(dst, acc, p); break;
+                        case 2: store_row<2, EPI_COLS>(dst, acc, p); break;
+                        default: store_row<1, EPI_COLS>(dst, acc, p); break;
                     }
                 } else {
 #pragma unroll

@@ -57,9 +57,12 @@ __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
                  "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// Arrive on a barrier of the pair (cluster address).  The epilogue's only
+// obligation to the MMA issuer is that its tensor-memory reads are complete
+// (tcgen05.wait::ld and fence::before_thread_sync precede the arrive), so no
+// cluster-scope release of ordinary memory is needed.
 __device__ __forceinline__ void arrive_remote(uint32_t cluster_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-                 : "memory");
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 // TMA load into this CTA's shared memory, completing on a barrier that may
 // live in the peer CTA (cluster address).
@@ -88,6 +91,9 @@ __device__ __forceinline__ void commit_pair(uint64_t *bar, uint16_t mask) {
         : "memory");
 }
 
+// LAZY: as in the one-SM leaf, running sums grow unreduced when no tile has
+// more units than ds.lazy_units.
+template <bool LAZY>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     k_leaf_tc2(const LeafProd *__restrict__ prods, const LeafTile *__restrict__ tiles,
                const LeafSeg *__restrict__ segs, int ntiles, const CUtensorMap *__restrict__ tmaps,
@@ -264,8 +270,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
                         const uint32_t a = (uint32_t)(xi + (int)off);
                         const uint32_t q = __umulhi(a, wsh);
                         const uint32_t r = a * w - q * p;  // [0, 2p)
-                        const uint32_t s = acc[cc * LD_COLS + e] + r;
-                        acc[cc * LD_COLS + e] = min(s, s - twop);
+                        if constexpr (LAZY) {
+                            acc[cc * LD_COLS + e] += r;
+                        } else {
+                            const uint32_t s = acc[cc * LD_COLS + e] + r;
+                            acc[cc * LD_COLS + e] = min(s, s - twop);
+                        }
                     }
                 }
                 fence_before();
@@ -274,6 +284,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
                 ++unit;
             }
             if (!ok) break;
+            if constexpr (LAZY) {
+#pragma unroll
+                for (int e = 0; e < EPI_COLS; ++e) acc[e] = reduce_2p(acc[e], p, m.barrett);
+            }
             const int64_t r = (int64_t)tl.tm * BM + rank * ROWS + quad * 32 + lane;
             const int64_t c0 = (int64_t)tl.tn * BN + colq * EPI_COLS;
             if (r < pr.rows) {
@@ -281,16 +295,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
                 const bool all_cols = c0 + EPI_COLS <= pr.cols;
                 const bool tri_ok = pr.tri == 0 || (pr.tri == 1 && c0 + EPI_COLS - 1 <= r) ||
                                     (pr.tri == 2 && c0 >= r);
-                const bool aligned = ((reinterpret_cast<uintptr_t>(orow + c0) & 15u) == 0);
-                if (all_cols && tri_ok && aligned) {
-#pragma unroll
-                    for (int e = 0; e < EPI_COLS; e += 4) {
-                        uint4 v4;
-                        v4.x = acc[e] >= p ? acc[e] - p : acc[e];
-                        v4.y = acc[e + 1] >= p ? acc[e + 1] - p : acc[e + 1];
-                        v4.z = acc[e + 2] >= p ? acc[e + 2] - p : acc[e + 2];
-                        v4.w = acc[e + 3] >= p ? acc[e + 3] - p : acc[e + 3];
-                        *reinterpret_cast<uint4 *>(orow + c0 + e) = v4;
+                if (all_cols && tri_ok) {
+                    uint32_t *dst = orow + c0;
+                    switch ((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u) {
+                        case 0: store_row<0, EPI_COLS>(dst, acc, p); break;
+                        case 1: store_row<3, EPI_COLS>(dst, acc, p); break;
+                        case 2: store_row<2, EPI_COLS>(dst, acc, p); break;
+                        default: store_row<1, EPI_COLS>(dst, acc, p); break;
                     }
                 } else {
 #pragma unroll
@@ -325,14 +336,16 @@ cudaError_t launch_leaf_tc2(const TcLaunch &L, int num_sms, cudaStream_t st) {
     static int max_pairs = 0;
     if (max_pairs == 0) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_leaf_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaFuncSetAttribute(k_leaf_tc2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_leaf_tc2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(2 * (num_sms / 2), 1, 1);
         cfg.blockDim = dim3(NUM_THREADS, 1, 1);
         cfg.dynamicSmemBytes = smem;
         int clusters = 0;
-        e = cudaOccupancyMaxActiveClusters(&clusters, k_leaf_tc2, &cfg);
+        e = cudaOccupancyMaxActiveClusters(&clusters, k_leaf_tc2<true>, &cfg);
         if (e != cudaSuccess || clusters <= 0) {
             cudaGetLastError();
             clusters = num_sms / 2;
@@ -340,9 +353,10 @@ cudaError_t launch_leaf_tc2(const TcLaunch &L, int num_sms, cudaStream_t st) {
         max_pairs = clusters;
     }
     const int pairs = L.ntiles < max_pairs ? L.ntiles : max_pairs;
-    k_leaf_tc2<<<2 * pairs, NUM_THREADS, smem, st>>>(
-        L.prods, L.tiles, L.segs, L.ntiles, reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp, L.ds,
-        L.err);
+    auto kern = L.max_units <= L.ds.lazy_units ? k_leaf_tc2<true> : k_leaf_tc2<false>;
+    kern<<<2 * pairs, NUM_THREADS, smem, st>>>(L.prods, L.tiles, L.segs, L.ntiles,
+                                               reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp,
+                                               L.ds, L.err);
     return cudaGetLastError();
 }
 

@@ -166,6 +166,31 @@ __device__ __forceinline__ void live_chunks(const LeafProd &pr, int64_t rbase, i
     }
 }
 
+// Running sums of the epilogue are reduced lazily: Barrett with
+// floor(2^32 / p) brings any uint32 sum into [0, 2p).
+__device__ __forceinline__ uint32_t reduce_2p(uint32_t x, uint32_t p, uint32_t barrett) {
+    return x - __umulhi(x, barrett) * p;
+}
+__device__ __forceinline__ uint32_t final_mod(uint32_t x, uint32_t p) { return x >= p ? x - p : x; }
+
+// One epilogue thread's N residues (sums below 2p) to a row at dst, where
+// dst + E0 is the first 16-byte aligned address: E0 leading scalar stores,
+// 16-byte stores, then the remaining scalars.
+template <int E0, int N>
+__device__ __forceinline__ void store_row(uint32_t *dst, const uint32_t (&acc)[N], uint32_t p) {
+#pragma unroll
+    for (int e = 0; e < E0; ++e) dst[e] = final_mod(acc[e], p);
+    constexpr int NV = (N - E0) / 4;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const int e = E0 + 4 * v;
+        *reinterpret_cast<uint4 *>(dst + e) = make_uint4(final_mod(acc[e], p), final_mod(acc[e + 1], p),
+                                                         final_mod(acc[e + 2], p), final_mod(acc[e + 3], p));
+    }
+#pragma unroll
+    for (int e = E0 + 4 * NV; e < N; ++e) dst[e] = final_mod(acc[e], p);
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16: D = f32, A = B = bf16,
 // both K-major, shape M×N.
 constexpr uint32_t idesc_bf16(int M, int N) {

@@ -29,7 +29,7 @@ def run_timed(A_host, p, levels, uplo, calls=2):
     n, k = A_host.shape
     dev = torch.device("cuda")
     A = A_host.to(dev)
-    plan = ffsyrk.Plan(p, n, k, leaf="tc", levels=levels)
+    plan = ffsyrk.Plan(p, n, k, leaf="tc", levels=levels, tile_ctas=1)  # the split is a one-SM-tile feature
     plan.set_timing(True)
     outs = []
     for _ in range(calls):
