@@ -479,7 +479,6 @@ void split_tail(Descs &D, int S, int slot_cap) {
     D.nslots = 0;
     const int T = (int)D.tiles.size();
     if (T == 0 || S < 2 || 2 * T > S) return;
-    const int R = T;
     const int DP = 0;
     struct Unit {
         int tile, sx0, sx1;
@@ -774,6 +773,12 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
     char *dd = pl->ws + pl->data_cap;
     const int kind = lay.leaf == FFSYRK_LEAF_TC_BF16 ? ARENA_BF16 : ARENA_U32;
     if (timed) cudaEventRecord(pl->ev[0], st);
+    // the one-SM leaf's work counters start at zero; cleared first, so that
+    // the leaf launch directly follows the grid that writes its operands
+    // (programmatic dependent launch)
+    const bool tc1 = lay.leaf == FFSYRK_LEAF_TC_BF16 && lay.ctas != 2;
+    if (tc1 && cudaMemsetAsync(dd + D.ctr_off, 0, (size_t)D.ctr_bytes, st) != cudaSuccess)
+        return FFSYRK_ERR_CUDA;
     if (g.L == 0) {
         e = launch_digitize(reinterpret_cast<const DigitizeJob *>(dd + D.digit_off), 1,
                             D.digit_max_rows, D.digit_max_kpad, pl->mp, pl->ds, kind, st);
@@ -810,8 +815,7 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
                 tl.part = pl->part;
                 tl.part_ctr = reinterpret_cast<unsigned int *>(dd + D.ctr_off + 16);
             }
-            e = cudaMemsetAsync(tl.tile_ctr, 0, (size_t)D.ctr_bytes, st);
-            if (e == cudaSuccess) e = launch_leaf_tc(tl, pl->sms, st);
+            e = launch_leaf_tc(tl, pl->sms, st);
         }
     } else {
         e = launch_leaf_i64_arrays(reinterpret_cast<const LeafProd *>(dd + D.prods_off),
@@ -1445,6 +1449,12 @@ cudaError_t batch_issue(BatchState *b, cudaStream_t st) {
     const bool tc = b->leaf == FFSYRK_LEAF_TC_BF16;
     const int kind = tc ? ARENA_BF16 : ARENA_U32;
     cudaError_t e = cudaSuccess;
+    // the leaf's work counter first: the leaf launch then directly follows
+    // the digit split (programmatic dependent launch)
+    if (tc) {
+        e = cudaMemsetAsync(dd + L.ctr_off, 0, sizeof(unsigned int), st);
+        if (e != cudaSuccess) return e;
+    }
     e = launch_digitize_flat(reinterpret_cast<const DigitizeJob *>(dd + L.jobs_off), L.njobs,
                              L.digit_blocks, b->mp, b->ds, kind, st);
     if (e != cudaSuccess) return e;
@@ -1460,8 +1470,7 @@ cudaError_t batch_issue(BatchState *b, cudaStream_t st) {
         tl.ds = b->ds;
         tl.err = b->err_dev;
         tl.tile_ctr = reinterpret_cast<unsigned int *>(dd + L.ctr_off);
-        e = cudaMemsetAsync(tl.tile_ctr, 0, sizeof(unsigned int), st);
-        if (e == cudaSuccess) e = launch_leaf_tc(tl, b->sms, st);
+        e = launch_leaf_tc(tl, b->sms, st);
     } else {
         e = launch_leaf_i64_arrays(reinterpret_cast<const LeafProd *>(dd + L.prods_off),
                                    reinterpret_cast<const LeafTile *>(dd + L.tiles_off), L.ntiles,

@@ -88,22 +88,16 @@ __device__ __forceinline__ void ymul(const YConst &y, uint32_t t0, uint32_t t1, 
     }
 }
 
+// Programmatic dependent launch: a kernel that produces the leaf's operands
+// lets the leaf launch right away; the leaf's prologue (barriers, tensor
+// memory, descriptors) then overlaps this grid's tail, and the leaf waits
+// (griddepcontrol.wait) before it reads any operand.
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 constexpr int PREP_THREADS = 128;  // threads per block
 constexpr int PREP_COLS = 8;       // columns per thread
 constexpr int PREP_ROWS = 2;       // rows per thread (independent loads in flight)
 
-// Four consecutive entries (row r, columns c..c+3) of a view, zero outside;
-// one 16-byte load when aligned and fully inside.
-__device__ __forceinline__ void ld_view4(const MatView &v, bool vec_ok, int64_t r, int64_t c,
-                                         uint32_t (&x)[4]) {
-    if (r < v.vr && c + 4 <= v.vc && vec_ok) {
-        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(v.ptr + r * v.ld + c));
-        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-    } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) x[e] = ld_view(v, r, c + e);
-    }
-}
 
 // Eight consecutive entries (row r, columns c..c+7) of a view, zero outside.
 // Inside the view they take two 16-byte loads when the row start is 16-byte
@@ -229,6 +223,7 @@ template <int D, bool U32, int YF, bool RED>
 __global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restrict__ nodes,
                                                        int64_t h, int64_t w, int64_t kpad, ModP m,
                                                        YConst y) {
+    allow_dependents();
     // 8 columns per thread: two 16-byte loads per quadrant row, one 16-byte
     // store per digit plane row
     const int64_t c = PREP_COLS * ((int64_t)blockIdx.x * PREP_THREADS + threadIdx.x);
@@ -321,6 +316,7 @@ constexpr int DIG_THREADS = 128;
 template <int D, bool U32>
 __global__ void __launch_bounds__(DIG_THREADS) k_digitize(const DigitizeJob *__restrict__ jobs,
                                                           ModP m) {
+    allow_dependents();
     const DigitizeJob &jb = jobs[blockIdx.z];
     const int64_t c = DIG_COLS * ((int64_t)blockIdx.x * DIG_THREADS + threadIdx.x);
     if (c >= jb.dst.kpad) return;
@@ -347,6 +343,7 @@ __global__ void __launch_bounds__(DIG_THREADS) k_digitize(const DigitizeJob *__r
 template <int D, bool U32>
 __global__ void __launch_bounds__(DIG_THREADS) k_digitize_flat(const DigitizeJob *__restrict__ jobs,
                                                                 int njobs, ModP m) {
+    allow_dependents();
     const int64_t b = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
     int lo = 0, hi = njobs - 1;
     while (lo < hi) {

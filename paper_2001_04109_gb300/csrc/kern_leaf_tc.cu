@@ -116,6 +116,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
     if (warp == PRODUCER_WARP) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
+            // the operands may still be being written by the preceding grid
+            asm volatile("griddepcontrol.wait;" ::: "memory");
             uint32_t it = 0, seq = 0;
             bool ok = true;
             for (uint32_t round = 0; ok; ++round) {
@@ -425,11 +427,22 @@ cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st) {
     const int nwork = L.entries ? L.nentries : L.ntiles;
     const int grid = nwork < num_sms ? nwork : num_sms;
     auto kern = L.max_units <= L.ds.lazy_units ? k_leaf_tc<true> : k_leaf_tc<false>;
-    kern<<<grid, NUM_THREADS, smem, st>>>(L.prods, L.tiles, L.segs, L.ntiles,
-                                          reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp, L.ds,
-                                          L.err, L.tile_ctr, L.pieces, L.entries,
-                                          L.entries ? L.nentries : L.ntiles, L.part, L.part_ctr);
-    return cudaGetLastError();
+    // programmatic dependent launch: the prologue may overlap the grid that
+    // writes the operands (the producer waits for it before its first load)
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NUM_THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int nentries = L.entries ? L.nentries : L.ntiles;
+    return cudaLaunchKernelEx(&cfg, kern, L.prods, L.tiles, L.segs, L.ntiles,
+                              reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp, L.ds, L.err,
+                              L.tile_ctr, L.pieces, L.entries, nentries, L.part, L.part_ctr);
 }
 
 }  // namespace fsk

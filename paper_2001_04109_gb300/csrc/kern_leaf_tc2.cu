@@ -141,6 +141,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     if (warp == PRODUCER_WARP) {
         // ---------------- TMA producer (both CTAs) ----------------
         if (lane == 0) {
+            // the operands may still be being written by the preceding grid
+            asm volatile("griddepcontrol.wait;" ::: "memory");
             uint32_t it = 0;
             bool ok = true;
             for (int t = pair; t < ntiles && ok; t += npairs) {
@@ -354,10 +356,19 @@ cudaError_t launch_leaf_tc2(const TcLaunch &L, int num_sms, cudaStream_t st) {
     }
     const int pairs = L.ntiles < max_pairs ? L.ntiles : max_pairs;
     auto kern = L.max_units <= L.ds.lazy_units ? k_leaf_tc2<true> : k_leaf_tc2<false>;
-    kern<<<2 * pairs, NUM_THREADS, smem, st>>>(L.prods, L.tiles, L.segs, L.ntiles,
-                                               reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp,
-                                               L.ds, L.err);
-    return cudaGetLastError();
+    // programmatic dependent launch, as for the one-SM leaf
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * pairs));
+    cfg.blockDim = dim3(NUM_THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, L.prods, L.tiles, L.segs, L.ntiles,
+                              reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp, L.ds, L.err);
 }
 
 }  // namespace fsk
