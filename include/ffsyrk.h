@@ -120,6 +120,23 @@ ffsyrk_status_t ffsyrk_with_plan(ffsyrk_plan_t plan, ffsyrk_uplo_t uplo, int64_t
 ffsyrk_status_t ffsyrk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p, const uint32_t *A,
                        int64_t lda, uint32_t *C, int64_t ldc, ffsyrk_stream_t stream);
 
+/* The update C ← α·A·Aᵀ + β·C mod p (Section 4.2, Table 4: the general
+ * operation whose schedule adds β·C into the blocks of the result).  Only the
+ * triangle `uplo` of C is read and written; the other strict triangle is not
+ * touched.  alpha and beta are any uint32 and are reduced mod p; α = 1,
+ * β = 0 is the plain product (ffsyrk_with_plan).  The current contents of
+ * C's triangle must be residues < p when β ≠ 0.  k = 0 gives C ← β·C.
+ * Same plan, argument and error rules as ffsyrk_with_plan. */
+ffsyrk_status_t ffsyrk_with_plan_update(ffsyrk_plan_t plan, ffsyrk_uplo_t uplo, int64_t n,
+                                        int64_t k, uint32_t p, uint32_t alpha, const uint32_t *A,
+                                        int64_t lda, uint32_t beta, uint32_t *C, int64_t ldc,
+                                        ffsyrk_stream_t stream);
+
+/* The same update through the internal plan cache (as ffsyrk).  Thread-safe. */
+ffsyrk_status_t ffsyrk_update(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
+                              const uint32_t *A, int64_t lda, uint32_t beta, uint32_t *C,
+                              int64_t ldc, ffsyrk_stream_t stream);
+
 /* `count` independent products C_t = A_t·A_tᵀ mod p of uneven sizes n[t] × k[t],
  * all with the same p and uplo.  n, k, lda, ldc are HOST arrays of `count`
  * values; A and C are HOST arrays of `count` DEVICE pointers.  Problems with

@@ -10,6 +10,8 @@ Contents
 * ``syrk_oracle.c`` / :func:`syrk` / :func:`syrk_rows` -- the plain
   schoolbook definition of lower(A·Aᵀ) mod p in 64-bit integers (the result
   Algorithm 2 of the paper reaches exactly, Section 3).
+* :func:`syrk_update` -- the definition of the update C ← α·A·Aᵀ + β·C mod
+  p on one triangle (Section 4.2, Table 4), from :func:`syrk`.
 * :mod:`oracle.field` -- primality, Legendre symbols, square roots and the
   skew-orthogonal Y of Section 3.1 (Prop. 3.2, Prop. 3.3, Algorithm 3).
 * :mod:`oracle.alg2` -- Algorithm 2 itself written step by step over F_p in
@@ -92,6 +94,25 @@ def syrk(A, p: int, uplo: str = "lower", threads: int | None = None) -> np.ndarr
                               threads or default_threads())
     if rc != 0:
         raise ValueError("oracle_syrk_modp rejected its arguments")
+    return C
+
+
+def syrk_update(A, p: int, alpha: int, C, beta: int, uplo: str = "lower",
+                threads: int | None = None) -> np.ndarray:
+    """C ← α·A·Aᵀ + β·C mod p on the triangle ``uplo`` (Section 4.2, Table 4).
+
+    The definition entry by entry: (α·(A·Aᵀ)[i][j] + β·C[i][j]) mod p where
+    the triangle is stored (j ≤ i for ``"lower"``, j ≥ i for ``"upper"``);
+    every other entry of C is returned unchanged.  α, β are reduced mod p;
+    C's triangle must hold residues < p.  Returns a new n×n uint32 array.
+    """
+    C = np.array(C, dtype=np.uint32, copy=True)
+    n = C.shape[0]
+    P = syrk(A, p, uplo, threads).astype(np.uint64)
+    a, b = np.uint64(int(alpha) % p), np.uint64(int(beta) % p)
+    mask = np.tril(np.ones((n, n), dtype=bool)) if uplo == "lower" else np.triu(np.ones((n, n), dtype=bool))
+    upd = (a * P + b * C.astype(np.uint64)) % np.uint64(p)  # < 2·p² < 2^49
+    C[mask] = upd[mask].astype(np.uint32)
     return C
 
 

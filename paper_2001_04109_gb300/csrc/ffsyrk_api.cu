@@ -370,9 +370,12 @@ struct ffsyrk_plan_st {
     unsigned int *err_host = nullptr, *err_dev = nullptr;  // mapped host word
     // last call, to skip re-planning when nothing changed
     bool have_last = false;
-    std::tuple<int64_t, int64_t, const uint32_t *, int64_t, uint32_t *, int64_t, int, int> last_key;
+    std::tuple<int64_t, int64_t, const uint32_t *, int64_t, uint32_t *, int64_t, int, int, uint32_t,
+               uint32_t, uint32_t>
+        last_key;
     Layout lay;
     Descs desc;
+    OutScale scale{};  // how the current call updates C
     // optional per-stage timing
     bool timing = false;
     bool timed_call = false;
@@ -597,6 +600,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         pr.kblocks = (int32_t)(lay.arena[0].kpad / 64);
         pr.plane_rows = lay.arena[0].rpad;
         pr.out = C;
+        pr.scale = pl->scale;
         pr.ldo = ldc;
         D.prods.push_back(pr);
         tri_tiles(D.tiles, 0, g.n, g.n, pr.tri, TM, TN, pr.kblocks * cost_mult);
@@ -681,6 +685,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
                 pn.ldg = h;
                 if (d == 0) {
                     pn.out = C;
+                    pn.scale = pl->scale;
                     pn.ldo = ldc;
                     pn.vn = g.n;
                     pn.upper = uplo == FFSYRK_UPPER;
@@ -799,6 +804,8 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
         tl.segs = reinterpret_cast<const LeafSeg *>(dd + D.segs_off);
         tl.ntiles = (int)D.tiles.size();
         tl.max_units = D.max_units;
+        tl.scaled = false;
+        for (const LeafProd &pr : D.prods) tl.scaled = tl.scaled || pr.scale.mode != 0;
         tl.tmaps = dd + D.tmap_off;
         tl.mp = pl->mp;
         tl.ds = pl->ds;
@@ -918,12 +925,14 @@ void record_work(ffsyrk_plan_st *pl) {
 }
 
 ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, const uint32_t *A,
-                        int64_t lda, uint32_t *C, int64_t ldc, cudaStream_t st) {
+                        int64_t lda, uint32_t *C, int64_t ldc, cudaStream_t st,
+                        const OutScale &sc = OutScale{}) {
     cudaError_t e;
     if (n == 0) return FFSYRK_SUCCESS;
-    if (k == 0) return cuda_status(launch_zero_tri(C, n, ldc, uplo == FFSYRK_UPPER, st));
+    if (k == 0)  // A·Aᵀ = 0: C ← β·C, or 0
+        return cuda_status(launch_scale_tri(C, n, ldc, uplo == FFSYRK_UPPER, sc, pl->p, st));
     const int L = choose_levels(pl, n, k);
-    auto key = std::make_tuple(n, k, A, lda, C, ldc, uplo, L);
+    auto key = std::make_tuple(n, k, A, lda, C, ldc, uplo, L, sc.mode, sc.alpha.w, sc.beta.w);
     if (!pl->have_last || key != pl->last_key) {
         Geometry g = make_geometry(n, k, L);
         Layout lay = make_layout(g, pl->leaf, pl->ds.D);
@@ -935,6 +944,7 @@ ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, cons
             pl->desc_pending = false;
         }
         pl->lay = lay;
+        pl->scale = sc;
         drop_graph(pl);
         ffsyrk_status_t s = build_descs(pl, uplo, A, lda, C, ldc);
         if (s != FFSYRK_SUCCESS) {
@@ -1274,6 +1284,13 @@ ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t pl, ffsyrk_plan_info_t *info)
 ffsyrk_status_t ffsyrk_with_plan(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n, int64_t k,
                                  uint32_t p, const uint32_t *A, int64_t lda, uint32_t *C,
                                  int64_t ldc, ffsyrk_stream_t stream) {
+    return ffsyrk_with_plan_update(pl, uplo, n, k, p, 1u, A, lda, 0u, C, ldc, stream);
+}
+
+ffsyrk_status_t ffsyrk_with_plan_update(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n, int64_t k,
+                                        uint32_t p, uint32_t alpha, const uint32_t *A, int64_t lda,
+                                        uint32_t beta, uint32_t *C, int64_t ldc,
+                                        ffsyrk_stream_t stream) {
     if (!pl) return FFSYRK_ERR_INVALID_ARG;
     if (p != pl->p) return FFSYRK_ERR_INVALID_ARG;
     if (uplo != FFSYRK_LOWER && uplo != FFSYRK_UPPER) return FFSYRK_ERR_INVALID_ARG;
@@ -1285,7 +1302,15 @@ ffsyrk_status_t ffsyrk_with_plan(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n
     cudaGetDevice(&cur);
     if (cur != pl->device) return FFSYRK_ERR_INVALID_ARG;
     if (pl->err_host[0] != 0) return FFSYRK_ERR_TIMEOUT;
-    return enqueue(pl, uplo, n, k, A, lda, C, ldc, reinterpret_cast<cudaStream_t>(stream));
+    OutScale sc{};
+    alpha %= p;
+    beta %= p;
+    if (alpha != 1u || beta != 0u) {
+        sc.mode = 1;
+        sc.alpha = make_mul(alpha, p);
+        sc.beta = make_mul(beta, p);
+    }
+    return enqueue(pl, uplo, n, k, A, lda, C, ldc, reinterpret_cast<cudaStream_t>(stream), sc);
 }
 
 ffsyrk_status_t ffsyrk_plan_set_timing(ffsyrk_plan_t pl, int32_t enable) {
@@ -1387,6 +1412,13 @@ constexpr size_t kCacheMax = 8;
 extern "C" ffsyrk_status_t ffsyrk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
                                   const uint32_t *A, int64_t lda, uint32_t *C, int64_t ldc,
                                   ffsyrk_stream_t stream) {
+    return ffsyrk_update(uplo, n, k, p, 1u, A, lda, 0u, C, ldc, stream);
+}
+
+extern "C" ffsyrk_status_t ffsyrk_update(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
+                                         uint32_t alpha, const uint32_t *A, int64_t lda,
+                                         uint32_t beta, uint32_t *C, int64_t ldc,
+                                         ffsyrk_stream_t stream) {
     ffsyrk_status_t s = validate_p(p);
     if (s != FFSYRK_SUCCESS) return s;
     if (n < 0 || k < 0) return FFSYRK_ERR_INVALID_ARG;
@@ -1409,7 +1441,7 @@ extern "C" ffsyrk_status_t ffsyrk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint
         it = g_cache.emplace(key, CacheEntry{pl, 0}).first;
     }
     it->second.last_use = ++g_clock;
-    return ffsyrk_with_plan(it->second.plan, uplo, n, k, p, A, lda, C, ldc, stream);
+    return ffsyrk_with_plan_update(it->second.plan, uplo, n, k, p, alpha, A, lda, beta, C, ldc, stream);
 }
 
 // ---- batched: many independent problems in one grouped launch ----

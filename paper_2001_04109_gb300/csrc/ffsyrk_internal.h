@@ -39,6 +39,28 @@ struct MulConst {
     uint32_t w_sh;
 };
 
+// How the kernel that writes the caller's C stores a result R (residues in
+// [0, p)): mode 0 stores R; mode 1 stores α·R + β·C_old mod p, the update
+// C ← α·A·Aᵀ + β·C of Table 4 applied where C is written (same result as
+// scaling the products and adding β·C blockwise as that schedule does).
+struct OutScale {
+    uint32_t mode;
+    MulConst alpha, beta;
+};
+#ifdef __CUDACC__
+// x·c mod p for x < 2^32 (Shoup's precomputed quotient c.w_sh = ⌊c.w·2^32/p⌋)
+__device__ __forceinline__ uint32_t mul_shoup(uint32_t x, MulConst c, uint32_t p) {
+    const uint32_t q = __umulhi(x, c.w_sh);
+    const uint32_t r = x * c.w - q * p;
+    return r >= p ? r - p : r;
+}
+// α·r + β·old mod p for r, old < p
+__device__ __forceinline__ uint32_t scale_out(uint32_t r, uint32_t old, const OutScale &s, uint32_t p) {
+    const uint32_t v = mul_shoup(r, s.alpha, p) + mul_shoup(old, s.beta, p);
+    return v >= p ? v - p : v;
+}
+#endif
+
 // The skew-orthogonal Y (Section 3.1): form 0 is i·I; form 1 is the
 // interleaved I ⊗ [[a, b], [−b, a]].
 struct YConst {
@@ -132,6 +154,7 @@ struct PostNode {
     int64_t ldo;
     int64_t vn;                    // rows/cols of `out` that exist (root: n)
     int upper;                     // write the upper triangle (transposed)
+    OutScale scale;                // root node only: how C is updated
 };
 
 // One leaf product out = X·Zᵀ mod p (rows × cols) on arena operands.
@@ -146,6 +169,7 @@ struct LeafProd {
     uint32_t *out;
     int64_t ldo;
     int64_t seg0;         // first segment in the launch's segment table
+    OutScale scale;       // a product that writes the caller's C: how it is updated
 };
 
 // One step of a tile's K schedule: digit pair (i, j) over k-blocks
@@ -208,6 +232,9 @@ int64_t digitize_flat_blocks(int64_t rows, int64_t kpad);
 cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP mp,
                         cudaStream_t st, bool upper);
 cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st);
+// the selected triangle for k = 0: zero, or β·C (sc.mode 1)
+cudaError_t launch_scale_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, const OutScale &sc,
+                             uint32_t p, cudaStream_t st);
 cudaError_t launch_leaf_i64_arrays(const LeafProd *prods_dev, const LeafTile *tiles_dev,
                                    int ntiles, const uint32_t *const *arenas_dev,
                                    const int64_t *kpad_dev, ModP mp, cudaStream_t st);
@@ -231,6 +258,7 @@ struct TcLaunch {
     uint32_t *part;           // partial-result slots, BM·BN residues each
     unsigned int *part_ctr;   // 8 per split tile, zero before the first launch
     int max_units;            // most units (accumulator drains) of any tile's K schedule
+    bool scaled;              // a product updates the caller's C (OutScale mode 1)
 };
 // Units (segments that open an accumulator) of a K schedule.
 int count_units(const LeafSeg *segs, int nseg);

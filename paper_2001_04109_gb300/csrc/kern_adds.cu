@@ -471,13 +471,15 @@ __global__ void __launch_bounds__(256) k_post(const PostNode *__restrict__ nodes
             const int64_t Cc = c0 + 4 * tx;
             const bool full = (j + 4 <= h) && (Cc + 3 < nd.vn) && (Cc + 3 <= R) &&
                               ((reinterpret_cast<uintptr_t>(orow + Cc) & 15u) == 0);
-            if (full) {
+            if (full && !nd.scale.mode) {
                 *reinterpret_cast<uint4 *>(orow + Cc) =
                     make_uint4(vals[q][0], vals[q][1], vals[q][2], vals[q][3]);
             } else {
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    if (j + e < h && Cc + e < nd.vn && Cc + e <= R) orow[Cc + e] = vals[q][e];
+                    if (j + e < h && Cc + e < nd.vn && Cc + e <= R)
+                        orow[Cc + e] = nd.scale.mode ? scale_out(vals[q][e], orow[Cc + e], nd.scale, p)
+                                                     : vals[q][e];
             }
         }
     } else {
@@ -494,7 +496,10 @@ __global__ void __launch_bounds__(256) k_post(const PostNode *__restrict__ nodes
             const int lc = ty + 8 * q;  // tile column
             const int64_t Cc = c0 + lc, R = r0 + tx;
             const bool inside = (i0 + tx < h) && (j0 + lc < h);
-            if (inside && R < nd.vn && Cc < nd.vn && Cc <= R) nd.out[Cc * nd.ldo + R] = so[tx][lc];
+            if (inside && R < nd.vn && Cc < nd.vn && Cc <= R) {
+                uint32_t *o = nd.out + Cc * nd.ldo + R;
+                *o = nd.scale.mode ? scale_out(so[tx][lc], *o, nd.scale, p) : so[tx][lc];
+            }
         }
     }
 }
@@ -517,17 +522,27 @@ __device__ __forceinline__ void ld4c(const uint32_t *base, int64_t ld, int64_t i
     }
 }
 __device__ __forceinline__ void st4(uint32_t *out, int64_t ldo, int64_t cend, int64_t R, int64_t Cc,
-                                    const uint32_t (&v)[4], bool lower_only) {
-    // row R, columns Cc..Cc+3 of the result; only c < cend and (lower_only: c ≤ R)
+                                    const uint32_t (&v)[4], bool lower_only, const OutScale &sc,
+                                    uint32_t p) {
+    // row R, columns Cc..Cc+3 of the result; only c < cend and (lower_only: c ≤ R);
+    // with sc.mode the stored value is α·v + β·old
     uint32_t *row = out + R * ldo;
     const bool full = Cc + 3 < cend && (!lower_only || Cc + 3 <= R) &&
                       ((reinterpret_cast<uintptr_t>(row + Cc) & 15u) == 0);
     if (full) {
-        *reinterpret_cast<uint4 *>(row + Cc) = make_uint4(v[0], v[1], v[2], v[3]);
+        uint4 *q = reinterpret_cast<uint4 *>(row + Cc);
+        if (sc.mode) {
+            const uint4 o = *q;
+            *q = make_uint4(scale_out(v[0], o.x, sc, p), scale_out(v[1], o.y, sc, p),
+                            scale_out(v[2], o.z, sc, p), scale_out(v[3], o.w, sc, p));
+        } else {
+            *q = make_uint4(v[0], v[1], v[2], v[3]);
+        }
     } else {
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-            if (Cc + e < cend && (!lower_only || Cc + e <= R)) row[Cc + e] = v[e];
+            if (Cc + e < cend && (!lower_only || Cc + e <= R))
+                row[Cc + e] = sc.mode ? scale_out(v[e], row[Cc + e], sc, p) : v[e];
     }
 }
 
@@ -600,10 +615,10 @@ __global__ void __launch_bounds__(256) k_post_fused(const PostNode *__restrict__
         // the quadrants end at column h (C11, C21) and 2h (C22); the result
         // has vn rows and columns
         const int64_t c_lo = h < nd.vn ? h : nd.vn, c_hi = 2 * h < nd.vn ? 2 * h : nd.vn;
-        if (i < nd.vn) st4(nd.out, nd.ldo, c_lo, i, iJ + tc, c11[q], diag);     // C11 = Low(U3)
+        if (i < nd.vn) st4(nd.out, nd.ldo, c_lo, i, iJ + tc, c11[q], diag, nd.scale, p);  // C11 = Low(U3)
         if (h + i < nd.vn) {
-            st4(nd.out, nd.ldo, c_lo, h + i, iJ + tc, o21, false);               // C21 = U4
-            st4(nd.out, nd.ldo, c_hi, h + i, h + iJ + tc, o22, diag);            // C22 = Low(U5)
+            st4(nd.out, nd.ldo, c_lo, h + i, iJ + tc, o21, false, nd.scale, p);              // C21 = U4
+            st4(nd.out, nd.ldo, c_hi, h + i, h + iJ + tc, o22, diag, nd.scale, p);           // C22 = Low(U5)
         }
     }
     if (!diag) {
@@ -616,17 +631,23 @@ __global__ void __launch_bounds__(256) k_post_fused(const PostNode *__restrict__
             uint32_t o[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) o[e] = red(sU[tc + e][r] + p4t[q][e] + p3t[q][e], m);
-            if (h + i < nd.vn) st4(nd.out, nd.ldo, h < nd.vn ? h : nd.vn, h + i, iI + tc, o, false);
+            if (h + i < nd.vn)
+                st4(nd.out, nd.ldo, h < nd.vn ? h : nd.vn, h + i, iI + tc, o, false, nd.scale, p);
         }
     }
 }
 
-// Zero row r0 + blockIdx.y of the selected triangle of C.
-__global__ void k_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, int64_t r0) {
+// Row r0 + blockIdx.y of the selected triangle of C for k = 0 (A·Aᵀ = 0):
+// zero, or β·C with an update (OutScale mode 1).
+__global__ void k_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, int64_t r0, OutScale sc,
+                           uint32_t p) {
     const int64_t r = r0 + blockIdx.y;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x)
-        if (upper ? c >= r : c <= r) C[r * ldc + c] = 0;
+        if (upper ? c >= r : c <= r) {
+            uint32_t *o = C + r * ldc + c;
+            *o = sc.mode ? mul_shoup(*o, sc.beta, p) : 0u;
+        }
 }
 
 template <int D, bool U32, int YF, bool RED>
@@ -726,15 +747,20 @@ cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP m
     return cudaGetLastError();
 }
 
-cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st) {
+cudaError_t launch_scale_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, const OutScale &sc,
+                             uint32_t p, cudaStream_t st) {
     for (int64_t r0 = 0; r0 < n; r0 += 65535) {
         const int64_t rows = std::min<int64_t>(65535, n - r0);
         dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 1024), (unsigned)rows);
-        k_zero_tri<<<grid, 256, 0, st>>>(C, n, ldc, upper, r0);
+        k_zero_tri<<<grid, 256, 0, st>>>(C, n, ldc, upper, r0, sc, p);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st) {
+    return launch_scale_tri(C, n, ldc, upper, OutScale{}, 3u, st);
 }
 
 }  // namespace fsk

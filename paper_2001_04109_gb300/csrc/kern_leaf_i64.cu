@@ -86,14 +86,11 @@ __global__ void __launch_bounds__(256) k_leaf_i64(const LeafProd *__restrict__ p
         for (int j = 0; j < 4; ++j) {
             const int64_t c = col0 + tx * 4 + j;
             if (r >= pr.rows || c >= pr.cols) continue;
+            const bool keep = pr.tri == 0 || (pr.tri == 1 && c <= r) || (pr.tri == 2 && c >= r);
+            if (!keep) continue;
+            uint32_t *o = pr.out + r * pr.ldo + c;
             const uint32_t v = (uint32_t)(acc[i][j] % p);
-            if (pr.tri == 0) {
-                pr.out[r * pr.ldo + c] = v;
-            } else if (pr.tri == 1) {
-                if (c <= r) pr.out[r * pr.ldo + c] = v;
-            } else {
-                if (c >= r) pr.out[r * pr.ldo + c] = v;
-            }
+            *o = pr.scale.mode ? scale_out(v, *o, pr.scale, p) : v;
         }
     }
 }

@@ -58,7 +58,7 @@ using namespace tc;
 // running sums may grow unreduced (one add per unit and element) and are
 // brought below 2p once, before the store; otherwise every unit's add is
 // followed by a conditional subtract that keeps them below 2p.
-template <bool LAZY>
+template <bool LAZY, bool SCALED>
 __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__restrict__ prods,
                                                              const LeafTile *__restrict__ tiles,
                                                              const LeafSeg *__restrict__ segs,
@@ -344,32 +344,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
                 if (lane == 0) part_ctr[pc.slot0 * EPI_WARPS + warp] = 0;  // ready for the next launch
             }
             // store the tile's residues
-            const int64_t r = (int64_t)tl.tm * BM + quad * 32 + lane;
-            const int64_t c0 = (int64_t)tl.tn * BN + colq * EPI_COLS;
-            if (r < pr.rows) {
-                uint32_t *orow = pr.out + r * pr.ldo;
-                const bool all_cols = c0 + EPI_COLS <= pr.cols;
-                const bool tri_ok = pr.tri == 0 || (pr.tri == 1 && c0 + EPI_COLS - 1 <= r) ||
-                                    (pr.tri == 2 && c0 >= r);
-                if (all_cols && tri_ok) {
-                    // rows of an odd ldc start at any 4-byte offset
-                    uint32_t *dst = orow + c0;
-                    switch ((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u) {
-                        case 0: store_row<0, EPI_COLS>(dst, acc, p); break;
-                        case 1: store_row<3, EPI_COLS>(dst, acc, p); break;
-                        case 2: store_row<2, EPI_COLS>(dst, acc, p); break;
-                        default: store_row<1, EPI_COLS>(dst, acc, p); break;
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < EPI_COLS; ++e) {
-                        const int64_t c = c0 + e;
-                        const bool keep = c < pr.cols && (pr.tri == 0 || (pr.tri == 1 && c <= r) ||
-                                                          (pr.tri == 2 && c >= r));
-                        if (keep) orow[c] = acc[e] >= p ? acc[e] - p : acc[e];
-                    }
-                }
-            }
+            store_tile_row<EPI_COLS, SCALED>(pr, (int64_t)tl.tm * BM + quad * 32 + lane,
+                                     (int64_t)tl.tn * BN + colq * EPI_COLS, acc, p);
         }
     }
     __syncthreads();
@@ -418,15 +394,17 @@ cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st) {
     const int smem = STAGES * STAGE_BYTES + 1024;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_leaf_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaSuccess;
+        for (auto fn : {k_leaf_tc<true, false>, k_leaf_tc<false, false>, k_leaf_tc<true, true>, k_leaf_tc<false, true>})
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     const int nwork = L.entries ? L.nentries : L.ntiles;
     const int grid = nwork < num_sms ? nwork : num_sms;
-    auto kern = L.max_units <= L.ds.lazy_units ? k_leaf_tc<true> : k_leaf_tc<false>;
+    const bool lazy = L.max_units <= L.ds.lazy_units;
+    auto kern = L.scaled ? (lazy ? k_leaf_tc<true, true> : k_leaf_tc<false, true>)
+                         : (lazy ? k_leaf_tc<true, false> : k_leaf_tc<false, false>);
     // programmatic dependent launch: the prologue may overlap the grid that
     // writes the operands (the producer waits for it before its first load)
     cudaLaunchAttribute attr[1];

@@ -93,7 +93,7 @@ __device__ __forceinline__ void commit_pair(uint64_t *bar, uint16_t mask) {
 
 // LAZY: as in the one-SM leaf, running sums grow unreduced when no tile has
 // more units than ds.lazy_units.
-template <bool LAZY>
+template <bool LAZY, bool SCALED>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     k_leaf_tc2(const LeafProd *__restrict__ prods, const LeafTile *__restrict__ tiles,
                const LeafSeg *__restrict__ segs, int ntiles, const CUtensorMap *__restrict__ tmaps,
@@ -290,31 +290,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
                 for (int e = 0; e < EPI_COLS; ++e) acc[e] = reduce_2p(acc[e], p, m.barrett);
             }
-            const int64_t r = (int64_t)tl.tm * BM + rank * ROWS + quad * 32 + lane;
-            const int64_t c0 = (int64_t)tl.tn * BN + colq * EPI_COLS;
-            if (r < pr.rows) {
-                uint32_t *orow = pr.out + r * pr.ldo;
-                const bool all_cols = c0 + EPI_COLS <= pr.cols;
-                const bool tri_ok = pr.tri == 0 || (pr.tri == 1 && c0 + EPI_COLS - 1 <= r) ||
-                                    (pr.tri == 2 && c0 >= r);
-                if (all_cols && tri_ok) {
-                    uint32_t *dst = orow + c0;
-                    switch ((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u) {
-                        case 0: store_row<0, EPI_COLS>(dst, acc, p); break;
-                        case 1: store_row<3, EPI_COLS>(dst, acc, p); break;
-                        case 2: store_row<2, EPI_COLS>(dst, acc, p); break;
-                        default: store_row<1, EPI_COLS>(dst, acc, p); break;
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < EPI_COLS; ++e) {
-                        const int64_t c = c0 + e;
-                        const bool keep = c < pr.cols && (pr.tri == 0 || (pr.tri == 1 && c <= r) ||
-                                                          (pr.tri == 2 && c >= r));
-                        if (keep) orow[c] = acc[e] >= p ? acc[e] - p : acc[e];
-                    }
-                }
-            }
+            store_tile_row<EPI_COLS, SCALED>(pr, (int64_t)tl.tm * BM + rank * ROWS + quad * 32 + lane,
+                                     (int64_t)tl.tn * BN + colq * EPI_COLS, acc, p);
         }
     }
     __syncthreads();
@@ -337,17 +314,16 @@ cudaError_t launch_leaf_tc2(const TcLaunch &L, int num_sms, cudaStream_t st) {
     const int smem = STAGES * STAGE_BYTES + 1024;
     static int max_pairs = 0;
     if (max_pairs == 0) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_leaf_tc2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_leaf_tc2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaSuccess;
+        for (auto fn : {k_leaf_tc2<true, false>, k_leaf_tc2<false, false>, k_leaf_tc2<true, true>, k_leaf_tc2<false, true>})
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(2 * (num_sms / 2), 1, 1);
         cfg.blockDim = dim3(NUM_THREADS, 1, 1);
         cfg.dynamicSmemBytes = smem;
         int clusters = 0;
-        e = cudaOccupancyMaxActiveClusters(&clusters, k_leaf_tc2<true>, &cfg);
+        e = cudaOccupancyMaxActiveClusters(&clusters, k_leaf_tc2<true, false>, &cfg);
         if (e != cudaSuccess || clusters <= 0) {
             cudaGetLastError();
             clusters = num_sms / 2;
@@ -355,7 +331,9 @@ cudaError_t launch_leaf_tc2(const TcLaunch &L, int num_sms, cudaStream_t st) {
         max_pairs = clusters;
     }
     const int pairs = L.ntiles < max_pairs ? L.ntiles : max_pairs;
-    auto kern = L.max_units <= L.ds.lazy_units ? k_leaf_tc2<true> : k_leaf_tc2<false>;
+    const bool lazy = L.max_units <= L.ds.lazy_units;
+    auto kern = L.scaled ? (lazy ? k_leaf_tc2<true, true> : k_leaf_tc2<false, true>)
+                         : (lazy ? k_leaf_tc2<true, false> : k_leaf_tc2<false, false>);
     // programmatic dependent launch, as for the one-SM leaf
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

@@ -191,6 +191,69 @@ __device__ __forceinline__ void store_row(uint32_t *dst, const uint32_t (&acc)[N
     for (int e = E0 + 4 * NV; e < N; ++e) dst[e] = final_mod(acc[e], p);
 }
 
+// The same with the output update C ← α·R + β·C_old (OutScale mode 1), for
+// a 16-byte aligned row.
+template <int E0, int N>
+__device__ __forceinline__ void store_row_scaled(uint32_t *dst, const uint32_t (&acc)[N], uint32_t p,
+                                                 const OutScale &sc) {
+    static_assert(E0 == 0 && N % 4 == 0, "aligned rows of whole 16-byte groups");
+#pragma unroll
+    for (int v = 0; v < N / 4; ++v) {
+        const int e = 4 * v;
+        uint4 *q = reinterpret_cast<uint4 *>(dst + e);
+        const uint4 o = *q;
+        *q = make_uint4(scale_out(final_mod(acc[e], p), o.x, sc, p), scale_out(final_mod(acc[e + 1], p), o.y, sc, p),
+                        scale_out(final_mod(acc[e + 2], p), o.z, sc, p), scale_out(final_mod(acc[e + 3], p), o.w, sc, p));
+    }
+}
+// One epilogue thread's row of N residues: full rows with 16-byte accesses
+// from the first aligned column, edge rows element by element.  SCALED: the
+// launch has a product that updates the caller's C (OutScale mode 1).
+template <int N, bool SCALED>
+__device__ __forceinline__ void store_tile_row(const LeafProd &pr, int64_t r, int64_t c0,
+                                               const uint32_t (&acc)[N], uint32_t p) {
+    if (r >= pr.rows) return;
+    uint32_t *orow = pr.out + r * pr.ldo;
+    const bool all_cols = c0 + N <= pr.cols;
+    const bool tri_ok = pr.tri == 0 || (pr.tri == 1 && c0 + N - 1 <= r) || (pr.tri == 2 && c0 >= r);
+    if (all_cols && tri_ok) {
+        // rows of an odd ldc start at any 4-byte offset
+        uint32_t *dst = orow + c0;
+        const unsigned mis = (unsigned)((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u);
+        if constexpr (SCALED) {
+            // the update reads C: 16-byte accesses on aligned rows only
+            if (!pr.scale.mode) {
+                for (int e = 0; e < N; ++e) dst[e] = final_mod(acc[e], p);
+            } else if (mis == 0) {
+                store_row_scaled<0, N>(dst, acc, p, pr.scale);
+            } else {
+#pragma unroll
+                for (int e = 0; e < N; ++e) dst[e] = scale_out(final_mod(acc[e], p), dst[e], pr.scale, p);
+            }
+        } else {
+            switch (mis) {
+                case 0: store_row<0, N>(dst, acc, p); break;
+                case 1: store_row<3, N>(dst, acc, p); break;
+                case 2: store_row<2, N>(dst, acc, p); break;
+                default: store_row<1, N>(dst, acc, p); break;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < N; ++e) {
+            const int64_t c = c0 + e;
+            const bool keep = c < pr.cols && (pr.tri == 0 || (pr.tri == 1 && c <= r) || (pr.tri == 2 && c >= r));
+            if (keep) {
+                const uint32_t v = final_mod(acc[e], p);
+                if constexpr (SCALED)
+                    orow[c] = pr.scale.mode ? scale_out(v, orow[c], pr.scale, p) : v;
+                else
+                    orow[c] = v;
+            }
+        }
+    }
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16: D = f32, A = B = bf16,
 // both K-major, shape M×N.
 constexpr uint32_t idesc_bf16(int M, int N) {

@@ -31,7 +31,8 @@ EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsy
            "ffsyrk", "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
            "ffsyrk_plan_set_timing", "ffsyrk_plan_get_timing", "ffsyrk_status_string",
            "ffsyrk_version", "ffsyrk_noalloc", "ffsyrk_leaf_schedule", "ffsyrk_digit_bounds",
-           "ffsyrk_digit_base", "ffsyrk_plan_selftest_timeout"]
+           "ffsyrk_digit_base", "ffsyrk_plan_selftest_timeout", "ffsyrk_with_plan_update",
+           "ffsyrk_update"]
 
 
 class FfsyrkError(RuntimeError):
@@ -85,6 +86,9 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_plan_destroy.argtypes = [vp]
             L.ffsyrk_with_plan.argtypes = [vp, i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
+            L.ffsyrk_with_plan_update.argtypes = [vp, i32, i64, i64, u32, u32, vp, i64, u32, vp, i64,
+                                                  vp]
+            L.ffsyrk_update.argtypes = [i32, i64, i64, u32, u32, vp, i64, u32, vp, i64, vp]
             L.ffsyrk_noalloc.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk_batched.argtypes = [i32, i64, P(i64), P(i64), u32, P(vp), P(i64), P(vp),
                                          P(i64), vp]
@@ -104,6 +108,7 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_digit_base.argtypes = [u32]
             L.ffsyrk_digit_base.restype = i32
             for name in ["ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan", "ffsyrk",
+                         "ffsyrk_with_plan_update", "ffsyrk_update",
                          "ffsyrk_noalloc",
                          "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
                          "ffsyrk_plan_set_timing", "ffsyrk_plan_get_timing"]:
@@ -171,14 +176,21 @@ class Plan:
                 "tile_ctas": i.tile_ctas, "autotuned": i.autotuned, "tuned_ms": i.tuned_ms}
 
     def __call__(self, A: torch.Tensor, C: torch.Tensor | None = None, uplo: str = "lower",
-                 stream=None) -> torch.Tensor:
+                 stream=None, alpha: int = 1, beta: int = 0) -> torch.Tensor:
+        """C = A·Aᵀ mod p, or the update C ← α·A·Aᵀ + β·C mod p (triangle ``uplo``)."""
         n, k = A.shape
         if C is None:
             C = torch.zeros((n, n), dtype=torch.int32, device=A.device)
         pa, lda = _mat_args(A, "A")
         pc, ldc = _mat_args(C, "C")
-        _check(lib().ffsyrk_with_plan(self._h, UPPER if uplo == "upper" else LOWER, n, k, self.p,
-                                      pa, lda, pc, ldc, _stream_handle(stream)), "ffsyrk_with_plan")
+        u = UPPER if uplo == "upper" else LOWER
+        if (alpha, beta) == (1, 0):
+            _check(lib().ffsyrk_with_plan(self._h, u, n, k, self.p, pa, lda, pc, ldc,
+                                          _stream_handle(stream)), "ffsyrk_with_plan")
+        else:
+            _check(lib().ffsyrk_with_plan_update(self._h, u, n, k, self.p, int(alpha) & 0xFFFFFFFF,
+                                                 pa, lda, int(beta) & 0xFFFFFFFF, pc, ldc,
+                                                 _stream_handle(stream)), "ffsyrk_with_plan_update")
         return C
 
     def set_timing(self, enable: bool = True) -> None:
@@ -237,15 +249,20 @@ def digit_base(p: int) -> int:
 
 
 def syrk(A: torch.Tensor, p: int, uplo: str = "lower", C: torch.Tensor | None = None,
-         stream=None) -> torch.Tensor:
-    """C = A·Aᵀ mod p (triangle ``uplo``) through the library's plan cache."""
+         stream=None, alpha: int = 1, beta: int = 0) -> torch.Tensor:
+    """C = A·Aᵀ mod p, or C ← α·A·Aᵀ + β·C mod p (triangle ``uplo``), through the plan cache."""
     n, k = A.shape
     if C is None:
         C = torch.zeros((n, n), dtype=torch.int32, device=A.device)
     pa, lda = _mat_args(A, "A")
     pc, ldc = _mat_args(C, "C")
-    _check(lib().ffsyrk(UPPER if uplo == "upper" else LOWER, n, k, int(p), pa, lda, pc, ldc,
-                        _stream_handle(stream)), "ffsyrk")
+    u = UPPER if uplo == "upper" else LOWER
+    if (alpha, beta) == (1, 0):
+        _check(lib().ffsyrk(u, n, k, int(p), pa, lda, pc, ldc, _stream_handle(stream)), "ffsyrk")
+    else:
+        _check(lib().ffsyrk_update(u, n, k, int(p), int(alpha) & 0xFFFFFFFF, pa, lda,
+                                   int(beta) & 0xFFFFFFFF, pc, ldc, _stream_handle(stream)),
+               "ffsyrk_update")
     return C
 
 

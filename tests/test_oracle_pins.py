@@ -112,3 +112,38 @@ def test_rows_match_full_and_edge_cases():
     assert oracle.syrk(np.zeros((0, 5), dtype=np.uint32), p).shape == (0, 0)
     with pytest.raises(ValueError):
         oracle.syrk_rows(A, p, [30])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_update_against_big_integers(seed):
+    # C ← α·A·Aᵀ + β·C on one triangle (Section 4.2, Table 4), written out in
+    # Python integers: only the triangle changes, α and β reduce mod p
+    rng = np.random.default_rng(100 + seed)
+    for p in [5, 65521, 131071, 8388593]:
+        n, k = int(rng.integers(1, 8)), int(rng.integers(1, 8))
+        A = rng.integers(0, 1 << 32, size=(n, k), dtype=np.uint64).astype(np.uint32)
+        C0 = rng.integers(0, p, size=(n, n), dtype=np.uint64).astype(np.uint32)
+        alpha, beta = int(rng.integers(0, 1 << 32)), int(rng.integers(0, 1 << 32))
+        full = bigint_syrk_full(A, p)
+        for uplo in ["lower", "upper"]:
+            got = oracle.syrk_update(A, p, alpha, C0, beta, uplo)
+            for i in range(n):
+                for j in range(n):
+                    inside = j <= i if uplo == "lower" else j >= i
+                    want = (alpha * full[i][j] + beta * int(C0[i, j])) % p if inside else int(C0[i, j])
+                    assert int(got[i, j]) == want, (p, uplo, i, j)
+
+
+def test_update_special_cases():
+    # α = 1, β = 0 is the product; α = 0 scales C; β = 1 accumulates
+    p = 65521
+    A = inputs.uniform_residues(9, 13, p, seed=8).numpy().view(np.uint32)
+    C0 = inputs.uniform_residues(9, 9, p, seed=9).numpy().view(np.uint32)
+    P = oracle.syrk(A, p, "lower")
+    low = np.tril(np.ones((9, 9), dtype=bool))
+    got = oracle.syrk_update(A, p, 1, C0, 0)
+    assert np.array_equal(got[low], P[low]) and np.array_equal(got[~low], C0[~low])
+    got = oracle.syrk_update(A, p, 0, C0, 3)
+    assert np.array_equal(got[low], (3 * C0[low].astype(np.uint64) % p).astype(np.uint32))
+    got = oracle.syrk_update(A, p, 1, C0, 1)
+    assert np.array_equal(got[low], ((P[low].astype(np.uint64) + C0[low]) % p).astype(np.uint32))
