@@ -137,6 +137,38 @@ ffsyrk_status_t ffsyrk_update(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t
                               const uint32_t *A, int64_t lda, uint32_t beta, uint32_t *C,
                               int64_t ldc, ffsyrk_stream_t stream);
 
+/* Symmetric product with diagonal scaling, C ← α·A·D·Aᵀ + β·C mod p with
+ * D = Diag(d[0..k−1]) (Section 5, Algorithm 5 "syrkd"; for an LDLᵀ update
+ * C ← C − A·D·Aᵀ take α = p − 1, β = 1).  d is a HOST array of k entries
+ * (any uint32, reduced mod p).  D is factored as Δ·Δᵀ without field
+ * extensions: a square root for each square d_j (0 included), the 2×2
+ * matrix of Algorithm 4 ("nrsyf") for each pair of non-squares, and one extra
+ * zero column of A when their number is odd; the scaled Ā = [A 0]·Δ goes
+ * through the same path as ffsyrk_with_plan_update.  The plan must have
+ * max_k ≥ k + 1 when d holds an odd number of non-squares
+ * (FFSYRK_ERR_TOO_LARGE otherwise).  The first call needing more scratch than
+ * the plan holds allocates it (cudaMalloc, after synchronising `stream`);
+ * the column table is copied from pageable host memory.  Other rules as for
+ * ffsyrk_with_plan_update. */
+ffsyrk_status_t ffsyrkd_with_plan_update(ffsyrk_plan_t plan, ffsyrk_uplo_t uplo, int64_t n,
+                                         int64_t k, uint32_t p, uint32_t alpha, const uint32_t *A,
+                                         int64_t lda, const uint32_t *d, uint32_t beta, uint32_t *C,
+                                         int64_t ldc, ffsyrk_stream_t stream);
+
+/* The same through the internal plan cache (plans made with max_k = k + 1).
+ * Thread-safe. */
+ffsyrk_status_t ffsyrkd_update(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
+                               const uint32_t *A, int64_t lda, const uint32_t *d, uint32_t beta,
+                               uint32_t *C, int64_t ldc, ffsyrk_stream_t stream);
+
+/* The factorisation step of Algorithm 5 on the host (for tests and tools;
+ * needs no GPU): for the k entries d, writes the column transform of
+ * Ā = [A 0]·Δ -- column c of Ā is u[c]·Ā_c + v[c]·Ā_{partner[c]}, partner
+ * −1 meaning none, Ā_c = 0 for c ≥ k -- into partner, u, v (each with room
+ * for k + 1 entries).  Returns the column count of Ā (k or k + 1), or −1. */
+int32_t ffsyrkd_factor(uint32_t p, int64_t k, const uint32_t *d, int32_t *partner, uint32_t *u,
+                       uint32_t *v);
+
 /* `count` independent products C_t = A_t·A_tᵀ mod p of uneven sizes n[t] × k[t],
  * all with the same p and uplo.  n, k, lda, ldc are HOST arrays of `count`
  * values; A and C are HOST arrays of `count` DEVICE pointers.  Problems with

@@ -12,6 +12,8 @@ Contents
   Algorithm 2 of the paper reaches exactly, Section 3).
 * :func:`syrk_update` -- the definition of the update C ← α·A·Aᵀ + β·C mod
   p on one triangle (Section 4.2, Table 4), from :func:`syrk`.
+* :func:`syrkd` -- the plain definition of A·D·Aᵀ mod p for a diagonal D
+  (the product Algorithm 5, syrkd, computes; Section 5), in ``syrk_oracle.c``.
 * :mod:`oracle.field` -- primality, Legendre symbols, square roots and the
   skew-orthogonal Y of Section 3.1 (Prop. 3.2, Prop. 3.3, Algorithm 3).
 * :mod:`oracle.alg2` -- Algorithm 2 itself written step by step over F_p in
@@ -57,6 +59,8 @@ def _load():
         lib.oracle_syrk_modp.restype = ctypes.c_int
         lib.oracle_syrk_rows.argtypes = [i64, i64, u32, p, i64, p, i64, p, i64, ctypes.c_int]
         lib.oracle_syrk_rows.restype = ctypes.c_int
+        lib.oracle_syrkd_modp.argtypes = [i64, i64, u32, p, i64, p, p, i64, ctypes.c_int, ctypes.c_int]
+        lib.oracle_syrkd_modp.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -113,6 +117,27 @@ def syrk_update(A, p: int, alpha: int, C, beta: int, uplo: str = "lower",
     mask = np.tril(np.ones((n, n), dtype=bool)) if uplo == "lower" else np.triu(np.ones((n, n), dtype=bool))
     upd = (a * P + b * C.astype(np.uint64)) % np.uint64(p)  # < 2·p² < 2^49
     C[mask] = upd[mask].astype(np.uint32)
+    return C
+
+
+def syrkd(A, d, p: int, uplo: str = "lower", threads: int | None = None) -> np.ndarray:
+    """Schoolbook A·Diag(d)·Aᵀ mod p of an n×k matrix and k diagonal entries.
+
+    Entries of A and d may be any uint32 (reduced mod p first).  ``uplo`` as
+    for :func:`syrk`; unwritten entries are 0.  Returns an n×n uint32 array.
+    """
+    A = _as_u32(A)
+    n, k = A.shape
+    dv = np.ascontiguousarray(np.asarray(d, dtype=np.uint64).astype(np.uint32))
+    if dv.shape != (k,):
+        raise ValueError("d must hold one entry per column of A")
+    C = np.zeros((n, n), dtype=np.uint32)
+    code = {"lower": 0, "upper": 1, "full": 2}[uplo]
+    rc = _load().oracle_syrkd_modp(n, k, p, A.ctypes.data, max(k, 1),
+                                   dv.ctypes.data if k else None, C.ctypes.data, max(n, 1), code,
+                                   threads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle_syrkd_modp rejected its arguments")
     return C
 
 

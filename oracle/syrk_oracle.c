@@ -47,6 +47,8 @@ typedef struct {
     int64_t n, k;
     uint64_t p;
     const uint32_t *A;
+    const uint32_t *B; /* the right-hand rows: A, or A with column l times d[l] */
+    const uint32_t *d; /* NULL, or the diagonal of D for A·D·Aᵀ */
     int64_t lda;
     uint32_t *C;
     int64_t ldc;
@@ -65,7 +67,7 @@ static void *worker(void *arg) {
             const uint32_t *ri = j->A + i * j->lda;
             uint32_t *out = j->C + r * j->ldc;
             for (int64_t c = 0; c < j->n; ++c)
-                out[c] = dot_mod_p(ri, j->A + c * j->lda, j->k, j->p);
+                out[c] = dot_mod_p(ri, j->B + c * j->lda, j->k, j->p);
         } else {
             int64_t i = r;
             const uint32_t *ri = j->A + i * j->lda;
@@ -73,7 +75,7 @@ static void *worker(void *arg) {
             if (j->kind == JOB_LOWER) c1 = i + 1;
             if (j->kind == JOB_UPPER) c0 = i;
             for (int64_t c = c0; c < c1; ++c)
-                j->C[i * j->ldc + c] = dot_mod_p(ri, j->A + c * j->lda, j->k, j->p);
+                j->C[i * j->ldc + c] = dot_mod_p(ri, j->B + c * j->lda, j->k, j->p);
         }
     }
     return NULL;
@@ -92,7 +94,20 @@ static uint32_t *reduce_copy(int64_t n, int64_t k, uint64_t p, const uint32_t *A
 static int run(job_t proto, int nthreads) {
     uint32_t *R = reduce_copy(proto.n, proto.k, proto.p, proto.A, proto.lda);
     if (!R) return -1;
+    uint32_t *S = NULL; /* with a diagonal: S[i][l] = R[i][l]·(d[l] mod p) mod p */
+    if (proto.d) {
+        S = reduce_copy(proto.n, proto.k, proto.p, R, proto.k > 0 ? proto.k : 1);
+        if (!S) {
+            free(R);
+            return -1;
+        }
+        for (int64_t i = 0; i < proto.n; ++i)
+            for (int64_t l = 0; l < proto.k; ++l)
+                S[i * proto.k + l] =
+                    (uint32_t)((uint64_t)R[i * proto.k + l] * (proto.d[l] % proto.p) % proto.p);
+    }
     proto.A = R;
+    proto.B = S ? S : R;
     proto.lda = proto.k > 0 ? proto.k : 1;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 1024) nthreads = 1024;
@@ -102,6 +117,7 @@ static int run(job_t proto, int nthreads) {
         free(th);
         free(jobs);
         free(R);
+        free(S);
         return -1;
     }
     int started = 0, rc = 0;
@@ -121,6 +137,7 @@ static int run(job_t proto, int nthreads) {
     free(th);
     free(jobs);
     free(R);
+    free(S);
     return rc < 0 && started == 0 ? -1 : 0;
 }
 
@@ -172,5 +189,30 @@ int oracle_syrk_rows(int64_t n, int64_t k, uint32_t p, const uint32_t *A, int64_
     j.ldc = ldo;
     j.rows = rows;
     j.nrows = nrows;
+    return run(j, nthreads);
+}
+
+/*
+ * A·D·Aᵀ mod p with D = Diag(d[0..k-1]) (the product Algorithm 5, syrkd,
+ * computes): C[i][j] = ( Σ_l (A[i][l] mod p)·(d[l] mod p)·(A[j][l] mod p) ) mod p,
+ * on the triangle uplo (0 lower, 1 upper, 2 every entry).  The right-hand row
+ * is scaled first, (A[j][l]·d[l]) mod p, so every product stays below p².
+ */
+int oracle_syrkd_modp(int64_t n, int64_t k, uint32_t p, const uint32_t *A, int64_t lda,
+                      const uint32_t *d, uint32_t *C, int64_t ldc, int uplo, int nthreads) {
+    if (n < 0 || k < 0 || p < 2 || lda < (k > 1 ? k : 1) || ldc < (n > 1 ? n : 1)) return -1;
+    if (uplo < 0 || uplo > 2 || (k > 0 && !d)) return -1;
+    if (n == 0) return 0;
+    job_t j;
+    memset(&j, 0, sizeof j);
+    j.kind = uplo == 0 ? JOB_LOWER : (uplo == 1 ? JOB_UPPER : JOB_FULL);
+    j.n = n;
+    j.k = k;
+    j.p = p;
+    j.A = A;
+    j.d = d;
+    j.lda = lda;
+    j.C = C;
+    j.ldc = ldc;
     return run(j, nthreads);
 }

@@ -256,6 +256,51 @@ EncodeTiledFn get_encode_fn() {
 namespace fsk {
 DigitScheme digit_scheme_for(uint32_t p) { return make_digits(p); }
 
+// Algorithm 5 (syrkd), planning step: Diag(d) = Δ·Δᵀ with Δ block diagonal
+// -- 1×1 blocks √d_c for squares (0 included), 2×2 blocks from Algorithm 4
+// (nrsyf) for consecutive pairs of non-squares, and, when their number is
+// odd, one extra column of A (zero) given the last non-square's d again.
+// Column c of Ā = [A 0]·Δ is u_c·Ā_c + v_c·Ā_{partner_c} (partner −1: none).
+// Returns the column count of Ā (k or k + 1).
+int64_t diag_factor(uint32_t p, int64_t k, const uint32_t *d, std::vector<int32_t> &partner,
+                    std::vector<uint32_t> &u, std::vector<uint32_t> &v) {
+    std::vector<int64_t> ns;  // columns with a non-square entry
+    partner.assign((size_t)k + 1, -1);
+    u.assign((size_t)k + 1, 0);
+    v.assign((size_t)k + 1, 0);
+    for (int64_t c = 0; c < k; ++c) {
+        const uint64_t dc = d[c] % p;
+        if (host::is_square(dc, p))
+            u[c] = (uint32_t)host::sqrt_mod(dc, p);
+        else
+            ns.push_back(c);
+    }
+    int64_t kk = k;
+    std::vector<uint64_t> dval;
+    for (int64_t c : ns) dval.push_back(d[c] % p);
+    if (ns.size() % 2 == 1) {
+        dval.push_back(dval.back());
+        ns.push_back(k);
+        kk = k + 1;
+    }
+    for (size_t q = 0; q + 1 < ns.size(); q += 2) {
+        const int64_t i = ns[q], j = ns[q + 1];
+        uint64_t a, b, c, e;
+        host::nrsyf(dval[q], dval[q + 1], p, a, b, c, e);
+        // [Ā_i Ā_j] = [A_i A_j]·[[a, b], [c, e]]
+        partner[i] = (int32_t)j;
+        u[i] = (uint32_t)a;
+        v[i] = (uint32_t)c;
+        partner[j] = (int32_t)i;
+        u[j] = (uint32_t)e;
+        v[j] = (uint32_t)b;
+    }
+    partner.resize((size_t)kk);
+    u.resize((size_t)kk);
+    v.resize((size_t)kk);
+    return kk;
+}
+
 int count_units(const LeafSeg *segs, int nseg) {
     int u = 0;
     for (int i = 0; i < nseg; ++i) u += segs[i].first ? 1 : 0;
@@ -376,6 +421,11 @@ struct ffsyrk_plan_st {
     Layout lay;
     Descs desc;
     OutScale scale{};  // how the current call updates C
+    // diagonal scaling (Algorithm 5): Ā = [A 0]·Δ and its column table
+    uint32_t *dbar = nullptr;
+    int64_t dbar_bytes = 0;
+    char *dtab = nullptr;
+    int64_t dtab_bytes = 0;
     // optional per-stage timing
     bool timing = false;
     bool timed_call = false;
@@ -976,6 +1026,8 @@ void destroy_plan(ffsyrk_plan_st *pl) {
         cudaFree(pl->ws);
     }
     if (pl->part) cudaFree(pl->part);
+    if (pl->dbar) cudaFree(pl->dbar);
+    if (pl->dtab) cudaFree(pl->dtab);
     drop_graph(pl);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     if (pl->desc_done) cudaEventDestroy(pl->desc_done);
@@ -1409,6 +1461,90 @@ uint64_t g_clock = 0;
 constexpr size_t kCacheMax = 8;
 }  // namespace
 
+ffsyrk_status_t ffsyrkd_with_plan_update(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n,
+                                         int64_t k, uint32_t p, uint32_t alpha, const uint32_t *A,
+                                         int64_t lda, const uint32_t *d, uint32_t beta, uint32_t *C,
+                                         int64_t ldc, ffsyrk_stream_t stream) {
+    if (!pl) return FFSYRK_ERR_INVALID_ARG;
+    if (p != pl->p) return FFSYRK_ERR_INVALID_ARG;
+    if (uplo != FFSYRK_LOWER && uplo != FFSYRK_UPPER) return FFSYRK_ERR_INVALID_ARG;
+    if (n < 0 || k < 0 || k >= INT32_MAX) return FFSYRK_ERR_INVALID_ARG;
+    if (lda < std::max<int64_t>(1, k) || ldc < std::max<int64_t>(1, n)) return FFSYRK_ERR_INVALID_ARG;
+    if (n > 0 && (C == nullptr || (k > 0 && (A == nullptr || d == nullptr)))) return FFSYRK_ERR_INVALID_ARG;
+    if (n == 0) return FFSYRK_SUCCESS;
+    std::vector<int32_t> partner;
+    std::vector<uint32_t> u, v;
+    const int64_t kk = diag_factor(p, k, d, partner, u, v);
+    if (n > pl->max_n || kk > pl->max_k) return FFSYRK_ERR_TOO_LARGE;
+    if (kk == 0) return ffsyrk_with_plan_update(pl, uplo, n, 0, p, alpha, A, std::max<int64_t>(1, k), beta, C, ldc, stream);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != pl->device) return FFSYRK_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // scratch for Ā (rows of a multiple of 4 entries) and the column table
+    const int64_t ldb = rup(kk, 4);
+    const int64_t need = n * ldb * 4;
+    const int64_t tab = rup(kk * 4, 64) + 2 * kk * (int64_t)sizeof(MulConst);
+    if (need > pl->dbar_bytes || tab > pl->dtab_bytes) {
+        cudaStreamSynchronize(st);
+        if (need > pl->dbar_bytes) {
+            if (pl->dbar) cudaFree(pl->dbar);
+            pl->dbar = nullptr;
+            pl->dbar_bytes = 0;
+            if (cudaMalloc(&pl->dbar, (size_t)need) != cudaSuccess) {
+                cudaGetLastError();
+                return FFSYRK_ERR_ALLOC;
+            }
+            pl->dbar_bytes = need;
+        }
+        if (tab > pl->dtab_bytes) {
+            if (pl->dtab) cudaFree(pl->dtab);
+            pl->dtab = nullptr;
+            pl->dtab_bytes = 0;
+            if (cudaMalloc(&pl->dtab, (size_t)tab) != cudaSuccess) {
+                cudaGetLastError();
+                return FFSYRK_ERR_ALLOC;
+            }
+            pl->dtab_bytes = tab;
+        }
+    }
+    std::vector<char> host((size_t)tab, 0);
+    std::vector<MulConst> uc((size_t)kk), vc((size_t)kk);
+    for (int64_t c = 0; c < kk; ++c) {
+        uc[(size_t)c] = make_mul(u[(size_t)c], p);
+        vc[(size_t)c] = make_mul(v[(size_t)c], p);
+    }
+    const int64_t uoff = rup(kk * 4, 64), voff = uoff + kk * (int64_t)sizeof(MulConst);
+    memcpy(host.data(), partner.data(), (size_t)kk * 4);
+    memcpy(host.data() + uoff, uc.data(), (size_t)kk * sizeof(MulConst));
+    memcpy(host.data() + voff, vc.data(), (size_t)kk * sizeof(MulConst));
+    // a pageable copy: staged before it returns, so `host` may go away
+    if (cudaMemcpyAsync(pl->dtab, host.data(), (size_t)tab, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return FFSYRK_ERR_CUDA;
+    if (launch_col_transform(A, lda, n, k, kk, reinterpret_cast<const int32_t *>(pl->dtab),
+                             reinterpret_cast<const MulConst *>(pl->dtab + uoff),
+                             reinterpret_cast<const MulConst *>(pl->dtab + voff), pl->dbar, ldb,
+                             pl->mp, st) != cudaSuccess)
+        return FFSYRK_ERR_CUDA;
+    return ffsyrk_with_plan_update(pl, uplo, n, kk, p, alpha, pl->dbar, ldb, beta, C, ldc, stream);
+}
+
+int32_t ffsyrkd_factor(uint32_t p, int64_t k, const uint32_t *d, int32_t *partner, uint32_t *u,
+                       uint32_t *v) {
+    if (validate_p(p) != FFSYRK_SUCCESS || k < 0 || k >= INT32_MAX || (k > 0 && !d) ||
+        !partner || !u || !v)
+        return -1;
+    std::vector<int32_t> pt;
+    std::vector<uint32_t> uu, vv;
+    const int64_t kk = diag_factor(p, k, d, pt, uu, vv);
+    for (int64_t c = 0; c < kk; ++c) {
+        partner[c] = pt[(size_t)c];
+        u[c] = uu[(size_t)c];
+        v[c] = vv[(size_t)c];
+    }
+    return (int32_t)kk;
+}
+
 extern "C" ffsyrk_status_t ffsyrk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
                                   const uint32_t *A, int64_t lda, uint32_t *C, int64_t ldc,
                                   ffsyrk_stream_t stream) {
@@ -1442,6 +1578,37 @@ extern "C" ffsyrk_status_t ffsyrk_update(ffsyrk_uplo_t uplo, int64_t n, int64_t 
     }
     it->second.last_use = ++g_clock;
     return ffsyrk_with_plan_update(it->second.plan, uplo, n, k, p, alpha, A, lda, beta, C, ldc, stream);
+}
+
+extern "C" ffsyrk_status_t ffsyrkd_update(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
+                                          uint32_t alpha, const uint32_t *A, int64_t lda,
+                                          const uint32_t *d, uint32_t beta, uint32_t *C,
+                                          int64_t ldc, ffsyrk_stream_t stream) {
+    ffsyrk_status_t s = validate_p(p);
+    if (s != FFSYRK_SUCCESS) return s;
+    if (n < 0 || k < 0 || k >= INT32_MAX) return FFSYRK_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFSYRK_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    // one more column than A for an odd number of non-squares in d
+    auto key = std::make_tuple(dev, p, n, k + 1);
+    auto it = g_cache.find(key);
+    if (it == g_cache.end()) {
+        if (g_cache.size() >= kCacheMax) {
+            auto victim = g_cache.begin();
+            for (auto jt = g_cache.begin(); jt != g_cache.end(); ++jt)
+                if (jt->second.last_use < victim->second.last_use) victim = jt;
+            ffsyrk_plan_destroy(victim->second.plan);
+            g_cache.erase(victim);
+        }
+        ffsyrk_plan_t pl = nullptr;
+        s = ffsyrk_plan(&pl, p, n, k + 1, nullptr);
+        if (s != FFSYRK_SUCCESS) return s;
+        it = g_cache.emplace(key, CacheEntry{pl, 0}).first;
+    }
+    it->second.last_use = ++g_clock;
+    return ffsyrkd_with_plan_update(it->second.plan, uplo, n, k, p, alpha, A, lda, d, beta, C, ldc,
+                                    stream);
 }
 
 // ---- batched: many independent problems in one grouped launch ----

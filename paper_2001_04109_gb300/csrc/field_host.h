@@ -130,6 +130,34 @@ inline YChoice choose_y(uint64_t p) {
     return y;
 }
 
+// A sum of two squares a² + b² ≡ k (mod p) for any k (Algorithm 3, SoS):
+// a square k is a² + 0²; otherwise, with s the least non-square, c² = s − 1
+// (a square, being smaller than s) and a² = k·s⁻¹ (a quotient of two
+// non-squares, so a square), a² + (a·c)² = a²·s = k.
+inline void sos(uint64_t k, uint64_t p, uint64_t &a, uint64_t &b) {
+    k %= p;
+    if (is_square(k, p)) {
+        a = sqrt_mod(k, p);
+        b = 0;
+        return;
+    }
+    const uint64_t s = least_non_square(p);
+    const uint64_t c = sqrt_mod(s - 1, p);
+    a = sqrt_mod(mulmod64(k, powmod64(s, p - 2, p), p), p);
+    b = mulmod64(a, c, p);
+}
+
+// Algorithm 4 (nrsyf): for two non-squares α, β a matrix Y = [[a, b], [c, d]]
+// with Y·Yᵀ = Diag(α, β): α = a² + b² (SoS), d = a·√(β/α), c = −b·d/a.
+// a ≠ 0 because α is not a square.
+inline void nrsyf(uint64_t alpha, uint64_t beta, uint64_t p, uint64_t &a, uint64_t &b, uint64_t &c,
+                  uint64_t &d) {
+    sos(alpha, p, a, b);
+    const uint64_t ainv = powmod64(a, p - 2, p);
+    d = mulmod64(a, sqrt_mod(mulmod64(beta, powmod64(alpha, p - 2, p), p), p), p);
+    c = (p - mulmod64(mulmod64(b, d, p), ainv, p)) % p;
+}
+
 // Balanced base-256 digits of s ∈ [−(p−1)/2, (p−1)/2]: the low D−1 digits lie
 // in [−128, 127]; the top one takes the rest.
 inline void split_digits(int64_t s, int D, int *d) {

@@ -32,7 +32,7 @@ EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsy
            "ffsyrk_plan_set_timing", "ffsyrk_plan_get_timing", "ffsyrk_status_string",
            "ffsyrk_version", "ffsyrk_noalloc", "ffsyrk_leaf_schedule", "ffsyrk_digit_bounds",
            "ffsyrk_digit_base", "ffsyrk_plan_selftest_timeout", "ffsyrk_with_plan_update",
-           "ffsyrk_update"]
+           "ffsyrk_update", "ffsyrkd_with_plan_update", "ffsyrkd_update", "ffsyrkd_factor"]
 
 
 class FfsyrkError(RuntimeError):
@@ -89,6 +89,11 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_with_plan_update.argtypes = [vp, i32, i64, i64, u32, u32, vp, i64, u32, vp, i64,
                                                   vp]
             L.ffsyrk_update.argtypes = [i32, i64, i64, u32, u32, vp, i64, u32, vp, i64, vp]
+            L.ffsyrkd_with_plan_update.argtypes = [vp, i32, i64, i64, u32, u32, vp, i64, P(u32), u32,
+                                                   vp, i64, vp]
+            L.ffsyrkd_update.argtypes = [i32, i64, i64, u32, u32, vp, i64, P(u32), u32, vp, i64, vp]
+            L.ffsyrkd_factor.argtypes = [u32, i64, P(u32), P(i32), P(u32), P(u32)]
+            L.ffsyrkd_factor.restype = i32
             L.ffsyrk_noalloc.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk_batched.argtypes = [i32, i64, P(i64), P(i64), u32, P(vp), P(i64), P(vp),
                                          P(i64), vp]
@@ -108,7 +113,8 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_digit_base.argtypes = [u32]
             L.ffsyrk_digit_base.restype = i32
             for name in ["ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan", "ffsyrk",
-                         "ffsyrk_with_plan_update", "ffsyrk_update",
+                         "ffsyrk_with_plan_update", "ffsyrk_update", "ffsyrkd_with_plan_update",
+                         "ffsyrkd_update",
                          "ffsyrk_noalloc",
                          "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
                          "ffsyrk_plan_set_timing", "ffsyrk_plan_get_timing"]:
@@ -193,6 +199,21 @@ class Plan:
                                                  _stream_handle(stream)), "ffsyrk_with_plan_update")
         return C
 
+    def syrkd(self, A: torch.Tensor, d, C: torch.Tensor | None = None, uplo: str = "lower",
+              stream=None, alpha: int = 1, beta: int = 0) -> torch.Tensor:
+        """C ← α·A·Diag(d)·Aᵀ + β·C mod p (Algorithm 5); d holds k host values."""
+        n, k = A.shape
+        if C is None:
+            C = torch.zeros((n, n), dtype=torch.int32, device=A.device)
+        pa, lda = _mat_args(A, "A")
+        pc, ldc = _mat_args(C, "C")
+        dv = _u32_array(d, k)
+        _check(lib().ffsyrkd_with_plan_update(self._h, UPPER if uplo == "upper" else LOWER, n, k,
+                                              self.p, int(alpha) & 0xFFFFFFFF, pa, lda, dv,
+                                              int(beta) & 0xFFFFFFFF, pc, ldc,
+                                              _stream_handle(stream)), "ffsyrkd_with_plan_update")
+        return C
+
     def set_timing(self, enable: bool = True) -> None:
         _check(lib().ffsyrk_plan_set_timing(self._h, 1 if enable else 0), "ffsyrk_plan_set_timing")
 
@@ -238,6 +259,41 @@ def digit_bounds(p: int) -> list[int]:
     if D < 0:
         raise ValueError("bad p")
     return [out[t] for t in range(D)]
+
+
+def _u32_array(d, k: int):
+    vals = [int(x) & 0xFFFFFFFF for x in (d.tolist() if hasattr(d, "tolist") else d)]
+    if len(vals) != k:
+        raise ValueError("d must hold one entry per column of A")
+    return (ctypes.c_uint32 * max(k, 1))(*vals)
+
+
+def syrkd(A: torch.Tensor, d, p: int, uplo: str = "lower", C: torch.Tensor | None = None,
+          stream=None, alpha: int = 1, beta: int = 0) -> torch.Tensor:
+    """C ← α·A·Diag(d)·Aᵀ + β·C mod p (Algorithm 5) through the plan cache."""
+    n, k = A.shape
+    if C is None:
+        C = torch.zeros((n, n), dtype=torch.int32, device=A.device)
+    pa, lda = _mat_args(A, "A")
+    pc, ldc = _mat_args(C, "C")
+    dv = _u32_array(d, k)
+    _check(lib().ffsyrkd_update(UPPER if uplo == "upper" else LOWER, n, k, int(p),
+                                int(alpha) & 0xFFFFFFFF, pa, lda, dv, int(beta) & 0xFFFFFFFF, pc, ldc,
+                                _stream_handle(stream)), "ffsyrkd_update")
+    return C
+
+
+def syrkd_factor(p: int, d) -> tuple[int, list[int], list[int], list[int]]:
+    """Algorithm 5's column transform for diagonal d: (columns of Ā, partner, u, v)."""
+    k = len(d)
+    dv = _u32_array(d, k)
+    pt = (ctypes.c_int32 * (k + 1))()
+    u = (ctypes.c_uint32 * (k + 1))()
+    v = (ctypes.c_uint32 * (k + 1))()
+    kk = lib().ffsyrkd_factor(int(p), k, dv, pt, u, v)
+    if kk < 0:
+        raise ValueError("bad p or d")
+    return kk, list(pt[:kk]), list(u[:kk]), list(v[:kk])
 
 
 def digit_base(p: int) -> int:
