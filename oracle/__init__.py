@@ -14,6 +14,8 @@ Contents
   p on one triangle (Section 4.2, Table 4), from :func:`syrk`.
 * :func:`syrkd` -- the plain definition of A·D·Aᵀ mod p for a diagonal D
   (the product Algorithm 5, syrkd, computes; Section 5), in ``syrk_oracle.c``.
+* :func:`syrkbd` -- the plain definition of A·B·Aᵀ mod p for a symmetric
+  tridiagonal B, which holds Algorithm 6's block-diagonal B (Section 5).
 * :mod:`oracle.field` -- primality, Legendre symbols, square roots and the
   skew-orthogonal Y of Section 3.1 (Prop. 3.2, Prop. 3.3, Algorithm 3).
 * :mod:`oracle.alg2` -- Algorithm 2 itself written step by step over F_p in
@@ -61,6 +63,9 @@ def _load():
         lib.oracle_syrk_rows.restype = ctypes.c_int
         lib.oracle_syrkd_modp.argtypes = [i64, i64, u32, p, i64, p, p, i64, ctypes.c_int, ctypes.c_int]
         lib.oracle_syrkd_modp.restype = ctypes.c_int
+        lib.oracle_syrkbd_modp.argtypes = [i64, i64, u32, p, i64, p, p, p, i64, ctypes.c_int,
+                                           ctypes.c_int]
+        lib.oracle_syrkbd_modp.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -138,6 +143,35 @@ def syrkd(A, d, p: int, uplo: str = "lower", threads: int | None = None) -> np.n
                                    threads or default_threads())
     if rc != 0:
         raise ValueError("oracle_syrkd_modp rejected its arguments")
+    return C
+
+
+def syrkbd(A, d, e, p: int, uplo: str = "lower", threads: int | None = None) -> np.ndarray:
+    """Schoolbook A·B·Aᵀ mod p, B symmetric tridiagonal: B[l][l] = d[l], B[l][l+1] = B[l+1][l] = e[l].
+
+    Algorithm 6 (syrkbd) takes a block-diagonal B with 1×1 and 2×2 blocks,
+    i.e. a tridiagonal B whose nonzero e[l] are never adjacent; the
+    definition here holds for any symmetric tridiagonal B.  ``e`` has k − 1
+    entries (or None).  Entries may be any uint32 (reduced mod p first).
+    """
+    A = _as_u32(A)
+    n, k = A.shape
+    dv = np.ascontiguousarray(np.asarray(d, dtype=np.uint64).astype(np.uint32))
+    if dv.shape != (k,):
+        raise ValueError("d must hold one entry per column of A")
+    ev = None
+    if e is not None and k > 1:
+        ev = np.ascontiguousarray(np.asarray(e, dtype=np.uint64).astype(np.uint32))
+        if ev.shape != (k - 1,):
+            raise ValueError("e must hold k - 1 entries")
+    C = np.zeros((n, n), dtype=np.uint32)
+    code = {"lower": 0, "upper": 1, "full": 2}[uplo]
+    rc = _load().oracle_syrkbd_modp(n, k, p, A.ctypes.data, max(k, 1),
+                                    dv.ctypes.data if k else None,
+                                    ev.ctypes.data if ev is not None else None, C.ctypes.data,
+                                    max(n, 1), code, threads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle_syrkbd_modp rejected its arguments")
     return C
 
 

@@ -48,7 +48,8 @@ typedef struct {
     uint64_t p;
     const uint32_t *A;
     const uint32_t *B; /* the right-hand rows: A, or A with column l times d[l] */
-    const uint32_t *d; /* NULL, or the diagonal of D for A·D·Aᵀ */
+    const uint32_t *d; /* NULL, or the diagonal of D for A·D·Aᵀ (of B for A·B·Aᵀ) */
+    const uint32_t *e; /* NULL, or B's first off-diagonal: B[l][l+1] = B[l+1][l] = e[l] */
     int64_t lda;
     uint32_t *C;
     int64_t ldc;
@@ -94,17 +95,27 @@ static uint32_t *reduce_copy(int64_t n, int64_t k, uint64_t p, const uint32_t *A
 static int run(job_t proto, int nthreads) {
     uint32_t *R = reduce_copy(proto.n, proto.k, proto.p, proto.A, proto.lda);
     if (!R) return -1;
-    uint32_t *S = NULL; /* with a diagonal: S[i][l] = R[i][l]·(d[l] mod p) mod p */
+    /* with a diagonal: S[i][l] = R[i][l]·(d[l] mod p) mod p; with an
+     * off-diagonal too, S = (A·B) mod p for the symmetric tridiagonal B:
+     * S[i][l] = R[i][l]·d[l] + R[i][l−1]·e[l−1] + R[i][l+1]·e[l] (mod p) */
+    uint32_t *S = NULL;
     if (proto.d) {
-        S = reduce_copy(proto.n, proto.k, proto.p, R, proto.k > 0 ? proto.k : 1);
+        const int64_t k = proto.k;
+        const uint64_t p = proto.p;
+        S = reduce_copy(proto.n, k, p, R, k > 0 ? k : 1);
         if (!S) {
             free(R);
             return -1;
         }
-        for (int64_t i = 0; i < proto.n; ++i)
-            for (int64_t l = 0; l < proto.k; ++l)
-                S[i * proto.k + l] =
-                    (uint32_t)((uint64_t)R[i * proto.k + l] * (proto.d[l] % proto.p) % proto.p);
+        for (int64_t i = 0; i < proto.n; ++i) {
+            const uint32_t *ri = R + i * k;
+            for (int64_t l = 0; l < k; ++l) {
+                uint64_t s = (uint64_t)ri[l] * (proto.d[l] % p) % p;
+                if (proto.e && l > 0) s += (uint64_t)ri[l - 1] * (proto.e[l - 1] % p) % p;
+                if (proto.e && l + 1 < k) s += (uint64_t)ri[l + 1] * (proto.e[l] % p) % p;
+                S[i * k + l] = (uint32_t)(s % p);
+            }
+        }
     }
     proto.A = R;
     proto.B = S ? S : R;
@@ -211,6 +222,35 @@ int oracle_syrkd_modp(int64_t n, int64_t k, uint32_t p, const uint32_t *A, int64
     j.p = p;
     j.A = A;
     j.d = d;
+    j.lda = lda;
+    j.C = C;
+    j.ldc = ldc;
+    return run(j, nthreads);
+}
+
+/*
+ * A·B·Aᵀ mod p for a symmetric tridiagonal B given by its diagonal d[0..k-1]
+ * and first off-diagonal e[0..k-2] (B[l][l+1] = B[l+1][l] = e[l]); this holds
+ * the block-diagonal B of Algorithm 6 (syrkbd, Section 5), whose 2×2 blocks
+ * sit on non-overlapping (l, l+1).  C[i][j] = Σ_l (A[i][l] mod p)·(A·B)[j][l]
+ * mod p with (A·B)[j][l] reduced mod p first; e may be NULL (B diagonal).
+ * Triangle uplo as above.  Returns 0, or -1 on bad arguments.
+ */
+int oracle_syrkbd_modp(int64_t n, int64_t k, uint32_t p, const uint32_t *A, int64_t lda,
+                       const uint32_t *d, const uint32_t *e, uint32_t *C, int64_t ldc, int uplo,
+                       int nthreads) {
+    if (n < 0 || k < 0 || p < 2 || lda < (k > 1 ? k : 1) || ldc < (n > 1 ? n : 1)) return -1;
+    if (uplo < 0 || uplo > 2 || (k > 0 && !d)) return -1;
+    if (n == 0) return 0;
+    job_t j;
+    memset(&j, 0, sizeof j);
+    j.kind = uplo == 0 ? JOB_LOWER : (uplo == 1 ? JOB_UPPER : JOB_FULL);
+    j.n = n;
+    j.k = k;
+    j.p = p;
+    j.A = A;
+    j.d = d;
+    j.e = k > 1 ? e : NULL;
     j.lda = lda;
     j.C = C;
     j.ldc = ldc;

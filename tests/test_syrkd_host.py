@@ -65,3 +65,39 @@ def test_oracle_syrkd_reduces_to_syrk():
     assert np.array_equal(oracle.syrkd(A, np.ones(23, np.uint32), p, "lower"), P.astype(np.uint32))
     assert np.array_equal(oracle.syrkd(A, np.full(23, 9, np.uint32), p, "lower"),
                           (9 * P % p).astype(np.uint32))
+
+
+def test_oracle_syrkbd_against_big_integers():
+    rng = np.random.default_rng(15)
+    for p in [3, 7, 65521, 131071]:
+        for _ in range(5):
+            n, k = int(rng.integers(1, 7)), int(rng.integers(1, 8))
+            A = rng.integers(0, 1 << 32, size=(n, k), dtype=np.uint64).astype(np.uint32)
+            d = rng.integers(0, 1 << 32, size=k, dtype=np.uint64).astype(np.uint32)
+            e = rng.integers(0, 1 << 32, size=max(k - 1, 0), dtype=np.uint64).astype(np.uint32)
+            B = [[0] * k for _ in range(k)]
+            for l in range(k):
+                B[l][l] = int(d[l])
+                if l + 1 < k:
+                    B[l][l + 1] = B[l + 1][l] = int(e[l])
+            want = [[sum(int(A[i, a]) * B[a][b] * int(A[j, b]) for a in range(k) for b in range(k)) % p
+                     for j in range(n)] for i in range(n)]
+            assert oracle.syrkbd(A, d, e, p, "full").tolist() == want
+
+
+def test_oracle_syrkbd_special_cases():
+    p = 65521
+    rng = np.random.default_rng(16)
+    A = rng.integers(0, 1 << 32, size=(9, 6), dtype=np.uint64).astype(np.uint32)
+    d = rng.integers(0, p, size=6)
+    # e = 0: the diagonal product
+    assert np.array_equal(oracle.syrkbd(A, d, np.zeros(5, np.uint32), p, "lower"),
+                          oracle.syrkd(A, d, p, "lower"))
+    # one antidiagonal block [[0, b], [b, 0]] on columns (2, 3): b·(a2·a3ᵀ + a3·a2ᵀ)
+    b = 12345
+    dz = np.zeros(6, np.uint32)
+    e = np.zeros(5, np.uint32)
+    e[2] = b
+    R = A.astype(object) % p
+    want = (b * (np.outer(R[:, 2], R[:, 3]) + np.outer(R[:, 3], R[:, 2]))) % p
+    assert oracle.syrkbd(A, dz, e, p, "full").tolist() == want.tolist()
