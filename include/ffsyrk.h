@@ -169,6 +169,39 @@ ffsyrk_status_t ffsyrkd_update(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_
 int32_t ffsyrkd_factor(uint32_t p, int64_t k, const uint32_t *d, int32_t *partner, uint32_t *u,
                        uint32_t *v);
 
+/* Symmetric product with block-diagonal scaling, C ← α·A·B·Aᵀ + β·C mod p
+ * (Section 5, Algorithm 6 "syrkbd", odd characteristic), with B symmetric,
+ * block diagonal with 1×1 and 2×2 blocks: d[0..k−1] is B's diagonal and
+ * e[0..k−2] its first off-diagonal, B[j][j+1] = B[j+1][j] = e[j]; a nonzero
+ * e[j] (mod p) opens the 2×2 block on columns j, j+1.  d and e are HOST
+ * arrays (any uint32, reduced mod p); e may be NULL (B = Diag(d), the same
+ * as ffsyrkd_with_plan_update).  Each block [[x, β], [β, γ]] is congruent to a
+ * diagonal one: for x = γ = 0 by the paper's antidiagonal identity (columns
+ * A_j ± A_{j+1}, diagonal ±β/2), otherwise by one elimination step; the
+ * resulting diagonal then goes through Algorithm 5, so Ā has k or k + 1
+ * columns.  FFSYRK_ERR_INVALID_ARG when two blocks overlap (e[j] and e[j+1]
+ * both nonzero mod p).  Other rules as for ffsyrkd_with_plan_update. */
+ffsyrk_status_t ffsyrkbd_with_plan_update(ffsyrk_plan_t plan, ffsyrk_uplo_t uplo, int64_t n,
+                                          int64_t k, uint32_t p, uint32_t alpha,
+                                          const uint32_t *A, int64_t lda, const uint32_t *d,
+                                          const uint32_t *e, uint32_t beta, uint32_t *C,
+                                          int64_t ldc, ffsyrk_stream_t stream);
+
+/* The same through the internal plan cache (plans made with max_k = k + 1).
+ * Thread-safe. */
+ffsyrk_status_t ffsyrkbd_update(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
+                                uint32_t alpha, const uint32_t *A, int64_t lda, const uint32_t *d,
+                                const uint32_t *e, uint32_t beta, uint32_t *C, int64_t ldc,
+                                ffsyrk_stream_t stream);
+
+/* The planning step of Algorithm 6 (with Algorithm 5) on the host, needing no
+ * GPU: writes Ā = A·W with A·B·Aᵀ = Ā·Āᵀ, column c of Ā being
+ * Σ_{t<4} w[4c+t]·A_{src[4c+t]} (src −1: unused term; every src < k).  src
+ * and w need room for 4·(k + 1) entries.  Returns the column count of Ā
+ * (k or k + 1), or −1 for a bad p, bad sizes or overlapping blocks. */
+int32_t ffsyrkbd_factor(uint32_t p, int64_t k, const uint32_t *d, const uint32_t *e, int32_t *src,
+                        uint32_t *w);
+
 /* `count` independent products C_t = A_t·A_tᵀ mod p of uneven sizes n[t] × k[t],
  * all with the same p and uplo.  n, k, lda, ldc are HOST arrays of `count`
  * values; A and C are HOST arrays of `count` DEVICE pointers.  Problems with

@@ -301,6 +301,101 @@ int64_t diag_factor(uint32_t p, int64_t k, const uint32_t *d, std::vector<int32_
     return kk;
 }
 
+// Ā = A·W with at most four nonzero entries per column of W: column c of Ā
+// is Σ_t w[4c+t]·A_{src[4c+t]} (src −1: unused).
+struct ColMix {
+    int64_t kk = 0;
+    std::vector<int32_t> src;
+    std::vector<uint32_t> w;
+};
+
+namespace {
+// column c of the mix gains coef·A_s: equal sources merge, and the zero
+// column s ≥ k that Algorithm 5 may add contributes nothing
+bool mix_add(ColMix &m, int64_t c, int64_t s, uint64_t coef, int64_t k, uint64_t p) {
+    coef %= p;
+    if (s >= k || coef == 0) return true;
+    int32_t *sc = &m.src[(size_t)(4 * c)];
+    uint32_t *wc = &m.w[(size_t)(4 * c)];
+    for (int t = 0; t < 4; ++t)
+        if (sc[t] == (int32_t)s) {
+            wc[t] = (uint32_t)((wc[t] + coef) % p);
+            return true;
+        }
+    for (int t = 0; t < 4; ++t)
+        if (sc[t] < 0) {
+            sc[t] = (int32_t)s;
+            wc[t] = (uint32_t)coef;
+            return true;
+        }
+    return false;
+}
+uint64_t inv_mod(uint64_t a, uint64_t p) { return host::powmod64(a % p, p - 2, p); }
+}  // namespace
+
+// Algorithm 6 (syrkbd) over odd p, planning step, for the symmetric B with
+// diagonal d and first off-diagonal e (e null: B = Diag(d), Algorithm 5
+// alone).  Each 2×2 block [[x, β], [β, γ]] (β ≠ 0 on columns j, j+1) becomes
+// T·Diag(d̄_j, d̄_{j+1})·Tᵀ: for x = γ = 0 the paper's antidiagonal identity,
+// T = [[1, 1], [1, −1]] and d̄ = (β/2, −β/2); for γ ≠ 0, T = [[1, β/γ], [0, 1]]
+// and d̄ = (x − β²/γ, γ); for x ≠ 0 = γ, T = [[1, 0], [β/x, 1]] and
+// d̄ = (x, −β²/x).  Then Diag(d̄) = Δ·Δᵀ (diag_factor), so A·B·Aᵀ = Ā·Āᵀ with
+// Ā = [A·T 0]·Δ.  Returns the column count kk of Ā (k or k + 1), or −1 when
+// two blocks overlap (e_j and e_{j+1} both nonzero mod p).
+int64_t block_factor(uint32_t p, int64_t k, const uint32_t *d, const uint32_t *e, ColMix &out) {
+    std::vector<uint32_t> dbar((size_t)k);
+    // column c of A·T: ta[c]·A_c + tb[c]·A_{mate[c]} (mate −1: none)
+    std::vector<int64_t> mate((size_t)k, -1);
+    std::vector<uint64_t> ta((size_t)k, 1), tb((size_t)k, 0);
+    for (int64_t c = 0; c < k; ++c) dbar[(size_t)c] = (uint32_t)(d[c] % p);
+    for (int64_t j = 0; e && j + 1 < k; ++j) {
+        const uint64_t beta = e[j] % p;
+        if (beta == 0) continue;
+        if (j + 2 < k && e[j + 1] % p != 0) return -1;
+        const uint64_t x = dbar[(size_t)j], g = dbar[(size_t)(j + 1)];
+        mate[(size_t)j] = j + 1;
+        mate[(size_t)(j + 1)] = j;
+        if (x == 0 && g == 0) {
+            const uint64_t h = host::mulmod64(beta, inv_mod(2, p), p);
+            tb[(size_t)j] = 1;        // A_j + A_{j+1}
+            tb[(size_t)(j + 1)] = 1;  // A_{j+1}·(−1) + A_j
+            ta[(size_t)(j + 1)] = p - 1;
+            dbar[(size_t)j] = (uint32_t)h;
+            dbar[(size_t)(j + 1)] = (uint32_t)((p - h) % p);
+        } else if (g != 0) {
+            const uint64_t r = host::mulmod64(beta, inv_mod(g, p), p);  // β/γ
+            tb[(size_t)j] = 0;
+            tb[(size_t)(j + 1)] = r;  // A_{j+1} + (β/γ)·A_j
+            dbar[(size_t)j] = (uint32_t)((x + p - host::mulmod64(beta, r, p)) % p);
+        } else {
+            const uint64_t r = host::mulmod64(beta, inv_mod(x, p), p);  // β/x
+            tb[(size_t)j] = r;  // A_j + (β/x)·A_{j+1}
+            tb[(size_t)(j + 1)] = 0;
+            dbar[(size_t)(j + 1)] = (uint32_t)((p - host::mulmod64(beta, r, p)) % p);
+        }
+        ++j;  // the block's second column is done
+    }
+    std::vector<int32_t> partner;
+    std::vector<uint32_t> u, v;
+    const int64_t kk = diag_factor(p, k, dbar.data(), partner, u, v);
+    out.kk = kk;
+    out.src.assign((size_t)(4 * kk), -1);
+    out.w.assign((size_t)(4 * kk), 0);
+    auto add_t = [&](int64_t c, int64_t col, uint64_t coef) {
+        // coef · (column col of [A·T 0])
+        if (col >= k) return true;
+        bool ok = mix_add(out, c, col, host::mulmod64(coef, ta[(size_t)col], p), k, p);
+        if (mate[(size_t)col] >= 0)
+            ok = ok && mix_add(out, c, mate[(size_t)col], host::mulmod64(coef, tb[(size_t)col], p), k, p);
+        return ok;
+    };
+    for (int64_t c = 0; c < kk; ++c) {
+        if (!add_t(c, c, u[(size_t)c])) return -1;
+        if (partner[(size_t)c] >= 0 && !add_t(c, partner[(size_t)c], v[(size_t)c])) return -1;
+    }
+    return kk;
+}
+
 int count_units(const LeafSeg *segs, int nseg) {
     int u = 0;
     for (int i = 0; i < nseg; ++i) u += segs[i].first ? 1 : 0;
@@ -1461,20 +1556,13 @@ uint64_t g_clock = 0;
 constexpr size_t kCacheMax = 8;
 }  // namespace
 
-ffsyrk_status_t ffsyrkd_with_plan_update(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n,
-                                         int64_t k, uint32_t p, uint32_t alpha, const uint32_t *A,
-                                         int64_t lda, const uint32_t *d, uint32_t beta, uint32_t *C,
-                                         int64_t ldc, ffsyrk_stream_t stream) {
-    if (!pl) return FFSYRK_ERR_INVALID_ARG;
-    if (p != pl->p) return FFSYRK_ERR_INVALID_ARG;
-    if (uplo != FFSYRK_LOWER && uplo != FFSYRK_UPPER) return FFSYRK_ERR_INVALID_ARG;
-    if (n < 0 || k < 0 || k >= INT32_MAX) return FFSYRK_ERR_INVALID_ARG;
-    if (lda < std::max<int64_t>(1, k) || ldc < std::max<int64_t>(1, n)) return FFSYRK_ERR_INVALID_ARG;
-    if (n > 0 && (C == nullptr || (k > 0 && (A == nullptr || d == nullptr)))) return FFSYRK_ERR_INVALID_ARG;
-    if (n == 0) return FFSYRK_SUCCESS;
-    std::vector<int32_t> partner;
-    std::vector<uint32_t> u, v;
-    const int64_t kk = diag_factor(p, k, d, partner, u, v);
+namespace {
+// C ← α·Ā·Āᵀ + β·C for Ā = A·W: the column mix runs into the plan's scratch,
+// then the plan's product of Ā
+ffsyrk_status_t run_colmix(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
+                           uint32_t alpha, const uint32_t *A, int64_t lda, const ColMix &mx,
+                           uint32_t beta, uint32_t *C, int64_t ldc, ffsyrk_stream_t stream) {
+    const int64_t kk = mx.kk;
     if (n > pl->max_n || kk > pl->max_k) return FFSYRK_ERR_TOO_LARGE;
     if (kk == 0) return ffsyrk_with_plan_update(pl, uplo, n, 0, p, alpha, A, std::max<int64_t>(1, k), beta, C, ldc, stream);
     int cur = 0;
@@ -1484,7 +1572,8 @@ ffsyrk_status_t ffsyrkd_with_plan_update(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, i
     // scratch for Ā (rows of a multiple of 4 entries) and the column table
     const int64_t ldb = rup(kk, 4);
     const int64_t need = n * ldb * 4;
-    const int64_t tab = rup(kk * 4, 64) + 2 * kk * (int64_t)sizeof(MulConst);
+    const int64_t woff = rup(kk * 16, 64);
+    const int64_t tab = woff + 4 * kk * (int64_t)sizeof(MulConst);
     if (need > pl->dbar_bytes || tab > pl->dtab_bytes) {
         cudaStreamSynchronize(st);
         if (need > pl->dbar_bytes) {
@@ -1509,24 +1598,52 @@ ffsyrk_status_t ffsyrkd_with_plan_update(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, i
         }
     }
     std::vector<char> host((size_t)tab, 0);
-    std::vector<MulConst> uc((size_t)kk), vc((size_t)kk);
-    for (int64_t c = 0; c < kk; ++c) {
-        uc[(size_t)c] = make_mul(u[(size_t)c], p);
-        vc[(size_t)c] = make_mul(v[(size_t)c], p);
-    }
-    const int64_t uoff = rup(kk * 4, 64), voff = uoff + kk * (int64_t)sizeof(MulConst);
-    memcpy(host.data(), partner.data(), (size_t)kk * 4);
-    memcpy(host.data() + uoff, uc.data(), (size_t)kk * sizeof(MulConst));
-    memcpy(host.data() + voff, vc.data(), (size_t)kk * sizeof(MulConst));
+    std::vector<MulConst> wc((size_t)(4 * kk));
+    for (int64_t t = 0; t < 4 * kk; ++t) wc[(size_t)t] = make_mul(mx.w[(size_t)t], p);
+    memcpy(host.data(), mx.src.data(), (size_t)(4 * kk) * 4);
+    memcpy(host.data() + woff, wc.data(), (size_t)(4 * kk) * sizeof(MulConst));
     // a pageable copy: staged before it returns, so `host` may go away
     if (cudaMemcpyAsync(pl->dtab, host.data(), (size_t)tab, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return FFSYRK_ERR_CUDA;
-    if (launch_col_transform(A, lda, n, k, kk, reinterpret_cast<const int32_t *>(pl->dtab),
-                             reinterpret_cast<const MulConst *>(pl->dtab + uoff),
-                             reinterpret_cast<const MulConst *>(pl->dtab + voff), pl->dbar, ldb,
-                             pl->mp, st) != cudaSuccess)
+    if (launch_col_mix(A, lda, n, kk, reinterpret_cast<const int32_t *>(pl->dtab),
+                       reinterpret_cast<const MulConst *>(pl->dtab + woff), pl->dbar, ldb, pl->mp,
+                       st) != cudaSuccess)
         return FFSYRK_ERR_CUDA;
     return ffsyrk_with_plan_update(pl, uplo, n, kk, p, alpha, pl->dbar, ldb, beta, C, ldc, stream);
+}
+
+ffsyrk_status_t check_scaled_args(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n, int64_t k,
+                                  uint32_t p, const uint32_t *A, int64_t lda, const uint32_t *d,
+                                  const uint32_t *C, int64_t ldc) {
+    if (!pl) return FFSYRK_ERR_INVALID_ARG;
+    if (p != pl->p) return FFSYRK_ERR_INVALID_ARG;
+    if (uplo != FFSYRK_LOWER && uplo != FFSYRK_UPPER) return FFSYRK_ERR_INVALID_ARG;
+    if (n < 0 || k < 0 || k >= INT32_MAX) return FFSYRK_ERR_INVALID_ARG;
+    if (lda < std::max<int64_t>(1, k) || ldc < std::max<int64_t>(1, n)) return FFSYRK_ERR_INVALID_ARG;
+    if (n > 0 && (C == nullptr || (k > 0 && (A == nullptr || d == nullptr)))) return FFSYRK_ERR_INVALID_ARG;
+    return FFSYRK_SUCCESS;
+}
+}  // namespace
+
+ffsyrk_status_t ffsyrkd_with_plan_update(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n,
+                                         int64_t k, uint32_t p, uint32_t alpha, const uint32_t *A,
+                                         int64_t lda, const uint32_t *d, uint32_t beta, uint32_t *C,
+                                         int64_t ldc, ffsyrk_stream_t stream) {
+    return ffsyrkbd_with_plan_update(pl, uplo, n, k, p, alpha, A, lda, d, nullptr, beta, C, ldc,
+                                     stream);
+}
+
+ffsyrk_status_t ffsyrkbd_with_plan_update(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n,
+                                          int64_t k, uint32_t p, uint32_t alpha,
+                                          const uint32_t *A, int64_t lda, const uint32_t *d,
+                                          const uint32_t *e, uint32_t beta, uint32_t *C,
+                                          int64_t ldc, ffsyrk_stream_t stream) {
+    ffsyrk_status_t s = check_scaled_args(pl, uplo, n, k, p, A, lda, d, C, ldc);
+    if (s != FFSYRK_SUCCESS) return s;
+    if (n == 0) return FFSYRK_SUCCESS;
+    ColMix mx;
+    if (block_factor(p, k, d, k > 1 ? e : nullptr, mx) < 0) return FFSYRK_ERR_INVALID_ARG;
+    return run_colmix(pl, uplo, n, k, p, alpha, A, lda, mx, beta, C, ldc, stream);
 }
 
 int32_t ffsyrkd_factor(uint32_t p, int64_t k, const uint32_t *d, int32_t *partner, uint32_t *u,
@@ -1545,11 +1662,51 @@ int32_t ffsyrkd_factor(uint32_t p, int64_t k, const uint32_t *d, int32_t *partne
     return (int32_t)kk;
 }
 
+int32_t ffsyrkbd_factor(uint32_t p, int64_t k, const uint32_t *d, const uint32_t *e,
+                        int32_t *src, uint32_t *w) {
+    if (validate_p(p) != FFSYRK_SUCCESS || k < 0 || k >= INT32_MAX || (k > 0 && !d) || !src || !w)
+        return -1;
+    ColMix mx;
+    if (block_factor(p, k, d, k > 1 ? e : nullptr, mx) < 0) return -1;
+    for (int64_t t = 0; t < 4 * mx.kk; ++t) {
+        src[t] = mx.src[(size_t)t];
+        w[t] = mx.w[(size_t)t];
+    }
+    return (int32_t)mx.kk;
+}
+
 extern "C" ffsyrk_status_t ffsyrk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
                                   const uint32_t *A, int64_t lda, uint32_t *C, int64_t ldc,
                                   ffsyrk_stream_t stream) {
     return ffsyrk_update(uplo, n, k, p, 1u, A, lda, 0u, C, ldc, stream);
 }
+
+namespace {
+// the cached plan for (device, p, n, kcap), made on first use; the cache
+// mutex must be held
+ffsyrk_status_t cached_plan(uint32_t p, int64_t n, int64_t kcap, ffsyrk_plan_t *out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFSYRK_ERR_CUDA;
+    auto key = std::make_tuple(dev, p, n, kcap);
+    auto it = g_cache.find(key);
+    if (it == g_cache.end()) {
+        if (g_cache.size() >= kCacheMax) {
+            auto victim = g_cache.begin();
+            for (auto jt = g_cache.begin(); jt != g_cache.end(); ++jt)
+                if (jt->second.last_use < victim->second.last_use) victim = jt;
+            ffsyrk_plan_destroy(victim->second.plan);
+            g_cache.erase(victim);
+        }
+        ffsyrk_plan_t pl = nullptr;
+        ffsyrk_status_t s = ffsyrk_plan(&pl, p, n, kcap, nullptr);
+        if (s != FFSYRK_SUCCESS) return s;
+        it = g_cache.emplace(key, CacheEntry{pl, 0}).first;
+    }
+    it->second.last_use = ++g_clock;
+    *out = it->second.plan;
+    return FFSYRK_SUCCESS;
+}
+}  // namespace
 
 extern "C" ffsyrk_status_t ffsyrk_update(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
                                          uint32_t alpha, const uint32_t *A, int64_t lda,
@@ -1558,57 +1715,33 @@ extern "C" ffsyrk_status_t ffsyrk_update(ffsyrk_uplo_t uplo, int64_t n, int64_t 
     ffsyrk_status_t s = validate_p(p);
     if (s != FFSYRK_SUCCESS) return s;
     if (n < 0 || k < 0) return FFSYRK_ERR_INVALID_ARG;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return FFSYRK_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_cache_mu);
-    auto key = std::make_tuple(dev, p, n, k);
-    auto it = g_cache.find(key);
-    if (it == g_cache.end()) {
-        if (g_cache.size() >= kCacheMax) {
-            auto victim = g_cache.begin();
-            for (auto jt = g_cache.begin(); jt != g_cache.end(); ++jt)
-                if (jt->second.last_use < victim->second.last_use) victim = jt;
-            ffsyrk_plan_destroy(victim->second.plan);
-            g_cache.erase(victim);
-        }
-        ffsyrk_plan_t pl = nullptr;
-        s = ffsyrk_plan(&pl, p, n, k, nullptr);
-        if (s != FFSYRK_SUCCESS) return s;
-        it = g_cache.emplace(key, CacheEntry{pl, 0}).first;
-    }
-    it->second.last_use = ++g_clock;
-    return ffsyrk_with_plan_update(it->second.plan, uplo, n, k, p, alpha, A, lda, beta, C, ldc, stream);
+    ffsyrk_plan_t pl = nullptr;
+    s = cached_plan(p, n, k, &pl);
+    if (s != FFSYRK_SUCCESS) return s;
+    return ffsyrk_with_plan_update(pl, uplo, n, k, p, alpha, A, lda, beta, C, ldc, stream);
 }
 
 extern "C" ffsyrk_status_t ffsyrkd_update(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
                                           uint32_t alpha, const uint32_t *A, int64_t lda,
                                           const uint32_t *d, uint32_t beta, uint32_t *C,
                                           int64_t ldc, ffsyrk_stream_t stream) {
+    return ffsyrkbd_update(uplo, n, k, p, alpha, A, lda, d, nullptr, beta, C, ldc, stream);
+}
+
+extern "C" ffsyrk_status_t ffsyrkbd_update(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
+                                           uint32_t alpha, const uint32_t *A, int64_t lda,
+                                           const uint32_t *d, const uint32_t *e, uint32_t beta,
+                                           uint32_t *C, int64_t ldc, ffsyrk_stream_t stream) {
     ffsyrk_status_t s = validate_p(p);
     if (s != FFSYRK_SUCCESS) return s;
     if (n < 0 || k < 0 || k >= INT32_MAX) return FFSYRK_ERR_INVALID_ARG;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return FFSYRK_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_cache_mu);
-    // one more column than A for an odd number of non-squares in d
-    auto key = std::make_tuple(dev, p, n, k + 1);
-    auto it = g_cache.find(key);
-    if (it == g_cache.end()) {
-        if (g_cache.size() >= kCacheMax) {
-            auto victim = g_cache.begin();
-            for (auto jt = g_cache.begin(); jt != g_cache.end(); ++jt)
-                if (jt->second.last_use < victim->second.last_use) victim = jt;
-            ffsyrk_plan_destroy(victim->second.plan);
-            g_cache.erase(victim);
-        }
-        ffsyrk_plan_t pl = nullptr;
-        s = ffsyrk_plan(&pl, p, n, k + 1, nullptr);
-        if (s != FFSYRK_SUCCESS) return s;
-        it = g_cache.emplace(key, CacheEntry{pl, 0}).first;
-    }
-    it->second.last_use = ++g_clock;
-    return ffsyrkd_with_plan_update(it->second.plan, uplo, n, k, p, alpha, A, lda, d, beta, C, ldc,
-                                    stream);
+    // one more column than A for an odd number of non-squares in the diagonal
+    ffsyrk_plan_t pl = nullptr;
+    s = cached_plan(p, n, k + 1, &pl);
+    if (s != FFSYRK_SUCCESS) return s;
+    return ffsyrkbd_with_plan_update(pl, uplo, n, k, p, alpha, A, lda, d, e, beta, C, ldc, stream);
 }
 
 // ---- batched: many independent problems in one grouped launch ----

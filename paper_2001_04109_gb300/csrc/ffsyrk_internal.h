@@ -232,10 +232,12 @@ int64_t digitize_flat_blocks(int64_t rows, int64_t kpad);
 cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP mp,
                         cudaStream_t st, bool upper);
 cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st);
-// Ā = [A 0]·Δ of Algorithm 5 (syrkd), Ā n × kk (see k_col_transform)
-cudaError_t launch_col_transform(const uint32_t *A, int64_t lda, int64_t n, int64_t k, int64_t kk,
-                                 const int32_t *partner, const MulConst *u, const MulConst *v,
-                                 uint32_t *B, int64_t ldb, ModP mp, cudaStream_t st);
+// Ā = A·W of Algorithms 5 and 6 (syrkd, syrkbd), Ā n × kk: column c is
+// Σ_t w[4c+t]·A_{src[4c+t]} over t < 4 (src −1 unused, else < k); src holds
+// 4·kk int32 on a 16-byte boundary (see k_col_mix)
+cudaError_t launch_col_mix(const uint32_t *A, int64_t lda, int64_t n, int64_t kk,
+                           const int32_t *src, const MulConst *w, uint32_t *B, int64_t ldb,
+                           ModP mp, cudaStream_t st);
 // the selected triangle for k = 0: zero, or β·C (sc.mode 1)
 cudaError_t launch_scale_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, const OutScale &sc,
                              uint32_t p, cudaStream_t st);

@@ -637,29 +637,29 @@ __global__ void __launch_bounds__(256) k_post_fused(const PostNode *__restrict__
     }
 }
 
-// Ā = [A 0]·Δ for the diagonal scaling of Algorithm 5 (syrkd): column c of
-// Ā is u_c·Ā_c + v_c·Ā_{partner_c} (partner −1: u_c·Ā_c alone), with A's
-// columns ≥ k reading as zero (the extra column for an odd number of
-// non-squares) and A's entries reduced mod p.  Grid: x = 256-column blocks,
-// y = rows (strided).
-__global__ void __launch_bounds__(256) k_col_transform(const uint32_t *__restrict__ A, int64_t lda,
-                                                       int64_t n, int64_t k, int64_t kk,
-                                                       const int32_t *__restrict__ partner,
-                                                       const MulConst *__restrict__ u,
-                                                       const MulConst *__restrict__ v, uint32_t *B,
-                                                       int64_t ldb, ModP m) {
+// Ā = A·W for the diagonal and block-diagonal scalings of Algorithms 5 and
+// 6 (syrkd, syrkbd): column c of Ā is Σ_t w_{c,t}·A_{src_{c,t}} over at most
+// four columns of A (src −1: an unused term), with A's entries reduced mod p.
+// The host drops terms on the zero column that an odd number of non-squares
+// adds, so every src is < k.  Grid: x = 256-column blocks, y = rows (strided).
+__global__ void __launch_bounds__(256) k_col_mix(const uint32_t *__restrict__ A, int64_t lda,
+                                                 int64_t n, int64_t kk,
+                                                 const int4 *__restrict__ src,
+                                                 const MulConst *__restrict__ w, uint32_t *B,
+                                                 int64_t ldb, ModP m) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= kk) return;
-    const int32_t pc = partner[c];
-    const MulConst uc = u[c], vc = v[c];
+    const int4 s = src[c];
+    const int sc[4] = {s.x, s.y, s.z, s.w};
+    MulConst wc[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) wc[t] = w[4 * c + t];
     for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
         const uint32_t *row = A + r * lda;
-        const uint32_t x = c < k ? red(__ldg(row + c), m) : 0u;
-        uint32_t y = mulc(x, uc, m.p);
-        if (pc >= 0) {
-            const uint32_t z = pc < k ? red(__ldg(row + pc), m) : 0u;
-            y = addm(y, mulc(z, vc, m.p), m.p);
-        }
+        uint32_t y = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (sc[t] >= 0) y = addm(y, mulc(red(__ldg(row + sc[t]), m), wc[t], m.p), m.p);
         B[r * ldb + c] = y;
     }
 }
@@ -790,12 +790,13 @@ cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cuda
     return launch_scale_tri(C, n, ldc, upper, OutScale{}, 3u, st);
 }
 
-cudaError_t launch_col_transform(const uint32_t *A, int64_t lda, int64_t n, int64_t k, int64_t kk,
-                                 const int32_t *partner, const MulConst *u, const MulConst *v,
-                                 uint32_t *B, int64_t ldb, ModP mp, cudaStream_t st) {
+cudaError_t launch_col_mix(const uint32_t *A, int64_t lda, int64_t n, int64_t kk,
+                           const int32_t *src, const MulConst *w, uint32_t *B, int64_t ldb,
+                           ModP mp, cudaStream_t st) {
     if (n == 0 || kk == 0) return cudaSuccess;
     dim3 grid((unsigned)((kk + 255) / 256), (unsigned)std::min<int64_t>(n, 4096));
-    k_col_transform<<<grid, 256, 0, st>>>(A, lda, n, k, kk, partner, u, v, B, ldb, mp);
+    k_col_mix<<<grid, 256, 0, st>>>(A, lda, n, kk, reinterpret_cast<const int4 *>(src), w, B, ldb,
+                                    mp);
     return cudaGetLastError();
 }
 

@@ -32,7 +32,8 @@ EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsy
            "ffsyrk_plan_set_timing", "ffsyrk_plan_get_timing", "ffsyrk_status_string",
            "ffsyrk_version", "ffsyrk_noalloc", "ffsyrk_leaf_schedule", "ffsyrk_digit_bounds",
            "ffsyrk_digit_base", "ffsyrk_plan_selftest_timeout", "ffsyrk_with_plan_update",
-           "ffsyrk_update", "ffsyrkd_with_plan_update", "ffsyrkd_update", "ffsyrkd_factor"]
+           "ffsyrk_update", "ffsyrkd_with_plan_update", "ffsyrkd_update", "ffsyrkd_factor",
+           "ffsyrkbd_with_plan_update", "ffsyrkbd_update", "ffsyrkbd_factor"]
 
 
 class FfsyrkError(RuntimeError):
@@ -94,6 +95,12 @@ def lib() -> ctypes.CDLL:
             L.ffsyrkd_update.argtypes = [i32, i64, i64, u32, u32, vp, i64, P(u32), u32, vp, i64, vp]
             L.ffsyrkd_factor.argtypes = [u32, i64, P(u32), P(i32), P(u32), P(u32)]
             L.ffsyrkd_factor.restype = i32
+            L.ffsyrkbd_with_plan_update.argtypes = [vp, i32, i64, i64, u32, u32, vp, i64, P(u32),
+                                                    P(u32), u32, vp, i64, vp]
+            L.ffsyrkbd_update.argtypes = [i32, i64, i64, u32, u32, vp, i64, P(u32), P(u32), u32, vp,
+                                          i64, vp]
+            L.ffsyrkbd_factor.argtypes = [u32, i64, P(u32), P(u32), P(i32), P(u32)]
+            L.ffsyrkbd_factor.restype = i32
             L.ffsyrk_noalloc.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk_batched.argtypes = [i32, i64, P(i64), P(i64), u32, P(vp), P(i64), P(vp),
                                          P(i64), vp]
@@ -114,7 +121,7 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_digit_base.restype = i32
             for name in ["ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan", "ffsyrk",
                          "ffsyrk_with_plan_update", "ffsyrk_update", "ffsyrkd_with_plan_update",
-                         "ffsyrkd_update",
+                         "ffsyrkd_update", "ffsyrkbd_with_plan_update", "ffsyrkbd_update",
                          "ffsyrk_noalloc",
                          "ffsyrk_batched", "ffsyrk_sync_status", "ffsyrk_plan_get_info",
                          "ffsyrk_plan_set_timing", "ffsyrk_plan_get_timing"]:
@@ -214,6 +221,22 @@ class Plan:
                                               _stream_handle(stream)), "ffsyrkd_with_plan_update")
         return C
 
+    def syrkbd(self, A: torch.Tensor, d, e, C: torch.Tensor | None = None, uplo: str = "lower",
+               stream=None, alpha: int = 1, beta: int = 0) -> torch.Tensor:
+        """C ← α·A·B·Aᵀ + β·C mod p (Algorithm 6): B block diagonal, diagonal d, off-diagonal e."""
+        n, k = A.shape
+        if C is None:
+            C = torch.zeros((n, n), dtype=torch.int32, device=A.device)
+        pa, lda = _mat_args(A, "A")
+        pc, ldc = _mat_args(C, "C")
+        dv = _u32_array(d, k)
+        ev = _u32_array(e, max(k - 1, 0)) if e is not None else None
+        _check(lib().ffsyrkbd_with_plan_update(self._h, UPPER if uplo == "upper" else LOWER, n, k,
+                                               self.p, int(alpha) & 0xFFFFFFFF, pa, lda, dv, ev,
+                                               int(beta) & 0xFFFFFFFF, pc, ldc,
+                                               _stream_handle(stream)), "ffsyrkbd_with_plan_update")
+        return C
+
     def set_timing(self, enable: bool = True) -> None:
         _check(lib().ffsyrk_plan_set_timing(self._h, 1 if enable else 0), "ffsyrk_plan_set_timing")
 
@@ -294,6 +317,39 @@ def syrkd_factor(p: int, d) -> tuple[int, list[int], list[int], list[int]]:
     if kk < 0:
         raise ValueError("bad p or d")
     return kk, list(pt[:kk]), list(u[:kk]), list(v[:kk])
+
+
+def syrkbd(A: torch.Tensor, d, e, p: int, uplo: str = "lower", C: torch.Tensor | None = None,
+           stream=None, alpha: int = 1, beta: int = 0) -> torch.Tensor:
+    """C ← α·A·B·Aᵀ + β·C mod p (Algorithm 6) through the plan cache."""
+    n, k = A.shape
+    if C is None:
+        C = torch.zeros((n, n), dtype=torch.int32, device=A.device)
+    pa, lda = _mat_args(A, "A")
+    pc, ldc = _mat_args(C, "C")
+    dv = _u32_array(d, k)
+    ev = _u32_array(e, max(k - 1, 0)) if e is not None else None
+    _check(lib().ffsyrkbd_update(UPPER if uplo == "upper" else LOWER, n, k, int(p),
+                                 int(alpha) & 0xFFFFFFFF, pa, lda, dv, ev, int(beta) & 0xFFFFFFFF,
+                                 pc, ldc, _stream_handle(stream)), "ffsyrkbd_update")
+    return C
+
+
+def syrkbd_factor(p: int, d, e) -> tuple[int, list[list[tuple[int, int]]]]:
+    """Algorithm 6's column mix for B (diagonal d, off-diagonal e): (columns of Ā, terms).
+
+    terms[c] lists (source column of A, coefficient) with Ā_c = Σ coef·A_src.
+    """
+    k = len(d)
+    dv = _u32_array(d, k)
+    ev = _u32_array(e, max(k - 1, 0)) if e is not None else None
+    src = (ctypes.c_int32 * (4 * (k + 1)))()
+    w = (ctypes.c_uint32 * (4 * (k + 1)))()
+    kk = lib().ffsyrkbd_factor(int(p), k, dv, ev, src, w)
+    if kk < 0:
+        raise ValueError("bad p, d or e (overlapping 2x2 blocks?)")
+    return kk, [[(src[4 * c + t], w[4 * c + t]) for t in range(4) if src[4 * c + t] >= 0]
+                for c in range(kk)]
 
 
 def digit_base(p: int) -> int:

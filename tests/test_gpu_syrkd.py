@@ -1,4 +1,5 @@
-"""GPU parity of C ← α·A·Diag(d)·Aᵀ + β·C mod p (Algorithm 5; marked gpu).
+"""GPU parity of C ← α·A·D·Aᵀ + β·C mod p, D diagonal (Algorithm 5) or
+block diagonal (Algorithm 6; marked gpu).
 
 The library factors Diag(d) = Δ·Δᵀ on the host (Algorithm 4 for pairs of
 non-squares), forms Ā = [A 0]·Δ on the device and runs the symmetric product
@@ -6,7 +7,9 @@ of Ā.  Against the oracle's schoolbook A·D·Aᵀ combined with the update's
 definition: squares only, non-squares in odd and even counts (the odd count
 adds a column), zeros in d, every depth and leaf, both triangles, α/β
 including the LDLᵀ-style update C − A·D·Aᵀ, k = 1, strides, the cached
-entry point, and a plan whose k bound is too small.
+entry point, and a plan whose k bound is too small.  For Algorithm 6:
+every kind of 2×2 block (antidiagonal, one zero corner, full), mixed with
+1×1 blocks, against the oracle's A·B·Aᵀ; overlapping blocks are rejected.
 """
 import numpy as np
 import pytest
@@ -145,4 +148,87 @@ def test_syrkd_plan_k_bound_too_small():
     assert e.value.code == ffsyrk.ERR_TOO_LARGE
     plan.syrkd(A, diag_values(k, p, "even_nonsq", seed=1))   # k columns: fits
     plan.sync_status()
+    plan.close()
+
+
+def block_diag(k, p, seed):
+    rng = np.random.default_rng(seed)
+    d = [int(x) for x in rng.integers(0, p, size=k)]
+    e = [0] * max(k - 1, 0)
+    j = 0
+    while j + 1 < k:
+        kind = int(rng.integers(0, 5))
+        if kind == 0:
+            j += 1
+            continue
+        e[j] = int(rng.integers(1, p))
+        if kind == 1:
+            d[j] = d[j + 1] = 0
+        elif kind == 2:
+            d[j] = 0
+        elif kind == 3:
+            d[j + 1] = 0
+        j += 2
+    return d, e
+
+
+def run_syrkbd(A_host, d, e, p, alpha=1, beta=0, uplo="lower", levels=None, plan=None, seed=1,
+               lda_pad=0):
+    n, k = A_host.shape
+    Abig = torch.full((n, k + lda_pad), 3, dtype=torch.int32, device="cuda")
+    Abig[:, :k] = A_host.cuda()
+    C0, mask = start_matrix(n, p, uplo, seed)
+    C = torch.from_numpy(C0.view(np.int32)).cuda()
+    own = plan is None
+    if own:
+        plan = ffsyrk.Plan(p, n, k + 1, levels=levels)
+    plan.syrkbd(Abig[:, :k], d, e, C, uplo=uplo, alpha=alpha, beta=beta)
+    plan.sync_status()
+    if own:
+        plan.close()
+    P = oracle.syrkbd(A_host.numpy(), np.array(d, dtype=np.uint64), np.array(e, dtype=np.uint64),
+                      p, "full").astype(np.uint64)
+    want = C0.copy()
+    upd = (np.uint64(alpha % p) * P + np.uint64(beta % p) * C0.astype(np.uint64)) % np.uint64(p)
+    want[mask] = upd[mask].astype(np.uint32)
+    assert np.array_equal(C.cpu().numpy().view(np.uint32), want), "A·B·Aᵀ differs from the oracle"
+
+
+@pytest.mark.parametrize("p", [65521, 131071, 8388593, 7])
+@pytest.mark.parametrize("levels", [0, 1])
+def test_syrkbd_block_kinds(p, levels):
+    n, k = 290, 211
+    A = inputs.arbitrary_u32(n, k, seed=p % 97)
+    d, e = block_diag(k, p, seed=p + levels)
+    run_syrkbd(A, d, e, p, levels=levels, lda_pad=levels)
+
+
+def test_syrkbd_update_upper_and_all_antidiagonal():
+    p = 131071
+    n, k = 333, 200
+    A = residues(n, k, p, seed=31)
+    d, e = block_diag(k, p, seed=5)
+    run_syrkbd(A, d, e, p, alpha=p - 1, beta=1, uplo="upper", levels=1)
+    # B = ⊕ [[0, β], [β, 0]]: every column takes part in an antidiagonal block
+    rng = np.random.default_rng(9)
+    e = [int(rng.integers(1, p)) if j % 2 == 0 else 0 for j in range(k - 1)]
+    run_syrkbd(A, [0] * k, e, p, alpha=5, beta=7, levels=0)
+
+
+def test_syrkbd_cached_and_rejects_overlap():
+    p = 65521
+    n, k = 150, 97
+    A = residues(n, k, p, seed=2)
+    d, e = block_diag(k, p, seed=3)
+    C = ffsyrk.syrkbd(A.cuda(), d, e, p)
+    torch.cuda.synchronize()
+    want = oracle.syrkbd(A.numpy(), np.array(d, dtype=np.uint64), np.array(e, dtype=np.uint64), p,
+                         "lower")
+    assert np.array_equal(C.cpu().numpy().view(np.uint32), want)
+    bad = list(e)
+    bad[10] = bad[11] = 1
+    plan = ffsyrk.Plan(p, n, k + 1)
+    with pytest.raises(ffsyrk.FfsyrkError) as err:
+        plan.syrkbd(A.cuda(), d, bad)
+    assert err.value.code == ffsyrk.ERR_INVALID_ARG
     plan.close()

@@ -101,3 +101,65 @@ def test_oracle_syrkbd_special_cases():
     R = A.astype(object) % p
     want = (b * (np.outer(R[:, 2], R[:, 3]) + np.outer(R[:, 3], R[:, 2]))) % p
     assert oracle.syrkbd(A, dz, e, p, "full").tolist() == want.tolist()
+
+
+def random_block_diag(k, p, rng):
+    """d, e of a symmetric block-diagonal B with every kind of 2×2 block."""
+    d = [int(x) for x in rng.integers(0, p, size=k)]
+    e = [0] * max(k - 1, 0)
+    j = 0
+    while j + 1 < k:
+        kind = int(rng.integers(0, 5))
+        if kind == 0:          # 1×1 block
+            j += 1
+            continue
+        e[j] = int(rng.integers(1, p))
+        if kind == 1:          # antidiagonal [[0, β], [β, 0]] (the paper's odd-p case)
+            d[j] = d[j + 1] = 0
+        elif kind == 2:        # [[0, β], [β, γ]], γ ≠ 0 (the antitriangular form)
+            d[j] = 0
+            d[j + 1] = int(rng.integers(1, p))
+        elif kind == 3:        # [[x, β], [β, 0]]
+            d[j + 1] = 0
+        j += 2
+    return d, e
+
+
+@pytest.mark.parametrize("p", [3, 5, 7, 13, 65521, 131071, 8388593])
+def test_block_factor_gives_w_w_t_equal_b(p):
+    rng = np.random.default_rng(p % 1009)
+    for k in [0, 1, 2, 3, 6, 11, 24]:
+        for _ in range(6):
+            d, e = random_block_diag(k, p, rng)
+            kk, terms = ffsyrk.syrkbd_factor(p, d, e)
+            assert kk in (k, k + 1)
+            W = [[0] * kk for _ in range(k)]
+            for c, ts in enumerate(terms):
+                assert len(ts) <= 4
+                for src, coef in ts:
+                    assert 0 <= src < k and W[src][c] == 0   # merged sources
+                    W[src][c] = coef
+            for i in range(k):
+                for j in range(k):
+                    got = sum(W[i][t] * W[j][t] for t in range(kk)) % p
+                    want = d[i] if i == j else (e[min(i, j)] if abs(i - j) == 1 else 0)
+                    assert got == want % p, (p, d, e, i, j)
+
+
+def test_block_factor_rejects_overlapping_blocks_and_matches_syrkd():
+    p = 65521
+    with pytest.raises(ValueError):
+        ffsyrk.syrkbd_factor(p, [1, 2, 3, 4], [5, 6, 0])
+    # e ≡ 0 mod p closes no block; e = None is Algorithm 5 alone
+    d = [3, 0, 17, 5, 65520]
+    kk1, t1 = ffsyrk.syrkbd_factor(p, d, [p, 0, 2 * p, 0])
+    kk2, t2 = ffsyrk.syrkbd_factor(p, d, None)
+    kk3, partner, u, v = ffsyrk.syrkd_factor(p, d)
+    assert kk1 == kk2 == kk3 and t1 == t2
+    for c in range(kk3):
+        want = {}
+        if c < len(d) and u[c]:
+            want[c] = u[c]
+        if partner[c] >= 0 and partner[c] < len(d) and v[c]:
+            want[partner[c]] = v[c]
+        assert dict(t2[c]) == want
