@@ -202,6 +202,14 @@ ffsyrk_status_t ffsyrkbd_update(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32
 int32_t ffsyrkbd_factor(uint32_t p, int64_t k, const uint32_t *d, const uint32_t *e, int32_t *src,
                         uint32_t *w);
 
+/* The same planning step as ffsyrkbd_factor, run by the device planner that
+ * ffsyrkbd_with_plan_update uses (on the current device, synchronously, with
+ * its own temporary buffers): the two are meant to give the same W entry for
+ * entry.  Returns the column count of Ā, −1 for bad arguments, −2 when a CUDA
+ * call or a device-side check fails. */
+int32_t ffsyrkbd_factor_device(uint32_t p, int64_t k, const uint32_t *d, const uint32_t *e,
+                               int32_t *src, uint32_t *w);
+
 /* `count` independent products C_t = A_t·A_tᵀ mod p of uneven sizes n[t] × k[t],
  * all with the same p and uplo.  n, k, lda, ldc are HOST arrays of `count`
  * values; A and C are HOST arrays of `count` DEVICE pointers.  Problems with

@@ -516,7 +516,10 @@ struct ffsyrk_plan_st {
     Layout lay;
     Descs desc;
     OutScale scale{};  // how the current call updates C
-    // diagonal scaling (Algorithm 5): Ā = [A 0]·Δ and its column table
+    // diagonal and block-diagonal scaling (Algorithms 5 and 6): Ā = A·W and
+    // the planner's scratch (W, the uploaded d and e, per-column state)
+    bool scale_ready = false;
+    ScaleConst sconst{};
     uint32_t *dbar = nullptr;
     int64_t dbar_bytes = 0;
     char *dtab = nullptr;
@@ -1557,57 +1560,149 @@ constexpr size_t kCacheMax = 8;
 }  // namespace
 
 namespace {
-// C ← α·Ā·Āᵀ + β·C for Ā = A·W: the column mix runs into the plan's scratch,
-// then the plan's product of Ā
-ffsyrk_status_t run_colmix(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
-                           uint32_t alpha, const uint32_t *A, int64_t lda, const ColMix &mx,
-                           uint32_t beta, uint32_t *C, int64_t ldc, ffsyrk_stream_t stream) {
-    const int64_t kk = mx.kk;
+ScaleConst make_scale_const(uint32_t p) {
+    ScaleConst f{};
+    f.p = p;
+    f.minv = UINT64_MAX / p;
+    uint32_t q = p - 1, sv = 0;
+    while ((q & 1) == 0) {
+        q >>= 1;
+        ++sv;
+    }
+    f.q = q;
+    f.s = sv;
+    const uint64_t z = host::least_non_square(p);
+    f.zq = (uint32_t)host::powmod64(z, q, p);
+    f.s_inv = (uint32_t)host::powmod64(z, p - 2, p);
+    f.c_sos = (uint32_t)host::sqrt_mod(z - 1, p);
+    f.inv2 = (p + 1) / 2;
+    return f;
+}
+
+// Parity of the number of non-squares on the diagonal d̄ that the planner
+// reaches (hence whether Ā needs the added column), without factoring: the
+// Legendre symbol is multiplicative, so it is that of the product of the
+// nonzero entries of d̄.  A 2×2 block [[x, β], [β, γ]] contributes the
+// product of its two entries of d̄, which equals its determinant xγ − β² up
+// to the square factor 1/4 (antidiagonal case), or γ alone when the
+// determinant is 0 (then d̄ = (0, γ)).  Eight independent running products
+// keep the loop short.  Returns 0 or 1, or −1 when two blocks overlap.
+int scale_parity(uint32_t p, int64_t k, const uint32_t *d, const uint32_t *e) {
+    const uint64_t minv = UINT64_MAX / p;
+    auto red = [&](uint64_t x) -> uint64_t {
+        const uint64_t q = (uint64_t)(((unsigned __int128)x * minv) >> 64);
+        const uint64_t r = x - q * p;
+        return r >= p ? r - p : r;
+    };
+    uint64_t acc[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    int lane = 0;
+    for (int64_t c = 0; c < k;) {
+        uint64_t v;
+        if (e && c + 1 < k && e[c] != 0 && e[c] % p != 0) {
+            if (c + 2 < k && e[c + 1] != 0 && e[c + 1] % p != 0) return -1;
+            const uint64_t x = d[c] % p, g = d[c + 1] % p, b = e[c] % p;
+            const uint64_t det = (red(x * g) + p - red(b * b)) % p;
+            v = det ? det : g;
+            c += 2;
+        } else {
+            v = d[c];
+            c += 1;
+        }
+        const uint64_t t = red(acc[lane] * v);  // < 2^24 · 2^32
+        if (t) acc[lane] = t;                   // t = 0 exactly when v ≡ 0: skipped
+        lane = (lane + 1) & 7;
+    }
+    uint64_t prod = 1;
+    for (uint64_t a : acc) prod = red(prod * a);
+    return host::euler(prod, p) == p - 1 ? 1 : 0;
+}
+
+// Offsets of the planner's scratch (bytes, 256-aligned sections).
+struct ScaleLayout {
+    int64_t src, w, din, ein, dbar, ta, tb, mate, flag, ns, cnt, total;
+    ScaleLayout(int64_t k, int64_t kk) {
+        const auto sec = [](int64_t b) { return rup(std::max<int64_t>(b, 1), 256); };
+        src = 0;
+        w = src + sec(16 * kk);
+        din = w + sec(32 * kk);
+        ein = din + 4 * k;  // right after d: one upload
+        dbar = din + sec(8 * k);
+        ta = dbar + sec(4 * k);
+        tb = ta + sec(4 * k);
+        mate = tb + sec(4 * k);
+        flag = mate + sec(4 * k);
+        ns = flag + sec(4 * k);
+        cnt = ns + sec(4 * k);
+        total = cnt + 256;
+    }
+    ScalePlan plan(char *base) const {
+        ScalePlan sp;
+        sp.src = reinterpret_cast<int4 *>(base + src);
+        sp.w = reinterpret_cast<uint4 *>(base + w);
+        sp.dbar = reinterpret_cast<uint32_t *>(base + dbar);
+        sp.ta = reinterpret_cast<uint32_t *>(base + ta);
+        sp.tb = reinterpret_cast<uint32_t *>(base + tb);
+        sp.mate = reinterpret_cast<int32_t *>(base + mate);
+        sp.flag = reinterpret_cast<uint32_t *>(base + flag);
+        sp.ns = reinterpret_cast<int32_t *>(base + ns);
+        sp.ns_count = reinterpret_cast<int64_t *>(base + cnt);
+        return sp;
+    }
+};
+
+// grows a device buffer to `need` bytes (after draining `st`)
+bool grow(void **buf, int64_t *have, int64_t need, cudaStream_t st) {
+    if (need <= *have) return true;
+    cudaStreamSynchronize(st);
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    if (cudaMalloc(buf, (size_t)need) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    *have = need;
+    return true;
+}
+
+// C ← α·Ā·Āᵀ + β·C for Ā = A·W, W planned on the device for B with diagonal
+// d and off-diagonal e (e null: B = Diag(d))
+ffsyrk_status_t run_scaled(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
+                           uint32_t alpha, const uint32_t *A, int64_t lda, const uint32_t *d,
+                           const uint32_t *e, uint32_t beta, uint32_t *C, int64_t ldc,
+                           ffsyrk_stream_t stream) {
+    const int par = scale_parity(p, k, d, e);
+    if (par < 0) return FFSYRK_ERR_INVALID_ARG;
+    const int64_t kk = k + par;
     if (n > pl->max_n || kk > pl->max_k) return FFSYRK_ERR_TOO_LARGE;
     if (kk == 0) return ffsyrk_with_plan_update(pl, uplo, n, 0, p, alpha, A, std::max<int64_t>(1, k), beta, C, ldc, stream);
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != pl->device) return FFSYRK_ERR_INVALID_ARG;
+    if (pl->err_host[0] != 0) return FFSYRK_ERR_TIMEOUT;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // scratch for Ā (rows of a multiple of 4 entries) and the column table
-    const int64_t ldb = rup(kk, 4);
-    const int64_t need = n * ldb * 4;
-    const int64_t woff = rup(kk * 16, 64);
-    const int64_t tab = woff + 4 * kk * (int64_t)sizeof(MulConst);
-    if (need > pl->dbar_bytes || tab > pl->dtab_bytes) {
-        cudaStreamSynchronize(st);
-        if (need > pl->dbar_bytes) {
-            if (pl->dbar) cudaFree(pl->dbar);
-            pl->dbar = nullptr;
-            pl->dbar_bytes = 0;
-            if (cudaMalloc(&pl->dbar, (size_t)need) != cudaSuccess) {
-                cudaGetLastError();
-                return FFSYRK_ERR_ALLOC;
-            }
-            pl->dbar_bytes = need;
-        }
-        if (tab > pl->dtab_bytes) {
-            if (pl->dtab) cudaFree(pl->dtab);
-            pl->dtab = nullptr;
-            pl->dtab_bytes = 0;
-            if (cudaMalloc(&pl->dtab, (size_t)tab) != cudaSuccess) {
-                cudaGetLastError();
-                return FFSYRK_ERR_ALLOC;
-            }
-            pl->dtab_bytes = tab;
-        }
+    if (!pl->scale_ready) {
+        pl->sconst = make_scale_const(p);
+        pl->scale_ready = true;
     }
-    std::vector<char> host((size_t)tab, 0);
-    std::vector<MulConst> wc((size_t)(4 * kk));
-    for (int64_t t = 0; t < 4 * kk; ++t) wc[(size_t)t] = make_mul(mx.w[(size_t)t], p);
-    memcpy(host.data(), mx.src.data(), (size_t)(4 * kk) * 4);
-    memcpy(host.data() + woff, wc.data(), (size_t)(4 * kk) * sizeof(MulConst));
-    // a pageable copy: staged before it returns, so `host` may go away
-    if (cudaMemcpyAsync(pl->dtab, host.data(), (size_t)tab, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    const int64_t ldb = rup(kk, 32);  // rows of Ā on 128-byte boundaries
+    const ScaleLayout L(k, kk);
+    if (!grow(reinterpret_cast<void **>(&pl->dbar), &pl->dbar_bytes, n * ldb * 4, st) ||
+        !grow(reinterpret_cast<void **>(&pl->dtab), &pl->dtab_bytes, L.total, st))
+        return FFSYRK_ERR_ALLOC;
+    // d and e in one pageable copy (staged before it returns, so `in` may go)
+    const bool has_e = e && k > 1;
+    std::vector<uint32_t> in((size_t)(has_e ? 2 * k - 1 : k));
+    memcpy(in.data(), d, (size_t)k * 4);
+    if (has_e) memcpy(in.data() + k, e, (size_t)(k - 1) * 4);
+    if (cudaMemcpyAsync(pl->dtab + L.din, in.data(), in.size() * 4, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
         return FFSYRK_ERR_CUDA;
-    if (launch_col_mix(A, lda, n, kk, reinterpret_cast<const int32_t *>(pl->dtab),
-                       reinterpret_cast<const MulConst *>(pl->dtab + woff), pl->dbar, ldb, pl->mp,
-                       st) != cudaSuccess)
+    const ScalePlan sp = L.plan(pl->dtab);
+    if (launch_scale_plan(reinterpret_cast<const uint32_t *>(pl->dtab + L.din),
+                          reinterpret_cast<const uint32_t *>(pl->dtab + L.ein), has_e, k, kk,
+                          pl->sconst, sp, pl->err_dev, st) != cudaSuccess ||
+        launch_col_mix(A, lda, n, kk, sp.src, sp.w, pl->dbar, ldb, pl->mp, st) != cudaSuccess)
         return FFSYRK_ERR_CUDA;
     return ffsyrk_with_plan_update(pl, uplo, n, kk, p, alpha, pl->dbar, ldb, beta, C, ldc, stream);
 }
@@ -1641,9 +1736,8 @@ ffsyrk_status_t ffsyrkbd_with_plan_update(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, 
     ffsyrk_status_t s = check_scaled_args(pl, uplo, n, k, p, A, lda, d, C, ldc);
     if (s != FFSYRK_SUCCESS) return s;
     if (n == 0) return FFSYRK_SUCCESS;
-    ColMix mx;
-    if (block_factor(p, k, d, k > 1 ? e : nullptr, mx) < 0) return FFSYRK_ERR_INVALID_ARG;
-    return run_colmix(pl, uplo, n, k, p, alpha, A, lda, mx, beta, C, ldc, stream);
+    return run_scaled(pl, uplo, n, k, p, alpha, A, lda, d, k > 1 ? e : nullptr, beta, C, ldc,
+                      stream);
 }
 
 int32_t ffsyrkd_factor(uint32_t p, int64_t k, const uint32_t *d, int32_t *partner, uint32_t *u,
@@ -1673,6 +1767,50 @@ int32_t ffsyrkbd_factor(uint32_t p, int64_t k, const uint32_t *d, const uint32_t
         w[t] = mx.w[(size_t)t];
     }
     return (int32_t)mx.kk;
+}
+
+int32_t ffsyrkbd_factor_device(uint32_t p, int64_t k, const uint32_t *d, const uint32_t *e,
+                               int32_t *src, uint32_t *w) {
+    if (validate_p(p) != FFSYRK_SUCCESS || k < 0 || k >= INT32_MAX || (k > 0 && !d) || !src || !w)
+        return -1;
+    const int par = scale_parity(p, k, d, k > 1 ? e : nullptr);
+    if (par < 0) return -1;
+    const int64_t kk = k + par;
+    if (kk == 0) return 0;
+    const ScaleLayout L(k, kk);
+    char *buf = nullptr;
+    unsigned int *err = nullptr;
+    if (cudaMalloc(&buf, (size_t)L.total) != cudaSuccess || cudaMalloc(&err, 4) != cudaSuccess) {
+        cudaGetLastError();
+        if (buf) cudaFree(buf);
+        return -2;
+    }
+    const bool has_e = e && k > 1;
+    std::vector<uint32_t> in((size_t)(has_e ? 2 * k - 1 : k));
+    memcpy(in.data(), d, (size_t)k * 4);
+    if (has_e) memcpy(in.data() + k, e, (size_t)(k - 1) * 4);
+    std::vector<int4> s4((size_t)kk);
+    std::vector<uint4> w4((size_t)(2 * kk));
+    unsigned int err_h = 0;
+    const ScalePlan sp = L.plan(buf);
+    bool ok = cudaMemset(err, 0, 4) == cudaSuccess &&
+              cudaMemcpy(buf + L.din, in.data(), in.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+              launch_scale_plan(reinterpret_cast<const uint32_t *>(buf + L.din),
+                                reinterpret_cast<const uint32_t *>(buf + L.ein), has_e, k, kk,
+                                make_scale_const(p), sp, err, nullptr) == cudaSuccess &&
+              cudaMemcpy(s4.data(), sp.src, (size_t)kk * 16, cudaMemcpyDeviceToHost) == cudaSuccess &&
+              cudaMemcpy(w4.data(), sp.w, (size_t)kk * 32, cudaMemcpyDeviceToHost) == cudaSuccess &&
+              cudaMemcpy(&err_h, err, 4, cudaMemcpyDeviceToHost) == cudaSuccess && err_h == 0;
+    cudaFree(buf);
+    cudaFree(err);
+    if (!ok) return -2;
+    for (int64_t c = 0; c < kk; ++c) {
+        const int4 a = s4[(size_t)c];
+        const uint4 b0 = w4[(size_t)(2 * c)], b1 = w4[(size_t)(2 * c + 1)];
+        src[4 * c] = a.x, src[4 * c + 1] = a.y, src[4 * c + 2] = a.z, src[4 * c + 3] = a.w;
+        w[4 * c] = b0.x, w[4 * c + 1] = b0.z, w[4 * c + 2] = b1.x, w[4 * c + 3] = b1.z;
+    }
+    return (int32_t)kk;
 }
 
 extern "C" ffsyrk_status_t ffsyrk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,

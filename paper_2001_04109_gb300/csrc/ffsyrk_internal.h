@@ -232,12 +232,39 @@ int64_t digitize_flat_blocks(int64_t rows, int64_t kpad);
 cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP mp,
                         cudaStream_t st, bool upper);
 cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st);
-// Ā = A·W of Algorithms 5 and 6 (syrkd, syrkbd), Ā n × kk: column c is
-// Σ_t w[4c+t]·A_{src[4c+t]} over t < 4 (src −1 unused, else < k); src holds
-// 4·kk int32 on a 16-byte boundary (see k_col_mix)
-cudaError_t launch_col_mix(const uint32_t *A, int64_t lda, int64_t n, int64_t kk,
-                           const int32_t *src, const MulConst *w, uint32_t *B, int64_t ldb,
-                           ModP mp, cudaStream_t st);
+// Constants of F_p for the scaling planner of Section 5 (from the host).
+struct ScaleConst {
+    uint32_t p;
+    uint64_t minv;   // ⌊(2^64 − 1)/p⌋: Barrett reduction of 64-bit values
+    uint32_t q, s;   // p − 1 = q·2^s with q odd
+    uint32_t zq;     // z^q, z the least non-square (Tonelli–Shanks)
+    uint32_t s_inv;  // 1/z
+    uint32_t c_sos;  // √(z − 1), a square because z − 1 < z (Algorithm 3)
+    uint32_t inv2;   // 1/2
+};
+// Device scratch of the scaling planner: W (kk columns, each up to four
+// (source, weight) pairs) and per-column state of the k columns of A.
+struct ScalePlan {
+    int4 *src;       // kk: source columns of A (−1 unused)
+    uint4 *w;        // 2·kk: per column four (weight, ⌊weight·2^32/p⌋) pairs
+    uint32_t *dbar;  // k: the diagonal after the 2×2 blocks are made diagonal
+    uint32_t *ta;    // k: column c of T is ta[c]·e_c + tb[c]·e_mate[c]
+    uint32_t *tb;
+    int32_t *mate;   // k: the other column of c's 2×2 block, or −1
+    uint32_t *flag;  // k: 1 where d̄ is a non-square
+    int32_t *ns;     // k: the non-square columns in column order
+    int64_t *ns_count;
+};
+// The planner's kernels: W for B with diagonal d_dev and off-diagonal e_dev
+// (device copies of k and k − 1 entries).  Sets bit 2 of *err if a check
+// fails (a 2×2 block needing a fifth term, a non-square given to the square
+// root, or an odd count of non-squares that kk = k does not admit).
+cudaError_t launch_scale_plan(const uint32_t *d_dev, const uint32_t *e_dev, bool has_e, int64_t k,
+                              int64_t kk, const ScaleConst &f, const ScalePlan &sp,
+                              unsigned int *err, cudaStream_t st);
+// Ā = A·W, Ā n × kk with row stride ldb (see k_col_mix)
+cudaError_t launch_col_mix(const uint32_t *A, int64_t lda, int64_t n, int64_t kk, const int4 *src,
+                           const uint4 *w, uint32_t *B, int64_t ldb, ModP mp, cudaStream_t st);
 // the selected triangle for k = 0: zero, or β·C (sc.mode 1)
 cudaError_t launch_scale_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, const OutScale &sc,
                              uint32_t p, cudaStream_t st);

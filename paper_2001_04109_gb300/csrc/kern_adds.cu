@@ -637,33 +637,6 @@ __global__ void __launch_bounds__(256) k_post_fused(const PostNode *__restrict__
     }
 }
 
-// Ā = A·W for the diagonal and block-diagonal scalings of Algorithms 5 and
-// 6 (syrkd, syrkbd): column c of Ā is Σ_t w_{c,t}·A_{src_{c,t}} over at most
-// four columns of A (src −1: an unused term), with A's entries reduced mod p.
-// The host drops terms on the zero column that an odd number of non-squares
-// adds, so every src is < k.  Grid: x = 256-column blocks, y = rows (strided).
-__global__ void __launch_bounds__(256) k_col_mix(const uint32_t *__restrict__ A, int64_t lda,
-                                                 int64_t n, int64_t kk,
-                                                 const int4 *__restrict__ src,
-                                                 const MulConst *__restrict__ w, uint32_t *B,
-                                                 int64_t ldb, ModP m) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= kk) return;
-    const int4 s = src[c];
-    const int sc[4] = {s.x, s.y, s.z, s.w};
-    MulConst wc[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) wc[t] = w[4 * c + t];
-    for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
-        const uint32_t *row = A + r * lda;
-        uint32_t y = 0;
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-            if (sc[t] >= 0) y = addm(y, mulc(red(__ldg(row + sc[t]), m), wc[t], m.p), m.p);
-        B[r * ldb + c] = y;
-    }
-}
-
 // Row r0 + blockIdx.y of the selected triangle of C for k = 0 (A·Aᵀ = 0):
 // zero, or β·C with an update (OutScale mode 1).
 __global__ void k_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, int64_t r0, OutScale sc,
@@ -788,16 +761,6 @@ cudaError_t launch_scale_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, con
 
 cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st) {
     return launch_scale_tri(C, n, ldc, upper, OutScale{}, 3u, st);
-}
-
-cudaError_t launch_col_mix(const uint32_t *A, int64_t lda, int64_t n, int64_t kk,
-                           const int32_t *src, const MulConst *w, uint32_t *B, int64_t ldb,
-                           ModP mp, cudaStream_t st) {
-    if (n == 0 || kk == 0) return cudaSuccess;
-    dim3 grid((unsigned)((kk + 255) / 256), (unsigned)std::min<int64_t>(n, 4096));
-    k_col_mix<<<grid, 256, 0, st>>>(A, lda, n, kk, reinterpret_cast<const int4 *>(src), w, B, ldb,
-                                    mp);
-    return cudaGetLastError();
 }
 
 }  // namespace fsk

@@ -12,6 +12,7 @@ import ctypes
 import os
 import threading
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -33,7 +34,8 @@ EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsy
            "ffsyrk_version", "ffsyrk_noalloc", "ffsyrk_leaf_schedule", "ffsyrk_digit_bounds",
            "ffsyrk_digit_base", "ffsyrk_plan_selftest_timeout", "ffsyrk_with_plan_update",
            "ffsyrk_update", "ffsyrkd_with_plan_update", "ffsyrkd_update", "ffsyrkd_factor",
-           "ffsyrkbd_with_plan_update", "ffsyrkbd_update", "ffsyrkbd_factor"]
+           "ffsyrkbd_with_plan_update", "ffsyrkbd_update", "ffsyrkbd_factor",
+           "ffsyrkbd_factor_device"]
 
 
 class FfsyrkError(RuntimeError):
@@ -101,6 +103,8 @@ def lib() -> ctypes.CDLL:
                                           i64, vp]
             L.ffsyrkbd_factor.argtypes = [u32, i64, P(u32), P(u32), P(i32), P(u32)]
             L.ffsyrkbd_factor.restype = i32
+            L.ffsyrkbd_factor_device.argtypes = [u32, i64, P(u32), P(u32), P(i32), P(u32)]
+            L.ffsyrkbd_factor_device.restype = i32
             L.ffsyrk_noalloc.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk_batched.argtypes = [i32, i64, P(i64), P(i64), u32, P(vp), P(i64), P(vp),
                                          P(i64), vp]
@@ -285,10 +289,25 @@ def digit_bounds(p: int) -> list[int]:
 
 
 def _u32_array(d, k: int):
-    vals = [int(x) & 0xFFFFFFFF for x in (d.tolist() if hasattr(d, "tolist") else d)]
-    if len(vals) != k:
-        raise ValueError("d must hold one entry per column of A")
-    return (ctypes.c_uint32 * max(k, 1))(*vals)
+    """k host values as a uint32 buffer for the library (wrapping like int(x) & 0xFFFFFFFF).
+
+    A contiguous numpy uint32 array passes without a copy; anything else
+    (lists, other integer dtypes, CPU tensors) is converted once by numpy.
+    """
+    if isinstance(d, torch.Tensor):
+        d = d.detach().cpu().numpy()
+    a = np.asarray(d)
+    if a.dtype != np.uint32:
+        if a.dtype == object or a.dtype.kind not in "iu":
+            a = np.array([int(x) & 0xFFFFFFFF for x in a.reshape(-1)], dtype=np.uint64)
+        a = (a.astype(np.int64, copy=False) & 0xFFFFFFFF) if a.dtype.kind == "i" else a
+        a = a.astype(np.uint32)
+    a = np.ascontiguousarray(a.reshape(-1))
+    if a.shape[0] != k:
+        raise ValueError("d must hold one entry per column of A (e: one fewer)")
+    if k == 0:
+        a = np.zeros(1, dtype=np.uint32)
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
 
 
 def syrkd(A: torch.Tensor, d, p: int, uplo: str = "lower", C: torch.Tensor | None = None,
@@ -348,6 +367,22 @@ def syrkbd_factor(p: int, d, e) -> tuple[int, list[list[tuple[int, int]]]]:
     kk = lib().ffsyrkbd_factor(int(p), k, dv, ev, src, w)
     if kk < 0:
         raise ValueError("bad p, d or e (overlapping 2x2 blocks?)")
+    return kk, [[(src[4 * c + t], w[4 * c + t]) for t in range(4) if src[4 * c + t] >= 0]
+                for c in range(kk)]
+
+
+def syrkbd_factor_device(p: int, d, e) -> tuple[int, list[list[tuple[int, int]]]]:
+    """As :func:`syrkbd_factor`, computed by the device planner (needs a GPU)."""
+    k = len(d)
+    dv = _u32_array(d, k)
+    ev = _u32_array(e, max(k - 1, 0)) if e is not None else None
+    src = (ctypes.c_int32 * (4 * (k + 1)))()
+    w = (ctypes.c_uint32 * (4 * (k + 1)))()
+    kk = lib().ffsyrkbd_factor_device(int(p), k, dv, ev, src, w)
+    if kk == -1:
+        raise ValueError("bad p, d or e (overlapping 2x2 blocks?)")
+    if kk < 0:
+        raise FfsyrkError(ERR_CUDA, "ffsyrkbd_factor_device")
     return kk, [[(src[4 * c + t], w[4 * c + t]) for t in range(4) if src[4 * c + t] >= 0]
                 for c in range(kk)]
 

@@ -232,3 +232,15 @@ def test_syrkbd_cached_and_rejects_overlap():
         plan.syrkbd(A.cuda(), d, bad)
     assert err.value.code == ffsyrk.ERR_INVALID_ARG
     plan.close()
+
+
+@pytest.mark.parametrize("p", [7, 11, 13, 97, 40961, 65521, 65537, 131071, 8388593])
+def test_device_planner_matches_host_planner(p):
+    # the device planner picks the same roots, pairs and term order as the
+    # host's: the whole table W agrees entry for entry
+    for seed in range(4):
+        for k in [1, 2, 5, 64, 257, 1000]:
+            d, e = block_diag(k, p, seed=seed * 7919 + k)
+            if seed == 3:
+                e = None
+            assert ffsyrk.syrkbd_factor_device(p, d, e) == ffsyrk.syrkbd_factor(p, d, e), (p, seed, k)

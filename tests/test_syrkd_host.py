@@ -125,7 +125,7 @@ def random_block_diag(k, p, rng):
     return d, e
 
 
-@pytest.mark.parametrize("p", [3, 5, 7, 13, 65521, 131071, 8388593])
+@pytest.mark.parametrize("p", [3, 5, 7, 13, 97, 40961, 65521, 65537, 131071, 8388593])
 def test_block_factor_gives_w_w_t_equal_b(p):
     rng = np.random.default_rng(p % 1009)
     for k in [0, 1, 2, 3, 6, 11, 24]:
