@@ -19,7 +19,8 @@ Contents
 * :mod:`oracle.field` -- primality, Legendre symbols, square roots and the
   skew-orthogonal Y of Section 3.1 (Prop. 3.2, Prop. 3.3, Algorithm 3).
 * :mod:`oracle.alg2` -- Algorithm 2 itself written step by step over F_p in
-  Python integers, for the block identities of the appendix proof.
+  Python integers, for the block identities of the appendix proof; its
+  general products optionally by :mod:`oracle.winograd` (Algorithm 1).
 * :mod:`oracle.cost` -- the operation-count recurrences behind Table 5 and
   Eq. (complexity) of Theorem 4.1.
 """

@@ -17,6 +17,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import field
+from . import winograd as _winograd
 
 
 def _obj(X) -> np.ndarray:
@@ -56,11 +57,13 @@ def pad_to(A, rows: int, cols: int) -> np.ndarray:
     return out
 
 
-def step(A, p: int, Y, syrk_rec, mirror: bool = True) -> dict:
+def step(A, p: int, Y, syrk_rec, mirror: bool = True, gemm=None) -> dict:
     """One level of Algorithm 2 on an even-sized A with a (k/2)×(k/2) Y.
 
     ``syrk_rec`` computes the three recursive products (lower triangle
-    only).  Returns every intermediate value under the paper's names.
+    only); ``gemm(X, Z)`` the two general products X·Z (default: the
+    classical product).  Returns every intermediate value under the paper's
+    names.
     """
     A = _obj(A) % p
     n, k = A.shape
@@ -76,8 +79,11 @@ def step(A, p: int, Y, syrk_rec, mirror: bool = True) -> dict:
     # 3 recursive syrk (P1, P2, P5) and 2 general (P3, P4) products
     P1 = syrk_rec(A11)
     P2 = syrk_rec(A12)
-    P3 = A22.dot(S4.T) % p
-    P4 = S1.dot(S2.T) % p
+    if gemm is None:
+        def gemm(X, Z):
+            return X.dot(Z) % p
+    P3 = _obj(gemm(A22, S4.T)) % p
+    P4 = _obj(gemm(S1, S2.T)) % p
     P5 = syrk_rec(S3)
     # 2 symmetric (half) additions
     U1 = (low(P1) + low(P5)) % p
@@ -98,12 +104,15 @@ def step(A, p: int, Y, syrk_rec, mirror: bool = True) -> dict:
 
 
 def syrk(A, p: int, levels: int, layout: str = "interleaved", params: dict | None = None,
-         mirror: bool = True) -> np.ndarray:
+         mirror: bool = True, winograd: int = 0) -> np.ndarray:
     """Low(A·Aᵀ) mod p by ``levels`` levels of Algorithm 2, then the classical base case.
 
     Odd sizes are zero padded: rows to an even count, columns to an even
     count (a multiple of 4 when Y has the 2×2 form, whose dimension k/2 must
-    be even).  The same Y constants are used at every level.
+    be even).  The same Y constants are used at every level.  With
+    ``winograd`` > 0 the two general products of a level with ``levels``
+    levels to go use min(winograd, levels − 1) levels of Algorithm 1 (the
+    paper's G-i variants take levels − 1, Section 4.2).
     """
     A = _obj(A) % p
     n, k = A.shape
@@ -117,9 +126,15 @@ def syrk(A, p: int, levels: int, layout: str = "interleaved", params: dict | Non
     Y = skew_y(p, k2 // 2, layout=layout, params=prm)
 
     def rec(X):
-        return syrk(X, p, levels - 1, layout=layout, params=prm, mirror=mirror)
+        return syrk(X, p, levels - 1, layout=layout, params=prm, mirror=mirror,
+                    winograd=winograd)
 
-    C = step(Ap, p, Y, rec, mirror=mirror)["C"]
+    sw = min(max(winograd, 0), levels - 1)
+
+    def gemm(X, Z):
+        return _winograd.product(X, Z, p, sw)
+
+    C = step(Ap, p, Y, rec, mirror=mirror, gemm=gemm)["C"]
     return C[:n, :n]
 
 

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle import alg2, cost, field
+from oracle import alg2, cost, field, winograd
 from paper_2001_04109_gb300 import inputs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -184,6 +184,61 @@ def test_planted_mistakes_are_caught():
     P4_wrong = st["S1"].dot(S2_wrong.T) % p
     U2 = (st["U1"] + P4_wrong) % p
     assert not np.array_equal((U2 + st["P3"]) % p, (Ao.dot(Ao.T) % p)[h:, :h])
+
+
+@pytest.mark.parametrize("p", [65521, 8388593, 7, 3])
+@pytest.mark.parametrize("shape", [(2, 2, 2), (4, 6, 8), (8, 4, 2), (10, 12, 6)])
+def test_winograd_step_is_the_product(p, shape):
+    # Algorithm 1 on even-sized blocks reaches A·B exactly, block by block
+    m, k, n = shape
+    rng = np.random.default_rng(m * 100 + k * 10 + n)
+    A = rng.integers(0, p, size=(m, k)).astype(object)
+    B = rng.integers(0, p, size=(k, n)).astype(object)
+    st = winograd.step(A, B, p, lambda X, Z: X.dot(Z) % p)
+    h, w, v = m // 2, k // 2, n // 2
+    AB = A.dot(B) % p
+    assert np.array_equal(st["C"], AB)
+    # the block identities behind the post-additions
+    assert np.array_equal(st["c3"], (A[:h, :w].dot(B[:w, :v]) + A[:h, w:].dot(B[w:, :v])) % p)
+    assert np.array_equal(st["c5"], AB[h:, v:])
+    # 8 pre-additions and 7 post-additions: 15 in all, 7 products
+    assert len([x for x in st if x[0] in "st"]) == 8 and len([x for x in st if x[0] == "c"]) == 7
+    assert len([x for x in st if x[0] == "p"]) == 7
+
+
+@pytest.mark.parametrize("levels", [1, 2, 3])
+def test_winograd_recursive_product(levels):
+    p = 131071
+    rng = np.random.default_rng(levels)
+    for m, k, n in [(16, 16, 16), (12, 20, 8), (7, 9, 5), (1, 4, 3)]:
+        A = rng.integers(0, p, size=(m, k)).astype(object)
+        B = rng.integers(0, p, size=(k, n)).astype(object)
+        assert np.array_equal(winograd.product(A, B, p, levels), A.dot(B) % p)
+
+
+def test_winograd_planted_sign_error_is_caught():
+    p = 65521
+    rng = np.random.default_rng(4)
+    A = rng.integers(0, p, size=(8, 8)).astype(object)
+    B = rng.integers(0, p, size=(8, 8)).astype(object)
+    st = winograd.step(A, B, p, lambda X, Z: X.dot(Z) % p)
+    # t4 = b21 + t3 (wrong sign) changes p3, hence c4 = C21
+    t4_bad = (B[4:, :4] + st["t3"]) % p
+    c4_bad = (st["c2"] + A[4:, 4:].dot(t4_bad)) % p
+    assert not np.array_equal(c4_bad, (A.dot(B) % p)[4:, :4])
+
+
+@pytest.mark.parametrize("p", [65521, 131071, 13])
+@pytest.mark.parametrize("shape", [(16, 16), (24, 40), (13, 11), (32, 8)])
+def test_alg2_with_winograd_general_products(p, shape):
+    # the G-i variants: levels of Algorithm 2, Algorithm 1 one level less
+    n, k = shape
+    A = inputs.uniform_residues(n, k, p, seed=n + 7 * k).numpy().view(np.uint32)
+    want = oracle.syrk(A, p, "lower")
+    for levels in [2, 3]:
+        for sw in [1, 2]:
+            got = alg2.syrk(A.astype(object), p, levels, winograd=sw)
+            assert np.array_equal(got.astype(np.uint32), want), (p, shape, levels, sw)
 
 
 def _table5():
