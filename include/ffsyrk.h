@@ -84,10 +84,17 @@ typedef struct {
                           per process and, if the environment variable
                           FFSYRK_TUNE_CACHE names a file, in that file.
                           0: depth from the built-in cost model.            */
-    int32_t reserved[4]; /* must be zero                                       */
+    int32_t winograd;  /* levels of Algorithm 1 (Winograd's variant of
+                          Strassen's product, Section 2) for the two general
+                          products P3, P4 of depth d, never more than
+                          L − 1 − d (the paper's G-i variants, Section 4.2,
+                          take exactly that): −1 (default) = as many as the
+                          built-in cost model finds worth it; 0 = none;
+                          w ≥ 1 = min(w, L − 1 − d) at every depth d.       */
+    int32_t reserved[3]; /* must be zero                                       */
 } ffsyrk_options_t;
 
-/* The defaults: automatic leaf and recursion depth. */
+/* The defaults: automatic leaf, recursion depth and Winograd levels. */
 void ffsyrk_options_default(ffsyrk_options_t *opts);
 
 /* Opaque plan: the field constants (p, Y), the digit scheme, the recursion
@@ -270,6 +277,8 @@ typedef struct {
     int32_t tile_ctas;   /* 1 or 2: SMs per tensor-core leaf tile at max_n  */
     int32_t autotuned;   /* 1 if levels/tile_ctas came from the autotuner    */
     float tuned_ms;      /* the winning candidate's time per call, or 0      */
+    int32_t winograd[6]; /* levels of Algorithm 1 for the general products of
+                            depth d = 0..5 at max_n × max_k (0 beyond L − 1) */
 } ffsyrk_plan_info_t;
 
 ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t plan, ffsyrk_plan_info_t *info);

@@ -96,6 +96,8 @@ struct Geometry {
     int L = 0;
     int64_t n = 0, k = 0, np = 0, kp = 0;
     int64_t h[kMaxLevels + 1] = {}, w[kMaxLevels + 1] = {};
+    // levels of Algorithm 1 (Winograd) for the general products of depth d
+    int sw[kMaxLevels] = {};
 };
 
 Geometry make_geometry(int64_t n, int64_t k, int L) {
@@ -130,12 +132,86 @@ struct Layout {
     int64_t s3_off[kMaxLevels + 1] = {};  // S3 node buffers of depth d (1 ≤ d ≤ L−1)
     int64_t r_off[kMaxLevels + 1] = {};   // node results of depth d (1 ≤ d ≤ L)
     int64_t g_off[kMaxLevels + 1] = {};   // P3/P4 of depth d (0 ≤ d ≤ L−1)
+    // Algorithm 1 on depth d's general products: uint32 operands at level
+    // l < sw[d] (4·3^d·7^l of h_{d+1+l} × roundup(w_{d+1+l}, 64)) and uint32
+    // products at level l ≥ 1 (2·3^d·7^l of h_{d+1+l}²)
+    int64_t swin_off[kMaxLevels][kMaxLevels + 1] = {};
+    int64_t swout_off[kMaxLevels][kMaxLevels + 1] = {};
     int64_t data_bytes = 0;
 };
 
+inline int64_t pow7(int d) {
+    int64_t r = 1;
+    while (d-- > 0) r *= 7;
+    return r;
+}
+
+// Levels of Algorithm 1 for a general product h×h×w.  One level removes 1/8
+// of its leaf multiply-adds (h²w·D²/8 digit products) and adds about
+// (16 + 3D)·h·w + 14·h² bytes of streaming traffic: both operands written as
+// uint32 and read back by the pre-additions, 7/4 as many digit planes, 7/4
+// as many product entries written by the leaf, read back and combined by the
+// post-additions.  Rates as in level_pays.
+bool sw_level_pays(int64_t h, int64_t w, int D) {
+    const double saved = (double)h * h * w * D * D / 8.0 / 8.5e14;
+    const double extra = ((16.0 + 3.0 * D) * h * w + 14.0 * (double)h * h) / 4.0e12;
+    return saved > extra && h >= 2048;
+}
+
+// The general products of depth d take sw[d] ≤ L − 1 − d levels of
+// Algorithm 1 (the paper's G-i variants use L − 1 − d), so that every block
+// they split into has a size of the geometry.  opt < 0: as many levels as
+// pay; otherwise min(opt, L − 1 − d).
+void set_winograd(Geometry &g, int opt, int D) {
+    for (int d = 0; d < kMaxLevels; ++d) g.sw[d] = 0;
+    for (int d = 0; d + 1 < g.L; ++d) {
+        const int top = g.L - 1 - d;
+        if (opt >= 0) {
+            g.sw[d] = std::min(opt, top);
+            continue;
+        }
+        int sv = 0;
+        while (sv < top && sw_level_pays(g.h[d + 1 + sv], g.w[d + 1 + sv], D)) ++sv;
+        g.sw[d] = sv;
+    }
+}
+
+// Arena (K = w_j) of depth d's general-product operands, their count, and
+// the first of them in that arena.  Without Algorithm 1 depth d's 4·3^d
+// operands sit in arena d + 1; with s levels their 4·3^d·7^s pieces sit in
+// arena d + 1 + s.  The 3^L leaf syrk operands follow in arena L.
+inline int gen_arena(const Geometry &g, int d) { return d + 1 + g.sw[d]; }
+inline int64_t gen_ops(const Geometry &g, int d) { return 4 * pow3(d) * pow7(g.sw[d]); }
+int64_t gen_base(const Geometry &g, int d) {
+    int64_t b = 0;
+    for (int e = 0; e < d; ++e)
+        if (gen_arena(g, e) == gen_arena(g, d)) b += gen_ops(g, e);
+    return b;
+}
+int64_t syrk_base(const Geometry &g) {
+    int64_t b = 0;
+    for (int d = 0; d < g.L; ++d)
+        if (gen_arena(g, d) == g.L) b += gen_ops(g, d);
+    return b;
+}
 int64_t arena_nops(const Geometry &g, int j) {
     if (g.L == 0) return 1;
-    return 4 * pow3(j - 1) + (j == g.L ? pow3(g.L) : 0);
+    int64_t n = 0;
+    for (int d = 0; d < g.L; ++d)
+        if (gen_arena(g, d) == j) n += gen_ops(g, d);
+    return n + (j == g.L ? pow3(g.L) : 0);
+}
+// Field multiply-adds of the leaf products (the lower triangle of each
+// syrk leaf counted once).
+double leaf_field_macs(const Geometry &g) {
+    if (g.L == 0) return (double)g.n * (g.n + 1) / 2 * (double)g.k;
+    double macs = 0;
+    for (int d = 0; d < g.L; ++d) {
+        const int j = gen_arena(g, d);
+        macs += 2.0 * (double)pow3(d) * (double)pow7(g.sw[d]) * (double)g.h[j] * g.h[j] *
+                (double)g.w[j];
+    }
+    return macs + (double)pow3(g.L) * (double)g.h[g.L] * (g.h[g.L] + 1) / 2 * (double)g.w[g.L];
 }
 
 Layout make_layout(const Geometry &g, int leaf, int D) {
@@ -164,6 +240,13 @@ Layout make_layout(const Geometry &g, int leaf, int D) {
     for (int d = 1; d <= g.L; ++d) lay.r_off[d] = take(pow3(d) * g.h[d] * g.h[d] * 4);
     for (int d = 0; d <= g.L - 1; ++d)
         lay.g_off[d] = take(2 * pow3(d) * g.h[d + 1] * g.h[d + 1] * 4);
+    for (int d = 0; d <= g.L - 1; ++d) {
+        for (int l = 0; l < g.sw[d]; ++l)
+            lay.swin_off[d][l] = take(4 * pow3(d) * pow7(l) * g.h[d + 1 + l] *
+                                      rup(g.w[d + 1 + l], 64) * 4);
+        for (int l = 1; l <= g.sw[d]; ++l)
+            lay.swout_off[d][l] = take(2 * pow3(d) * pow7(l) * g.h[d + 1 + l] * g.h[d + 1 + l] * 4);
+    }
     lay.data_bytes = off;
     return lay;
 }
@@ -172,6 +255,10 @@ Layout make_layout(const Geometry &g, int leaf, int D) {
 struct Descs {
     std::vector<PrepNode> prep[kMaxLevels];
     std::vector<PostNode> post[kMaxLevels];
+    // Algorithm 1 jobs of depth d, level l (1 ≤ l ≤ sw[d])
+    std::vector<SwPreJob> swpre[kMaxLevels][kMaxLevels + 1];
+    std::vector<SwPostJob> swpost[kMaxLevels][kMaxLevels + 1];
+    int64_t swpre_off[kMaxLevels][kMaxLevels + 1] = {}, swpost_off[kMaxLevels][kMaxLevels + 1] = {};
     std::vector<LeafProd> prods;
     std::vector<LeafTile> tiles;
     std::vector<DigitizeJob> digit;
@@ -203,9 +290,9 @@ int64_t leaf_tiles_bound(const Geometry &g, int leaf, int64_t *nprods_out = null
         ntiles = ((g.n + tm - 1) / tm) * ((g.n + tn - 1) / tn);
     } else {
         for (int d = 0; d < g.L; ++d) {
-            int64_t h = g.h[d + 1];
-            ntiles += 2 * pow3(d) * ((h + tm - 1) / tm) * ((h + tn - 1) / tn);
-            nprods += 2 * pow3(d);
+            const int64_t h = g.h[gen_arena(g, d)], np = 2 * pow3(d) * pow7(g.sw[d]);
+            ntiles += np * ((h + tm - 1) / tm) * ((h + tn - 1) / tn);
+            nprods += np;
         }
         int64_t h = g.h[g.L];
         ntiles += pow3(g.L) * ((h + tm - 1) / tm) * ((h + tn - 1) / tn);
@@ -218,7 +305,11 @@ int64_t leaf_tiles_bound(const Geometry &g, int leaf, int64_t *nprods_out = null
 int64_t desc_capacity(const Geometry &g, int leaf) {
     // generous bound for the descriptor blob of any shape ≤ g
     int64_t b = 0;
-    for (int d = 0; d < g.L; ++d) b += pow3(d) * (sizeof(PrepNode) + sizeof(PostNode)) + 2 * 256;
+    for (int d = 0; d < g.L; ++d) {
+        b += pow3(d) * (sizeof(PrepNode) + sizeof(PostNode)) + 2 * 256;
+        for (int l = 1; l <= g.sw[d]; ++l)
+            b += pow3(d) * pow7(l - 1) * (4 * sizeof(SwPreJob) + 2 * sizeof(SwPostJob)) + 2 * 256;
+    }
     int64_t nprods = 1;
     const int64_t ntiles = leaf_tiles_bound(g, leaf, &nprods);
     b += nprods * sizeof(LeafProd) + ntiles * sizeof(LeafTile);
@@ -497,6 +588,7 @@ struct ffsyrk_plan_st {
     int leaf = FFSYRK_LEAF_TC_BF16;
     int levels_opt = FFSYRK_LEVELS_AUTO;
     int ctas_opt = 0;
+    int sw_opt = -1;  // levels of Algorithm 1: −1 automatic, else the cap
     int64_t max_n = 0, max_k = 0;
     int L_max = 0;  // levels used at the max shape
     // device workspace: data region then descriptor region
@@ -540,6 +632,14 @@ struct ffsyrk_plan_st {
     float tuned_ms = 0.f;
 };
 
+// The geometry of one call: sizes of every depth and the levels of
+// Algorithm 1 for its general products.
+Geometry plan_geometry(const ffsyrk_plan_st *pl, int64_t n, int64_t k, int L) {
+    Geometry g = make_geometry(n, k, L);
+    set_winograd(g, pl->sw_opt, pl->ds.D);
+    return g;
+}
+
 namespace {
 
 // One more level of Algorithm 2 on an n×k (sub)problem pays when the leaf
@@ -579,14 +679,7 @@ int choose_ctas(const ffsyrk_plan_st *pl, const Geometry &g) {
     if (pl->leaf != FFSYRK_LEAF_TC_BF16 || pl->ds.base != 256) return 1;
     if (leaf_tiles_bound(g, pl->leaf) < pl->sms) return 1;
     // digit multiply-adds of the leaf over a measured ≈ 9e14 per second
-    double macs = 0;
-    if (g.L == 0) {
-        macs = (double)g.n * (g.n + 1) / 2 * (double)g.k;
-    } else {
-        for (int d = 0; d < g.L; ++d)
-            macs += 2.0 * std::pow(3.0, d) * (double)g.h[d + 1] * g.h[d + 1] * (double)g.w[d + 1];
-        macs += std::pow(3.0, g.L) * (double)g.h[g.L] * (g.h[g.L] + 1) / 2 * (double)g.w[g.L];
-    }
+    const double macs = leaf_field_macs(g);
     const double est_ms = macs * pl->ds.D * pl->ds.D / 9e14 * 1e3;
     return est_ms < 40.0 ? 2 : 1;
 }
@@ -760,17 +853,34 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     } else {
         // node views, depth by depth
         std::vector<MatView> views{MatView{A, lda, g.n, g.k}};
+        const int64_t sb = syrk_base(g);
         for (int d = 0; d < g.L; ++d) {
             const int64_t h = g.h[d + 1], w = g.w[d + 1];
+            const int sw = g.sw[d];            // levels of Algorithm 1 for this depth
+            const int ja = gen_arena(g, d);    // arena of its general-product operands
+            const int64_t gb = gen_base(g, d);
+            // uint32 operand `idx` at Algorithm-1 level l, and product `idx` at level l ≥ 1
+            auto swin = [&](int l, int64_t idx) {
+                return reinterpret_cast<uint32_t *>(ws + lay.swin_off[d][l]) +
+                       idx * g.h[d + 1 + l] * rup(g.w[d + 1 + l], 64);
+            };
+            auto swout = [&](int l, int64_t idx) {
+                return reinterpret_cast<uint32_t *>(ws + lay.swout_off[d][l]) +
+                       idx * g.h[d + 1 + l] * g.h[d + 1 + l];
+            };
             std::vector<MatView> next;
             for (int64_t t = 0; t < (int64_t)views.size(); ++t) {
                 const MatView &X = views[t];
                 PrepNode nd{};
                 nd.X = X;
-                for (int q = 0; q < 4; ++q) nd.gemm[q] = operand(d + 1, 4 * t + q);
+                // X22, S4 (P3 = X22·S4ᵀ) and S1, S2 (P4 = S1·S2ᵀ): digit planes, or
+                // uint32 rows that Algorithm 1's pre-additions split further
+                for (int q = 0; q < 4; ++q)
+                    nd.gemm[q] = sw == 0 ? operand(ja, gb + 4 * t + q)
+                                         : OperandDst{swin(0, 4 * t + q), 0, rup(w, 64), h};
                 if (d == g.L - 1) {
                     for (int q = 0; q < 3; ++q)
-                        nd.leaf[q] = operand(g.L, 4 * pow3(g.L - 1) + 3 * t + q);
+                        nd.leaf[q] = operand(g.L, sb + 3 * t + q);
                     nd.s3 = nullptr;
                     nd.s3_ld = 0;
                 } else {
@@ -785,21 +895,55 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
                     next.push_back(s3);
                 }
                 D.prep[d].push_back(nd);
-                // the two general products of this node
+                // the two general products of this node (gp = 2t + q), each
+                // directly, or as the 7^sw products of sw levels of Algorithm 1
                 for (int q = 0; q < 2; ++q) {
-                    LeafProd pr{};
-                    pr.arena = d + 1;
-                    pr.tri = 0;
-                    pr.a_row0 = operand(d + 1, 4 * t + 2 * q).row0;
-                    pr.b_row0 = operand(d + 1, 4 * t + 2 * q + 1).row0;
-                    pr.rows = pr.cols = h;
-                    pr.kblocks = (int32_t)(lay.arena[d + 1].kpad / 64);
-                    pr.plane_rows = lay.arena[d + 1].rpad;
-                    pr.out = gbuf(d, t, q);
-                    pr.ldo = h;
-                    D.prods.push_back(pr);
-                    tri_tiles(D.tiles, (int)D.prods.size() - 1, h, h, 0, TM, TN,
-                              pr.kblocks * cost_mult);
+                    const int64_t gp = 2 * t + q, n7 = pow7(sw);
+                    for (int l = 1; l <= sw; ++l) {
+                        // pre-additions: level l − 1 operands into 7 pieces each
+                        const int64_t npar = pow7(l - 1);
+                        for (int side = 0; side < 2; ++side)
+                            for (int64_t ip = 0; ip < npar; ++ip) {
+                                SwPreJob jb{};
+                                jb.X = swin(l - 1, (2 * gp + side) * npar + ip);
+                                jb.ldx = rup(g.w[d + l], 64);
+                                jb.side = side;
+                                for (int m = 0; m < 7; ++m) {
+                                    const int64_t child = (2 * gp + side) * pow7(l) + 7 * ip + m;
+                                    jb.dst[m] = l < sw ? OperandDst{swin(l, child), 0,
+                                                                    rup(g.w[d + 1 + l], 64),
+                                                                    g.h[d + 1 + l]}
+                                                       : operand(ja, gb + child);
+                                }
+                                D.swpre[d][l].push_back(jb);
+                            }
+                    }
+                    const int64_t hj = g.h[ja];
+                    for (int64_t idx = 0; idx < n7; ++idx) {
+                        LeafProd pr{};
+                        pr.arena = ja;
+                        pr.tri = 0;
+                        pr.a_row0 = operand(ja, gb + (2 * gp) * n7 + idx).row0;
+                        pr.b_row0 = operand(ja, gb + (2 * gp + 1) * n7 + idx).row0;
+                        pr.rows = pr.cols = hj;
+                        pr.kblocks = (int32_t)(lay.arena[ja].kpad / 64);
+                        pr.plane_rows = lay.arena[ja].rpad;
+                        pr.out = sw == 0 ? gbuf(d, t, q) : swout(sw, gp * n7 + idx);
+                        pr.ldo = hj;
+                        D.prods.push_back(pr);
+                        tri_tiles(D.tiles, (int)D.prods.size() - 1, hj, hj, 0, TM, TN,
+                                  pr.kblocks * cost_mult);
+                    }
+                    // post-additions, deepest level first, down to P3 or P4
+                    for (int l = sw; l >= 1; --l) {
+                        const int64_t npar = pow7(l - 1);
+                        for (int64_t ip = 0; ip < npar; ++ip) {
+                            SwPostJob jb{};
+                            for (int m = 0; m < 7; ++m) jb.P[m] = swout(l, gp * pow7(l) + 7 * ip + m);
+                            jb.C = l == 1 ? gbuf(d, t, q) : swout(l - 1, gp * npar + ip);
+                            D.swpost[d][l].push_back(jb);
+                        }
+                    }
                 }
             }
             views.swap(next);
@@ -810,7 +954,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
             LeafProd pr{};
             pr.arena = g.L;
             pr.tri = 1;
-            pr.a_row0 = pr.b_row0 = operand(g.L, 4 * pow3(g.L - 1) + t).row0;
+            pr.a_row0 = pr.b_row0 = operand(g.L, sb + t).row0;
             pr.rows = pr.cols = hL;
             pr.kblocks = (int32_t)(lay.arena[g.L].kpad / 64);
             pr.plane_rows = lay.arena[g.L].rpad;
@@ -867,6 +1011,10 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     for (int d = 0; d < g.L; ++d) {
         D.prep_off[d] = slot((int64_t)D.prep[d].size() * sizeof(PrepNode), 256);
         D.post_off[d] = slot((int64_t)D.post[d].size() * sizeof(PostNode), 256);
+        for (int l = 1; l <= g.sw[d]; ++l) {
+            D.swpre_off[d][l] = slot((int64_t)D.swpre[d][l].size() * sizeof(SwPreJob), 256);
+            D.swpost_off[d][l] = slot((int64_t)D.swpost[d][l].size() * sizeof(SwPostJob), 256);
+        }
     }
     D.prods_off = slot((int64_t)D.prods.size() * sizeof(LeafProd), 256);
     D.tiles_off = slot((int64_t)D.tiles.size() * sizeof(LeafTile), 256);
@@ -886,6 +1034,12 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     for (int d = 0; d < g.L; ++d) {
         memcpy(hb + D.prep_off[d], D.prep[d].data(), D.prep[d].size() * sizeof(PrepNode));
         memcpy(hb + D.post_off[d], D.post[d].data(), D.post[d].size() * sizeof(PostNode));
+        for (int l = 1; l <= g.sw[d]; ++l) {
+            memcpy(hb + D.swpre_off[d][l], D.swpre[d][l].data(),
+                   D.swpre[d][l].size() * sizeof(SwPreJob));
+            memcpy(hb + D.swpost_off[d][l], D.swpost[d][l].data(),
+                   D.swpost[d][l].size() * sizeof(SwPostJob));
+        }
     }
     memcpy(hb + D.prods_off, D.prods.data(), D.prods.size() * sizeof(LeafProd));
     memcpy(hb + D.tiles_off, D.tiles.data(), D.tiles.size() * sizeof(LeafTile));
@@ -910,7 +1064,7 @@ ffsyrk_status_t validate_p(uint32_t p) {
 }
 
 int64_t workspace_need(const ffsyrk_plan_st *pl, int64_t n, int64_t k, int L, int64_t *desc) {
-    Geometry g = make_geometry(n, k, L);
+    const Geometry g = plan_geometry(pl, n, k, L);
     Layout lay = make_layout(g, pl->leaf, pl->ds.D);
     *desc = desc_capacity(g, pl->leaf);
     return lay.data_bytes;
@@ -938,10 +1092,20 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
         if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
     } else {
         for (int d = 0; d < g.L; ++d) {
+            // with Algorithm 1 at this depth, the general products' operands are
+            // written as uint32 rows (d < L − 1: no leaf operands at this depth)
             e = launch_prep(reinterpret_cast<const PrepNode *>(dd + D.prep_off[d]),
-                            (int)D.prep[d].size(), g.h[d + 1], g.w[d + 1], lay.arena[d + 1].kpad,
-                            pl->mp, pl->yc, pl->ds, kind, /*reduce_input=*/true, st);
+                            (int)D.prep[d].size(), g.h[d + 1], g.w[d + 1], rup(g.w[d + 1], 64),
+                            pl->mp, pl->yc, pl->ds, g.sw[d] > 0 ? (int)ARENA_U32 : kind,
+                            /*reduce_input=*/true, st);
             if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+            for (int l = 1; l <= g.sw[d]; ++l) {
+                e = launch_sw_pre(reinterpret_cast<const SwPreJob *>(dd + D.swpre_off[d][l]),
+                                  (int)D.swpre[d][l].size(), g.h[d + 1 + l], g.w[d + 1 + l],
+                                  rup(g.w[d + 1 + l], 64), pl->mp, pl->ds,
+                                  l < g.sw[d] ? (int)ARENA_U32 : kind, st);
+                if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+            }
         }
     }
     if (timed) cudaEventRecord(pl->ev[1], st);
@@ -982,6 +1146,11 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
     if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
     if (timed) cudaEventRecord(pl->ev[2], st);
     for (int d = g.L - 1; d >= 0; --d) {
+        for (int l = g.sw[d]; l >= 1; --l) {
+            e = launch_sw_post(reinterpret_cast<const SwPostJob *>(dd + D.swpost_off[d][l]),
+                               (int)D.swpost[d][l].size(), g.h[d + 1 + l], pl->mp, st);
+            if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+        }
         bool upper = false;
         for (const PostNode &pn : D.post[d]) upper = upper || pn.upper;
         e = launch_post(reinterpret_cast<const PostNode *>(dd + D.post_off[d]),
@@ -1045,6 +1214,7 @@ void record_work(ffsyrk_plan_st *pl) {
     const Geometry &g = lay.g;
     const Descs &D = pl->desc;
     pl->last_launches = g.L == 0 ? 2 : 2 * g.L + 1;
+    for (int d = 0; d < g.L; ++d) pl->last_launches += 2 * g.sw[d];
     pl->last_leaf_launches = 1;
     int split = 0, whole = 0;
     for (const LeafPiece &q : D.pieces) {
@@ -1060,16 +1230,8 @@ void record_work(ffsyrk_plan_st *pl) {
         f += (pr.tri == 0 ? (double)pr.rows * pr.cols : (double)pr.rows * (pr.rows + 1) / 2) * K;
     }
     pl->last_tensor_macs = f * (lay.leaf == FFSYRK_LEAF_TC_BF16 ? pl->ds.D * pl->ds.D : 1);
-    // useful work counts the unpadded K of every product
-    double u = 0;
-    if (g.L == 0) {
-        u = (double)g.n * (g.n + 1) / 2 * (double)g.k;
-    } else {
-        for (int d = 0; d < g.L; ++d)
-            u += 2.0 * std::pow(3.0, d) * (double)g.h[d + 1] * g.h[d + 1] * (double)g.w[d + 1];
-        u += std::pow(3.0, g.L) * (double)g.h[g.L] * (g.h[g.L] + 1) / 2 * (double)g.w[g.L];
-    }
-    pl->last_field_macs = u;
+    // field multiply-adds of the method (padded block sizes, unpadded K at L = 0)
+    pl->last_field_macs = leaf_field_macs(g);
 }
 
 ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, const uint32_t *A,
@@ -1082,7 +1244,7 @@ ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, cons
     const int L = choose_levels(pl, n, k);
     auto key = std::make_tuple(n, k, A, lda, C, ldc, uplo, L, sc.mode, sc.alpha.w, sc.beta.w);
     if (!pl->have_last || key != pl->last_key) {
-        Geometry g = make_geometry(n, k, L);
+        const Geometry g = plan_geometry(pl, n, k, L);
         Layout lay = make_layout(g, pl->leaf, pl->ds.D);
         lay.ctas = choose_ctas(pl, g);
         if (lay.data_bytes > pl->data_cap) return FFSYRK_ERR_TOO_LARGE;
@@ -1291,6 +1453,7 @@ void ffsyrk_options_default(ffsyrk_options_t *o) {
     memset(o, 0, sizeof *o);
     o->leaf = FFSYRK_LEAF_AUTO;
     o->levels = FFSYRK_LEVELS_AUTO;
+    o->winograd = -1;
 }
 
 ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int64_t max_k,
@@ -1308,7 +1471,8 @@ ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
     if (o.levels < FFSYRK_LEVELS_AUTO || o.levels > kMaxLevels) return FFSYRK_ERR_INVALID_ARG;
     if (o.tile_ctas < 0 || o.tile_ctas > 2) return FFSYRK_ERR_INVALID_ARG;
     if (o.autotune < 0 || o.autotune > 1) return FFSYRK_ERR_INVALID_ARG;
-    for (int i = 0; i < 4; ++i)
+    if (o.winograd < -1 || o.winograd > kMaxLevels) return FFSYRK_ERR_INVALID_ARG;
+    for (int i = 0; i < 3; ++i)
         if (o.reserved[i] != 0) return FFSYRK_ERR_INVALID_ARG;
 
     int dev = 0;
@@ -1334,6 +1498,7 @@ ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
     pl->leaf = (o.leaf == FFSYRK_LEAF_AUTO) ? FFSYRK_LEAF_TC_BF16 : o.leaf;
     pl->levels_opt = o.levels;
     pl->ctas_opt = o.tile_ctas;
+    pl->sw_opt = o.winograd;
     pl->max_n = max_n;
     pl->max_k = max_k;
     pl->L_max = choose_levels(pl, max_n, max_k);
@@ -1425,9 +1590,9 @@ ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t pl, ffsyrk_plan_info_t *info)
     info->workspace_bytes = pl->ws_bytes;
     info->autotuned = pl->autotuned ? 1 : 0;
     info->tuned_ms = pl->tuned_ms;
-    info->tile_ctas = pl->leaf == FFSYRK_LEAF_TC_BF16
-                          ? choose_ctas(pl, make_geometry(pl->max_n, pl->max_k, pl->L_max))
-                          : 1;
+    const Geometry g = plan_geometry(pl, pl->max_n, pl->max_k, pl->L_max);
+    info->tile_ctas = pl->leaf == FFSYRK_LEAF_TC_BF16 ? choose_ctas(pl, g) : 1;
+    for (int d = 0; d < 6 && d < kMaxLevels; ++d) info->winograd[d] = g.sw[d];
     return FFSYRK_SUCCESS;
 }
 

@@ -232,6 +232,30 @@ int64_t digitize_flat_blocks(int64_t rows, int64_t kpad);
 cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP mp,
                         cudaStream_t st, bool upper);
 cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st);
+// One operand of a general product L·Rᵀ split by one level of Algorithm 1
+// (Winograd's variant of Strassen's product): X is 2hh × 2ww uint32
+// residues (row stride ldx, a multiple of 4); side 0 writes the left
+// operands of p1..p7, side 1 the right ones, into dst[0..6] (each hh rows).
+struct SwPreJob {
+    const uint32_t *X;
+    int64_t ldx;
+    int side;
+    OperandDst dst[7];
+};
+// The post-additions of one level of Algorithm 1: the 7 products p1..p7
+// (hh × hh, row stride hh) into C = [[c3, c7], [c4, c5]] (2hh × 2hh, row
+// stride 2hh).
+struct SwPostJob {
+    const uint32_t *P[7];
+    uint32_t *C;
+};
+// out_kind: ARENA_U32 writes uint32 rows (another level follows, or the
+// int64 leaf), otherwise the digit planes of the tensor-core leaf
+cudaError_t launch_sw_pre(const SwPreJob *jobs_dev, int njobs, int64_t hh, int64_t ww,
+                          int64_t kpad, ModP mp, DigitScheme ds, int out_kind, cudaStream_t st);
+cudaError_t launch_sw_post(const SwPostJob *jobs_dev, int njobs, int64_t hh, ModP mp,
+                           cudaStream_t st);
+
 // Constants of F_p for the scaling planner of Section 5 (from the host).
 struct ScaleConst {
     uint32_t p;

@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "ffsyrk_internal.h"
+#include "operand_digits.cuh"
 
 namespace fsk {
 namespace {
@@ -43,36 +44,6 @@ __device__ __forceinline__ uint32_t mulc(uint32_t x, MulConst c, uint32_t p) {
 
 __device__ __forceinline__ uint32_t ld_view(const MatView &v, int64_t r, int64_t c) {
     return (r < v.vr && c < v.vc) ? __ldg(v.ptr + r * v.ld + c) : 0u;
-}
-
-// Float bits of the small integer d (|d| < 2^22) without a conversion
-// instruction: 1.5·2^23 + d is exact in FP32, so subtracting 1.5·2^23 leaves
-// exactly d.  For |d| ≤ 256 the low 16 bits are zero, i.e. the high half is
-// the exact bf16 encoding of d.
-__device__ __forceinline__ uint32_t small_int_f32_bits(int d) {
-    return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f);
-}
-__device__ __forceinline__ int sbyte(int s) {
-    int d;
-    asm("bfe.s32 %0, %1, 0, 8;" : "=r"(d) : "r"(s));
-    return d;
-}
-// Low signed digit of s in the scheme's base, leaving the rest in s.  Byte
-// digits (base 256) are the low byte read as signed; for a balanced base b
-// (two digits, |s| ≤ (p−1)/2 < 2^16, |s/b| < 182) the quotient is rounded to
-// nearest: the float quotient s·(1/b) is off by less than 182·2^-23 < 2^-15,
-// far less than the distance 1/b from a tie to any other value, so
-// |digit| ≤ b/2 holds.
-__device__ __forceinline__ int low_digit(int &s, const ModP &m) {
-    if (m.dbase == 256u) {
-        const int d = sbyte(s);
-        s = (s - d) >> 8;
-        return d;
-    }
-    const int q = __float2int_rn(__int2float_rn(s) * m.dinv);
-    const int d = s - (int)m.dbase * q;
-    s = q;
-    return d;
 }
 
 template <int YF>
@@ -146,42 +117,6 @@ __device__ __forceinline__ void ld_view8(const MatView &v, bool vec_ok, int64_t 
 
 // Store four residues at (row r, columns c..c+3): one 8-byte store per digit
 // plane (bf16) or one 16-byte store (uint32).
-// Store eight residues at (row r, columns c..c+7) of an operand: one
-// 16-byte store per digit plane (bf16) or two (uint32).
-template <int D, bool U32>
-__device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, const uint32_t (&v)[8],
-                                     const ModP &m) {
-    if (d.arena == nullptr) return;
-    if constexpr (U32) {
-        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(d.arena) + (d.row0 + r) * d.kpad + c);
-        dst[0] = make_uint4(v[0], v[1], v[2], v[3]);
-        dst[1] = make_uint4(v[4], v[5], v[6], v[7]);
-    } else {
-        int sv[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) sv[e] = v[e] > m.half ? (int)v[e] - (int)m.p : (int)v[e];
-        uint32_t *base = static_cast<uint32_t *>(d.arena);
-#pragma unroll
-        for (int t = 0; t < D; ++t) {
-            uint32_t w[4];
-#pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-                int d0, d1;
-                if (t == D - 1) {
-                    d0 = sv[e];
-                    d1 = sv[e + 1];
-                } else {
-                    d0 = low_digit(sv[e], m);
-                    d1 = low_digit(sv[e + 1], m);
-                }
-                w[e / 2] = __byte_perm(small_int_f32_bits(d0), small_int_f32_bits(d1), 0x7632);
-            }
-            *reinterpret_cast<uint4 *>(base + (((d.row0 + t * d.rpad + r) * d.kpad + c) >> 1)) =
-                make_uint4(w[0], w[1], w[2], w[3]);
-        }
-    }
-}
-
 template <int D, bool U32>
 __device__ __forceinline__ void put4(const OperandDst &d, int64_t r, int64_t c, const uint32_t (&v)[4],
                                      const ModP &m) {

@@ -47,7 +47,7 @@ class FfsyrkError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("tile_ctas", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("winograd", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -56,7 +56,7 @@ class PlanInfo(ctypes.Structure):
                 ("levels", ctypes.c_int32), ("digits", ctypes.c_int32),
                 ("chunk_k", ctypes.c_int32 * 9), ("workspace_bytes", ctypes.c_int64),
                 ("tile_ctas", ctypes.c_int32), ("autotuned", ctypes.c_int32),
-                ("tuned_ms", ctypes.c_float)]
+                ("tuned_ms", ctypes.c_float), ("winograd", ctypes.c_int32 * 6)]
 
 
 class Timing(ctypes.Structure):
@@ -163,13 +163,16 @@ def _mat_args(X: torch.Tensor, name: str):
     return X.data_ptr(), ld
 
 
-def make_options(leaf=None, levels=None, tile_ctas=None, autotune=False) -> Options:
+def make_options(leaf=None, levels=None, tile_ctas=None, autotune=False,
+                 winograd=None) -> Options:
+    """Plan options; winograd: None = automatic, 0 = off, w = at most w levels of Algorithm 1."""
     o = Options()
     lib().ffsyrk_options_default(ctypes.byref(o))
     o.leaf = _LEAVES[leaf] if not isinstance(leaf, int) else leaf
     o.levels = LEVELS_AUTO if levels is None else int(levels)
     o.tile_ctas = 0 if tile_ctas is None else int(tile_ctas)
     o.autotune = 1 if autotune else 0
+    o.winograd = -1 if winograd is None else int(winograd)
     return o
 
 
@@ -177,10 +180,10 @@ class Plan:
     """An ffsyrk plan: p, Y, digits, depth and workspace for n ≤ max_n, k ≤ max_k."""
 
     def __init__(self, p: int, max_n: int, max_k: int, leaf=None, levels=None, tile_ctas=None,
-                 autotune=False):
+                 autotune=False, winograd=None):
         self.p = int(p)
         self._h = ctypes.c_void_p()
-        o = make_options(leaf, levels, tile_ctas, autotune)
+        o = make_options(leaf, levels, tile_ctas, autotune, winograd)
         _check(lib().ffsyrk_plan(ctypes.byref(self._h), self.p, int(max_n), int(max_k),
                                  ctypes.byref(o)), "ffsyrk_plan")
 
@@ -190,7 +193,8 @@ class Plan:
         return {"p": i.p, "y_form": i.y_form, "y_a": i.y_a, "y_b": i.y_b, "y_cost": i.y_cost,
                 "leaf": i.leaf, "levels": i.levels, "digits": i.digits,
                 "chunk_k": list(i.chunk_k), "workspace_bytes": i.workspace_bytes,
-                "tile_ctas": i.tile_ctas, "autotuned": i.autotuned, "tuned_ms": i.tuned_ms}
+                "tile_ctas": i.tile_ctas, "autotuned": i.autotuned, "tuned_ms": i.tuned_ms,
+                "winograd": list(i.winograd)}
 
     def __call__(self, A: torch.Tensor, C: torch.Tensor | None = None, uplo: str = "lower",
                  stream=None, alpha: int = 1, beta: int = 0) -> torch.Tensor:

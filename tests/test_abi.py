@@ -59,12 +59,15 @@ def test_bad_arguments_rejected(lib):
     assert lib.ffsyrk_plan(None, 65521, 4, 4, None) == ffsyrk.ERR_INVALID_ARG
     o = ffsyrk.Options()
     lib.ffsyrk_options_default(ctypes.byref(o))
-    assert o.leaf == ffsyrk.LEAF_AUTO and o.levels == ffsyrk.LEVELS_AUTO
+    assert o.leaf == ffsyrk.LEAF_AUTO and o.levels == ffsyrk.LEVELS_AUTO and o.winograd == -1
     o.levels = 99
     h = ctypes.c_void_p()
     assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
     o.levels = 1
     o.reserved[2] = 5
+    assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
+    o.reserved[2] = 0
+    o.winograd = -2
     assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
     # batched argument checks happen before any device call
     I64 = ctypes.c_int64 * 1
