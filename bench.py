@@ -288,7 +288,8 @@ def run_ours(args):
     C = torch.zeros((n, n), dtype=torch.int32, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
-    plan = ffsyrk.Plan(p, n, k, leaf=args.leaf, levels=levels, tile_ctas=args.tile_ctas)
+    plan = ffsyrk.Plan(p, n, k, leaf=args.leaf, levels=levels, tile_ctas=args.tile_ctas,
+                       winograd=args.winograd)
     info = plan.info()
     sampler = ClockSampler(local)
     if ws > 1:
@@ -351,7 +352,8 @@ def run_ours(args):
         C_pins = [torch.empty((n, n), dtype=torch.int32).pin_memory() for _ in range(2)]
         A_devs = [torch.empty_like(A) for _ in range(2)]
         C_devs = [torch.zeros_like(C) for _ in range(2)]
-        plans = [ffsyrk.Plan(p, n, k, leaf=args.leaf, levels=levels, tile_ctas=args.tile_ctas)
+        plans = [ffsyrk.Plan(p, n, k, leaf=args.leaf, levels=levels, tile_ctas=args.tile_ctas,
+                             winograd=args.winograd)
                  for _ in range(2)]
         s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
         s_cmp = stream
@@ -395,11 +397,16 @@ def run_ours(args):
     # comparators: classical SYRK from the same leaves; the int64 CUDA-core leaf
     compare = {}
     if not args.no_compare:
-        for name, leaf, lv in [("classical_tc", "tc", 0), ("fast_i64", "i64", levels),
-                               ("classical_i64", "i64", 0)]:
+        legs = [("classical_tc", "tc", 0, None), ("fast_i64", "i64", levels, None),
+                ("classical_i64", "i64", 0, None)]
+        if any(info["winograd"]):
+            # the same depth with the general products computed classically
+            legs.append(("fast_tc_no_winograd", "tc", info["levels"], 0))
+        for name, leaf, lv, wg in legs:
             if name.endswith("i64") and n * n * k > 2 ** 40:
                 continue
-            pl = ffsyrk.Plan(p, n, k, leaf=leaf, levels=lv)
+            pl = ffsyrk.Plan(p, n, k, leaf=leaf, levels=lv, winograd=wg,
+                             tile_ctas=args.tile_ctas if wg == 0 else None)
             st = max(2, min(args.steps, 5))
             cms, cstage = time_plan(pl, A, C, st, 2, flush, stream)
             cm = sum(cms) / len(cms)
@@ -419,6 +426,7 @@ def run_ours(args):
                 "dtype": "u32", "data": "synthetic",
                 "config": {"workload": args.workload, "description": desc, "n": n, "k": k,
                            "p": p, "levels": info["levels"], "digits": info["digits"],
+                           "winograd": info["winograd"][: info["levels"]],
                            "leaf": {1: "tc_bf16", 2: "i64"}[info["leaf"]],
                            "tile_ctas": info["tile_ctas"],
                            "y_form": "scalar" if info["y_form"] == 0 else "2x2",
@@ -605,6 +613,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--levels", type=int, default=None)
+    ap.add_argument("--winograd", type=int, default=None,
+                    help="levels of Algorithm 1 for the general products (default: cost model)")
     ap.add_argument("--leaf", choices=["tc", "i64"], default="tc")
     ap.add_argument("--tile-ctas", type=int, choices=[0, 1, 2], default=0,
                     help="tensor-core leaf tiles: 0 auto, 1 one SM, 2 SM pairs")
