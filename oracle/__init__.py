@@ -16,6 +16,8 @@ Contents
   (the product Algorithm 5, syrkd, computes; Section 5), in ``syrk_oracle.c``.
 * :func:`syrkbd` -- the plain definition of A·B·Aᵀ mod p for a symmetric
   tridiagonal B, which holds Algorithm 6's block-diagonal B (Section 5).
+* :func:`herk` -- the plain definition of A·Aᴴ over F_{p²} = F_p[i]/(i² − r)
+  (Section 3.2, conjugate transposition), in ``syrk_oracle.c``.
 * :mod:`oracle.field` -- primality, Legendre symbols, square roots and the
   skew-orthogonal Y of Section 3.1 (Prop. 3.2, Prop. 3.3, Algorithm 3).
 * :mod:`oracle.alg2` -- Algorithm 2 itself written step by step over F_p in
@@ -67,6 +69,8 @@ def _load():
         lib.oracle_syrkbd_modp.argtypes = [i64, i64, u32, p, i64, p, p, p, i64, ctypes.c_int,
                                            ctypes.c_int]
         lib.oracle_syrkbd_modp.restype = ctypes.c_int
+        lib.oracle_herk_modp.argtypes = [i64, i64, u32, u32, p, i64, p, p, i64, ctypes.c_int]
+        lib.oracle_herk_modp.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -174,6 +178,26 @@ def syrkbd(A, d, e, p: int, uplo: str = "lower", threads: int | None = None) -> 
     if rc != 0:
         raise ValueError("oracle_syrkbd_modp rejected its arguments")
     return C
+
+
+def herk(A, p: int, r: int, uplo: str = "lower") -> tuple[np.ndarray, np.ndarray]:
+    """A·Aᴴ over F_{p²} = F_p[i]/(i² − r) by definition; A interleaved (n × 2k: Re, Im, ...).
+
+    Returns (Re C, Im C) as n×n uint32 arrays, the triangle ``uplo`` written
+    ("full": every entry, each computed on its own), the rest 0.
+    """
+    A = _as_u32(A)
+    n, k2 = A.shape
+    if k2 % 2:
+        raise ValueError("A must hold (Re, Im) pairs: an even number of columns")
+    Cre = np.zeros((n, n), dtype=np.uint32)
+    Cim = np.zeros((n, n), dtype=np.uint32)
+    code = {"lower": 0, "upper": 1, "full": 2}[uplo]
+    rc = _load().oracle_herk_modp(n, k2 // 2, p, r, A.ctypes.data, max(k2, 1), Cre.ctypes.data,
+                                  Cim.ctypes.data, max(n, 1), code)
+    if rc != 0:
+        raise ValueError("oracle_herk_modp rejected its arguments")
+    return Cre, Cim
 
 
 def syrk_rows(A, p: int, rows, threads: int | None = None) -> np.ndarray:

@@ -256,3 +256,39 @@ int oracle_syrkbd_modp(int64_t n, int64_t k, uint32_t p, const uint32_t *A, int6
     j.ldc = ldc;
     return run(j, nthreads);
 }
+
+/*
+ * Hermitian product over F_{p²} = F_p[i]/(i² − r), r a non-square mod p
+ * (Section 3.2, "Conjugate transpose"): C = A·Aᴴ, C[j][l] = Σ_t A[j][t]·conj(A[l][t])
+ * with conj(x + y·i) = x − y·i (the Frobenius map x ↦ x^p).  Written out:
+ * (a + b·i)(c − d·i) = (ac − r·bd) + (bc − ad)·i.  A is interleaved: row j
+ * holds Re A[j][0], Im A[j][0], Re A[j][1], ... (2k uint32, stride lda);
+ * entries may be any uint32 (reduced mod p first).  Re C and Im C go to
+ * Cre and Cim (stride ldc) on the triangle uplo (0 lower, 1 upper, 2 all).
+ * Every term is reduced before it is added, so nothing can overflow.
+ * Single-threaded (small cases only).  Returns 0, or -1 on bad arguments.
+ */
+int oracle_herk_modp(int64_t n, int64_t k, uint32_t p, uint32_t r, const uint32_t *A, int64_t lda,
+                     uint32_t *Cre, uint32_t *Cim, int64_t ldc, int uplo) {
+    if (n < 0 || k < 0 || p < 3 || lda < (2 * k > 1 ? 2 * k : 1) || ldc < (n > 1 ? n : 1)) return -1;
+    if (uplo < 0 || uplo > 2) return -1;
+    const uint64_t P = p, R = r % p;
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t l0 = 0, l1 = n;
+        if (uplo == 0) l1 = j + 1;
+        if (uplo == 1) l0 = j;
+        for (int64_t l = l0; l < l1; ++l) {
+            uint64_t re = 0, im = 0;
+            for (int64_t t = 0; t < k; ++t) {
+                const uint64_t a = A[j * lda + 2 * t] % P, b = A[j * lda + 2 * t + 1] % P;
+                const uint64_t c = A[l * lda + 2 * t] % P, d = A[l * lda + 2 * t + 1] % P;
+                const uint64_t bd = b * d % P;
+                re = (re + a * c % P + (P - R * bd % P)) % P;
+                im = (im + b * c % P + (P - a * d % P)) % P;
+            }
+            Cre[j * ldc + l] = (uint32_t)re;
+            Cim[j * ldc + l] = (uint32_t)im;
+        }
+    }
+    return 0;
+}
