@@ -217,6 +217,45 @@ int32_t ffsyrkbd_factor(uint32_t p, int64_t k, const uint32_t *d, const uint32_t
 int32_t ffsyrkbd_factor_device(uint32_t p, int64_t k, const uint32_t *d, const uint32_t *e,
                                int32_t *src, uint32_t *w);
 
+/* ---- Hermitian product over F_{p²} (Section 3.2, "Conjugate transpose") ----
+ *
+ * C = A·Aᴴ for A ∈ F_{p²}^{n×k}, F_{p²} = F_p[i]/(i² − r) with r a non-square
+ * mod p, conjugation x + y·i ↦ x − y·i (the Frobenius map).  A is stored
+ * interleaved as an n × 2k uint32 matrix Z (row j: Re A[j][0], Im A[j][0],
+ * Re A[j][1], …; row stride lda ≥ 2k, entries any uint32, reduced mod p).
+ * The result goes to two n × n uint32 matrices (row stride ldc), the
+ * triangle `uplo` of Re C (symmetric) and of Im C (antisymmetric, zero
+ * diagonal); the other strict triangles are not touched.
+ *
+ * The paper runs Algorithm 2 over F_{p²} with a Y satisfying Y·Yᴴ = −I.
+ * This library computes the same C through products over F_p:
+ * Re C = Z·Diag(1, −r, 1, −r, …)·Zᵀ (Algorithm 2 on Z, plain when r = −1,
+ * otherwise through the diagonal scaling of Algorithm 5) and
+ * Im C = Z·(Z·Jᵀ)ᵀ with J = I ⊗ [[0, −1], [1, 0]], one triangular general
+ * product on the classical leaf (its operand Z·Jᵀ is digit-split directly
+ * from Z).  A plan holds one plan of each kind. */
+typedef struct ffherk_plan_st *ffherk_plan_t;
+
+/* A plan for n ≤ max_n, k ≤ max_k (k counts F_{p²} columns).  r must be a
+ * non-square mod p (FFSYRK_ERR_INVALID_ARG otherwise), e.g. p − 1 when
+ * p ≡ 3 (mod 4).  opts applies to the real part's plan (levels, leaf,
+ * tile widths, Winograd); the imaginary part always runs at depth 0. */
+ffsyrk_status_t ffherk_plan(ffherk_plan_t *plan, uint32_t p, uint32_t r, int64_t max_n,
+                            int64_t max_k, const ffsyrk_options_t *opts);
+ffsyrk_status_t ffherk_plan_destroy(ffherk_plan_t plan);
+/* Re C and Im C (triangle uplo) on `stream`; asynchronous like
+ * ffsyrk_with_plan.  Cre and Cim must not overlap each other or A. */
+ffsyrk_status_t ffherk_with_plan(ffherk_plan_t plan, ffsyrk_uplo_t uplo, int64_t n, int64_t k,
+                                 const uint32_t *A, int64_t lda, uint32_t *Cre, uint32_t *Cim,
+                                 int64_t ldc, ffsyrk_stream_t stream);
+/* ffsyrk_sync_status for both of the plan's parts. */
+ffsyrk_status_t ffherk_sync_status(ffherk_plan_t plan, ffsyrk_stream_t stream);
+/* The same through an internal cache of plans keyed by (device, p, r, n, k).
+ * Thread-safe. */
+ffsyrk_status_t ffherk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p, uint32_t r,
+                       const uint32_t *A, int64_t lda, uint32_t *Cre, uint32_t *Cim, int64_t ldc,
+                       ffsyrk_stream_t stream);
+
 /* `count` independent products C_t = A_t·A_tᵀ mod p of uneven sizes n[t] × k[t],
  * all with the same p and uplo.  n, k, lda, ldc are HOST arrays of `count`
  * values; A and C are HOST arrays of `count` DEVICE pointers.  Problems with

@@ -98,6 +98,9 @@ struct Geometry {
     int64_t h[kMaxLevels + 1] = {}, w[kMaxLevels + 1] = {};
     // levels of Algorithm 1 (Winograd) for the general products of depth d
     int sw[kMaxLevels] = {};
+    // L = 0 only: lower(X·Yᵀ) with Y = X·Jᵀ (the imaginary part of a
+    // Hermitian product, Section 3.2): two operands in the arena
+    bool gemmt = false;
 };
 
 Geometry make_geometry(int64_t n, int64_t k, int L) {
@@ -195,7 +198,7 @@ int64_t syrk_base(const Geometry &g) {
     return b;
 }
 int64_t arena_nops(const Geometry &g, int j) {
-    if (g.L == 0) return 1;
+    if (g.L == 0) return g.gemmt ? 2 : 1;
     int64_t n = 0;
     for (int d = 0; d < g.L; ++d)
         if (gen_arena(g, d) == j) n += gen_ops(g, d);
@@ -316,7 +319,7 @@ int64_t desc_capacity(const Geometry &g, int leaf) {
     // tail split: items ≤ tiles + 2 CTAs' shares, entries ≤ tiles + CTAs + 1, counters
     b += (ntiles + 2 * kMaxCtas) * (int64_t)(sizeof(LeafTile) + sizeof(LeafPiece)) +
          (ntiles + kMaxCtas + 2) * 4 + 2 * kMaxCtas * 32 + 4 * 256;
-    b += (kMaxLevels + 1) * (128 + 16) + 10 * 256 + sizeof(DigitizeJob);
+    b += (kMaxLevels + 1) * (128 + 16) + 10 * 256 + 2 * sizeof(DigitizeJob);
     // segment tables: at most L + 1 distinct K per call, ≤ 40 segments per 16 k-blocks
     b += (int64_t)(g.L + 1) * ((g.kp / 64 + 16) / 16 + 1) * 40 * (int64_t)sizeof(LeafSeg);
     return rup(b, kAlign);
@@ -589,6 +592,7 @@ struct ffsyrk_plan_st {
     int levels_opt = FFSYRK_LEVELS_AUTO;
     int ctas_opt = 0;
     int sw_opt = -1;  // levels of Algorithm 1: −1 automatic, else the cap
+    bool gemmt = false;  // the imaginary-part plan of a Hermitian product (L = 0)
     int64_t max_n = 0, max_k = 0;
     int L_max = 0;  // levels used at the max shape
     // device workspace: data region then descriptor region
@@ -637,6 +641,7 @@ struct ffsyrk_plan_st {
 Geometry plan_geometry(const ffsyrk_plan_st *pl, int64_t n, int64_t k, int L) {
     Geometry g = make_geometry(n, k, L);
     set_winograd(g, pl->sw_opt, pl->ds.D);
+    g.gemmt = pl->gemmt && L == 0;
     return g;
 }
 
@@ -836,7 +841,9 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         LeafProd pr{};
         pr.arena = 0;
         pr.tri = uplo == FFSYRK_UPPER ? 2 : 1;
+        const Arena &a0 = lay.arena[0];
         pr.a_row0 = pr.b_row0 = 0;
+        if (g.gemmt) pr.b_row0 = a0.planes * a0.rpad;  // the second operand, A·Jᵀ
         pr.rows = pr.cols = g.n;
         pr.kblocks = (int32_t)(lay.arena[0].kpad / 64);
         pr.plane_rows = lay.arena[0].rpad;
@@ -845,9 +852,11 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         pr.ldo = ldc;
         D.prods.push_back(pr);
         tri_tiles(D.tiles, 0, g.n, g.n, pr.tri, TM, TN, pr.kblocks * cost_mult);
-        const Arena &a0 = lay.arena[0];
         D.digit.push_back(DigitizeJob{MatView{A, lda, g.n, g.k}, g.n,
                                       OperandDst{a0.base, 0, a0.kpad, a0.rpad}});
+        if (g.gemmt)
+            D.digit.push_back(DigitizeJob{MatView{A, lda, g.n, g.k}, g.n,
+                                          OperandDst{a0.base, pr.b_row0, a0.kpad, a0.rpad}, 0, 1});
         D.digit_max_rows = g.n;
         D.digit_max_kpad = a0.kpad;
     } else {
@@ -1087,8 +1096,9 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
     if (tc1 && cudaMemsetAsync(dd + D.ctr_off, 0, (size_t)D.ctr_bytes, st) != cudaSuccess)
         return FFSYRK_ERR_CUDA;
     if (g.L == 0) {
-        e = launch_digitize(reinterpret_cast<const DigitizeJob *>(dd + D.digit_off), 1,
-                            D.digit_max_rows, D.digit_max_kpad, pl->mp, pl->ds, kind, st);
+        e = launch_digitize(reinterpret_cast<const DigitizeJob *>(dd + D.digit_off),
+                            (int)D.digit.size(), D.digit_max_rows, D.digit_max_kpad, pl->mp,
+                            pl->ds, kind, st);
         if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
     } else {
         for (int d = 0; d < g.L; ++d) {
@@ -1241,7 +1251,7 @@ ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, cons
     if (n == 0) return FFSYRK_SUCCESS;
     if (k == 0)  // A·Aᵀ = 0: C ← β·C, or 0
         return cuda_status(launch_scale_tri(C, n, ldc, uplo == FFSYRK_UPPER, sc, pl->p, st));
-    const int L = choose_levels(pl, n, k);
+    const int L = pl->gemmt ? 0 : choose_levels(pl, n, k);
     auto key = std::make_tuple(n, k, A, lda, C, ldc, uplo, L, sc.mode, sc.alpha.w, sc.beta.w);
     if (!pl->have_last || key != pl->last_key) {
         const Geometry g = plan_geometry(pl, n, k, L);
@@ -1456,8 +1466,19 @@ void ffsyrk_options_default(ffsyrk_options_t *o) {
     o->winograd = -1;
 }
 
+namespace {
+ffsyrk_status_t plan_create(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int64_t max_k,
+                            const ffsyrk_options_t *opts, bool gemmt);
+}  // namespace
+
 ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int64_t max_k,
                             const ffsyrk_options_t *opts) {
+    return plan_create(plan, p, max_n, max_k, opts, false);
+}
+
+namespace {
+ffsyrk_status_t plan_create(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int64_t max_k,
+                            const ffsyrk_options_t *opts, bool gemmt) {
     if (!plan) return FFSYRK_ERR_INVALID_ARG;
     *plan = nullptr;
     ffsyrk_status_t s = validate_p(p);
@@ -1496,7 +1517,8 @@ ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
     pl->ds = make_digits(p);
     pl->mp = make_modp(p, pl->ds);
     pl->leaf = (o.leaf == FFSYRK_LEAF_AUTO) ? FFSYRK_LEAF_TC_BF16 : o.leaf;
-    pl->levels_opt = o.levels;
+    pl->gemmt = gemmt;
+    pl->levels_opt = gemmt ? 0 : o.levels;
     pl->ctas_opt = o.tile_ctas;
     pl->sw_opt = o.winograd;
     pl->max_n = max_n;
@@ -1504,7 +1526,7 @@ ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
     pl->L_max = choose_levels(pl, max_n, max_k);
 
     const bool tuning = o.autotune != 0 && o.levels == FFSYRK_LEVELS_AUTO && o.tile_ctas == 0 &&
-                        max_n > 0 && max_k > 0;
+                        max_n > 0 && max_k > 0 && !gemmt;
     // capacity: the largest layout over the depths this plan may use
     int64_t data = 0, desc = 0;
     {
@@ -1568,6 +1590,7 @@ ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
     *plan = pl;
     return FFSYRK_SUCCESS;
 }
+}  // namespace
 
 ffsyrk_status_t ffsyrk_plan_destroy(ffsyrk_plan_t plan) {
     destroy_plan(plan);
@@ -2045,6 +2068,129 @@ extern "C" ffsyrk_status_t ffsyrkbd_update(ffsyrk_uplo_t uplo, int64_t n, int64_
     s = cached_plan(p, n, k + 1, &pl);
     if (s != FFSYRK_SUCCESS) return s;
     return ffsyrkbd_with_plan_update(pl, uplo, n, k, p, alpha, A, lda, d, e, beta, C, ldc, stream);
+}
+
+// ---- Hermitian product over F_{p²} (Section 3.2) ----
+struct ffherk_plan_st {
+    ffsyrk_plan_t re = nullptr;  // Re C = Z·Diag(1, −r, …)·Zᵀ
+    ffsyrk_plan_t im = nullptr;  // Im C = lower(Z·(Z·Jᵀ)ᵀ), depth 0
+    uint32_t p = 0, r = 0;
+    int64_t max_n = 0, max_k = 0;
+    std::vector<uint32_t> d;  // (1, −r, 1, −r, …)
+};
+
+extern "C" ffsyrk_status_t ffherk_plan_destroy(ffherk_plan_t hp) {
+    if (!hp) return FFSYRK_SUCCESS;
+    if (hp->re) ffsyrk_plan_destroy(hp->re);
+    if (hp->im) ffsyrk_plan_destroy(hp->im);
+    delete hp;
+    return FFSYRK_SUCCESS;
+}
+
+extern "C" ffsyrk_status_t ffherk_plan(ffherk_plan_t *plan, uint32_t p, uint32_t r, int64_t max_n,
+                                       int64_t max_k, const ffsyrk_options_t *opts) {
+    if (!plan) return FFSYRK_ERR_INVALID_ARG;
+    *plan = nullptr;
+    ffsyrk_status_t s = validate_p(p);
+    if (s != FFSYRK_SUCCESS) return s;
+    if (max_n < 0 || max_k < 0 || max_k > (int64_t(1) << 22)) return FFSYRK_ERR_INVALID_ARG;
+    const uint64_t rr = r % p;
+    if (rr == 0 || host::euler(rr, p) != p - 1) return FFSYRK_ERR_INVALID_ARG;
+    ffherk_plan_st *hp = new (std::nothrow) ffherk_plan_st();
+    if (!hp) return FFSYRK_ERR_ALLOC;
+    hp->p = p;
+    hp->r = (uint32_t)rr;
+    hp->max_n = max_n;
+    hp->max_k = max_k;
+    // the real part may need one added column (Algorithm 5, odd count of non-squares)
+    s = plan_create(&hp->re, p, max_n, 2 * max_k + 1, opts, false);
+    if (s == FFSYRK_SUCCESS) {
+        ffsyrk_options_t o;
+        ffsyrk_options_default(&o);
+        if (opts) {
+            o.leaf = opts->leaf;
+            o.tile_ctas = opts->tile_ctas;
+        }
+        s = plan_create(&hp->im, p, max_n, 2 * max_k, &o, true);
+    }
+    if (s != FFSYRK_SUCCESS) {
+        ffherk_plan_destroy(hp);
+        return s;
+    }
+    *plan = hp;
+    return FFSYRK_SUCCESS;
+}
+
+extern "C" ffsyrk_status_t ffherk_with_plan(ffherk_plan_t hp, ffsyrk_uplo_t uplo, int64_t n,
+                                            int64_t k, const uint32_t *A, int64_t lda,
+                                            uint32_t *Cre, uint32_t *Cim, int64_t ldc,
+                                            ffsyrk_stream_t stream) {
+    if (!hp || (uplo != FFSYRK_LOWER && uplo != FFSYRK_UPPER)) return FFSYRK_ERR_INVALID_ARG;
+    if (n < 0 || k < 0 || lda < std::max<int64_t>(1, 2 * k) || ldc < std::max<int64_t>(1, n))
+        return FFSYRK_ERR_INVALID_ARG;
+    if (n > hp->max_n || k > hp->max_k) return FFSYRK_ERR_TOO_LARGE;
+    if (n == 0) return FFSYRK_SUCCESS;
+    if (!Cre || !Cim || Cre == Cim || (k > 0 && !A)) return FFSYRK_ERR_INVALID_ARG;
+    const uint32_t p = hp->p;
+    ffsyrk_status_t s;
+    if (hp->r == p - 1 || k == 0) {
+        // i² = −1: Re C = Z·Zᵀ
+        s = ffsyrk_with_plan(hp->re, uplo, n, 2 * k, p, A, lda, Cre, ldc, stream);
+    } else {
+        if ((int64_t)hp->d.size() < 2 * k) {
+            hp->d.resize((size_t)(2 * k));
+            for (int64_t t = 0; t < k; ++t) {
+                hp->d[(size_t)(2 * t)] = 1;
+                hp->d[(size_t)(2 * t + 1)] = p - hp->r;
+            }
+        }
+        s = ffsyrkd_with_plan_update(hp->re, uplo, n, 2 * k, p, 1u, A, lda, hp->d.data(), 0u, Cre,
+                                     ldc, stream);
+    }
+    if (s != FFSYRK_SUCCESS) return s;
+    return ffsyrk_with_plan(hp->im, uplo, n, 2 * k, p, A, lda, Cim, ldc, stream);
+}
+
+extern "C" ffsyrk_status_t ffherk_sync_status(ffherk_plan_t hp, ffsyrk_stream_t stream) {
+    if (!hp) return FFSYRK_ERR_INVALID_ARG;
+    const ffsyrk_status_t a = ffsyrk_sync_status(hp->re, stream);
+    const ffsyrk_status_t b = ffsyrk_sync_status(hp->im, stream);
+    return a != FFSYRK_SUCCESS ? a : b;
+}
+
+namespace {
+std::mutex g_herk_mu;
+std::map<std::tuple<int, uint32_t, uint32_t, int64_t, int64_t>, std::pair<ffherk_plan_t, uint64_t>>
+    g_herk_cache;
+uint64_t g_herk_clock = 0;
+}  // namespace
+
+extern "C" ffsyrk_status_t ffherk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p, uint32_t r,
+                                  const uint32_t *A, int64_t lda, uint32_t *Cre, uint32_t *Cim,
+                                  int64_t ldc, ffsyrk_stream_t stream) {
+    ffsyrk_status_t s = validate_p(p);
+    if (s != FFSYRK_SUCCESS) return s;
+    if (n < 0 || k < 0) return FFSYRK_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFSYRK_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_herk_mu);
+    auto key = std::make_tuple(dev, p, r % p, n, k);
+    auto it = g_herk_cache.find(key);
+    if (it == g_herk_cache.end()) {
+        if (g_herk_cache.size() >= 4) {
+            auto victim = g_herk_cache.begin();
+            for (auto jt = g_herk_cache.begin(); jt != g_herk_cache.end(); ++jt)
+                if (jt->second.second < victim->second.second) victim = jt;
+            ffherk_plan_destroy(victim->second.first);
+            g_herk_cache.erase(victim);
+        }
+        ffherk_plan_t hp = nullptr;
+        s = ffherk_plan(&hp, p, r, n, k, nullptr);
+        if (s != FFSYRK_SUCCESS) return s;
+        it = g_herk_cache.emplace(key, std::make_pair(hp, uint64_t(0))).first;
+    }
+    it->second.second = ++g_herk_clock;
+    return ffherk_with_plan(it->second.first, uplo, n, k, A, lda, Cre, Cim, ldc, stream);
 }
 
 // ---- batched: many independent problems in one grouped launch ----

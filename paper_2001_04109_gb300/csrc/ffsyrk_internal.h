@@ -143,6 +143,10 @@ struct DigitizeJob {
     int64_t rows;
     OperandDst dst;
     int64_t block0;  // first block of this job in a flattened launch (prefix sum)
+    // 1: split X·Jᵀ instead of X, J = I ⊗ [[0, −1], [1, 0]]: each column
+    // pair (x, y) becomes (−y, x) (the conjugation step of the Hermitian
+    // product over F_p[i], Section 3.2)
+    int conj;
 };
 
 // One post-addition node: combines the five products into the node result.

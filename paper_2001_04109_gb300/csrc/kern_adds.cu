@@ -267,6 +267,15 @@ __global__ void __launch_bounds__(DIG_THREADS) k_digitize(const DigitizeJob *__r
             if (r >= jb.rows) break;
 #pragma unroll
             for (int e = 0; e < 8; ++e) v[i][e] = red(v[i][e], m);
+            if (jb.conj) {
+                // c is a multiple of 8: the column pairs (2t, 2t+1) stay together
+#pragma unroll
+                for (int e = 0; e < 8; e += 2) {
+                    const uint32_t x = v[i][e], y = v[i][e + 1];
+                    v[i][e] = y ? m.p - y : 0u;
+                    v[i][e + 1] = x;
+                }
+            }
             put8<D, U32>(jb.dst, r, c, v[i], m);
         }
     }

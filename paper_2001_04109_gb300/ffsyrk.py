@@ -35,7 +35,8 @@ EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsy
            "ffsyrk_digit_base", "ffsyrk_plan_selftest_timeout", "ffsyrk_with_plan_update",
            "ffsyrk_update", "ffsyrkd_with_plan_update", "ffsyrkd_update", "ffsyrkd_factor",
            "ffsyrkbd_with_plan_update", "ffsyrkbd_update", "ffsyrkbd_factor",
-           "ffsyrkbd_factor_device"]
+           "ffsyrkbd_factor_device", "ffherk_plan", "ffherk_plan_destroy", "ffherk_with_plan",
+           "ffherk_sync_status", "ffherk"]
 
 
 class FfsyrkError(RuntimeError):
@@ -105,6 +106,14 @@ def lib() -> ctypes.CDLL:
             L.ffsyrkbd_factor.restype = i32
             L.ffsyrkbd_factor_device.argtypes = [u32, i64, P(u32), P(u32), P(i32), P(u32)]
             L.ffsyrkbd_factor_device.restype = i32
+            L.ffherk_plan.argtypes = [P(vp), u32, u32, i64, i64, P(Options)]
+            L.ffherk_plan_destroy.argtypes = [vp]
+            L.ffherk_with_plan.argtypes = [vp, i32, i64, i64, vp, i64, vp, vp, i64, vp]
+            L.ffherk_sync_status.argtypes = [vp, vp]
+            L.ffherk.argtypes = [i32, i64, i64, u32, u32, vp, i64, vp, vp, i64, vp]
+            for name in ["ffherk_plan", "ffherk_plan_destroy", "ffherk_with_plan",
+                         "ffherk_sync_status", "ffherk"]:
+                getattr(L, name).restype = i32
             L.ffsyrk_noalloc.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk_batched.argtypes = [i32, i64, P(i64), P(i64), u32, P(vp), P(i64), P(vp),
                                          P(i64), vp]
@@ -270,6 +279,75 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class HerkPlan:
+    """A plan for C = A·Aᴴ over F_{p²} = F_p[i]/(i² − r) (r a non-square mod p).
+
+    A is an n × 2k int32/uint32 tensor of interleaved (Re, Im) residues; the
+    result is the triangle ``uplo`` of Re C and Im C in two n × n tensors.
+    """
+
+    def __init__(self, p: int, r: int, max_n: int, max_k: int, leaf=None, levels=None,
+                 tile_ctas=None, winograd=None):
+        self.p, self.r = int(p), int(r)
+        self._h = ctypes.c_void_p()
+        o = make_options(leaf, levels, tile_ctas, False, winograd)
+        _check(lib().ffherk_plan(ctypes.byref(self._h), self.p, self.r & 0xFFFFFFFF, int(max_n),
+                                 int(max_k), ctypes.byref(o)), "ffherk_plan")
+
+    def __call__(self, A: torch.Tensor, Cre: torch.Tensor | None = None,
+                 Cim: torch.Tensor | None = None, uplo: str = "lower", stream=None):
+        n, k2 = A.shape
+        if k2 % 2:
+            raise ValueError("A must hold (Re, Im) pairs: an even number of columns")
+        if Cre is None:
+            Cre = torch.zeros((n, n), dtype=torch.int32, device=A.device)
+        if Cim is None:
+            Cim = torch.zeros((n, n), dtype=torch.int32, device=A.device)
+        pa, lda = _mat_args(A, "A")
+        pr, ldr = _mat_args(Cre, "Cre")
+        pi, ldi = _mat_args(Cim, "Cim")
+        if ldr != ldi:
+            raise ValueError("Cre and Cim must have the same row stride")
+        _check(lib().ffherk_with_plan(self._h, UPPER if uplo == "upper" else LOWER, n, k2 // 2,
+                                      pa, lda, pr, pi, ldr, _stream_handle(stream)),
+               "ffherk_with_plan")
+        return Cre, Cim
+
+    def sync_status(self, stream=None) -> None:
+        _check(lib().ffherk_sync_status(self._h, _stream_handle(stream)), "ffherk_sync_status")
+
+    def close(self) -> None:
+        if self._h:
+            lib().ffherk_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def herk(A: torch.Tensor, p: int, r: int, uplo: str = "lower", Cre: torch.Tensor | None = None,
+         Cim: torch.Tensor | None = None, stream=None):
+    """(Re C, Im C) of C = A·Aᴴ over F_p[i]/(i² − r) through the plan cache (A interleaved)."""
+    n, k2 = A.shape
+    if k2 % 2:
+        raise ValueError("A must hold (Re, Im) pairs: an even number of columns")
+    if Cre is None:
+        Cre = torch.zeros((n, n), dtype=torch.int32, device=A.device)
+    if Cim is None:
+        Cim = torch.zeros((n, n), dtype=torch.int32, device=A.device)
+    pa, lda = _mat_args(A, "A")
+    pr, ldr = _mat_args(Cre, "Cre")
+    pi, ldi = _mat_args(Cim, "Cim")
+    if ldr != ldi:
+        raise ValueError("Cre and Cim must have the same row stride")
+    _check(lib().ffherk(UPPER if uplo == "upper" else LOWER, n, k2 // 2, int(p),
+                        int(r) & 0xFFFFFFFF, pa, lda, pr, pi, ldr, _stream_handle(stream)), "ffherk")
+    return Cre, Cim
 
 
 def leaf_schedule(p: int, kblocks: int) -> list[tuple[int, int, int, int, bool]]:

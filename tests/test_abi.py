@@ -23,7 +23,7 @@ def lib():
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "ffsyrk.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(ffsyrk\w*)\s*\(", text)))
+    return sorted(set(re.findall(r"\b((?:ffsyrk|ffherk)\w*)\s*\(", text)))
 
 
 def test_exports_every_declared_symbol(lib):
