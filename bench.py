@@ -441,6 +441,93 @@ def run_ours(args):
     return 0
 
 
+OPS = {
+    "update": "C ← α·A·Aᵀ + β·C mod p (Section 4.2, Table 4)",
+    "syrkd": "C = A·Diag(d)·Aᵀ mod p, d uniform in [1, p) (Algorithm 5)",
+    "syrkbd": "C = A·B·Aᵀ mod p, B block diagonal: a 2×2 block on every third column pair (Algorithm 6)",
+    "herk": "C = A·Aᴴ over F_p[i]/(i² − r), A read as n × k/2 interleaved (Re, Im) pairs (Section 3.2)",
+}
+
+
+def run_op(args):
+    """One of the operations beyond the plain product on the workload's A, timed like it.
+
+    The value is n²k / t with k the uint32 columns of A (for the Hermitian
+    product: k/2 columns over F_{p²}); the plain product of the same A on its
+    own plan is timed beside it.  Parity of these operations is checked by the
+    GPU tests, not here.
+    """
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from paper_2001_04109_gb300 import ffsyrk, inputs
+
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    n, k, p, desc = WORKLOADS[args.workload]
+    stream = torch.cuda.current_stream()
+    A = inputs.uniform_residues(n, k, p, seed=2).cuda()
+    C = inputs.uniform_residues(n, n, p, seed=3).cuda()
+    C2 = torch.zeros_like(C)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(7)
+    d = rng.integers(1, p, size=k).astype(np.uint32)
+    e = np.zeros(max(k - 1, 0), dtype=np.uint32)
+    e[0::6] = rng.integers(1, p, size=e[0::6].shape[0])
+    kw = dict(leaf=args.leaf, levels=args.levels, tile_ctas=args.tile_ctas, winograd=args.winograd)
+    if args.op == "herk":
+        r = p - 1 if p % 4 == 3 else next(x for x in range(2, p) if pow(x, (p - 1) // 2, p) == p - 1)
+        plan = ffsyrk.HerkPlan(p, r, n, k // 2, **kw)
+        call = lambda: plan(A[:, : 2 * (k // 2)], C, C2, stream=stream)
+        extra = {"r": r}
+    else:
+        plan = ffsyrk.Plan(p, n, k + 1, **kw)
+        extra = {}
+        if args.op == "update":
+            call = lambda: plan(A, C, stream=stream, alpha=31337, beta=4242)
+            extra = {"alpha": 31337, "beta": 4242}
+        elif args.op == "syrkd":
+            call = lambda: plan.syrkd(A, d, C, stream=stream)
+        else:
+            call = lambda: plan.syrkbd(A, d, e, C, stream=stream)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for s_ in range(steps):
+            flush.zero_()
+            ev[s_][0].record(stream)
+            fn()
+            ev[s_][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    ms = timed(call, args.steps, args.warmup)
+    clocks = sampler.stop()
+    plan.sync_status()
+    base = ffsyrk.Plan(p, n, k, **kw)
+    base_ms = timed(lambda: base(A, C2, stream=stream), args.steps, args.warmup)
+    info = base.info()
+    base.close()
+    plan.close()
+    step_ms = statistics.median(ms)
+    line = {"metric": f"{args.op}: effective ops/s (n²k/t) on 1 GB300", "value": n * n * k / (step_ms * 1e-3),
+            "unit": "ops/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_ms, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.workload, "op": args.op, "description": OPS[args.op],
+                       "n": n, "k": k, "p": p, "levels": info["levels"],
+                       "winograd": info["winograd"][: info["levels"]],
+                       "l2": "flushed between steps (512 MiB write)", **extra},
+            "plain_product_ms": statistics.median(base_ms), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def batch_problem(t, shapes, p, device):
     from paper_2001_04109_gb300 import inputs
     n, k = shapes[t]
@@ -624,6 +711,8 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--ref-budget", type=float, default=6.0)
+    ap.add_argument("--op", choices=["syrk"] + sorted(OPS), default="syrk",
+                    help="time another operation on the workload's A instead of the plain product")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
@@ -632,6 +721,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.op != "syrk":
+        return run_op(args)
     return run_ours(args)
 
 

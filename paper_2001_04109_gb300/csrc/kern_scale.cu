@@ -289,9 +289,11 @@ __global__ void __launch_bounds__(128) k_scale_pairs(int64_t k, int64_t kk, Scal
 }
 
 // Ā = A·W: column c of Ā is Σ_t w_{c,t}·A_{src_{c,t}} over at most four
-// columns of A (src −1: unused, else < k), A's entries reduced mod p.  One
-// thread per column of a 256-column block, each looping over many rows
-// (grid y strides the rows), so W's column is loaded once per thread.
+// columns of A (the used terms first, src −1 after them), with A's entries
+// any uint32: Shoup's product x·w mod p needs no reduction of x < 2^32.  One
+// thread per column of a 256-column block, each looping over many rows (grid
+// y strides the rows, four rows per step with their loads issued first), so
+// W's column is loaded once per thread and only its used terms are computed.
 __global__ void __launch_bounds__(256) k_col_mix(const uint32_t *__restrict__ A, int64_t lda,
                                                  int64_t n, int64_t kk,
                                                  const int4 *__restrict__ src,
@@ -303,35 +305,30 @@ __global__ void __launch_bounds__(256) k_col_mix(const uint32_t *__restrict__ A,
     const uint4 w01 = w[2 * c], w23 = w[2 * c + 1];
     const int sc[4] = {s4.x, s4.y, s4.z, s4.w};
     const MulConst wc[4] = {{w01.x, w01.y}, {w01.z, w01.w}, {w23.x, w23.y}, {w23.z, w23.w}};
-    // four rows per step, their (up to 16) loads issued before any use
+    const int nt = (sc[0] >= 0) + (sc[1] >= 0) + (sc[2] >= 0) + (sc[3] >= 0);
+    const uint32_t p = m.p;
     const int64_t gy = gridDim.y;
     for (int64_t r0 = blockIdx.y; r0 < n; r0 += 4 * gy) {
-        uint32_t x[4][4];
+        uint32_t y[4] = {0u, 0u, 0u, 0u};
+        for (int t = 0; t < nt; ++t) {
+            uint32_t x[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int64_t r = r0 + q * gy;
+            for (int q = 0; q < 4; ++q) {
+                const int64_t r = r0 + q * gy;
+                x[q] = r < n ? __ldg(A + r * lda + sc[t]) : 0u;
+            }
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
-                x[q][t] = (r < n && sc[t] >= 0) ? __ldg(A + r * lda + sc[t]) : 0u;
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t qq = __umulhi(x[q], wc[t].w_sh);
+                uint32_t v = x[q] * wc[t].w - qq * p;  // in [0, 2p)
+                v = v >= p ? v - p : v;
+                y[q] = fadd(y[q], v, p);
+            }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int64_t r = r0 + q * gy;
-            if (r >= n) break;
-            uint32_t y = 0;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                // x mod p for x < 2^32 (Barrett on 32 bits), then x·w (Shoup);
-                // an unused term has w = 0 and adds 0
-                const uint32_t xv = x[q][t];
-                uint32_t xr = xv - __umulhi(xv, m.barrett) * m.p;
-                xr = xr >= m.p ? xr - m.p : xr;
-                const uint32_t qq = __umulhi(xr, wc[t].w_sh);
-                uint32_t v = xr * wc[t].w - qq * m.p;
-                v = v >= m.p ? v - m.p : v;
-                y = fadd(y, v, m.p);
-            }
-            B[r * ldb + c] = y;
+            if (r < n) B[r * ldb + c] = y[q];
         }
     }
 }
