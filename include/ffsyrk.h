@@ -122,6 +122,22 @@ ffsyrk_status_t ffsyrk_with_plan(ffsyrk_plan_t plan, ffsyrk_uplo_t uplo, int64_t
                                  uint32_t p, const uint32_t *A, int64_t lda, uint32_t *C,
                                  int64_t ldc, ffsyrk_stream_t stream);
 
+/* C = A·Aᵀ mod p for HOST matrices, with a plan: A (n × k, row stride lda)
+ * is copied to device memory the plan owns (allocated on the first such call,
+ * max_n × max_k and max_n × max_n uint32), the product runs there, and the
+ * whole n × n result comes back to the host matrix C (row stride ldc): the
+ * triangle `uplo` of A·Aᵀ mod p and zeros in the other strict triangle (one
+ * contiguous copy when ldc = n: full-rate transfers, unlike copies of a
+ * triangle's shorter rows).  Everything is enqueued on `stream`: the call
+ * returns before the copies finish, and the host buffers must stay valid
+ * until the stream has drained them (pinned host memory lets the copies
+ * overlap other work; pageable memory works but copies synchronously).
+ * Calls on one plan reuse its device buffers, so a pipeline of calls uses one
+ * plan per call in flight. */
+ffsyrk_status_t ffsyrk_host(ffsyrk_plan_t plan, ffsyrk_uplo_t uplo, int64_t n, int64_t k,
+                            uint32_t p, const uint32_t *A, int64_t lda, uint32_t *C, int64_t ldc,
+                            ffsyrk_stream_t stream);
+
 /* C = A·Aᵀ mod p with default options, through an internal per-device plan
  * cache keyed by (p, shape).  Thread-safe. */
 ffsyrk_status_t ffsyrk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p, const uint32_t *A,

@@ -618,6 +618,10 @@ struct ffsyrk_plan_st {
     ScaleConst sconst{};
     uint32_t *dbar = nullptr;
     int64_t dbar_bytes = 0;
+    // host-buffer entry point: device copies of A and C (made on first use)
+    uint32_t *host_a = nullptr, *host_c = nullptr;
+    int64_t host_lda = 0, host_n = -1;
+    int host_uplo = -1;
     char *dtab = nullptr;
     int64_t dtab_bytes = 0;
     // optional per-stage timing
@@ -1298,6 +1302,8 @@ void destroy_plan(ffsyrk_plan_st *pl) {
     if (pl->part) cudaFree(pl->part);
     if (pl->dbar) cudaFree(pl->dbar);
     if (pl->dtab) cudaFree(pl->dtab);
+    if (pl->host_a) cudaFree(pl->host_a);
+    if (pl->host_c) cudaFree(pl->host_c);
     drop_graph(pl);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     if (pl->desc_done) cudaEventDestroy(pl->desc_done);
@@ -1623,6 +1629,57 @@ ffsyrk_status_t ffsyrk_with_plan(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n
                                  uint32_t p, const uint32_t *A, int64_t lda, uint32_t *C,
                                  int64_t ldc, ffsyrk_stream_t stream) {
     return ffsyrk_with_plan_update(pl, uplo, n, k, p, 1u, A, lda, 0u, C, ldc, stream);
+}
+
+ffsyrk_status_t ffsyrk_host(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p,
+                            const uint32_t *A, int64_t lda, uint32_t *C, int64_t ldc,
+                            ffsyrk_stream_t stream) {
+    if (!pl || p != pl->p || (uplo != FFSYRK_LOWER && uplo != FFSYRK_UPPER)) return FFSYRK_ERR_INVALID_ARG;
+    if (n < 0 || k < 0 || lda < std::max<int64_t>(1, k) || ldc < std::max<int64_t>(1, n))
+        return FFSYRK_ERR_INVALID_ARG;
+    if (n > pl->max_n || k > pl->max_k) return FFSYRK_ERR_TOO_LARGE;
+    if (n == 0) return FFSYRK_SUCCESS;
+    if (!C || (k > 0 && !A)) return FFSYRK_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!pl->host_a) {
+        // rows of A on 16-byte boundaries; C square
+        const int64_t la = rup(std::max<int64_t>(pl->max_k, 1), 4);
+        cudaStreamSynchronize(st);
+        if (cudaMalloc(&pl->host_a, (size_t)(std::max<int64_t>(pl->max_n, 1) * la * 4)) != cudaSuccess ||
+            cudaMalloc(&pl->host_c, (size_t)(std::max<int64_t>(pl->max_n, 1) * std::max<int64_t>(pl->max_n, 1) * 4)) != cudaSuccess) {
+            cudaGetLastError();
+            if (pl->host_a) cudaFree(pl->host_a);
+            pl->host_a = nullptr;
+            return FFSYRK_ERR_ALLOC;
+        }
+        pl->host_lda = la;
+    }
+    const int64_t la = pl->host_lda, lc = n;
+    // the device C keeps zeros outside the triangle written for (n, uplo)
+    if (pl->host_n != n || pl->host_uplo != (int)uplo) {
+        if (cudaMemsetAsync(pl->host_c, 0, (size_t)(n * n * 4), st) != cudaSuccess)
+            return FFSYRK_ERR_CUDA;
+        pl->host_n = n;
+        pl->host_uplo = (int)uplo;
+    }
+    if (k > 0) {
+        const cudaError_t e =
+            (lda == k && la == k)
+                ? cudaMemcpyAsync(pl->host_a, A, (size_t)(n * k * 4), cudaMemcpyHostToDevice, st)
+                : cudaMemcpy2DAsync(pl->host_a, (size_t)la * 4, A, (size_t)lda * 4, (size_t)k * 4,
+                                    (size_t)n, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+    }
+    ffsyrk_status_t s = ffsyrk_with_plan(pl, uplo, n, k, p, pl->host_a, la, pl->host_c, lc, stream);
+    if (s != FFSYRK_SUCCESS) return s;
+    // the whole n × n result in one copy: contiguous transfers run at the
+    // link's full rate, unlike a triangle's worth of shorter rows
+    const cudaError_t e =
+        ldc == n ? cudaMemcpyAsync(C, pl->host_c, (size_t)(n * n * 4), cudaMemcpyDeviceToHost, st)
+                 : cudaMemcpy2DAsync(C, (size_t)ldc * 4, pl->host_c, (size_t)lc * 4, (size_t)n * 4,
+                                     (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+    return FFSYRK_SUCCESS;
 }
 
 ffsyrk_status_t ffsyrk_with_plan_update(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n, int64_t k,

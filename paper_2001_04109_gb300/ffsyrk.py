@@ -36,7 +36,7 @@ EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsy
            "ffsyrk_update", "ffsyrkd_with_plan_update", "ffsyrkd_update", "ffsyrkd_factor",
            "ffsyrkbd_with_plan_update", "ffsyrkbd_update", "ffsyrkbd_factor",
            "ffsyrkbd_factor_device", "ffherk_plan", "ffherk_plan_destroy", "ffherk_with_plan",
-           "ffherk_sync_status", "ffherk"]
+           "ffherk_sync_status", "ffherk", "ffsyrk_host"]
 
 
 class FfsyrkError(RuntimeError):
@@ -111,8 +111,10 @@ def lib() -> ctypes.CDLL:
             L.ffherk_with_plan.argtypes = [vp, i32, i64, i64, vp, i64, vp, vp, i64, vp]
             L.ffherk_sync_status.argtypes = [vp, vp]
             L.ffherk.argtypes = [i32, i64, i64, u32, u32, vp, i64, vp, vp, i64, vp]
+            L.ffsyrk_host.argtypes = [vp, i32, i64, i64, u32, vp, i64, vp, i64, vp]
+            L.ffsyrk_host.restype = i32
             for name in ["ffherk_plan", "ffherk_plan_destroy", "ffherk_with_plan",
-                         "ffherk_sync_status", "ffherk"]:
+                         "ffherk_sync_status", "ffherk", "ffsyrk_host"]:
                 getattr(L, name).restype = i32
             L.ffsyrk_noalloc.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk_batched.argtypes = [i32, i64, P(i64), P(i64), u32, P(vp), P(i64), P(vp),
@@ -221,6 +223,18 @@ class Plan:
             _check(lib().ffsyrk_with_plan_update(self._h, u, n, k, self.p, int(alpha) & 0xFFFFFFFF,
                                                  pa, lda, int(beta) & 0xFFFFFFFF, pc, ldc,
                                                  _stream_handle(stream)), "ffsyrk_with_plan_update")
+        return C
+
+    def host(self, A: torch.Tensor, C: torch.Tensor, uplo: str = "lower", stream=None) -> torch.Tensor:
+        """C = A·Aᵀ mod p for CPU tensors A (n × k) and C (n × n): copies in, computes, copies the
+        triangle back, all enqueued on ``stream`` (pin both tensors for asynchronous copies)."""
+        if A.is_cuda or C.is_cuda:
+            raise ValueError("host() takes CPU tensors")
+        n, k = A.shape
+        pa, lda = _mat_args(A, "A")
+        pc, ldc = _mat_args(C, "C")
+        _check(lib().ffsyrk_host(self._h, UPPER if uplo == "upper" else LOWER, n, k, self.p, pa,
+                                 lda, pc, ldc, _stream_handle(stream)), "ffsyrk_host")
         return C
 
     def syrkd(self, A: torch.Tensor, d, C: torch.Tensor | None = None, uplo: str = "lower",
