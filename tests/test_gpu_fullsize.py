@@ -5,7 +5,9 @@ Every workload the benchmark times, at its full size, with the same inputs
 sampled output rows -- first and last rows, tile boundaries, rows of every
 tile band, near-diagonal entries -- against the oracle computed row by row.
 The classical path (depth 0) is checked next to the fast one where the
-benchmark compares them.  The batch of 2048 uneven problems is checked on a
+benchmark compares them.  Every full-size result is also checked whole by
+Freivalds' test, C·x ≡ A·(Aᵀ·x) mod p for two random x, in exact integer
+arithmetic that shares nothing with the library.  The batch of 2048 uneven problems is checked on a
 seeded sample of whole problems.
 """
 import numpy as np
@@ -30,6 +32,36 @@ def sample_rows(n, count, seed):
     rows = set(r for r in fixed if 0 <= r < n)
     rows.update(int(r) for r in rng.integers(0, n, size=count))
     return np.array(sorted(rows), dtype=np.int64)
+
+
+def freivalds(A_host, p, C_dev, seed, vectors=2):
+    """C·x ≡ A·(Aᵀ·x) mod p for random x, C the full symmetric matrix of the lower triangle.
+
+    Exact in uint64 (residues < 2^24, sums of ≤ 2^15 products < 2^61, in row
+    chunks); a wrong entry anywhere in the triangle escapes one vector with
+    probability at most 1/p.  Independent of the library and of the oracle.
+    """
+    A = A_host.numpy().view(np.uint32).astype(np.uint64) % np.uint64(p)
+    n, k = A.shape
+    P = np.uint64(p)
+    C = C_dev.cpu().numpy().view(np.uint32)
+    rng = np.random.default_rng(seed)
+    chunk = 2048
+    for _ in range(vectors):
+        x = rng.integers(0, p, size=n, dtype=np.uint64)
+        # A·(Aᵀ·x), with k and n ≤ 2^15 terms per sum
+        atx = np.zeros(k, dtype=np.uint64)
+        for r0 in range(0, n, chunk):
+            atx = (atx + (A[r0:r0 + chunk].T @ x[r0:r0 + chunk]) % P) % P
+        want = (A @ atx) % P
+        # tril(C)·x + tril(C, −1)ᵀ·x
+        got = np.zeros(n, dtype=np.uint64)
+        for r0 in range(0, n, chunk):
+            L = np.tril(C[r0:r0 + chunk].astype(np.uint64), k=r0)          # rows r0.., lower part
+            got[r0:r0 + chunk] = (got[r0:r0 + chunk] + (L @ x) % P) % P
+            S = np.tril(C[r0:r0 + chunk].astype(np.uint64), k=r0 - 1)      # strict lower part
+            got = (got + (S.T @ x[r0:r0 + chunk]) % P) % P
+        assert np.array_equal(got, want), "Freivalds check failed: some entry of C is wrong"
 
 
 def check_rows(A_host, p, C_dev, rows):
@@ -63,6 +95,7 @@ def test_workload_sampled_rows(n, k, p, depths):
         plan(A, C)
         plan.sync_status()
         check_rows(A_host, p, C, rows)
+        freivalds(A_host, p, C, seed=n + k + (levels or 0))
         plan.close()
         del C
     torch.cuda.empty_cache()
@@ -78,7 +111,8 @@ def test_large_d3_three_levels_sampled_rows():
     plan = ffsyrk.Plan(p, n, k, levels=3)
     plan(A, C)
     plan.sync_status()
-    check_rows(A_host, p, C, sample_rows(n, 6, seed=7))
+    check_rows(A_host, p, C, sample_rows(n, 48, seed=7))
+    freivalds(A_host, p, C, seed=32768)
     plan.close()
     del A, C
     torch.cuda.empty_cache()
