@@ -808,6 +808,101 @@ void split_tail(Descs &D, int S, int slot_cap) {
     D.nslots = slots;
 }
 
+// Balance the tail of the SM-pair leaf (stream-K style).  With T tiles on P
+// pairs the plain round-robin takes ceil(T/P) tile times.  When the last wave
+// is at most 45 % full, the tiles of the last two waves are cut at unit
+// boundaries into P shares of equal estimated time, one contiguous share per
+// pair after its whole round-robin tiles, so the launch takes about T/P tile
+// times.  Shares follow the tile order, so the tiles that run at the same
+// time stay within about 1.5 waves of each other (their operand panels
+// shared in L2).  A tile cut into several pieces is finished by whichever
+// piece completes last (each SM of the pair publishes its 128-row half; see
+// LeafPiece).  Per pair the work list is entries[pair] .. entries[pair+1].
+// Measured on GB300 (p = 65521, K = n, leaf ms): 3072² 0.145 → 0.107,
+// 3584² 0.170 → 0.150, 4608² 0.309 → 0.258.  With a fuller last wave the
+// extra work of the cut tiles costs more than the idle SMs it fills: every
+// SM is then busy and the leaf is bound by L2 bandwidth (4096², 1.79 waves:
+// 0.186 → 0.193; 5120²: 0.338 → 0.344; 4096 × 16384 with the whole launch
+// cut: 0.668 → 0.790).
+void split_pairs(Descs &D, int P, int slot_cap) {
+    D.pieces.clear();
+    D.entries.clear();
+    D.nslots = 0;
+    const int T = (int)D.tiles.size();
+    if (P < 2 || T <= P) return;
+    const double waves = (double)T / P;
+    const double fill = waves - std::floor(waves);
+    if (fill == 0.0 || fill > 0.45) return;
+    const int DP = ((T / P) - 1) * P;  // whole tiles, round-robin
+    struct Unit {
+        int tile, sx0, sx1;
+        double cost;
+    };
+    std::vector<Unit> units;
+    double total = 0;
+    for (int i = DP; i < T; ++i) {
+        const LeafProd &pr = D.prods[D.tiles[i].prod];
+        int start = 0;
+        double c = 0;
+        for (int sx = 0; sx <= pr.nseg; ++sx) {
+            const bool boundary = sx == pr.nseg || (sx > start && D.segs[pr.seg0 + sx].first);
+            if (boundary && sx > start) {
+                units.push_back(Unit{i, start, sx, c + kUnitCost});
+                total += c + kUnitCost;
+                start = sx;
+                c = 0;
+            }
+            if (sx < pr.nseg) c += D.segs[pr.seg0 + sx].nkb;
+        }
+    }
+    if ((int)units.size() < P) return;
+    const double target = total / P;
+    struct Piece {
+        int share, tile, sx0, sx1;
+    };
+    std::vector<Piece> ps;
+    double cum = 0;
+    for (const Unit &u : units) {
+        const int sh = std::min(P - 1, (int)((cum + u.cost / 2) / target));
+        cum += u.cost;
+        if (!ps.empty() && ps.back().share == sh && ps.back().tile == u.tile)
+            ps.back().sx1 = u.sx1;
+        else
+            ps.push_back(Piece{sh, u.tile, u.sx0, u.sx1});
+    }
+    std::vector<int> npieces(T, 0);
+    for (const Piece &q : ps) ++npieces[q.tile];
+    int slots = 0;  // pieces of tiles that are cut
+    for (int i = DP; i < T; ++i)
+        if (npieces[i] > 1) slots += npieces[i];
+    if (2 * slots > slot_cap) return;  // two halves per piece
+    std::vector<int> slot0(T, -1), seen(T, 0);
+    for (int i = DP, next = 0; i < T; ++i)
+        if (npieces[i] > 1) {
+            slot0[i] = next;
+            next += npieces[i];
+        }
+    std::vector<std::vector<Piece>> by_share(P);
+    for (const Piece &q : ps) by_share[q.share].push_back(q);
+    std::vector<LeafTile> items;
+    for (int pr_ = 0; pr_ < P; ++pr_) {
+        D.entries.push_back((int32_t)items.size());
+        for (int i = pr_; i < DP; i += P) {
+            items.push_back(D.tiles[i]);
+            D.pieces.push_back(LeafPiece{0, D.prods[D.tiles[i].prod].nseg, -1, 0, 1});
+        }
+        for (const Piece &q : by_share[pr_]) {
+            items.push_back(D.tiles[q.tile]);
+            D.pieces.push_back(LeafPiece{q.sx0, q.sx1, slot0[q.tile],
+                                         (int16_t)(slot0[q.tile] >= 0 ? seen[q.tile]++ : 0),
+                                         (int16_t)npieces[q.tile]});
+        }
+    }
+    D.entries.push_back((int32_t)items.size());
+    D.tiles.swap(items);
+    D.nslots = 2 * slots;
+}
+
 // Build every descriptor of one call into pl->desc and the staging blob.
 ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int64_t lda,
                             uint32_t *C, int64_t ldc) {
@@ -1011,6 +1106,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     std::stable_sort(D.tiles.begin(), D.tiles.end(),
                      [](const LeafTile &a, const LeafTile &b) { return a.cost > b.cost; });
     if (tc && !pair) split_tail(D, pl->sms, pl->part_slots);
+    if (pair) split_pairs(D, pl->sms / 2, pl->part_slots);
     D.ctr_bytes = 16 + (int64_t)D.nslots * 8 * 4;
 
     // pack the blob
@@ -1097,7 +1193,9 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
     // the leaf launch directly follows the grid that writes its operands
     // (programmatic dependent launch)
     const bool tc1 = lay.leaf == FFSYRK_LEAF_TC_BF16 && lay.ctas != 2;
-    if (tc1 && cudaMemsetAsync(dd + D.ctr_off, 0, (size_t)D.ctr_bytes, st) != cudaSuccess)
+    const bool tc2_split = lay.leaf == FFSYRK_LEAF_TC_BF16 && lay.ctas == 2 && !D.entries.empty();
+    if ((tc1 || tc2_split) &&
+        cudaMemsetAsync(dd + D.ctr_off, 0, (size_t)D.ctr_bytes, st) != cudaSuccess)
         return FFSYRK_ERR_CUDA;
     if (g.L == 0) {
         e = launch_digitize(reinterpret_cast<const DigitizeJob *>(dd + D.digit_off),
@@ -1139,6 +1237,13 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
         tl.tile_ctr = reinterpret_cast<unsigned int *>(dd + D.ctr_off);
         if (lay.ctas == 2) {
             tl.tile_ctr = nullptr;
+            if (!D.entries.empty()) {
+                tl.pieces = reinterpret_cast<const LeafPiece *>(dd + D.pieces_off);
+                tl.entries = reinterpret_cast<const int32_t *>(dd + D.entries_off);
+                tl.nentries = (int)D.entries.size() - 1;  // pairs
+                tl.part = pl->part;
+                tl.part_ctr = reinterpret_cast<unsigned int *>(dd + D.ctr_off + 16);
+            }
             e = launch_leaf_tc2(tl, pl->sms, st);
         } else {
             if (!D.entries.empty()) {

@@ -98,7 +98,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     k_leaf_tc2(const LeafProd *__restrict__ prods, const LeafTile *__restrict__ tiles,
                const LeafSeg *__restrict__ segs, int ntiles, const CUtensorMap *__restrict__ tmaps,
                ModP m,
-               const __grid_constant__ DigitScheme ds, unsigned int *err) {
+               const __grid_constant__ DigitScheme ds, unsigned int *err,
+               const LeafPiece *__restrict__ pieces, const int32_t *__restrict__ entries,
+               uint32_t *part, unsigned int *part_ctr) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
     __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], drain_bar;
@@ -110,6 +112,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
     const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+    // this pair's items: its own list (tiles and pieces of tiles, K range
+    // [sx0, sx1) of the schedule), or every npairs-th tile
+    const int q0 = entries ? entries[pair] : pair;
+    const int q1 = entries ? entries[pair + 1] : ntiles;
+    const int qstep = entries ? 1 : npairs;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -145,13 +152,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
             asm volatile("griddepcontrol.wait;" ::: "memory");
             uint32_t it = 0;
             bool ok = true;
-            for (int t = pair; t < ntiles && ok; t += npairs) {
+            for (int t = q0; t < q1 && ok; t += qstep) {
                 const LeafTile tl = tiles[t];
                 const LeafProd pr = prods[tl.prod];
+                const int sx0 = pieces ? pieces[t].sx0 : 0, sx1 = pieces ? pieces[t].sx1 : pr.nseg;
                 const CUtensorMap *tm = tmaps + pr.arena;
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tm)
                              : "memory");
-                for (int sx = 0; sx < pr.nseg && ok; ++sx) {
+                for (int sx = sx0; sx < sx1 && ok; ++sx) {
                     const LeafSeg sg = segs[pr.seg0 + sx];
                     const int ya = (int)(pr.a_row0 + (int64_t)(sg.ij >> 4) * pr.plane_rows +
                                          (int64_t)tl.tm * BM + rank * ROWS);
@@ -183,11 +191,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
         if (lane == 0 && rank == 0) {
             uint32_t it = 0, unit = 0;
             bool ok = true;
-            for (int t = pair; t < ntiles && ok; t += npairs) {
+            for (int t = q0; t < q1 && ok; t += qstep) {
                 const LeafProd pr = prods[tiles[t].prod];
+                const int sx0 = pieces ? pieces[t].sx0 : 0, sx1 = pieces ? pieces[t].sx1 : pr.nseg;
                 bool open = false;  // a unit's accumulator is being filled
                 uint32_t b = 0, tmem_d = 0;
-                for (int sx = 0; sx < pr.nseg; ++sx) {
+                for (int sx = sx0; sx < sx1; ++sx) {
                     const LeafSeg sg = segs[pr.seg0 + sx];
                     if (sg.first) {
                         if (open) {
@@ -237,16 +246,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
                                          mapa_rank(su32(&acce_bar[1]), 0)};
         uint32_t unit = 0;
         bool ok = true;
-        for (int t = pair; t < ntiles && ok; t += npairs) {
+        for (int t = q0; t < q1 && ok; t += qstep) {
             const LeafTile tl = tiles[t];
             const LeafProd pr = prods[tl.prod];
+            const int sx0 = pieces ? pieces[t].sx0 : 0, sx1 = pieces ? pieces[t].sx1 : pr.nseg;
             uint32_t acc[EPI_COLS];
 #pragma unroll
             for (int e = 0; e < EPI_COLS; ++e) acc[e] = 0;
             int lo = 0, hi = 0;  // 16-column chunks of this warp that hold stored entries
             live_chunks(pr, (int64_t)tl.tm * BM + rank * ROWS + quad * 32, (int64_t)tl.tn * BN + colq * EPI_COLS,
                         EPI_COLS / LD_COLS, lo, hi);
-            for (int sx = 0; sx < pr.nseg; ++sx) {
+            for (int sx = sx0; sx < sx1; ++sx) {
                 const LeafSeg sg = segs[pr.seg0 + sx];
                 if (!sg.first) continue;  // one drain per unit
                 const uint32_t b = unit & 1u;
@@ -290,6 +300,50 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
                 for (int e = 0; e < EPI_COLS; ++e) acc[e] = reduce_2p(acc[e], p, m.barrett);
             }
+            const LeafPiece pc = pieces ? pieces[t] : LeafPiece{0, 0, -1, 0, 1};
+            if (pc.slot0 >= 0) {
+                // a piece of a shared tile: this CTA publishes the residues of
+                // its 128 rows; per warp and CTA rank, the piece that finishes
+                // last adds the others' and stores (no waiting on other pairs)
+                uint32_t *mine = part + ((int64_t)(2 * (pc.slot0 + pc.j) + rank) * (ROWS * BN)) +
+                                 threadIdx.x * EPI_COLS;
+#pragma unroll
+                for (int e = 0; e < EPI_COLS; e += 4) {
+                    uint4 v4;
+                    v4.x = acc[e] >= p ? acc[e] - p : acc[e];
+                    v4.y = acc[e + 1] >= p ? acc[e + 1] - p : acc[e + 1];
+                    v4.z = acc[e + 2] >= p ? acc[e + 2] - p : acc[e + 2];
+                    v4.w = acc[e + 3] >= p ? acc[e + 3] - p : acc[e + 3];
+                    *reinterpret_cast<uint4 *>(mine + e) = v4;
+                }
+                __threadfence();
+                __syncwarp();
+                unsigned int *ctr = &part_ctr[(2 * pc.slot0 + rank) * EPI_WARPS + warp];
+                unsigned int prev = 0;
+                if (lane == 0) prev = atomicAdd(ctr, 1u);
+                prev = __shfl_sync(0xffffffffu, prev, 0);
+                if (prev != (unsigned)(pc.npieces - 1)) continue;
+                __threadfence();
+#pragma unroll 1
+                for (int q = 0; q < pc.npieces; ++q) {
+                    if (q == pc.j) continue;
+                    const uint32_t *other = part +
+                                            ((int64_t)(2 * (pc.slot0 + q) + rank) * (ROWS * BN)) +
+                                            threadIdx.x * EPI_COLS;
+#pragma unroll
+                    for (int e = 0; e < EPI_COLS; e += 4) {
+                        const uint4 o = __ldcg(reinterpret_cast<const uint4 *>(other + e));
+                        // acc < 2p and o < p: one conditional subtract keeps it below 2p
+                        const uint32_t s0 = acc[e] + o.x, s1 = acc[e + 1] + o.y,
+                                       s2 = acc[e + 2] + o.z, s3 = acc[e + 3] + o.w;
+                        acc[e] = min(s0, s0 - twop);
+                        acc[e + 1] = min(s1, s1 - twop);
+                        acc[e + 2] = min(s2, s2 - twop);
+                        acc[e + 3] = min(s3, s3 - twop);
+                    }
+                }
+                if (lane == 0) *ctr = 0;  // ready for the next launch
+            }
             store_tile_row<EPI_COLS, SCALED>(pr, (int64_t)tl.tm * BM + rank * ROWS + quad * 32 + lane,
                                      (int64_t)tl.tn * BN + colq * EPI_COLS, acc, p);
         }
@@ -330,7 +384,8 @@ cudaError_t launch_leaf_tc2(const TcLaunch &L, int num_sms, cudaStream_t st) {
         }
         max_pairs = clusters;
     }
-    const int pairs = L.ntiles < max_pairs ? L.ntiles : max_pairs;
+    // with per-pair work lists the grid has exactly one pair per list
+    const int pairs = L.entries ? L.nentries : (L.ntiles < max_pairs ? L.ntiles : max_pairs);
     const bool lazy = L.max_units <= L.ds.lazy_units;
     auto kern = L.scaled ? (lazy ? k_leaf_tc2<true, true> : k_leaf_tc2<false, true>)
                          : (lazy ? k_leaf_tc2<true, false> : k_leaf_tc2<false, false>);
@@ -346,7 +401,8 @@ cudaError_t launch_leaf_tc2(const TcLaunch &L, int num_sms, cudaStream_t st) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, L.prods, L.tiles, L.segs, L.ntiles,
-                              reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp, L.ds, L.err);
+                              reinterpret_cast<const CUtensorMap *>(L.tmaps), L.mp, L.ds, L.err,
+                              L.pieces, L.entries, L.part, L.part_ctr);
 }
 
 }  // namespace fsk

@@ -13,7 +13,8 @@ import numpy as np
 import pytest
 import torch
 
-from paper_2001_04109_gb300 import ffsyrk
+import oracle
+from paper_2001_04109_gb300 import ffsyrk, inputs
 from parity_util import SENTINEL, check_against_oracle, residues
 
 pytestmark = pytest.mark.gpu
@@ -74,3 +75,38 @@ def test_no_split_for_short_tiles():
     outs, t = run_timed(A, p, 0, "lower", calls=1)
     assert t["split_tiles"] == 0, t
     check_against_oracle(A, p, outs[0])
+
+
+@pytest.mark.parametrize("n,cut", [(2560, False), (3072, True), (3584, True), (4096, False),
+                                   (4608, True)])
+def test_pair_tiles_balanced_last_waves(n, cut):
+    # SM-pair tiles: the lower 256×256 tiles of n² leave a last wave on the
+    # 76 pairs that is 3 % (3072: 78 tiles), 38 % (3584) or 25 % (4608) full,
+    # so the last two waves are cut into equal shares; 2560 (55 tiles) and
+    # 4096 (1.79 waves) stay whole.  The result stays exact, also for the update.
+    p = 65521
+    k = 1100
+    A = inputs.uniform_residues(n, k, p, seed=n)
+    plan = ffsyrk.Plan(p, n, k, leaf="tc", levels=0, tile_ctas=2)
+    C = torch.zeros((n, n), dtype=torch.int32, device="cuda")
+    plan.set_timing(True)
+    plan(A.cuda(), C)
+    plan.sync_status()
+    assert (plan.timing()["split_tiles"] > 0) == cut, plan.timing()
+    plan.set_timing(False)
+    rows = np.array(sorted({0, 1, 255, 256, 511, n // 2, n - 257, n - 256, n - 1} |
+                           set(np.random.default_rng(n).integers(0, n, 24).tolist())), dtype=np.int64)
+    want = oracle.syrk_rows(A.numpy(), p, rows)
+    got = C[torch.from_numpy(rows).cuda()].cpu().numpy().view(np.uint32)
+    for t, r in enumerate(rows):
+        assert np.array_equal(got[t, : r + 1], want[t, : r + 1]), f"row {r}"
+    C0 = inputs.uniform_residues(n, n, p, seed=1).cuda()
+    C1 = C0.clone()
+    plan(A.cuda(), C1, alpha=5, beta=7)
+    plan.sync_status()
+    old = C0.cpu().numpy().view(np.uint32)[rows].astype(np.uint64)
+    got = C1[torch.from_numpy(rows).cuda()].cpu().numpy().view(np.uint32)
+    w2 = (5 * want.astype(np.uint64) + 7 * old) % p
+    for t, r in enumerate(rows):
+        assert np.array_equal(got[t, : r + 1], w2[t, : r + 1].astype(np.uint32)), f"update row {r}"
+    plan.close()
