@@ -282,8 +282,12 @@ __global__ void __launch_bounds__(DIG_THREADS) k_digitize(const DigitizeJob *__r
 }
 
 // The same digit split over a flattened block list: block b belongs to the
-// job t with block0[t] ≤ b < block0[t+1] (binary search), then to one row
-// block and one column block of that job.
+// job t with block0[t] ≤ b < block0[t+1] (binary search), then to a band of
+// rows of that job.  A job of width kpad has kpad/8 threads per row; when
+// that is fewer than the block's threads, one block covers several rows at
+// once (rows r0, r0 + rpt, … with rpt = threads / (kpad/8)), so narrow
+// problems keep the block's threads busy; wider jobs take several blocks per
+// row band, as k_digitize does.
 template <int D, bool U32>
 __global__ void __launch_bounds__(DIG_THREADS) k_digitize_flat(const DigitizeJob *__restrict__ jobs,
                                                                 int njobs, ModP m) {
@@ -295,19 +299,31 @@ __global__ void __launch_bounds__(DIG_THREADS) k_digitize_flat(const DigitizeJob
         if (jobs[mid].block0 <= b) lo = mid; else hi = mid - 1;
     }
     const DigitizeJob &jb = jobs[lo];
-    const int64_t gx = (jb.dst.kpad / DIG_COLS + DIG_THREADS - 1) / DIG_THREADS;
     const int64_t local = b - jb.block0;
-    const int64_t rb = local / gx, cb = local - rb * gx;
-    if (rb * DIG_ROWS >= jb.rows) return;
-    const int64_t c = DIG_COLS * (cb * DIG_THREADS + threadIdx.x);
-    if (c >= jb.dst.kpad) return;
+    const int64_t tpr = jb.dst.kpad / DIG_COLS;  // threads per row
+    int64_t c, r0, rstep;
+    if (tpr >= DIG_THREADS) {
+        const int64_t gx = (tpr + DIG_THREADS - 1) / DIG_THREADS;
+        const int64_t rb = local / gx, cb = local - rb * gx;
+        c = DIG_COLS * (cb * DIG_THREADS + threadIdx.x);
+        r0 = rb * DIG_ROWS;
+        rstep = 1;
+        if (c >= jb.dst.kpad) return;
+    } else {
+        const int64_t rpt = DIG_THREADS / tpr;
+        if (threadIdx.x >= rpt * tpr) return;
+        c = DIG_COLS * (threadIdx.x % tpr);
+        r0 = local * rpt * DIG_ROWS + threadIdx.x / tpr;
+        rstep = rpt;
+    }
+    if (r0 >= jb.rows) return;
     const bool vec_ok = ((reinterpret_cast<uintptr_t>(jb.X.ptr) & 15u) == 0) && ((jb.X.ld & 3) == 0);
     uint32_t v[DIG_ROWS][8];
 #pragma unroll
-    for (int i = 0; i < DIG_ROWS; ++i) ld_view8(jb.X, vec_ok, rb * DIG_ROWS + i, c, v[i]);
+    for (int i = 0; i < DIG_ROWS; ++i) ld_view8(jb.X, vec_ok, r0 + i * rstep, c, v[i]);
 #pragma unroll
     for (int i = 0; i < DIG_ROWS; ++i) {
-        const int64_t r = rb * DIG_ROWS + i;
+        const int64_t r = r0 + i * rstep;
         if (r >= jb.rows) break;
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[i][e] = red(v[i][e], m);
@@ -651,7 +667,13 @@ cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_
 }
 
 int64_t digitize_flat_blocks(int64_t rows, int64_t kpad) {
-    return ((rows + DIG_ROWS - 1) / DIG_ROWS) * ((kpad / DIG_COLS + DIG_THREADS - 1) / DIG_THREADS);
+    // the block layout of k_digitize_flat
+    const int64_t tpr = kpad / DIG_COLS;
+    if (rows <= 0 || tpr <= 0) return 0;
+    if (tpr >= DIG_THREADS)
+        return ((rows + DIG_ROWS - 1) / DIG_ROWS) * ((tpr + DIG_THREADS - 1) / DIG_THREADS);
+    const int64_t per_block = (DIG_THREADS / tpr) * DIG_ROWS;
+    return (rows + per_block - 1) / per_block;
 }
 
 cudaError_t launch_digitize_flat(const DigitizeJob *jobs_dev, int njobs, int64_t total_blocks,
