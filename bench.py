@@ -189,7 +189,8 @@ def run_reference(args):
 
     from paper_2001_04109_gb300 import inputs
     if args.workload == "batched":
-        shapes = inputs.batch_shapes(BATCH["count"], BATCH["lo"], BATCH["hi"], BATCH["seed"])
+        count0 = args.batch_count or BATCH["count"]
+        shapes = inputs.batch_shapes(count0, BATCH["lo"], BATCH["hi"], BATCH["seed"])
         vals, base = [], None
         for s in range(args.warmup + args.steps):
             r = cpu_batched_rate(shapes, BATCH["p"], args.ref_budget)
@@ -543,7 +544,8 @@ def run_batched(args):
     torch.cuda.set_device(local)
     __graft_entry__.build()
     p = BATCH["p"]
-    shapes = inputs.batch_shapes(BATCH["count"], BATCH["lo"], BATCH["hi"], BATCH["seed"])
+    count0 = args.batch_count or BATCH["count"]
+    shapes = inputs.batch_shapes(count0, BATCH["lo"], BATCH["hi"], BATCH["seed"])
     count = len(shapes)
     # all problems live in one contiguous input and one contiguous output buffer
     a_off = np.cumsum([0] + [n * k for n, k in shapes])
@@ -703,6 +705,8 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--ref-budget", type=float, default=6.0)
+    ap.add_argument("--batch-count", type=int, default=None,
+                    help="problems in the batched workload (default 2048; fewer for profiling)")
     ap.add_argument("--op", choices=["syrk"] + sorted(OPS), default="syrk",
                     help="time another operation on the workload's A instead of the plain product")
     args = ap.parse_args()
