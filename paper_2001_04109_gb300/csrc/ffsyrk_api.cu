@@ -616,6 +616,10 @@ struct ffsyrk_plan_st {
     // the planner's scratch (W, the uploaded d and e, per-column state)
     bool scale_ready = false;
     ScaleConst sconst{};
+    uint32_t *scale_host = nullptr;  // pinned staging of d and e
+    int64_t scale_host_words = 0;
+    cudaEvent_t scale_done = nullptr;
+    bool scale_pending = false;
     uint32_t *dbar = nullptr;
     int64_t dbar_bytes = 0;
     // host-buffer entry point: device copies of A and C (made on first use)
@@ -1412,6 +1416,8 @@ void destroy_plan(ffsyrk_plan_st *pl) {
     drop_graph(pl);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     if (pl->desc_done) cudaEventDestroy(pl->desc_done);
+    if (pl->scale_done) cudaEventDestroy(pl->scale_done);
+    if (pl->scale_host) cudaFreeHost(pl->scale_host);
     for (cudaEvent_t &ev : pl->ev)
         if (ev) cudaEventDestroy(ev);
     if (pl->desc_host) cudaFreeHost(pl->desc_host);
@@ -2040,14 +2046,33 @@ ffsyrk_status_t run_scaled(ffsyrk_plan_t pl, ffsyrk_uplo_t uplo, int64_t n, int6
     if (!grow(reinterpret_cast<void **>(&pl->dbar), &pl->dbar_bytes, n * ldb * 4, st) ||
         !grow(reinterpret_cast<void **>(&pl->dtab), &pl->dtab_bytes, L.total, st))
         return FFSYRK_ERR_ALLOC;
-    // d and e in one pageable copy (staged before it returns, so `in` may go)
+    // d and e in one asynchronous copy from the plan's pinned staging buffer,
+    // reused once the previous call's copy has left it
     const bool has_e = e && k > 1;
-    std::vector<uint32_t> in((size_t)(has_e ? 2 * k - 1 : k));
-    memcpy(in.data(), d, (size_t)k * 4);
-    if (has_e) memcpy(in.data() + k, e, (size_t)(k - 1) * 4);
-    if (cudaMemcpyAsync(pl->dtab + L.din, in.data(), in.size() * 4, cudaMemcpyHostToDevice, st) !=
-        cudaSuccess)
+    const int64_t words = has_e ? 2 * k - 1 : k;
+    if (pl->scale_pending) {
+        cudaEventSynchronize(pl->scale_done);
+        pl->scale_pending = false;
+    }
+    if (words > pl->scale_host_words) {
+        if (pl->scale_host) cudaFreeHost(pl->scale_host);
+        pl->scale_host = nullptr;
+        pl->scale_host_words = 0;
+        if (cudaMallocHost(&pl->scale_host, (size_t)words * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return FFSYRK_ERR_ALLOC;
+        }
+        pl->scale_host_words = words;
+    }
+    if (!pl->scale_done && cudaEventCreateWithFlags(&pl->scale_done, cudaEventDisableTiming) != cudaSuccess)
         return FFSYRK_ERR_CUDA;
+    memcpy(pl->scale_host, d, (size_t)k * 4);
+    if (has_e) memcpy(pl->scale_host + k, e, (size_t)(k - 1) * 4);
+    if (cudaMemcpyAsync(pl->dtab + L.din, pl->scale_host, (size_t)words * 4, cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+        return FFSYRK_ERR_CUDA;
+    cudaEventRecord(pl->scale_done, st);
+    pl->scale_pending = true;
     const ScalePlan sp = L.plan(pl->dtab);
     if (launch_scale_plan(reinterpret_cast<const uint32_t *>(pl->dtab + L.din),
                           reinterpret_cast<const uint32_t *>(pl->dtab + L.ein), has_e, k, kk,

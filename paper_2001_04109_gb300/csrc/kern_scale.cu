@@ -53,17 +53,27 @@ __device__ uint32_t fpow(uint32_t a, uint32_t e, const ScaleConst &f) {
 __device__ __forceinline__ uint32_t finv(uint32_t a, const ScaleConst &f) {
     return fpow(a, f.p - 2, f);
 }
-// a nonzero residue that is not a square (Euler's criterion)
-__device__ __forceinline__ bool nonsquare(uint32_t a, const ScaleConst &f) {
-    return a != 0 && fpow(a, (f.p - 1) / 2, f) != 1;
+// The start of Tonelli–Shanks for a ≠ 0, from one exponentiation:
+// x = a^((q−1)/2), t = a^q = x²·a, r = a^((q+1)/2) = x·a (p − 1 = q·2^s).
+// Euler's criterion is a^((p−1)/2) = t^(2^(s−1)): a is a square exactly when
+// s − 1 squarings take t to 1.
+struct TsStart {
+    uint32_t t, r;
+};
+__device__ __forceinline__ TsStart ts_start(uint32_t a, const ScaleConst &f) {
+    const uint32_t x = fpow(a, (f.q - 1) / 2, f);
+    return TsStart{fmul(fmul(x, x, f), a, f), fmul(x, a, f)};
 }
-// Tonelli–Shanks root of a square a (the same steps, and so the same root,
-// as the host planner).  Every loop is bounded by the 2-adic valuation s of
-// p − 1; a non-square input (never produced by the planner) sets *bad.
-__device__ uint32_t fsqrt(uint32_t a, const ScaleConst &f, bool *bad) {
-    if (a == 0) return 0;
-    if ((f.p & 3u) == 3u) return fpow(a, (f.p + 1) / 4, f);
-    uint32_t M = f.s, c = f.zq, t = fpow(a, f.q, f), r = fpow(a, (f.q + 1) / 2, f);
+__device__ __forceinline__ bool ts_is_square(uint32_t t, const ScaleConst &f) {
+    uint32_t e = t;
+    for (uint32_t i = 1; i < f.s; ++i) e = fmul(e, e, f);
+    return e == 1;
+}
+// Tonelli–Shanks from (t, r) of a square: the same steps, and so the same
+// root, as the host planner.  Every loop is bounded by the 2-adic valuation
+// s of p − 1; a non-square (never produced by the planner) sets *bad.
+__device__ uint32_t ts_finish(TsStart st, const ScaleConst &f, bool *bad) {
+    uint32_t M = f.s, c = f.zq, t = st.t, r = st.r;
     for (int guard = 0; t != 1; ++guard) {
         uint32_t i = 0, t2 = t;
         while (t2 != 1 && i < M) {
@@ -82,6 +92,9 @@ __device__ uint32_t fsqrt(uint32_t a, const ScaleConst &f, bool *bad) {
         r = fmul(r, b, f);
     }
     return r;
+}
+__device__ __forceinline__ uint32_t fsqrt(uint32_t a, const ScaleConst &f, bool *bad) {
+    return a == 0 ? 0u : ts_finish(ts_start(a, f), f, bad);
 }
 
 // One column of W under construction: up to four (source column, weight).
@@ -192,11 +205,14 @@ __global__ void __launch_bounds__(256) k_scale_cols(const uint32_t *__restrict__
     sp.ta[c] = ta;
     sp.tb[c] = tb;
     sp.mate[c] = mate;
-    const bool ns = nonsquare(dbar, f);
+    // one exponentiation gives both the Legendre symbol and the start of the
+    // square root
+    const TsStart st = dbar ? ts_start(dbar, f) : TsStart{1u, 0u};
+    const bool ns = dbar != 0 && !ts_is_square(st.t, f);
     sp.flag[c] = ns ? 1u : 0u;
     if (!ns) {
         bool bad = false;
-        const uint32_t u = fsqrt(dbar, f, &bad);
+        const uint32_t u = dbar ? ts_finish(st, f, &bad) : 0u;
         // √d̄_c·T_c, in the host planner's term order (column c, then mate)
         col.add(c, fmul(u, ta, f), k, p, &bad);
         if (mate >= 0) col.add(mate, fmul(u, tb, f), k, p, &bad);
@@ -268,13 +284,14 @@ __global__ void __launch_bounds__(128) k_scale_pairs(int64_t k, int64_t kk, Scal
     const uint32_t alpha = sp.dbar[i];
     const uint32_t beta = j < k ? sp.dbar[j] : alpha;
     // Algorithm 3 for the non-square α: a² = α/s, b = a·√(s − 1), s the
-    // least non-square
+    // least non-square; then dd = a·√(β/α), c = −b·dd/a.  Written as two
+    // independent chains, a → 1/a and 1/α → √(β/α), which the SM overlaps.
     const uint32_t a = fsqrt(fmul(alpha, f.s_inv, f), f, &bad);
-    const uint32_t b = fmul(a, f.c_sos, f);
+    const uint32_t alpha_inv = finv(alpha, f);
     const uint32_t ainv = finv(a, f);
-    // 1/α = (1/a)²/s; dd = a·√(β/α), c = −b·dd/a
-    const uint32_t alpha_inv = fmul(fmul(ainv, ainv, f), f.s_inv, f);
-    const uint32_t dd = fmul(a, fsqrt(fmul(beta, alpha_inv, f), f, &bad), f);
+    const uint32_t root = fsqrt(fmul(beta, alpha_inv, f), f, &bad);
+    const uint32_t b = fmul(a, f.c_sos, f);
+    const uint32_t dd = fmul(a, root, f);
     const uint32_t c = fneg(fmul(fmul(b, dd, f), ainv, f), p);
     WCol ci, cj;
     ci.clear();
