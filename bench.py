@@ -155,6 +155,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int) -> float:
+    """The largest x over the ranks of the process group (x itself for one rank).
+
+    Replicas time their own steps; the job's time is the slowest rank's.  The
+    reduction runs on the GPU under NCCL and on the CPU under gloo.
+    """
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_oracle_rate(A_np, p, budget_s: float):
     """Time the schoolbook oracle on a bounded row sample; effective n²k/s of the full product."""
     import numpy as np
@@ -303,10 +319,7 @@ def run_ours(args):
         dist.barrier()
     clocks = sampler.stop()
     step_ms = sum(ms) / len(ms)
-    if ws > 1:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(step_ms, ws)
     value = ws * n * n * k / (step_ms * 1e-3)
     leaf_ms = statistics.mean(s["leaf_ms"] for s in stage)
     tmacs = stage[-1]["field_macs"] * info["digits"] ** 2
@@ -597,10 +610,7 @@ def run_batched(args):
     clocks = sampler.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
     step_ms = sum(ms) / len(ms)
-    if ws > 1:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(step_ms, ws)
     value = ws * ops / (step_ms * 1e-3)
     info = ffsyrk.Plan(p, 8, 8, leaf="tc", levels=0).info()
     D = info["digits"]
