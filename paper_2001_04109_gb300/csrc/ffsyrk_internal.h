@@ -320,6 +320,8 @@ struct TcLaunch {
     unsigned int *part_ctr;   // 8 per split tile, zero before the first launch
     int max_units;            // most units (accumulator drains) of any tile's K schedule
     bool scaled;              // a product updates the caller's C (OutScale mode 1)
+    bool short_tiles;         // 1-CTA leaf: many tiles of few k-blocks (a batch of small
+                              // problems): drain with 16 epilogue warps
 };
 // Units (segments that open an accumulator) of a K schedule.
 int count_units(const LeafSeg *segs, int nseg);

@@ -43,11 +43,18 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;            // 16 KB
 constexpr int B_BYTES = BN * BK * 2;            // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // 48 KB
-constexpr int EPI_WARPS = 8;
-constexpr int PRODUCER_WARP = 8, MMA_WARP = 9;
-constexpr int NUM_THREADS = 32 * (EPI_WARPS + 2);  // no other warps: every warp has exactly one role
-constexpr int EPI_COLS = BN / (EPI_WARPS / 4);  // columns per epilogue thread (128)
-constexpr int LD_COLS = 16;  // TMEM columns per tcgen05.ld (128 residues + 16 loads fit 168 regs)
+// Epilogue warps: EW = 8 (the default: 128 running sums per thread in 168
+// registers) or 16 (64 per thread, four warps per scheduler instead of two,
+// for launches of many short tiles, whose accumulator drains come every few
+// k-blocks).  Warps 0..EW−1 drain, warp EW produces, warp EW + 1 issues MMAs.
+template <int EW>
+struct Roles {
+    static constexpr int EPI_WARPS = EW;
+    static constexpr int PRODUCER_WARP = EW, MMA_WARP = EW + 1;
+    static constexpr int NUM_THREADS = 32 * (EW + 2);  // every warp has exactly one role
+    static constexpr int EPI_COLS = BN / (EW / 4);     // columns per epilogue thread
+};
+constexpr int LD_COLS = 16;  // TMEM columns per tcgen05.ld
 constexpr int RING = 4;      // tiles handed from the producer to the MMA and epilogue warps
 constexpr int TMEM_COLS = 512;
 
@@ -58,8 +65,8 @@ using namespace tc;
 // running sums may grow unreduced (one add per unit and element) and are
 // brought below 2p once, before the store; otherwise every unit's add is
 // followed by a conditional subtract that keeps them below 2p.
-template <bool LAZY, bool SCALED>
-__global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__restrict__ prods,
+template <bool LAZY, bool SCALED, int EW>
+__global__ void __launch_bounds__(Roles<EW>::NUM_THREADS, 1) k_leaf_tc(const LeafProd *__restrict__ prods,
                                                              const LeafTile *__restrict__ tiles,
                                                              const LeafSeg *__restrict__ segs,
                                                              int ntiles,
@@ -72,6 +79,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_leaf_tc(const LeafProd *__re
                                                              const int32_t *__restrict__ entries,
                                                              int nentries, uint32_t *part,
                                                              unsigned int *part_ctr) {
+    constexpr int EPI_WARPS = Roles<EW>::EPI_WARPS, PRODUCER_WARP = Roles<EW>::PRODUCER_WARP,
+                  MMA_WARP = Roles<EW>::MMA_WARP, EPI_COLS = Roles<EW>::EPI_COLS;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
     __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], drain_bar;
@@ -395,7 +404,8 @@ cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st) {
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaSuccess;
-        for (auto fn : {k_leaf_tc<true, false>, k_leaf_tc<false, false>, k_leaf_tc<true, true>, k_leaf_tc<false, true>})
+        for (auto fn : {k_leaf_tc<true, false, 8>, k_leaf_tc<false, false, 8>, k_leaf_tc<true, true, 8>,
+                        k_leaf_tc<false, true, 8>, k_leaf_tc<true, false, 16>})
             if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
@@ -403,8 +413,11 @@ cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st) {
     const int nwork = L.entries ? L.nentries : L.ntiles;
     const int grid = nwork < num_sms ? nwork : num_sms;
     const bool lazy = L.max_units <= L.ds.lazy_units;
-    auto kern = L.scaled ? (lazy ? k_leaf_tc<true, true> : k_leaf_tc<false, true>)
-                         : (lazy ? k_leaf_tc<true, false> : k_leaf_tc<false, false>);
+    // many short tiles: the 16-warp epilogue (plain lazy stores only)
+    const bool wide_epi = L.short_tiles && lazy && !L.scaled;
+    auto kern = wide_epi ? k_leaf_tc<true, false, 16>
+                : L.scaled ? (lazy ? k_leaf_tc<true, true, 8> : k_leaf_tc<false, true, 8>)
+                           : (lazy ? k_leaf_tc<true, false, 8> : k_leaf_tc<false, false, 8>);
     // programmatic dependent launch: the prologue may overlap the grid that
     // writes the operands (the producer waits for it before its first load)
     cudaLaunchAttribute attr[1];
@@ -412,7 +425,7 @@ cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(NUM_THREADS);
+    cfg.blockDim = dim3(wide_epi ? Roles<16>::NUM_THREADS : Roles<8>::NUM_THREADS);
     cfg.dynamicSmemBytes = (size_t)smem;
     cfg.stream = st;
     cfg.attrs = attr;
