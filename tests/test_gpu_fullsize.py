@@ -7,9 +7,14 @@ tile band, near-diagonal entries -- against the oracle computed row by row.
 The classical path (depth 0) is checked next to the fast one where the
 benchmark compares them.  Every full-size result is also checked whole by
 Freivalds' test, C·x ≡ A·(Aᵀ·x) mod p for two random x, in exact integer
-arithmetic that shares nothing with the library.  The batch of 2048 uneven problems is checked on a
+arithmetic that shares nothing with the library, and, where
+tests/golden/fullsize_sha256.txt holds the oracle's digest of the whole
+lower triangle (every workload but A 32768²), bit for bit against it.  The batch of 2048 uneven problems is checked on a
 seeded sample of whole problems.
 """
+import hashlib
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -64,6 +69,28 @@ def freivalds(A_host, p, C_dev, seed, vectors=2):
         assert np.array_equal(got, want), "Freivalds check failed: some entry of C is wrong"
 
 
+def stored_digests():
+    """(n, k, p) → SHA-256 of the oracle's lower triangle (tests/golden/fullsize_sha256.txt)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize_sha256.txt")
+    out = {}
+    if os.path.exists(path):
+        for line in open(path):
+            if line.startswith("#") or not line.strip():
+                continue
+            n, k, p, seed, digest = line.split()
+            if int(seed) == 2:
+                out[(int(n), int(k), int(p))] = digest
+    return out
+
+
+def lower_sha256(C_dev) -> str:
+    C = np.ascontiguousarray(C_dev.cpu().numpy().view(np.uint32).astype("<u4", copy=False))
+    h = hashlib.sha256()
+    for i in range(C.shape[0]):
+        h.update(C[i, : i + 1].tobytes())
+    return h.hexdigest()
+
+
 def check_rows(A_host, p, C_dev, rows):
     want = oracle.syrk_rows(A_host.numpy(), p, rows)
     got = C_dev[torch.from_numpy(rows).cuda()].cpu().numpy().view(np.uint32)
@@ -96,6 +123,9 @@ def test_workload_sampled_rows(n, k, p, depths):
         plan.sync_status()
         check_rows(A_host, p, C, rows)
         freivalds(A_host, p, C, seed=n + k + (levels or 0))
+        digest = stored_digests().get((n, k, p))
+        if digest is not None:  # the whole triangle, bit for bit, against the oracle's
+            assert lower_sha256(C) == digest, f"lower triangle differs from the oracle ({levels})"
         plan.close()
         del C
     torch.cuda.empty_cache()

@@ -147,3 +147,29 @@ def test_update_special_cases():
     assert np.array_equal(got[low], (3 * C0[low].astype(np.uint64) % p).astype(np.uint32))
     got = oracle.syrk_update(A, p, 1, C0, 1)
     assert np.array_equal(got[low], ((P[low].astype(np.uint64) + C0[low]) % p).astype(np.uint32))
+
+
+def test_fullsize_digests_cover_the_benchmark_workloads():
+    # tests/golden/fullsize_sha256.txt is written by make_fullsize_sha256.py
+    # from the oracle alone; the GPU full-size tests compare whole triangles
+    # against it.  Every benchmark workload the oracle finishes in minutes
+    # has a digest (A 32768² is checked by sampled rows and Freivalds' test).
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize_sha256.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    have = {(int(n), int(k), int(p)) for n, k, p, seed, d in rows if int(seed) == 2 and len(d) == 64}
+    for w in [(256, 256, 65521), (4096, 4096, 65521), (4096, 16384, 131071), (8192, 8192, 65521),
+              (16384, 4096, 131071), (16383, 4097, 131071), (16384, 16384, 65521)]:
+        assert w in have, w
+    # the digest format on a small case: rows of the lower triangle in order
+    import hashlib
+    import numpy as np
+    import oracle
+    from paper_2001_04109_gb300 import inputs
+    A = inputs.uniform_residues(37, 23, 65521, seed=2).numpy().view(np.uint32)
+    C = oracle.syrk(A, 65521, "lower")
+    h = hashlib.sha256()
+    for i in range(37):
+        h.update(C[i, : i + 1].astype("<u4").tobytes())
+    flat = np.concatenate([C[i, : i + 1] for i in range(37)]).astype("<u4").tobytes()
+    assert h.hexdigest() == hashlib.sha256(flat).hexdigest()
