@@ -69,25 +69,37 @@ def freivalds(A_host, p, C_dev, seed, vectors=2):
         assert np.array_equal(got, want), "Freivalds check failed: some entry of C is wrong"
 
 
+def _golden():
+    """The digest script of tests/golden (its hashing is the one the stored digests used)."""
+    import importlib.util
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "make_fullsize_sha256.py")
+    spec = importlib.util.spec_from_file_location("make_fullsize_sha256", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
 def stored_digests():
-    """(n, k, p) → SHA-256 of the oracle's lower triangle (tests/golden/fullsize_sha256.txt)."""
+    """Key → SHA-256 of the oracle's lower triangles (tests/golden/fullsize_sha256.txt):
+    (n, k, p) for seed-2 workloads, ("batched", count, lo, hi, p, seed) for the batch."""
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize_sha256.txt")
     out = {}
     if os.path.exists(path):
         for line in open(path):
             if line.startswith("#") or not line.strip():
                 continue
-            n, k, p, seed, digest = line.split()
-            if int(seed) == 2:
-                out[(int(n), int(k), int(p))] = digest
+            f = line.split()
+            if f[0] == "batched":
+                out[("batched",) + tuple(int(x) for x in f[1:6])] = f[6]
+            elif int(f[3]) == 2:
+                out[(int(f[0]), int(f[1]), int(f[2]))] = f[4]
     return out
 
 
 def lower_sha256(C_dev) -> str:
-    C = np.ascontiguousarray(C_dev.cpu().numpy().view(np.uint32).astype("<u4", copy=False))
     h = hashlib.sha256()
-    for i in range(C.shape[0]):
-        h.update(C[i, : i + 1].tobytes())
+    _golden().lower_update(h, C_dev.cpu().numpy().view(np.uint32))
     return h.hexdigest()
 
 
@@ -143,6 +155,9 @@ def test_large_d3_three_levels_sampled_rows():
     plan.sync_status()
     check_rows(A_host, p, C, sample_rows(n, 48, seed=7))
     freivalds(A_host, p, C, seed=32768)
+    digest = stored_digests().get((n, k, p))
+    if digest is not None:  # the whole triangle against the oracle's
+        assert lower_sha256(C) == digest, "lower triangle differs from the oracle"
     plan.close()
     del A, C
     torch.cuda.empty_cache()
@@ -162,3 +177,10 @@ def test_batched_2048_uneven_sampled_problems():
         n, _ = shapes[t]
         rows = sample_rows(n, 16, seed=t)
         check_rows(As[t].cpu(), p, Cs[t], rows)
+    digest = stored_digests().get(("batched", 2048, 32, 2048, p, seed))
+    if digest is not None:  # every problem's whole triangle against the oracle's
+        g = _golden()
+        h = hashlib.sha256()
+        for C in Cs:
+            g.lower_update(h, C.cpu().numpy().view(np.uint32))
+        assert h.hexdigest() == digest, "some problem of the batch differs from the oracle"

@@ -152,24 +152,33 @@ def test_update_special_cases():
 def test_fullsize_digests_cover_the_benchmark_workloads():
     # tests/golden/fullsize_sha256.txt is written by make_fullsize_sha256.py
     # from the oracle alone; the GPU full-size tests compare whole triangles
-    # against it.  Every benchmark workload the oracle finishes in minutes
-    # has a digest (A 32768² is checked by sampled rows and Freivalds' test).
-    import os
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize_sha256.txt")
-    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
-    have = {(int(n), int(k), int(p)) for n, k, p, seed, d in rows if int(seed) == 2 and len(d) == 64}
-    for w in [(256, 256, 65521), (4096, 4096, 65521), (4096, 16384, 131071), (8192, 8192, 65521),
-              (16384, 4096, 131071), (16383, 4097, 131071), (16384, 16384, 65521)]:
-        assert w in have, w
-    # the digest format on a small case: rows of the lower triangle in order
+    # against it with the script's own hashing (lower_update).
     import hashlib
+    import importlib.util
+    import os
     import numpy as np
     import oracle
     from paper_2001_04109_gb300 import inputs
+    here = os.path.dirname(os.path.abspath(__file__))
+    rows = [ln.split() for ln in open(os.path.join(here, "golden", "fullsize_sha256.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    have = {(int(r[0]), int(r[1]), int(r[2])) for r in rows if r[0] != "batched" and len(r[4]) == 64}
+    for w in [(256, 256, 65521), (4096, 4096, 65521), (4096, 16384, 131071), (8192, 8192, 65521),
+              (16384, 4096, 131071), (16383, 4097, 131071), (16384, 16384, 65521)]:
+        assert w in have, w
+    spec = importlib.util.spec_from_file_location(
+        "make_fullsize_sha256", os.path.join(here, "golden", "make_fullsize_sha256.py"))
+    g = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(g)
+    # a workload's digest: the rows of its lower triangle in order
     A = inputs.uniform_residues(37, 23, 65521, seed=2).numpy().view(np.uint32)
     C = oracle.syrk(A, 65521, "lower")
-    h = hashlib.sha256()
-    for i in range(37):
-        h.update(C[i, : i + 1].astype("<u4").tobytes())
     flat = np.concatenate([C[i, : i + 1] for i in range(37)]).astype("<u4").tobytes()
-    assert h.hexdigest() == hashlib.sha256(flat).hexdigest()
+    assert g.workload_digest(37, 23, 65521) == hashlib.sha256(flat).hexdigest()
+    # a batch's digest: the problems' triangles in problem order, built as the GPU test builds it
+    shapes = inputs.batch_shapes(5, 32, 64, 5)
+    h = hashlib.sha256()
+    for t, (n, k) in enumerate(shapes):
+        At = inputs.uniform_residues(n, k, 65521, seed=5 * 100000 + t).numpy().view(np.uint32)
+        g.lower_update(h, oracle.syrk(At, 65521, "lower"))
+    assert g.batch_digest(5, 32, 64, 65521, 5) == h.hexdigest()
