@@ -13,11 +13,13 @@
  * - Matrices are row-major.  A is n×k with leading dimension lda ≥ max(1,k);
  *   C is n×n with ldc ≥ max(1,n).  Any lda/ldc is accepted (no alignment
  *   requirement).  Entries of A may be any uint32; they are reduced mod p.
- * - A and C are DEVICE pointers owned by the caller.  The library never
- *   frees or retains them beyond the call.
+ * - A and C are DEVICE pointers owned by the caller (ffsyrk_host alone takes
+ *   host matrices; the diagonals of the scaled products are host arrays).
+ *   The library never frees or retains them beyond the call.
  * - uplo = FFSYRK_LOWER writes C[i][j] = (A·Aᵀ)[i][j] mod p for j ≤ i
  *   (canonical, in [0, p)); FFSYRK_UPPER writes the same values at C[j][i].
- *   The other strict triangle of C is never read or written.
+ *   The other strict triangle of C is never read or written (ffsyrk_host
+ *   returns the whole host matrix, zeros there).
  * - n = 0 is a no-op; k = 0 writes zeros to the selected triangle.
  * - p must be an odd prime with 3 ≤ p < 2^24 (FFSYRK_ERR_NOT_PRIME for a
  *   composite, FFSYRK_ERR_UNSUPPORTED_P for 2 or p ≥ 2^24).
