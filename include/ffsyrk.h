@@ -114,6 +114,18 @@ typedef struct ffsyrk_plan_st *ffsyrk_plan_t;
 ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int64_t max_k,
                             const ffsyrk_options_t *opts);
 
+/* Device memory a plan made by ffsyrk_plan with these arguments allocates at
+ * creation, computed on the host (no GPU needed, for capacity planning):
+ * *workspace_bytes = the plan's workspace (ffsyrk_plan_info_t's
+ * workspace_bytes), *slot_bytes (may be NULL) = the partial-result slots of
+ * shared tiles for a device with `sms` SMs (0: 152, GB300).  Buffers made on
+ * first use are not included (the scaled products' Ā and planner table, the
+ * host entry point's copies of A and C).  Same argument checks as
+ * ffsyrk_plan. */
+ffsyrk_status_t ffsyrk_workspace_query(uint32_t p, int64_t max_n, int64_t max_k,
+                                       const ffsyrk_options_t *opts, int32_t sms,
+                                       int64_t *workspace_bytes, int64_t *slot_bytes);
+
 /* Free the plan's workspace.  Synchronises the device work it enqueued.
  * NULL is accepted. */
 ffsyrk_status_t ffsyrk_plan_destroy(ffsyrk_plan_t plan);

@@ -1584,6 +1584,69 @@ void ffsyrk_options_default(ffsyrk_options_t *o) {
 }
 
 namespace {
+// The options with defaults filled in, checked.
+ffsyrk_status_t checked_options(const ffsyrk_options_t *opts, ffsyrk_options_t *o) {
+    ffsyrk_options_default(o);
+    if (opts) *o = *opts;
+    if (o->leaf < FFSYRK_LEAF_AUTO || o->leaf > FFSYRK_LEAF_I64) return FFSYRK_ERR_INVALID_ARG;
+    if (o->levels < FFSYRK_LEVELS_AUTO || o->levels > kMaxLevels) return FFSYRK_ERR_INVALID_ARG;
+    if (o->tile_ctas < 0 || o->tile_ctas > 2) return FFSYRK_ERR_INVALID_ARG;
+    if (o->autotune < 0 || o->autotune > 1) return FFSYRK_ERR_INVALID_ARG;
+    if (o->winograd < -1 || o->winograd > kMaxLevels) return FFSYRK_ERR_INVALID_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (o->reserved[i] != 0) return FFSYRK_ERR_INVALID_ARG;
+    return FFSYRK_SUCCESS;
+}
+
+// The host half of a plan (field constants, digits, options, depth at the
+// largest shape); no device call.  Returns whether the autotuner will run.
+bool plan_setup(ffsyrk_plan_st *pl, uint32_t p, int64_t max_n, int64_t max_k,
+                const ffsyrk_options_t &o, bool gemmt) {
+    pl->p = p;
+    pl->ych = host::choose_y(p);
+    pl->yc.form = pl->ych.form;
+    pl->yc.a = make_mul((uint32_t)pl->ych.a, p);
+    pl->yc.b = make_mul((uint32_t)pl->ych.b, p);
+    pl->ds = make_digits(p);
+    pl->mp = make_modp(p, pl->ds);
+    pl->leaf = (o.leaf == FFSYRK_LEAF_AUTO) ? FFSYRK_LEAF_TC_BF16 : o.leaf;
+    pl->gemmt = gemmt;
+    pl->levels_opt = gemmt ? 0 : o.levels;
+    pl->ctas_opt = o.tile_ctas;
+    pl->sw_opt = o.winograd;
+    pl->max_n = max_n;
+    pl->max_k = max_k;
+    pl->L_max = choose_levels(pl, max_n, max_k);
+    return o.autotune != 0 && o.levels == FFSYRK_LEVELS_AUTO && o.tile_ctas == 0 && max_n > 0 &&
+           max_k > 0 && !gemmt;
+}
+
+// Workspace capacity: the largest layout over the depths the plan may use.
+void plan_capacity(const ffsyrk_plan_st *pl, bool tuning, int64_t *data, int64_t *desc) {
+    std::vector<int> Ls{pl->L_max};
+    if (tuning)
+        for (int L : tune_levels(pl->max_n, pl->max_k)) Ls.push_back(L);
+    *data = 0;
+    *desc = 0;
+    for (int L : Ls) {
+        int64_t dc = 0;
+        const int64_t db = workspace_need(pl, std::max<int64_t>(pl->max_n, 1),
+                                          std::max<int64_t>(pl->max_k, 1), L, &dc);
+        *data = std::max(*data, db);
+        *desc = std::max(*desc, dc);
+    }
+}
+
+// Partial-result slots of shared tiles: at most two per CTA, and no more
+// than the units of all tiles at the largest shape.
+int part_slots_for(const ffsyrk_plan_st *pl, int sms) {
+    const Geometry g0 = make_geometry(std::max<int64_t>(pl->max_n, 1), std::max<int64_t>(pl->max_k, 1), 0);
+    const int64_t units = leaf_tiles_bound(g0, pl->leaf) * ((g0.kp / 64 + 15) / 16 + 1) * pl->ds.D * pl->ds.D;
+    return (int)std::min<int64_t>(std::min<int64_t>(2 * sms, 2 * kMaxCtas), units);
+}
+}  // namespace
+
+namespace {
 ffsyrk_status_t plan_create(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int64_t max_k,
                             const ffsyrk_options_t *opts, bool gemmt);
 }  // namespace
@@ -1591,6 +1654,29 @@ ffsyrk_status_t plan_create(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
 ffsyrk_status_t ffsyrk_plan(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int64_t max_k,
                             const ffsyrk_options_t *opts) {
     return plan_create(plan, p, max_n, max_k, opts, false);
+}
+
+ffsyrk_status_t ffsyrk_workspace_query(uint32_t p, int64_t max_n, int64_t max_k,
+                                       const ffsyrk_options_t *opts, int32_t sms,
+                                       int64_t *workspace_bytes, int64_t *slot_bytes) {
+    ffsyrk_status_t s = validate_p(p);
+    if (s != FFSYRK_SUCCESS) return s;
+    if (max_n < 0 || max_k < 0 || max_n > (int64_t(1) << 20) || max_k > (int64_t(1) << 24) ||
+        sms < 0 || !workspace_bytes)
+        return FFSYRK_ERR_INVALID_ARG;
+    ffsyrk_options_t o;
+    s = checked_options(opts, &o);
+    if (s != FFSYRK_SUCCESS) return s;
+    ffsyrk_plan_st pl;
+    const bool tuning = plan_setup(&pl, p, max_n, max_k, o, false);
+    int64_t data = 0, desc = 0;
+    plan_capacity(&pl, tuning, &data, &desc);
+    *workspace_bytes = data + desc;
+    if (slot_bytes)
+        *slot_bytes = pl.leaf == FFSYRK_LEAF_TC_BF16
+                          ? (int64_t)part_slots_for(&pl, sms ? sms : 152) * leaf_tc_bm() * leaf_tc_bn() * 4
+                          : 0;
+    return FFSYRK_SUCCESS;
 }
 
 namespace {
@@ -1603,15 +1689,8 @@ ffsyrk_status_t plan_create(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
     if (max_n < 0 || max_k < 0 || max_n > (int64_t(1) << 20) || max_k > (int64_t(1) << 24))
         return FFSYRK_ERR_INVALID_ARG;
     ffsyrk_options_t o;
-    ffsyrk_options_default(&o);
-    if (opts) o = *opts;
-    if (o.leaf < FFSYRK_LEAF_AUTO || o.leaf > FFSYRK_LEAF_I64) return FFSYRK_ERR_INVALID_ARG;
-    if (o.levels < FFSYRK_LEVELS_AUTO || o.levels > kMaxLevels) return FFSYRK_ERR_INVALID_ARG;
-    if (o.tile_ctas < 0 || o.tile_ctas > 2) return FFSYRK_ERR_INVALID_ARG;
-    if (o.autotune < 0 || o.autotune > 1) return FFSYRK_ERR_INVALID_ARG;
-    if (o.winograd < -1 || o.winograd > kMaxLevels) return FFSYRK_ERR_INVALID_ARG;
-    for (int i = 0; i < 3; ++i)
-        if (o.reserved[i] != 0) return FFSYRK_ERR_INVALID_ARG;
+    s = checked_options(opts, &o);
+    if (s != FFSYRK_SUCCESS) return s;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return FFSYRK_ERR_CUDA;
@@ -1627,36 +1706,9 @@ ffsyrk_status_t plan_create(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
     pl->sms = sms;
     pl->p = p;
 
-    pl->ych = host::choose_y(p);
-    pl->yc.form = pl->ych.form;
-    pl->yc.a = make_mul((uint32_t)pl->ych.a, p);
-    pl->yc.b = make_mul((uint32_t)pl->ych.b, p);
-    pl->ds = make_digits(p);
-    pl->mp = make_modp(p, pl->ds);
-    pl->leaf = (o.leaf == FFSYRK_LEAF_AUTO) ? FFSYRK_LEAF_TC_BF16 : o.leaf;
-    pl->gemmt = gemmt;
-    pl->levels_opt = gemmt ? 0 : o.levels;
-    pl->ctas_opt = o.tile_ctas;
-    pl->sw_opt = o.winograd;
-    pl->max_n = max_n;
-    pl->max_k = max_k;
-    pl->L_max = choose_levels(pl, max_n, max_k);
-
-    const bool tuning = o.autotune != 0 && o.levels == FFSYRK_LEVELS_AUTO && o.tile_ctas == 0 &&
-                        max_n > 0 && max_k > 0 && !gemmt;
-    // capacity: the largest layout over the depths this plan may use
+    const bool tuning = plan_setup(pl, p, max_n, max_k, o, gemmt);
     int64_t data = 0, desc = 0;
-    {
-        std::vector<int> Ls{pl->L_max};
-        if (tuning)
-            for (int L : tune_levels(max_n, max_k)) Ls.push_back(L);
-        for (int L : Ls) {
-            int64_t dc = 0;
-            int64_t db = workspace_need(pl, std::max<int64_t>(max_n, 1), std::max<int64_t>(max_k, 1), L, &dc);
-            data = std::max(data, db);
-            desc = std::max(desc, dc);
-        }
-    }
+    plan_capacity(pl, tuning, &data, &desc);
     pl->data_cap = data;
     pl->desc_cap = desc;
     pl->ws_bytes = data + desc;
@@ -1669,10 +1721,7 @@ ffsyrk_status_t plan_create(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
     if (pl->leaf == FFSYRK_LEAF_TC_BF16) {
         // partial-result slots of the tail split: at most two per CTA, and no
         // more than the units of all tiles at the largest shape
-        const Geometry g0 = make_geometry(std::max<int64_t>(max_n, 1), std::max<int64_t>(max_k, 1), 0);
-        const int64_t units = leaf_tiles_bound(g0, pl->leaf) *
-                              ((g0.kp / 64 + 15) / 16 + 1) * pl->ds.D * pl->ds.D;
-        pl->part_slots = (int)std::min<int64_t>(std::min<int64_t>(2 * sms, 2 * kMaxCtas), units);
+        pl->part_slots = part_slots_for(pl, sms);
         const size_t bytes = (size_t)pl->part_slots * leaf_tc_bm() * leaf_tc_bn() * 4;
         if (cudaMalloc(&pl->part, bytes) != cudaSuccess) {
             cudaGetLastError();

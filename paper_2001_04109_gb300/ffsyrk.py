@@ -36,7 +36,7 @@ EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsy
            "ffsyrk_update", "ffsyrkd_with_plan_update", "ffsyrkd_update", "ffsyrkd_factor",
            "ffsyrkbd_with_plan_update", "ffsyrkbd_update", "ffsyrkbd_factor",
            "ffsyrkbd_factor_device", "ffherk_plan", "ffherk_plan_destroy", "ffherk_with_plan",
-           "ffherk_sync_status", "ffherk", "ffsyrk_host"]
+           "ffherk_sync_status", "ffherk", "ffsyrk_host", "ffsyrk_workspace_query"]
 
 
 class FfsyrkError(RuntimeError):
@@ -113,8 +113,10 @@ def lib() -> ctypes.CDLL:
             L.ffherk.argtypes = [i32, i64, i64, u32, u32, vp, i64, vp, vp, i64, vp]
             L.ffsyrk_host.argtypes = [vp, i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk_host.restype = i32
+            L.ffsyrk_workspace_query.argtypes = [u32, i64, i64, P(Options), i32, P(i64), P(i64)]
+            L.ffsyrk_workspace_query.restype = i32
             for name in ["ffherk_plan", "ffherk_plan_destroy", "ffherk_with_plan",
-                         "ffherk_sync_status", "ffherk", "ffsyrk_host"]:
+                         "ffherk_sync_status", "ffherk", "ffsyrk_host", "ffsyrk_workspace_query"]:
                 getattr(L, name).restype = i32
             L.ffsyrk_noalloc.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk_batched.argtypes = [i32, i64, P(i64), P(i64), u32, P(vp), P(i64), P(vp),
@@ -362,6 +364,16 @@ def herk(A: torch.Tensor, p: int, r: int, uplo: str = "lower", Cre: torch.Tensor
     _check(lib().ffherk(UPPER if uplo == "upper" else LOWER, n, k2 // 2, int(p),
                         int(r) & 0xFFFFFFFF, pa, lda, pr, pi, ldr, _stream_handle(stream)), "ffherk")
     return Cre, Cim
+
+
+def workspace_query(p: int, max_n: int, max_k: int, leaf=None, levels=None, tile_ctas=None,
+                    autotune=False, winograd=None, sms: int = 0) -> tuple[int, int]:
+    """(workspace bytes, shared-tile slot bytes) a Plan with these arguments allocates (no GPU)."""
+    o = make_options(leaf, levels, tile_ctas, autotune, winograd)
+    ws, sl = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ffsyrk_workspace_query(int(p), int(max_n), int(max_k), ctypes.byref(o), int(sms),
+                                        ctypes.byref(ws), ctypes.byref(sl)), "ffsyrk_workspace_query")
+    return ws.value, sl.value
 
 
 def leaf_schedule(p: int, kblocks: int) -> list[tuple[int, int, int, int, bool]]:

@@ -97,3 +97,21 @@ def test_autotune_option_validated(lib):
     o.autotune = 0
     o.tile_ctas = 3
     assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
+
+
+def test_workspace_query_without_gpu(lib):
+    # capacity planning on the host: the workspace a plan would allocate
+    ws = {n: ffsyrk.workspace_query(65521, n, n)[0] for n in (1024, 4096, 8192)}
+    assert 0 < ws[1024] < ws[4096] < ws[8192]
+    # Winograd levels add their uint32 operands, pieces and products
+    on = ffsyrk.workspace_query(8388593, 32768, 32768, levels=3)[0]
+    off = ffsyrk.workspace_query(8388593, 32768, 32768, levels=3, winograd=0)[0]
+    assert on > 2 * off > 0
+    # the int64 leaf has no shared-tile slots; the tensor leaf scales them with the SMs
+    assert ffsyrk.workspace_query(65521, 4096, 4096, leaf="i64")[1] == 0
+    s152 = ffsyrk.workspace_query(65521, 4096, 4096)[1]
+    assert 0 < ffsyrk.workspace_query(65521, 4096, 4096, sms=76)[1] <= s152
+    with pytest.raises(ffsyrk.FfsyrkError):
+        ffsyrk.workspace_query(65521, -1, 4)
+    with pytest.raises(ffsyrk.FfsyrkError):
+        ffsyrk.workspace_query(65520, 4, 4)   # not prime

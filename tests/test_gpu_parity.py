@@ -116,3 +116,11 @@ def test_y_choice_is_skew_orthogonal():
         else:
             assert info["y_form"] == 1 and (a * a + b * b) % p == p - 1
             assert info["y_cost"] == (2 if p % 8 == 3 else 3)
+
+
+def test_workspace_query_matches_plans():
+    for p, n, k, kw in [(65521, 4096, 4096, {}), (131071, 3000, 5000, {"levels": 2}),
+                        (8388593, 2048, 2048, {"levels": 3, "winograd": 2})]:
+        plan = ffsyrk.Plan(p, n, k, **kw)
+        assert plan.info()["workspace_bytes"] == ffsyrk.workspace_query(p, n, k, **kw)[0]
+        plan.close()
