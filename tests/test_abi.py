@@ -115,3 +115,35 @@ def test_workspace_query_without_gpu(lib):
         ffsyrk.workspace_query(65521, -1, 4)
     with pytest.raises(ffsyrk.FfsyrkError):
         ffsyrk.workspace_query(65520, 4, 4)   # not prime
+
+
+def test_other_entry_points_check_arguments_first(lib):
+    # every check below returns before the device is touched
+    import ctypes
+    from oracle import field
+    E = ffsyrk
+    h = ctypes.c_void_p(123)
+    # the Hermitian plan wants a prime p and i² = r a non-square mod p
+    assert lib.ffherk_plan(None, 65521, 17, 8, 8, None) == E.ERR_INVALID_ARG
+    assert lib.ffherk_plan(ctypes.byref(h), 65535, 3, 8, 8, None) == E.ERR_NOT_PRIME
+    assert h.value is None
+    for p in (13, 65521):                       # p ≡ 1 mod 4: −1 is a square there
+        square = (5 * 5) % p
+        assert field.legendre(p - 1, p) == 1
+        for r in (0, p, p - 1, square):
+            assert lib.ffherk_plan(ctypes.byref(h), p, r, 8, 8, None) == E.ERR_INVALID_ARG, (p, r)
+    assert lib.ffherk_plan(ctypes.byref(h), 65521, 17, -1, 8, None) == E.ERR_INVALID_ARG
+    assert lib.ffherk_plan_destroy(None) == E.SUCCESS
+    assert lib.ffherk_with_plan(None, 0, 4, 4, None, 8, None, None, 4, None) == E.ERR_INVALID_ARG
+    assert lib.ffherk_sync_status(None, None) == E.ERR_INVALID_ARG
+    assert lib.ffherk(0, 4, 4, 4, 3, None, 8, None, None, 4, None) == E.ERR_NOT_PRIME
+    assert lib.ffherk(0, -1, 4, 65521, 17, None, 8, None, None, 4, None) == E.ERR_INVALID_ARG
+    # host-buffer product and the scaled products
+    assert lib.ffsyrk_host(None, 0, 4, 4, 65521, None, 4, None, 4, None) == E.ERR_INVALID_ARG
+    assert lib.ffsyrkbd_with_plan_update(None, 0, 4, 4, 65521, 1, None, 4, None, None, 0, None, 4,
+                                         None) == E.ERR_INVALID_ARG
+    assert lib.ffsyrkbd_update(0, 4, 4, 65535, 1, None, 4, None, None, 0, None, 4, None) == \
+        E.ERR_NOT_PRIME
+    assert lib.ffsyrkbd_update(0, 4, -1, 65521, 1, None, 4, None, None, 0, None, 4, None) == \
+        E.ERR_INVALID_ARG
+    assert lib.ffsyrk_update(0, 4, 4, 2, 1, None, 4, 0, None, 4, None) == E.ERR_UNSUPPORTED_P
