@@ -9,8 +9,9 @@ benchmark compares them.  Every full-size result is also checked whole by
 Freivalds' test, C·x ≡ A·(Aᵀ·x) mod p for two random x, in exact integer
 arithmetic that shares nothing with the library, and, where
 tests/golden/fullsize_sha256.txt holds the oracle's digest of the whole
-lower triangle (every workload but A 32768²), bit for bit against it.  The batch of 2048 uneven problems is checked on a
-seeded sample of whole problems.
+lower triangle, bit for bit against it.  The batch of 2048 uneven problems
+is checked on a seeded sample of problems' rows and, through the stored
+digest, on every problem's whole triangle.
 """
 import hashlib
 import os
