@@ -29,7 +29,12 @@ def balanced_digits(s, D, b):
     return out
 
 
-@pytest.mark.parametrize("p", [3, 251, 257, 65521, 65537, 131071, 131041, 8388593, 16777213])
+# 509 / 521: the last one-digit and the first two-digit prime; 131321 / 131357:
+# the last two-digit (balanced base) and the first three-digit prime
+DIGIT_EDGES = [509, 521, 131321, 131357]
+
+
+@pytest.mark.parametrize("p", [3, 251, 257, 65521, 65537, 131071, 131041, 8388593, 16777213] + DIGIT_EDGES)
 def test_digit_bounds_cover_every_residue(p):
     bounds = ffsyrk.digit_bounds(p)
     b = ffsyrk.digit_base(p)
@@ -47,8 +52,10 @@ def test_digit_bounds_cover_every_residue(p):
 
 
 @pytest.mark.parametrize("p,base,bounds", [(65521, 256, [128, 128]), (131071, 362, [181, 181]),
-                                           (8388593, 256, [128, 128, 64]), (251, 256, [125])])
-def test_digit_base_balances_the_two_digit_primes_above_2_16(p, base, bounds):
+                                           (8388593, 256, [128, 128, 64]), (251, 256, [125]),
+                                           (509, 256, [254]), (521, 256, [128, 1]),
+                                           (131321, 362, [181, 181]), (131357, 256, [128, 128, 1])])
+def test_digit_base_and_bounds(p, base, bounds):
     # below 2^16 byte digits are already balanced; p = 131071 with bytes would
     # need a top digit of 256 (chunks of 4 k-blocks for the top pair), the
     # balanced base 362 bounds both digits by 181 (8 k-blocks for every pair)
@@ -59,7 +66,7 @@ def test_digit_base_balances_the_two_digit_primes_above_2_16(p, base, bounds):
         assert min(nkb for *_, nkb, first in ffsyrk.leaf_schedule(p, 64) if first) >= 4
 
 
-@pytest.mark.parametrize("p", [251, 65521, 131071, 8388593])
+@pytest.mark.parametrize("p", [251, 65521, 131071, 8388593] + DIGIT_EDGES)
 @pytest.mark.parametrize("kblocks", [1, 3, 4, 5, 16, 17, 33, 64, 513])
 def test_schedule_units_exact_and_complete(p, kblocks):
     bounds = ffsyrk.digit_bounds(p)
