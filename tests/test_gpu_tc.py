@@ -36,8 +36,9 @@ def test_small_classical(n, k):
     check_against_oracle(A, p, C)
 
 
-# (p, symmetric residue whose signed base-256 digits are all at their bound)
-BOUND_CASES = [(65521, 32640), (131071, 65408), (8388593, 4161408)]
+# (p, symmetric residue whose signed digits, in the base the library takes for p,
+# all sit at their bounds: 131071 uses the balanced base 362, digits (−181, 181))
+BOUND_CASES = [(65521, 32640), (131071, 65341), (8388593, 4161408)]
 
 
 @pytest.mark.parametrize("p,s", BOUND_CASES)

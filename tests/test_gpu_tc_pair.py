@@ -36,7 +36,7 @@ def test_pair_shapes(n, k, levels):
     check_against_oracle(A, p, C)
 
 
-@pytest.mark.parametrize("p,s", [(65521, 32640), (131071, 65408), (8388593, 4161408)])
+@pytest.mark.parametrize("p,s", [(65521, 32640), (131071, 65341), (8388593, 4161408)])
 def test_pair_exact_at_fp32_bound(p, s):
     n, k = 520, 4096 + 64
     sign = np.where((np.arange(n)[:, None] + np.arange(k)[None, :]) % 3 == 0, -1, 1)

@@ -95,3 +95,12 @@ def test_same_weight_pairs_share_a_unit_for_short_k():
     assert units == 3
     segs = ffsyrk.leaf_schedule(8388593, 4)
     assert sum(1 for s in segs if s[4]) == 5   # one unit per weight class, D = 3
+
+
+@pytest.mark.parametrize("p,s", [(509, 254), (521, 128), (131321, 65341), (131357, 32640),
+                                 (65521, 32640), (131071, 65341), (8388593, 4161408)])
+def test_bound_residues_reach_every_digit_bound(p, s):
+    # the GPU tests' extreme inputs: every digit of s sits at its bound
+    bounds = ffsyrk.digit_bounds(p)
+    d = balanced_digits(s, len(bounds), ffsyrk.digit_base(p))
+    assert [abs(x) for x in d] == bounds
