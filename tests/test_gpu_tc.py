@@ -2,8 +2,9 @@
 
 The leaf accumulates bf16 digit products in FP32 over K-chunks sized so that
 |partial sum| ≤ 2^24.  These inputs put every digit at its largest magnitude
-with one sign, so every chunk sum lands exactly on ±2^24: any loss of
-integer precision in the tensor-core accumulation would show up here.
+with one sign, so every chunk sum reaches its unit's limit (exactly ±2^24
+for byte digits at p = 65521): any loss of integer precision in the
+tensor-core accumulation would show up here.
 """
 import numpy as np
 import pytest
