@@ -340,7 +340,7 @@ typedef struct {
     int32_t y_cost;      /* y of Thm 4.1: 1, 2 or 3                       */
     int32_t leaf;        /* ffsyrk_leaf_t actually used                   */
     int32_t levels;      /* recursion levels L for max_n × max_k          */
-    int32_t digits;      /* D, signed base-256 digits per residue          */
+    int32_t digits;      /* D, signed digits per residue (ffsyrk_digit_base) */
     int32_t chunk_k[9];  /* K-chunk per digit pair (i*3+j), TC leaf       */
     int64_t workspace_bytes;
     int32_t tile_ctas;   /* 1 or 2: SMs per tensor-core leaf tile at max_n  */

@@ -69,7 +69,7 @@ struct YConst {
     MulConst b;  // b (form 1)
 };
 
-// Signed base-256 digits of the symmetric residue and the per-pair
+// Signed digits of the symmetric residue and the per-pair
 // chunk lengths that keep every FP32 partial sum an exact integer.
 // Residues in signed form s ∈ [−(p−1)/2, (p−1)/2] are written as
 // s = Σ_t d_t·base^t with D signed digits, every |d_t| ≤ 256 (exact in bf16).
@@ -334,7 +334,8 @@ int leaf_tc2_bm();
 int leaf_tc2_bn();
 int leaf_i64_tile();
 
-// The signed base-256 digit scheme and chunk lengths the planner uses for p.
+// The signed digit scheme (base 256, or a balanced base) and chunk lengths
+// the planner uses for p.
 DigitScheme digit_scheme_for(uint32_t p);
 
 // A kernel whose bounded wait runs out (after limit_ns) and records it in err.

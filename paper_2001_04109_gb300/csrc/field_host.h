@@ -3,7 +3,7 @@
 // Primality (deterministic Miller-Rabin), Legendre symbols, Tonelli-Shanks
 // square roots, a square root of −1 (Prop. 3.2), the sum-of-two-squares
 // decomposition a² + b² ≡ −1 (Algorithm 3, "SoS"), the p ≡ 3 (mod 8) case
-// a = 1, b = √−2 (proof of Thm 4.1), and the signed base-256 digit scheme
+// a = 1, b = √−2 (proof of Thm 4.1), and the signed byte-digit split
 // with the chunk lengths that keep FP32 tensor-core sums exact.
 #pragma once
 #include <stdint.h>

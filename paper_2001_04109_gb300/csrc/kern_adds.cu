@@ -2,7 +2,8 @@
 //
 //  * prep: the 4 pre-additions S1 = (A21 − A11)·Y, S2 = A22 − A21·Y,
 //    S3 = S1 − A22, S4 = S3 + A12 of every node of one recursion depth, fused
-//    with the signed base-256 digit split that feeds the leaf products.
+//    with the signed digit split (base 256, or the balanced base of some
+//    two-digit primes) that feeds the leaf products.
 //  * digitize: the digit split alone, for the classical path's operands.
 //  * post: the post-additions Low(U1) = Low(P1 + P5), Low(U3) = Low(P1 + P2),
 //    Up(U1) = Low(U1)ᵀ, U2 = U1 + P4, U4 = U2 + P3, Low(U5) = Low(U2 + P4ᵀ),
