@@ -7,6 +7,7 @@ k-block) is accumulated exactly once.  The digit bounds themselves are
 checked by brute force over all symmetric residues of small primes and at
 the extremes of the large ones.
 """
+import numpy as np
 import pytest
 
 import __graft_entry__
@@ -104,3 +105,21 @@ def test_bound_residues_reach_every_digit_bound(p, s):
     bounds = ffsyrk.digit_bounds(p)
     d = balanced_digits(s, len(bounds), ffsyrk.digit_base(p))
     assert [abs(x) for x in d] == bounds
+
+
+@pytest.mark.parametrize("p", [251, 509, 521, 65521, 131071, 131357, 8388593, 16777213])
+def test_digit_products_rebuild_the_product(p):
+    # Σ_{i,j} b^{i+j}·D_i·D_jᵀ = S·Sᵀ over the integers (S the signed
+    # residues), hence ≡ X·Xᵀ mod p with the weights b^{i+j} taken mod p
+    b = ffsyrk.digit_base(p)
+    D = len(ffsyrk.digit_bounds(p))
+    rng = np.random.default_rng(p)
+    X = rng.integers(0, p, size=(6, 9)).astype(object)
+    h = (p - 1) // 2
+    S = np.where(X > h, X - p, X)
+    digits = np.array([[balanced_digits(int(s), D, b) for s in row] for row in S], dtype=object)
+    Dt = [digits[:, :, t] for t in range(D)]
+    exact = sum(b ** (i + j) * Dt[i].dot(Dt[j].T) for i in range(D) for j in range(D))
+    assert np.array_equal(exact, S.dot(S.T))
+    weighted = sum(pow(b, i + j, p) * Dt[i].dot(Dt[j].T) for i in range(D) for j in range(D))
+    assert np.array_equal(weighted % p, X.dot(X.T) % p)
