@@ -153,7 +153,10 @@ ffsyrk_status_t ffsyrk_host(ffsyrk_plan_t plan, ffsyrk_uplo_t uplo, int64_t n, i
                             ffsyrk_stream_t stream);
 
 /* C = A·Aᵀ mod p with default options, through an internal per-device plan
- * cache keyed by (p, shape).  Thread-safe. */
+ * cache keyed by (p, shape): at most 8 plans, the least recently used one
+ * released first.  If a new plan's workspace cannot be allocated, the cache
+ * releases this device's plans (waiting for their work) and tries once more.
+ * Thread-safe. */
 ffsyrk_status_t ffsyrk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p, const uint32_t *A,
                        int64_t lda, uint32_t *C, int64_t ldc, ffsyrk_stream_t stream);
 
@@ -280,8 +283,8 @@ ffsyrk_status_t ffherk_with_plan(ffherk_plan_t plan, ffsyrk_uplo_t uplo, int64_t
                                  int64_t ldc, ffsyrk_stream_t stream);
 /* ffsyrk_sync_status for both of the plan's parts. */
 ffsyrk_status_t ffherk_sync_status(ffherk_plan_t plan, ffsyrk_stream_t stream);
-/* The same through an internal cache of plans keyed by (device, p, r, n, k).
- * Thread-safe. */
+/* The same through an internal cache of plans keyed by (device, p, r, n, k):
+ * at most 4, released as in ffsyrk's cache.  Thread-safe. */
 ffsyrk_status_t ffherk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint32_t p, uint32_t r,
                        const uint32_t *A, int64_t lda, uint32_t *Cre, uint32_t *Cim, int64_t ldc,
                        ffsyrk_stream_t stream);

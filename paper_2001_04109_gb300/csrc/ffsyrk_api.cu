@@ -2261,6 +2261,21 @@ ffsyrk_status_t cached_plan(uint32_t p, int64_t n, int64_t kcap, ffsyrk_plan_t *
         }
         ffsyrk_plan_t pl = nullptr;
         ffsyrk_status_t s = ffsyrk_plan(&pl, p, n, kcap, nullptr);
+        if (s == FFSYRK_ERR_ALLOC) {
+            // the workspaces of this device's cached plans may hold the
+            // memory: release them and try once more
+            bool freed = false;
+            for (auto jt = g_cache.begin(); jt != g_cache.end();) {
+                if (std::get<0>(jt->first) == dev) {
+                    ffsyrk_plan_destroy(jt->second.plan);
+                    jt = g_cache.erase(jt);
+                    freed = true;
+                } else {
+                    ++jt;
+                }
+            }
+            if (freed) s = ffsyrk_plan(&pl, p, n, kcap, nullptr);
+        }
         if (s != FFSYRK_SUCCESS) return s;
         it = g_cache.emplace(key, CacheEntry{pl, 0}).first;
     }
@@ -2422,6 +2437,20 @@ extern "C" ffsyrk_status_t ffherk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint
         }
         ffherk_plan_t hp = nullptr;
         s = ffherk_plan(&hp, p, r, n, k, nullptr);
+        if (s == FFSYRK_ERR_ALLOC && !g_herk_cache.empty()) {
+            // release this device's cached HERK plans and try once more
+            bool freed = false;
+            for (auto jt = g_herk_cache.begin(); jt != g_herk_cache.end();) {
+                if (std::get<0>(jt->first) == dev) {
+                    ffherk_plan_destroy(jt->second.first);
+                    jt = g_herk_cache.erase(jt);
+                    freed = true;
+                } else {
+                    ++jt;
+                }
+            }
+            if (freed) s = ffherk_plan(&hp, p, r, n, k, nullptr);
+        }
         if (s != FFSYRK_SUCCESS) return s;
         it = g_herk_cache.emplace(key, std::make_pair(hp, uint64_t(0))).first;
     }
