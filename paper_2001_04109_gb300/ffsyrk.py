@@ -228,8 +228,10 @@ class Plan:
         return C
 
     def host(self, A: torch.Tensor, C: torch.Tensor, uplo: str = "lower", stream=None) -> torch.Tensor:
-        """C = A·Aᵀ mod p for CPU tensors A (n × k) and C (n × n): copies in, computes, copies the
-        triangle back, all enqueued on ``stream`` (pin both tensors for asynchronous copies)."""
+        """C = A·Aᵀ mod p for CPU tensors A (n × k) and C (n × n): copies A in, computes, and copies
+        the n × n result back (the triangle ``uplo``, zeros in the other strict triangle), all
+        enqueued on ``stream``; pin both tensors for asynchronous copies, and synchronise the
+        stream before reading C."""
         if A.is_cuda or C.is_cuda:
             raise ValueError("host() takes CPU tensors")
         n, k = A.shape
