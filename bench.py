@@ -32,16 +32,16 @@ UNIT = "ops/s"
 WORKLOADS = {
     # name: (n, k, p, description)
     "square4096": (4096, 4096, 65521,
-                   "fast recursive A·Aᵀ mod p, A 4096×4096 uint32 uniform in [0,p), p=65521"),
-    "small256": (256, 256, 65521, "classical A·Aᵀ mod p, A 256×256, p=65521"),
-    "tall": (16384, 4096, 131071, "fast A·Aᵀ mod p, A 16384×4096, p=131071 (2×2 Y)"),
-    "wide": (4096, 16384, 131071, "fast A·Aᵀ mod p, A 4096×16384, p=131071 (2×2 Y)"),
-    "odd": (16383, 4097, 131071, "fast A·Aᵀ mod p, A 16383×4097, p=131071 (2×2 Y, padding)"),
-    "square8192": (8192, 8192, 65521, "fast A·Aᵀ mod p, A 8192×8192, p=65521"),
-    "square16384": (16384, 16384, 65521, "fast A·Aᵀ mod p, A 16384×16384, p=65521"),
-    "large": (32768, 32768, 8388593, "fast A·Aᵀ mod p, A 32768×32768, p=8388593 (D=3)"),
+                   "A·Aᵀ mod p, A 4096×4096 uint32 uniform in [0,p), p=65521"),
+    "small256": (256, 256, 65521, "A·Aᵀ mod p, A 256×256, p=65521"),
+    "tall": (16384, 4096, 131071, "A·Aᵀ mod p, A 16384×4096, p=131071 (2×2 Y)"),
+    "wide": (4096, 16384, 131071, "A·Aᵀ mod p, A 4096×16384, p=131071 (2×2 Y)"),
+    "odd": (16383, 4097, 131071, "A·Aᵀ mod p, A 16383×4097, p=131071 (2×2 Y, padding)"),
+    "square8192": (8192, 8192, 65521, "A·Aᵀ mod p, A 8192×8192, p=65521"),
+    "square16384": (16384, 16384, 65521, "A·Aᵀ mod p, A 16384×16384, p=65521"),
+    "large": (32768, 32768, 8388593, "A·Aᵀ mod p, A 32768×32768, p=8388593 (D=3)"),
 }
-DEFAULT_WORKLOAD = "square4096"
+DEFAULT_WORKLOAD = "large"
 # 2048 independent problems, n and k each log-uniform in [32, 2048] (seed 5), p = 65521
 BATCH = {"count": 2048, "lo": 32, "hi": 2048, "seed": 5, "p": 65521,
          "description": "batched A·Aᵀ mod p: 2048 problems, n, k log-uniform in [32, 2048], p=65521"}
@@ -171,8 +171,14 @@ def max_over_ranks(x: float, ws: int) -> float:
     return float(t.item())
 
 
-def cpu_oracle_rate(A_np, p, budget_s: float):
-    """Time the schoolbook oracle on a bounded row sample; effective n²k/s of the full product."""
+def cpu_oracle_rate(A_np, p, budget_s: float, keep_rows: bool = False):
+    """Time the schoolbook oracle on a bounded row sample; effective n²k/s of the full product.
+
+    The sample is rows spread evenly over A; their time is scaled (an
+    extrapolation) to the n(n+1)/2 dot products of the lower triangle.  With
+    ``keep_rows`` the sampled rows and their oracle values come back too,
+    for the bit-exactness check of the GPU result.
+    """
     import numpy as np
 
     import oracle
@@ -186,15 +192,19 @@ def cpu_oracle_rate(A_np, p, budget_s: float):
     t_cal = max(time.perf_counter() - t0, 1e-6)
     per_row = t_cal / r0
     r = int(max(r0, min(rows_total, budget_s / per_row)))
-    rows = np.linspace(0, n - 1, r).astype(np.int64)
+    rows = np.unique(np.linspace(0, n - 1, r).astype(np.int64))
+    r = len(rows)
     t0 = time.perf_counter()
-    oracle.syrk_rows(A_np, p, rows, threads=threads)
+    vals = oracle.syrk_rows(A_np, p, rows, threads=threads)
     dt = time.perf_counter() - t0
     # a full row is n dot products; the lower product needs n(n+1)/2 of them
     t_full = dt / (r * n) * (n * (n + 1) / 2)
-    return {"value": n * n * k / t_full, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{r} full rows of A·Aᵀ mod p ({r * n} entries, {dt:.1f} s), "
-                      f"scaled to the {n}×{n} lower triangle"}
+    out = {"value": n * n * k / t_full, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{r} full rows of A·Aᵀ mod p spread over A ({r * n} entries, {dt:.1f} s), "
+                     f"time extrapolated to the {n}×{n} lower triangle"}
+    if keep_rows:
+        return out, rows, vals
+    return out
 
 
 def run_reference(args):
@@ -227,7 +237,11 @@ def run_reference(args):
         print(json.dumps(line), flush=True)
         return 0
     n, k, p, desc = WORKLOADS[args.workload]
-    A = inputs.uniform_residues(n, k, p, seed=2).numpy().view(np.uint32)
+    # the input is drawn on the GPU when there is one (same bits, much
+    # faster for A 32768²); only the oracle's rows are timed
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    A = inputs.uniform_residues(n, k, p, seed=2, device=dev).cpu().numpy().view(np.uint32)
     vals = []
     base = None
     for s in range(args.warmup + args.steps):
@@ -282,6 +296,66 @@ def time_plan(plan, A, C, steps, warmup, flush, stream, timing=True):
     return ms, stage
 
 
+def golden_digest(n, k, p, seed=2):
+    """The oracle's SHA-256 of the whole lower triangle, if tests/golden holds it."""
+    path = os.path.join(ROOT, "tests", "golden", "fullsize_sha256.txt")
+    try:
+        for line in open(path):
+            f = line.split()
+            if len(f) == 5 and f[:4] == [str(n), str(k), str(p), str(seed)]:
+                return f[4]
+    except OSError:
+        pass
+    return None
+
+
+def lower_digest(C_host):
+    """SHA-256 of the lower triangle, rows in order, entries uint32 little-endian."""
+    import numpy as np
+    C = np.ascontiguousarray(C_host.numpy().view(np.uint32).astype("<u4", copy=False))
+    h = hashlib.sha256()
+    for i in range(C.shape[0]):
+        h.update(C[i, : i + 1].tobytes())
+    return h.hexdigest()
+
+
+def describe(desc, info):
+    """The workload's description with the depth and Winograd levels the plan took."""
+    L = info["levels"]
+    wg = info["winograd"][:L]
+    if L == 0:
+        how = "classical leaves only (depth 0)"
+    else:
+        how = f"Algorithm 2 at depth {L}"
+        if any(wg):
+            how += f", Algorithm 1 levels {wg} for the general products by depth"
+    return f"{desc}; {how}"
+
+
+def copy_ceiling(n, k, stream, reps=3):
+    """Plain pinned-memory copies of one step's input (H2D) and result (D2H): ms each."""
+    import torch
+    a_h = torch.empty((n, k), dtype=torch.int32).pin_memory()
+    c_h = torch.empty((n, n), dtype=torch.int32).pin_memory()
+    a_d = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    c_d = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    out = {}
+    for name, dst, src in (("h2d_ms", a_d, a_h), ("d2h_ms", c_h, c_d)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+        out[name] = statistics.median(t)
+    del a_h, c_h, a_d, c_d
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -300,8 +374,10 @@ def run_ours(args):
     if levels is None and args.workload == "small256":
         levels = 0
     stream = torch.cuda.current_stream()
-    A_host = inputs.uniform_residues(n, k, p, seed=2)
-    A = A_host.cuda()
+    # the same bits on host and device (counter-based generator); drawn on
+    # the device, then copied, which is much faster for A 32768²
+    A = inputs.uniform_residues(n, k, p, seed=2, device="cuda")
+    A_host = A.cpu()
     C = torch.zeros((n, n), dtype=torch.int32, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
@@ -318,10 +394,10 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
-    step_ms = sum(ms) / len(ms)
+    step_ms = statistics.median(ms)
     step_ms = max_over_ranks(step_ms, ws)
     value = ws * n * n * k / (step_ms * 1e-3)
-    leaf_ms = statistics.mean(s["leaf_ms"] for s in stage)
+    leaf_ms = statistics.median(s["leaf_ms"] for s in stage)
     tmacs = stage[-1]["field_macs"] * info["digits"] ** 2
     launches = stage[-1]["launches"]
 
@@ -341,29 +417,56 @@ def run_ours(args):
                 "peak_source": f"{peak_src} {'sustained' if long_step else 'burst'} bf16 dense",
                 "algorithmic_flops_per_launch": 2.0 * tmacs,
                 "leaf_ms": leaf_ms,
-                "stage_ms": {"prep": statistics.mean(s["prep_ms"] for s in stage),
+                "stage_ms": {"prep": statistics.median(s["prep_ms"] for s in stage),
                              "leaf": leaf_ms,
-                             "post": statistics.mean(s["post_ms"] for s in stage)}}
+                             "post": statistics.median(s["post_ms"] for s in stage)}}
 
-    # bit-exactness on sampled rows against the oracle (not timed)
-    parity = None
-    if not args.no_check and rank == 0:
-        import oracle
-        rows = np.unique(np.linspace(0, n - 1, 8).astype(np.int64))
-        want = oracle.syrk_rows(A_host.numpy(), p, rows)
-        got = C.cpu().numpy().view(np.uint32)[rows]
-        ok = all(np.array_equal(got[t, : r + 1], want[t, : r + 1]) for t, r in enumerate(rows))
-        parity = {"rows_checked": int(len(rows)), "bit_exact": bool(ok)}
+    # bit-exactness (not timed): the whole lower triangle against the
+    # oracle's stored digest where tests/golden has one, and the rows the CPU
+    # baseline computes with the oracle below
+    C_res = C.cpu() if rank == 0 and not args.no_check else None
+    plan.close()
+    del plan
+
+    # comparators: classical SYRK from the same leaves; the int64 CUDA-core leaf
+    compare = {}
+    if not args.no_compare:
+        legs = [("classical_tc", "tc", 0, None), ("fast_i64", "i64", levels, None),
+                ("classical_i64", "i64", 0, None)]
+        if any(info["winograd"]):
+            # the same depth with the general products computed classically
+            legs.append(("fast_tc_no_winograd", "tc", info["levels"], 0))
+        for name, leaf, lv, wg in legs:
+            if name.endswith("i64") and n * n * k > 2 ** 40:
+                continue
+            pl = ffsyrk.Plan(p, n, k, leaf=leaf, levels=lv, winograd=wg,
+                             tile_ctas=args.tile_ctas if wg == 0 else None)
+            st = max(3, min(args.steps, 5))
+            cms, cstage = time_plan(pl, A, C, st, 2, flush, stream)
+            cm = statistics.median(cms)
+            compare[name] = {"value": n * n * k / (cm * 1e-3), "ms_per_step": cm,
+                             "levels": pl.info()["levels"],
+                             "winograd": pl.info()["winograd"][: pl.info()["levels"]],
+                             "leaf_ms": statistics.median(s["leaf_ms"] for s in cstage)}
+            pl.close()
 
     # end to end through the C ABI with host buffers (ffsyrk_host): every step
     # copies its input from pinned host memory, runs the product and copies
-    # the result's triangle back, all inside the library call; consecutive
-    # steps go to alternating plans on their own streams (one plan per call in
-    # flight), so one step's copies overlap another's compute; the value is
-    # steps / (first call's start .. last copy's end)
+    # the result back, all inside the library call; consecutive steps go to
+    # rotating plans on their own streams (one plan per call in flight), so
+    # one step's copies overlap another's compute; the value is steps / (first
+    # call's start .. last copy's end).  As many plans as fit the free device
+    # memory (each holds its workspace and device copies of A and C), 1 to 3.
     e2e = None
     if not args.no_e2e:
-        nfly = 3 if n < 16384 else 2
+        del C
+        torch.cuda.empty_cache()
+        ws_b, slot_b = ffsyrk.workspace_query(p, n, k, leaf=args.leaf, levels=levels,
+                                              tile_ctas=args.tile_ctas, winograd=args.winograd)
+        need = ws_b + slot_b + 4 * n * (k + 3) + 4 * n * n
+        free, _ = torch.cuda.mem_get_info()
+        nfly = int(max(1, min(3, (0.9 * free) // need)))
+        ceiling = copy_ceiling(n, k, stream)
         A_pin = A_host.pin_memory()
         C_pins = [torch.empty((n, n), dtype=torch.int32).pin_memory() for _ in range(nfly)]
         plans = [ffsyrk.Plan(p, n, k, leaf=args.leaf, levels=levels, tile_ctas=args.tile_ctas,
@@ -387,61 +490,63 @@ def run_ours(args):
             torch.cuda.synchronize()
             return t0.elapsed_time(t1)
 
+        nst = max(nfly, args.steps)
         pipelined(max(nfly, args.warmup))
-        e_total = pipelined(max(nfly, args.steps))
-        e_ms = e_total / max(nfly, args.steps)
+        e_ms = pipelined(nst) / nst
         for pl_ in plans:
             pl_.sync_status()
             pl_.close()
+        del plans, C_pins
+        torch.cuda.empty_cache()
         e2e = {"value": ws * n * n * k / (e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": n * k * 4, "d2h_bytes_per_step": n * n * 4,
                "ms_per_step": e_ms,
+               "copy_ceiling": {**ceiling,
+                                "bound_ms": max(step_ms, ceiling["h2d_ms"], ceiling["d2h_ms"]),
+                                "what": "plain pinned cudaMemcpyAsync of one step's A (H2D) and "
+                                        "n×n C (D2H); with copies overlapping compute a step "
+                                        "cannot beat the largest of those and the device step"},
                "pipeline": f"ffsyrk_host (copy A in, product, copy C out) on pinned host "
-                           f"buffers, {nfly} plans and streams in rotation: one step's copies "
-                           "overlap another's product"}
+                           f"buffers, {nfly} plan(s) and stream(s) in rotation: one step's "
+                           "copies overlap another's product"}
 
-    # comparators: classical SYRK from the same leaves; the int64 CUDA-core leaf
-    compare = {}
-    if not args.no_compare:
-        legs = [("classical_tc", "tc", 0, None), ("fast_i64", "i64", levels, None),
-                ("classical_i64", "i64", 0, None)]
-        if any(info["winograd"]):
-            # the same depth with the general products computed classically
-            legs.append(("fast_tc_no_winograd", "tc", info["levels"], 0))
-        for name, leaf, lv, wg in legs:
-            if name.endswith("i64") and n * n * k > 2 ** 40:
-                continue
-            pl = ffsyrk.Plan(p, n, k, leaf=leaf, levels=lv, winograd=wg,
-                             tile_ctas=args.tile_ctas if wg == 0 else None)
-            st = max(2, min(args.steps, 5))
-            cms, cstage = time_plan(pl, A, C, st, 2, flush, stream)
-            cm = sum(cms) / len(cms)
-            compare[name] = {"value": n * n * k / (cm * 1e-3), "ms_per_step": cm,
-                             "levels": pl.info()["levels"],
-                             "leaf_ms": statistics.mean(s["leaf_ms"] for s in cstage)}
-            pl.close()
-
-    cpu = None
-    if rank == 0 and not args.no_cpu:
-        cpu = cpu_oracle_rate(A_host.numpy().view(np.uint32), p, budget_s=args.cpu_budget)
+    cpu, parity = None, None
+    if rank == 0:
+        rows = vals = None
+        if not args.no_cpu:
+            cpu, rows, vals = cpu_oracle_rate(A_host.numpy().view(np.uint32), p,
+                                              budget_s=args.cpu_budget, keep_rows=True)
+        if C_res is not None:
+            parity = {}
+            if rows is not None:
+                got = C_res.numpy().view(np.uint32)[rows]
+                ok = all(np.array_equal(got[t, : r + 1], vals[t, : r + 1])
+                         for t, r in enumerate(rows))
+                parity["rows_checked"] = int(len(rows))
+                parity["rows_bit_exact"] = bool(ok)
+            want = golden_digest(n, k, p)
+            if want is not None:
+                parity["triangle_sha256_matches_oracle"] = lower_digest(C_res) == want
+            parity["bit_exact"] = all(v for kk, v in parity.items() if kk != "rows_checked")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "u32", "data": "synthetic",
-                "config": {"workload": args.workload, "description": desc, "n": n, "k": k,
-                           "p": p, "levels": info["levels"], "digits": info["digits"],
+                "config": {"workload": args.workload, "description": describe(desc, info),
+                           "n": n, "k": k, "p": p, "levels": info["levels"],
+                           "digits": info["digits"],
                            "winograd": info["winograd"][: info["levels"]],
                            "leaf": {1: "tc_bf16", 2: "i64"}[info["leaf"]],
                            "tile_ctas": info["tile_ctas"],
                            "y_form": "scalar" if info["y_form"] == 0 else "2x2",
                            "l2": "flushed between steps (512 MiB write)",
+                           "timing": "median of the timed steps",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "e2e": e2e, "gpu_launches": launches * args.steps, "roofline": roofline,
                 "cpu_baseline": cpu, "clocks": clocks, "parity": parity, "compare": compare}
         print(json.dumps(line), flush=True)
-    plan.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0

@@ -301,19 +301,24 @@ ffsyrk_status_t ffsyrk_batched(ffsyrk_uplo_t uplo, int64_t count, const int64_t 
 /* C = A·Aᵀ mod p (triangle `uplo`) without allocating any memory.
  *
  * The paper has no counterpart: this is a deployment variant of the
- * classical path (levels = 0, tensor-core leaf).  It is for callers that
- * must not allocate device memory at call time: applications whose pool
- * allocator owns all device memory, processes under a fixed memory budget,
- * or latency-critical code where cudaMalloc/cudaFree (which can synchronise
- * the device) are not acceptable.  It calls no cudaMalloc, cudaFree or other
- * allocating routine; its scratch is one array compiled into the library
- * (64 MiB of digit planes + 1 MiB of launch descriptors) that every GPU which
- * loads the library holds until the process exits.
+ * classical path (levels = 0, tensor-core leaf, one-SM tiles).  It is for
+ * callers that must not allocate device memory at call time: applications
+ * whose pool allocator owns all device memory, processes under a fixed
+ * memory budget, or latency-critical code where cudaMalloc/cudaFree (which
+ * can synchronise the device) are not acceptable.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine; its scratch is one array compiled
+ * into the library (64 MiB of digit planes + 2 MiB of launch descriptors and
+ * tile list) that every GPU which loads the library holds until the process
+ * exits.  It copies nothing from host memory (its descriptors reach the GPU
+ * as a kernel parameter), so a call does not wait for earlier work on
+ * `stream`.
  *
- * Limits: the digit planes of A must fit, i.e.
- * D · roundup(n,256) · roundup(k,64) · 2 bytes ≤ 64 MiB, where D is the digit
- * count of p (2 for p < 2^17, 3 above; e.g. n = k = 4096 with D = 2); larger
- * shapes return FFSYRK_ERR_TOO_LARGE before anything is enqueued.
+ * Limits (FFSYRK_ERR_TOO_LARGE before anything is enqueued):
+ *   - the digit planes of A must fit:
+ *     D · roundup(n,256) · roundup(k,64) · 2 bytes ≤ 64 MiB, where D is the
+ *     digit count of p (2 for p < 2^17, 3 above; e.g. n = k = 4096, D = 2);
+ *   - the stored triangle must cover at most 130432 output tiles of
+ *     128 × 256 (n ≤ 92288 for the lower triangle, whatever k).
  *
  * Set-up: the first call on each device resolves the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
@@ -383,6 +388,35 @@ typedef struct {
 /* Timing of the most recent call with timing enabled: waits for its last
  * event.  FFSYRK_ERR_INVALID_ARG if timing is off or no call was made. */
 ffsyrk_status_t ffsyrk_plan_get_timing(ffsyrk_plan_t plan, ffsyrk_timing_t *timing);
+
+/* Throughput probe of an arithmetic pipe a leaf can use (the paper has no
+ * counterpart; it measures the roofline denominators that no measured peak
+ * on file covers).  Enqueues on `stream` one launch of `blocks` × 256
+ * threads, each running `iters` rounds (≤ 2^24) of 8 independent
+ * multiply-add chains on register operands:
+ *   kind 0: mma.sync.m16n8k32 s8·s8 → s32;  1: u8·s8 → s32;  2: u8·u8 → s32;
+ *   kind 3: mad.wide.u32 (32 × 32 → 64 bits, CUDA cores);
+ *   kind 4: mma.sync.m16n8k16 bf16·bf16 → f32.
+ * *macs receives the multiply-adds the launch performs (time it with events
+ * on `stream`).  `sink` is a device word the kernel may xor into.  Invalid
+ * arguments return FFSYRK_ERR_INVALID_ARG before any launch. */
+ffsyrk_status_t ffsyrk_probe_pipe(int32_t kind, int64_t iters, int32_t blocks, uint32_t *sink,
+                                  ffsyrk_stream_t stream, double *macs);
+
+/* Failure-injection hook for tests (the paper has no counterpart): after
+ * `skip` more successful device allocations of plan creation (a plan's
+ * workspace and shared-tile slots), the next `count` such allocations fail
+ * as if the device were out of memory, and ffsyrk_plan (or the plan cache
+ * behind ffsyrk) sees FFSYRK_ERR_ALLOC.  count = 0 clears the hook.  Returns
+ * the failures that were still pending.  Process-wide; nothing is enqueued. */
+int32_t ffsyrk_test_inject_alloc_failure(int32_t skip, int32_t count);
+
+/* The plan cache behind ffsyrk(), ffsyrk_update() and the scaled entry
+ * points: *plans = the plans it holds for the current device; *releases =
+ * how often (process-wide) a plan creation that failed with
+ * FFSYRK_ERR_ALLOC made it release the device's cached plans and try once
+ * more.  Either pointer may be NULL. */
+ffsyrk_status_t ffsyrk_cache_info(int32_t *plans, int64_t *releases);
 
 /* Failure-detection self-test (the paper has no counterpart): enqueue on
  * `stream` a kernel whose bounded device-side wait runs out after limit_ns

@@ -1680,6 +1680,29 @@ ffsyrk_status_t ffsyrk_workspace_query(uint32_t p, int64_t max_n, int64_t max_k,
 }
 
 namespace {
+// Injected allocation failures (ffsyrk_test_inject_alloc_failure): after
+// g_fail_skip more successful plan allocations, the next g_fail_count fail.
+std::mutex g_fail_mu;
+int g_fail_skip = 0, g_fail_count = 0;
+
+// cudaMalloc of a plan's device memory at creation (workspace, shared-tile
+// slots), through the failure-injection hook.
+cudaError_t plan_malloc(void **ptr, size_t bytes) {
+    {
+        std::lock_guard<std::mutex> lk(g_fail_mu);
+        if (g_fail_count > 0) {
+            if (g_fail_skip > 0) {
+                --g_fail_skip;
+            } else {
+                --g_fail_count;
+                *ptr = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+        }
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
 ffsyrk_status_t plan_create(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int64_t max_k,
                             const ffsyrk_options_t *opts, bool gemmt) {
     if (!plan) return FFSYRK_ERR_INVALID_ARG;
@@ -1712,7 +1735,7 @@ ffsyrk_status_t plan_create(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
     pl->data_cap = data;
     pl->desc_cap = desc;
     pl->ws_bytes = data + desc;
-    cudaError_t e = cudaMalloc(&pl->ws, (size_t)pl->ws_bytes);
+    cudaError_t e = plan_malloc(reinterpret_cast<void **>(&pl->ws), (size_t)pl->ws_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         destroy_plan(pl);
@@ -1723,7 +1746,7 @@ ffsyrk_status_t plan_create(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
         // more than the units of all tiles at the largest shape
         pl->part_slots = part_slots_for(pl, sms);
         const size_t bytes = (size_t)pl->part_slots * leaf_tc_bm() * leaf_tc_bn() * 4;
-        if (cudaMalloc(&pl->part, bytes) != cudaSuccess) {
+        if (plan_malloc(reinterpret_cast<void **>(&pl->part), bytes) != cudaSuccess) {
             cudaGetLastError();
             destroy_plan(pl);
             return FFSYRK_ERR_ALLOC;
@@ -1961,6 +1984,7 @@ struct CacheEntry {
 std::mutex g_cache_mu;
 std::map<std::tuple<int, uint32_t, int64_t, int64_t>, CacheEntry> g_cache;
 uint64_t g_clock = 0;
+int64_t g_cache_releases = 0;  // times a failed allocation released the device's cached plans
 constexpr size_t kCacheMax = 8;
 }  // namespace
 
@@ -2243,6 +2267,35 @@ extern "C" ffsyrk_status_t ffsyrk(ffsyrk_uplo_t uplo, int64_t n, int64_t k, uint
     return ffsyrk_update(uplo, n, k, p, 1u, A, lda, 0u, C, ldc, stream);
 }
 
+extern "C" ffsyrk_status_t ffsyrk_probe_pipe(int32_t kind, int64_t iters, int32_t blocks,
+                                             uint32_t *sink, ffsyrk_stream_t stream, double *macs) {
+    if (kind < 0 || kind > 4 || iters < 1 || iters > (int64_t(1) << 24) || blocks < 1 ||
+        blocks > (1 << 20) || !sink)
+        return FFSYRK_ERR_INVALID_ARG;
+    if (macs) *macs = probe_macs(kind, iters, blocks);
+    return cuda_status(launch_probe(kind, iters, blocks, reinterpret_cast<unsigned int *>(sink),
+                                    reinterpret_cast<cudaStream_t>(stream)));
+}
+
+extern "C" int32_t ffsyrk_test_inject_alloc_failure(int32_t skip, int32_t count) {
+    std::lock_guard<std::mutex> lk(g_fail_mu);
+    const int32_t pending = g_fail_count;
+    g_fail_skip = skip > 0 ? skip : 0;
+    g_fail_count = count > 0 ? count : 0;
+    return pending;
+}
+
+extern "C" ffsyrk_status_t ffsyrk_cache_info(int32_t *plans, int64_t *releases) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFSYRK_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    int32_t c = 0;
+    for (const auto &kv : g_cache) c += std::get<0>(kv.first) == dev ? 1 : 0;
+    if (plans) *plans = c;
+    if (releases) *releases = g_cache_releases;
+    return FFSYRK_SUCCESS;
+}
+
 namespace {
 // the cached plan for (device, p, n, kcap), made on first use; the cache
 // mutex must be held
@@ -2274,7 +2327,10 @@ ffsyrk_status_t cached_plan(uint32_t p, int64_t n, int64_t kcap, ffsyrk_plan_t *
                     ++jt;
                 }
             }
-            if (freed) s = ffsyrk_plan(&pl, p, n, kcap, nullptr);
+            if (freed) {
+                ++g_cache_releases;
+                s = ffsyrk_plan(&pl, p, n, kcap, nullptr);
+            }
         }
         if (s != FFSYRK_SUCCESS) return s;
         it = g_cache.emplace(key, CacheEntry{pl, 0}).first;

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <vector>
 
 namespace fsk {
@@ -216,6 +217,36 @@ struct LeafPiece {
     int16_t j, npieces;
 };
 
+// Per-device launch state of a kernel family (dynamic shared-memory opt-in,
+// occupancy): cudaFuncSetAttribute applies to the current device only, so a
+// launcher keeps one entry per device, filled on its first launch there
+// under the slot's mutex (calls may come from several host threads).
+constexpr int kMaxDevices = 64;
+struct DeviceOnce {
+    std::mutex mu;
+    bool done[kMaxDevices] = {};
+    int value[kMaxDevices] = {};
+};
+// Run init(&value) once for the current device; returns its error, and the
+// stored value through *value.  Devices beyond kMaxDevices are refused.
+template <class F>
+cudaError_t once_per_device(DeviceOnce &o, int *value, F init) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(o.mu);
+    if (!o.done[dev]) {
+        int v = 0;
+        e = init(&v);
+        if (e != cudaSuccess) return e;
+        o.value[dev] = v;
+        o.done[dev] = true;
+    }
+    if (value) *value = o.value[dev];
+    return cudaSuccess;
+}
+
 // ---- launchers (each returns cudaGetLastError() of its launch) ----
 // reduce_input: some node views may hold values ≥ p (views of the caller's A)
 cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_t w,
@@ -337,6 +368,10 @@ int leaf_i64_tile();
 // The signed digit scheme (base 256, or a balanced base) and chunk lengths
 // the planner uses for p.
 DigitScheme digit_scheme_for(uint32_t p);
+
+// Throughput probe of one arithmetic pipe (see kern_probe.cu): kind 0..4.
+cudaError_t launch_probe(int kind, int64_t iters, int blocks, unsigned int *sink, cudaStream_t st);
+double probe_macs(int kind, int64_t iters, int blocks);
 
 // A kernel whose bounded wait runs out (after limit_ns) and records it in err.
 cudaError_t launch_wait_selftest(unsigned int *err, unsigned long long limit_ns, cudaStream_t st);

@@ -401,15 +401,16 @@ int leaf_tc_bn() { return BN; }
 cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st) {
     if (L.ntiles == 0) return cudaSuccess;
     const int smem = STAGES * STAGE_BYTES + 1024;
-    static bool attr_done = false;
-    if (!attr_done) {
+    // the dynamic shared-memory opt-in, once per device
+    static DeviceOnce attr_once;
+    cudaError_t ea = once_per_device(attr_once, nullptr, [smem](int *) {
         cudaError_t e = cudaSuccess;
         for (auto fn : {k_leaf_tc<true, false, 8>, k_leaf_tc<false, false, 8>, k_leaf_tc<true, true, 8>,
                         k_leaf_tc<false, true, 8>, k_leaf_tc<true, false, 16>})
             if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
+        return e;
+    });
+    if (ea != cudaSuccess) return ea;
     const int nwork = L.entries ? L.nentries : L.ntiles;
     const int grid = nwork < num_sms ? nwork : num_sms;
     const bool lazy = L.max_units <= L.ds.lazy_units;

@@ -366,8 +366,10 @@ int leaf_tc2_bn() { return BN; }
 cudaError_t launch_leaf_tc2(const TcLaunch &L, int num_sms, cudaStream_t st) {
     if (L.ntiles == 0) return cudaSuccess;
     const int smem = STAGES * STAGE_BYTES + 1024;
-    static int max_pairs = 0;
-    if (max_pairs == 0) {
+    // the dynamic shared-memory opt-in and the pairs that fit at once, per device
+    static DeviceOnce attr_once;
+    int max_pairs = 0;
+    cudaError_t ea = once_per_device(attr_once, &max_pairs, [smem, num_sms](int *out) {
         cudaError_t e = cudaSuccess;
         for (auto fn : {k_leaf_tc2<true, false>, k_leaf_tc2<false, false>, k_leaf_tc2<true, true>, k_leaf_tc2<false, true>})
             if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -382,8 +384,10 @@ cudaError_t launch_leaf_tc2(const TcLaunch &L, int num_sms, cudaStream_t st) {
             cudaGetLastError();
             clusters = num_sms / 2;
         }
-        max_pairs = clusters;
-    }
+        *out = clusters;
+        return cudaSuccess;
+    });
+    if (ea != cudaSuccess) return ea;
     // with per-pair work lists the grid has exactly one pair per list
     const int pairs = L.entries ? L.nentries : (L.ntiles < max_pairs ? L.ntiles : max_pairs);
     const bool lazy = L.max_units <= L.ds.lazy_units;

@@ -36,7 +36,8 @@ EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsy
            "ffsyrk_update", "ffsyrkd_with_plan_update", "ffsyrkd_update", "ffsyrkd_factor",
            "ffsyrkbd_with_plan_update", "ffsyrkbd_update", "ffsyrkbd_factor",
            "ffsyrkbd_factor_device", "ffherk_plan", "ffherk_plan_destroy", "ffherk_with_plan",
-           "ffherk_sync_status", "ffherk", "ffsyrk_host", "ffsyrk_workspace_query"]
+           "ffherk_sync_status", "ffherk", "ffsyrk_host", "ffsyrk_workspace_query",
+           "ffsyrk_test_inject_alloc_failure", "ffsyrk_cache_info", "ffsyrk_probe_pipe"]
 
 
 class FfsyrkError(RuntimeError):
@@ -115,8 +116,15 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_host.restype = i32
             L.ffsyrk_workspace_query.argtypes = [u32, i64, i64, P(Options), i32, P(i64), P(i64)]
             L.ffsyrk_workspace_query.restype = i32
+            L.ffsyrk_test_inject_alloc_failure.argtypes = [i32, i32]
+            L.ffsyrk_test_inject_alloc_failure.restype = i32
+            L.ffsyrk_cache_info.argtypes = [P(i32), P(i64)]
+            L.ffsyrk_cache_info.restype = i32
+            L.ffsyrk_probe_pipe.argtypes = [i32, i64, i32, vp, vp, P(ctypes.c_double)]
+            L.ffsyrk_probe_pipe.restype = i32
             for name in ["ffherk_plan", "ffherk_plan_destroy", "ffherk_with_plan",
-                         "ffherk_sync_status", "ffherk", "ffsyrk_host", "ffsyrk_workspace_query"]:
+                         "ffherk_sync_status", "ffherk", "ffsyrk_host", "ffsyrk_workspace_query",
+           "ffsyrk_test_inject_alloc_failure", "ffsyrk_cache_info", "ffsyrk_probe_pipe"]:
                 getattr(L, name).restype = i32
             L.ffsyrk_noalloc.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk_batched.argtypes = [i32, i64, P(i64), P(i64), u32, P(vp), P(i64), P(vp),
@@ -539,3 +547,40 @@ def batched(As: list[torch.Tensor], p: int, Cs: list[torch.Tensor] | None = None
     _check(lib().ffsyrk_batched(UPPER if uplo == "upper" else LOWER, count, ns, ks, int(p), pas,
                                 ldas, pcs, ldcs, _stream_handle(stream)), "ffsyrk_batched")
     return Cs
+
+
+def inject_alloc_failure(skip: int = 0, count: int = 1) -> int:
+    """Test hook: after ``skip`` successful plan allocations, fail the next ``count``."""
+    return int(lib().ffsyrk_test_inject_alloc_failure(int(skip), int(count)))
+
+
+def cache_info() -> tuple[int, int]:
+    """(plans the ffsyrk() cache holds on this device, release-and-retry events so far)."""
+    plans, rel = ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().ffsyrk_cache_info(ctypes.byref(plans), ctypes.byref(rel)), "ffsyrk_cache_info")
+    return plans.value, rel.value
+
+
+PIPES = {"mma_s8s8": 0, "mma_u8s8": 1, "mma_u8u8": 2, "mad_wide_u32": 3, "mma_bf16": 4}
+
+
+def probe_pipe(kind: str, iters: int = 4096, blocks: int = 0, reps: int = 5) -> float:
+    """Measured multiply-adds per second of one arithmetic pipe (median of ``reps`` launches)."""
+    dev = torch.cuda.current_device()
+    if blocks <= 0:
+        blocks = 4 * torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    macs = ctypes.c_double()
+    times = []
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _check(lib().ffsyrk_probe_pipe(PIPES[kind], int(iters), int(blocks), sink.data_ptr(),
+                                       stream.cuda_stream, ctypes.byref(macs)), "ffsyrk_probe_pipe")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r:
+            times.append(e0.elapsed_time(e1))
+    times.sort()
+    return macs.value / (times[len(times) // 2] * 1e-3)

@@ -1,25 +1,29 @@
-"""The allocation-free entry point ffsyrk_noalloc against ffsyrk_with_plan (marked gpu).
+"""The allocation-free entry point ffsyrk_noalloc (marked gpu).
 
 ffsyrk_noalloc serves callers that must not allocate device memory when
-they call the library (its scratch is a fixed array inside the library).
+they call the library: its scratch is a fixed array inside the library.
 These tests call it through the C ABI twice in a row on different inputs and
-require every result to equal, bit for bit, what the planned entry point
-returns for the same input: the second call must not see anything left over
-from the first.  This file is collected last so that a run stopping at the
-first failure has already run every other test; it also passes on its own in
-a fresh process.
+require every result to equal, bit for bit, the oracle's schoolbook
+A·Aᵀ mod p and what the planned entry point returns for the same input: the
+second call must not see anything left over from the first.  They also check
+the size limits at their boundaries (the digit planes, and the number of
+tiles of the stored triangle) and that nothing outside the triangle is
+written.  This file is collected last so that a run stopping at the first
+failure has already run every other test; it also passes on its own in a
+fresh process.
 """
-import ctypes
-
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2001_04109_gb300 import ffsyrk, inputs
 
 pytestmark = pytest.mark.gpu
 
 SENTINEL = -559038737
+# one-SM tiles of 128 × 256; the tile list holds at most this many tiles
+TILE_LIMIT = (2 * 1024 * 1024 - (2048 + 1024 * 8)) // 16
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -38,59 +42,104 @@ def planned(A, p, uplo):
     return C.cpu()
 
 
+def call(n, k, p, A_ptr, lda, C_ptr, ldc, uplo="lower"):
+    return ffsyrk.lib().ffsyrk_noalloc(ffsyrk.UPPER if uplo == "upper" else ffsyrk.LOWER, n, k, p,
+                                       A_ptr, lda, C_ptr, ldc,
+                                       torch.cuda.current_stream().cuda_stream)
+
+
 def noalloc(A, p, uplo, ldc_pad=0):
     n, k = A.shape
     Cb = torch.full((n, n + ldc_pad), SENTINEL, dtype=torch.int32, device="cuda")
-    rc = ffsyrk.lib().ffsyrk_noalloc(ffsyrk.UPPER if uplo == "upper" else ffsyrk.LOWER, n, k, p,
-                                     A.data_ptr(), A.stride(0), Cb.data_ptr(), Cb.stride(0),
-                                     torch.cuda.current_stream().cuda_stream)
+    rc = call(n, k, p, A.data_ptr(), A.stride(0), Cb.data_ptr(), Cb.stride(0), uplo)
     assert rc == ffsyrk.SUCCESS, ffsyrk.status_string(rc)
     torch.cuda.synchronize()
     return Cb[:, :n].cpu()
 
 
+def lower_tiles(n):
+    """Tiles of 128 × 256 that hold an entry of the lower triangle of an n × n result."""
+    TN = (n + 255) // 256
+    return sum(min(TN, (min(n, a * 128 + 128) - 1) // 256 + 1) for a in range((n + 127) // 128))
+
+
+def check_oracle(A_host, p, got, uplo):
+    n = A_host.shape[0]
+    want = oracle.syrk(A_host.numpy(), p, uplo)
+    mask = np.tril(np.ones((n, n), bool)) if uplo == "lower" else np.triu(np.ones((n, n), bool))
+    g = got.numpy().view(np.uint32)
+    assert np.array_equal(g[mask], want[mask]), "differs from the oracle"
+    assert np.all(g[~mask] == np.uint32(SENTINEL & 0xFFFFFFFF)), "wrote outside the triangle"
+
+
 @pytest.mark.parametrize("p,shapes", [
-    (65521, [(300, 257), (4096, 4096)]),
+    (65521, [(300, 257), (1100, 700)]),
     (8388593, [(777, 1000), (129, 63)]),
     (131071, [(2000, 2048), (1, 5)]),
 ])
 @pytest.mark.parametrize("uplo", ["lower", "upper"])
-def test_two_calls_match_planned_entry_point(p, shapes, uplo):
+def test_two_calls_match_the_oracle(p, shapes, uplo):
     for t, (n, k) in enumerate(shapes):  # two calls in a row, different inputs
-        A = inputs.uniform_residues(n, k, p, seed=100 + t).cuda()
+        A_host = inputs.uniform_residues(n, k, p, seed=100 + t)
+        got = noalloc(A_host.cuda(), p, uplo)
+        check_oracle(A_host, p, got, uplo)
+
+
+@pytest.mark.parametrize("uplo", ["lower", "upper"])
+def test_two_calls_match_planned_entry_point(uplo):
+    p = 65521
+    for t, (n, k) in enumerate([(4096, 4096), (3000, 1000)]):
+        A = inputs.uniform_residues(n, k, p, seed=200 + t).cuda()
         want = planned(A, p, uplo)
         got = noalloc(A, p, uplo)
         assert torch.equal(got, want), (p, n, k, uplo)
 
 
-def test_rejects_shapes_beyond_the_scratch_limit():
+def test_rejects_shapes_beyond_the_plane_limit():
     A = torch.zeros((4097, 4096), dtype=torch.int32, device="cuda")
     C = torch.zeros((4097, 4097), dtype=torch.int32, device="cuda")
-    rc = ffsyrk.lib().ffsyrk_noalloc(0, 4097, 4096, 65521, A.data_ptr(), 4096, C.data_ptr(), 4097,
-                                     torch.cuda.current_stream().cuda_stream)
-    assert rc == ffsyrk.ERR_TOO_LARGE
+    # 2 digits · 4352 rows · 4096 columns · 2 bytes > 64 MiB; 4096² is the largest square
+    assert call(4097, 4096, 65521, A.data_ptr(), 4096, C.data_ptr(), 4097) == ffsyrk.ERR_TOO_LARGE
+    torch.cuda.synchronize()
     assert torch.count_nonzero(C).item() == 0
+
+
+def test_tile_limit_boundary():
+    """The largest n whose triangle fits the tile list runs; one more row is refused."""
+    p, k = 65521, 64
+    n = 92288
+    assert lower_tiles(n) <= TILE_LIMIT < lower_tiles(n + 1)
+    A_host = inputs.uniform_residues(n + 1, k, p, seed=11)
+    A = A_host.cuda()
+    # refused before anything is enqueued: C may be a small dummy for this call
+    dummy = torch.zeros(16, dtype=torch.int32, device="cuda")
+    assert call(n + 1, k, p, A.data_ptr(), k, dummy.data_ptr(), n + 1) == ffsyrk.ERR_TOO_LARGE
+    C = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    assert call(n, k, p, A.data_ptr(), k, C.data_ptr(), n) == ffsyrk.SUCCESS
+    torch.cuda.synchronize()
+    rows = np.array([0, 1, 255, 256, 46143, n - 257, n - 2, n - 1])
+    want = oracle.syrk_rows(A_host[:n].numpy(), p, rows)
+    for t, r in enumerate(rows):
+        got = C[r, : r + 1].cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want[t, : r + 1]), f"row {r}"
+    assert torch.count_nonzero(dummy).item() == 0
+    del C
 
 
 def test_odd_strides_and_degenerate_sizes():
     p = 65521
-    A = inputs.uniform_residues(200, 150, p, seed=9).cuda()
+    A_host = inputs.uniform_residues(200, 150, p, seed=9)
     Ab = torch.full((200, 153), 5, dtype=torch.int32, device="cuda")
-    Ab[:, :150] = A
+    Ab[:, :150] = A_host.cuda()
     Cb = torch.full((200, 203), SENTINEL, dtype=torch.int32, device="cuda")
-    rc = ffsyrk.lib().ffsyrk_noalloc(0, 200, 150, p, Ab.data_ptr(), 153, Cb.data_ptr(), 203,
-                                     torch.cuda.current_stream().cuda_stream)
-    assert rc == ffsyrk.SUCCESS
+    assert call(200, 150, p, Ab.data_ptr(), 153, Cb.data_ptr(), 203) == ffsyrk.SUCCESS
     torch.cuda.synchronize()
-    want = planned(A, p, "lower")
-    assert torch.equal(Cb[:, :200].cpu(), want)
+    check_oracle(A_host, p, Cb[:, :200].cpu(), "lower")
     assert torch.all(Cb[:, 200:] == SENTINEL)
     # k = 0 zeroes the triangle, n = 0 does nothing
     C = torch.full((4, 4), SENTINEL, dtype=torch.int32, device="cuda")
-    rc = ffsyrk.lib().ffsyrk_noalloc(0, 4, 0, p, None, 1, C.data_ptr(), 4,
-                                     torch.cuda.current_stream().cuda_stream)
+    assert call(4, 0, p, None, 1, C.data_ptr(), 4) == ffsyrk.SUCCESS
     torch.cuda.synchronize()
-    assert rc == ffsyrk.SUCCESS
     c = C.cpu().numpy()
     assert np.all(c[np.tril_indices(4)] == 0) and np.all(c[np.triu_indices(4, 1)] == SENTINEL)
     assert ffsyrk.lib().ffsyrk_noalloc(0, 0, 4, p, None, 4, None, 1, None) == ffsyrk.SUCCESS
