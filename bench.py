@@ -428,26 +428,40 @@ def run_ours(args):
     plan.close()
     del plan
 
-    # comparators: classical SYRK from the same leaves; the int64 CUDA-core leaf
+    # comparators: classical SYRK from the same leaves; the same method on the
+    # warp-level INT8 tensor leaf and on the CUDA-core int64 leaf, each with
+    # its leaf's multiply-add rate against the measured rate of its pipe
     compare = {}
     if not args.no_compare:
-        legs = [("classical_tc", "tc", 0, None), ("fast_i64", "i64", levels, None),
+        from paper_2001_04109_gb300.ffsyrk import probe_pipe
+        pipe_peak = {"i8": probe_pipe("mma_s8s8", iters=2048, reps=3),
+                     "i64": probe_pipe("mad_wide_u32", iters=512, reps=3)}
+        legs = [("classical_tc", "tc", 0, None), ("fast_i8", "i8", levels, None),
+                ("classical_i8", "i8", 0, None), ("fast_i64", "i64", levels, None),
                 ("classical_i64", "i64", 0, None)]
         if any(info["winograd"]):
             # the same depth with the general products computed classically
             legs.append(("fast_tc_no_winograd", "tc", info["levels"], 0))
         for name, leaf, lv, wg in legs:
-            if name.endswith("i64") and n * n * k > 2 ** 40:
-                continue
             pl = ffsyrk.Plan(p, n, k, leaf=leaf, levels=lv, winograd=wg,
                              tile_ctas=args.tile_ctas if wg == 0 else None)
-            st = max(3, min(args.steps, 5))
-            cms, cstage = time_plan(pl, A, C, st, 2, flush, stream)
+            slow = leaf != "tc" and n * n * k > 2 ** 36  # calls of 0.1 s or more
+            st = 2 if slow else max(3, min(args.steps, 5))
+            cms, cstage = time_plan(pl, A, C, st, 1 if slow else 2, flush, stream)
             cm = statistics.median(cms)
-            compare[name] = {"value": n * n * k / (cm * 1e-3), "ms_per_step": cm,
-                             "levels": pl.info()["levels"],
-                             "winograd": pl.info()["winograd"][: pl.info()["levels"]],
-                             "leaf_ms": statistics.median(s["leaf_ms"] for s in cstage)}
+            pinfo = pl.info()
+            leg = {"value": n * n * k / (cm * 1e-3), "ms_per_step": cm,
+                   "levels": pinfo["levels"], "winograd": pinfo["winograd"][: pinfo["levels"]],
+                   "leaf_ms": statistics.median(s["leaf_ms"] for s in cstage)}
+            if leaf in pipe_peak:
+                # leaf multiply-adds of its pipe: D² byte products per field
+                # multiply-add (INT8), one 32×32→64 multiply-add (int64)
+                macs = cstage[-1]["tensor_macs"]
+                rate = macs / (leg["leaf_ms"] * 1e-3)
+                leg["leaf_pipe"] = {"macs_per_s": rate, "peak_macs_per_s": pipe_peak[leaf],
+                                    "frac": rate / pipe_peak[leaf], "digits": pinfo["digits"],
+                                    "peak_source": "ffsyrk_probe_pipe in this run"}
+            compare[name] = leg
             pl.close()
 
     # end to end through the C ABI with host buffers (ffsyrk_host): every step
@@ -801,6 +815,30 @@ def cpu_batched_rate(shapes, p, budget_s):
                                         f"range ({t_used:.1f} s)"}
 
 
+def run_probe_pipes():
+    """Measured multiply-adds per second of each pipe a leaf can use (ffsyrk_probe_pipe)."""
+    import torch
+
+    import __graft_entry__
+    from paper_2001_04109_gb300 import ffsyrk
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sampler = ClockSampler(0)
+    sampler.start()
+    rates = {}
+    for kind in ffsyrk.PIPES:
+        iters = 2048 if kind == "mad_wide_u32" else 8192
+        ffsyrk.probe_pipe(kind, iters=iters // 8, reps=1)  # warm-up
+        rates[kind] = ffsyrk.probe_pipe(kind, iters=iters, blocks=4 * sms, reps=5)
+    clocks = sampler.stop()
+    out = {"probe": "multiply-adds per second (median of 5 launches), register operands, "
+                    f"8 independent chains per thread, {4 * sms} blocks of 256 threads",
+           "macs_per_s": rates, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -824,7 +862,16 @@ def main():
                     help="problems in the batched workload (default 2048; fewer for profiling)")
     ap.add_argument("--op", choices=["syrk"] + sorted(OPS), default="syrk",
                     help="time another operation on the workload's A instead of the plain product")
+    ap.add_argument("--shape", type=int, nargs=3, metavar=("N", "K", "P"), default=None,
+                    help="replace the workload's n, k and p (for profiling other sizes)")
+    ap.add_argument("--probe-pipes", action="store_true",
+                    help="print the measured multiply-add rates of the arithmetic pipes and exit")
     args = ap.parse_args()
+    if args.probe_pipes:
+        return run_probe_pipes()
+    if args.shape is not None and args.workload != "batched":
+        n_, k_, p_ = args.shape
+        WORKLOADS[args.workload] = (n_, k_, p_, f"A·Aᵀ mod p, A {n_}×{k_}, p={p_}")
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
         # each step one bounded oracle sample; the whole run stays within a few minutes

@@ -64,7 +64,11 @@ typedef enum {
     FFSYRK_LEAF_AUTO = 0,    /* the tensor-core leaf                          */
     FFSYRK_LEAF_TC_BF16 = 1, /* tcgen05.mma kind::f16 on exact 8-bit digits,
                                 FP32 TMEM accumulators, reduction per K-chunk */
-    FFSYRK_LEAF_I64 = 2      /* CUDA-core 32×32→64-bit multiply-add leaf      */
+    FFSYRK_LEAF_I64 = 2,     /* CUDA-core 32×32→64-bit multiply-add leaf      */
+    FFSYRK_LEAF_I8 = 3       /* warp-level INT8 tensor path (mma.sync
+                                m16n8k32, u8/s8 bytes of the two's-complement
+                                residue, int32 register accumulators,
+                                reduction per weight class; Section 4.2)     */
 } ffsyrk_leaf_t;
 
 #define FFSYRK_LEVELS_AUTO (-1)
@@ -436,6 +440,19 @@ ffsyrk_status_t ffsyrk_plan_selftest_timeout(ffsyrk_plan_t plan, int64_t limit_n
  * Σ 64·count·bound(i)·bound(j) ≤ 2^24 with the bounds of
  * ffsyrk_digit_bounds(). */
 int32_t ffsyrk_leaf_schedule(uint32_t p, int32_t kblocks, int32_t *out, int32_t cap);
+
+/* The same for the INT8 leaf (FFSYRK_LEAF_I8), for a leaf K of
+ * 128·kblocks: digits are the bytes of the two's-complement symmetric
+ * residue (unsigned below the top digit, signed at the top); every unit
+ * holds one weight class i + j and satisfies
+ * Σ 128·count·bound(i)·bound(j) ≤ 2^30 with the bounds of
+ * ffsyrk_i8_digit_bounds(). */
+int32_t ffsyrk_i8_schedule(uint32_t p, int32_t kblocks, int32_t *out, int32_t cap);
+
+/* The INT8 leaf's digit count of p (the least D whose top byte holds the
+ * sign of every symmetric residue) and the bound on |digit t| (255 below
+ * the top digit).  Returns D, or −1. */
+int32_t ffsyrk_i8_digit_bounds(uint32_t p, int32_t *max_digit);
 
 /* The signed digit count D of p and the bound on |digit t| for t < D
  * (written to max_digit[0..D−1]), for the digit base ffsyrk_digit_base(p).

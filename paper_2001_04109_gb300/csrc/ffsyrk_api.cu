@@ -91,6 +91,33 @@ DigitScheme make_digits(uint32_t p) {
     return ds;
 }
 
+// The INT8 leaf's digits: the D bytes of the two's complement of the
+// symmetric residue s ∈ [−H, H], H = (p−1)/2, with D the least count whose
+// top byte holds the sign (H < 2^(8D−1)); low digits are unsigned bytes
+// (bound 255), the top digit a signed byte bounded by ⌈H / 256^(D−1)⌉.
+DigitScheme make_digits_i8(uint32_t p) {
+    DigitScheme ds{};
+    const int64_t H = (p - 1) / 2;
+    int D = 1;
+    while (D < kMaxDigits && H > (int64_t(1) << (8 * D - 1)) - 1) ++D;
+    ds.D = D;
+    ds.base = 256;
+    const int64_t low = int64_t(1) << (8 * (D - 1));
+    for (int t = 0; t < D; ++t)
+        ds.max_digit[t] = t == D - 1 ? (int)std::max<int64_t>(1, (H + low - 1) / low) : 255;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            const int64_t kc = kSegI8.bound / ((int64_t)ds.max_digit[i] * ds.max_digit[j]);
+            ds.chunk_kb[i][j] = (int)std::max<int64_t>(1, kc / kSegI8.kbw);
+            uint64_t w = 1;
+            for (int e = 0; e < i + j; ++e) w = w * 256u % p;
+            ds.weight[i][j] = make_mul((uint32_t)w, p);
+        }
+    ds.offset = (uint32_t)((kSegI8.bound + p - 1) / p * p);
+    ds.lazy_units = 0;  // the INT8 leaf reduces its residue sums after every unit
+    return ds;
+}
+
 // ---- geometry of one call ----
 struct Geometry {
     int L = 0;
@@ -222,6 +249,7 @@ Layout make_layout(const Geometry &g, int leaf, int D) {
     lay.g = g;
     lay.leaf = leaf;
     const bool tc = leaf == FFSYRK_LEAF_TC_BF16;
+    const bool i8 = leaf == FFSYRK_LEAF_I8;  // D is then the INT8 digit count
     int64_t off = 0;
     auto take = [&](int64_t bytes) {
         int64_t o = off;
@@ -232,10 +260,11 @@ Layout make_layout(const Geometry &g, int leaf, int D) {
     lay.narenas = g.L == 0 ? 1 : g.L;
     for (int j = j0; j <= (g.L == 0 ? 0 : g.L); ++j) {
         Arena &a = lay.arena[j];
-        a.kind = tc ? ARENA_BF16 : ARENA_U32;
-        a.planes = tc ? D : 1;
+        a.kind = tc ? ARENA_BF16 : i8 ? ARENA_I8 : ARENA_U32;
+        a.planes = (tc || i8) ? D : 1;
         a.rpad = rup(std::max<int64_t>(g.h[j], 1), 256);
-        a.kpad = rup(std::max<int64_t>(g.w[j], 1), 64);
+        // 128-byte rows of k-blocks: 64 bf16 digits or 128 byte digits
+        a.kpad = rup(std::max<int64_t>(g.w[j], 1), i8 ? 128 : 64);
         a.rows = arena_nops(g, j) * a.planes * a.rpad;
         lay.arena_off[j] = take(a.bytes());
     }
@@ -288,7 +317,8 @@ constexpr int64_t kMaxCtas = 256;
 int64_t leaf_tiles_bound(const Geometry &g, int leaf, int64_t *nprods_out = nullptr) {
     int64_t nprods = 1;
     int64_t ntiles = 0;
-    const int64_t tm = leaf == FFSYRK_LEAF_TC_BF16 ? 128 : 64, tn = leaf == FFSYRK_LEAF_TC_BF16 ? 256 : 64;
+    const int64_t tm = leaf == FFSYRK_LEAF_I64 ? 64 : 128,
+                  tn = leaf == FFSYRK_LEAF_TC_BF16 ? 256 : leaf == FFSYRK_LEAF_I8 ? 128 : 64;
     if (g.L == 0) {
         ntiles = ((g.n + tm - 1) / tm) * ((g.n + tn - 1) / tn);
     } else {
@@ -349,6 +379,7 @@ EncodeTiledFn get_encode_fn() {
 
 namespace fsk {
 DigitScheme digit_scheme_for(uint32_t p) { return make_digits(p); }
+DigitScheme digit_scheme_i8(uint32_t p) { return make_digits_i8(p); }
 
 // Algorithm 5 (syrkd), planning step: Diag(d) = Δ·Δᵀ with Δ block diagonal
 // -- 1×1 blocks √d_c for squares (0 included), 2×2 blocks from Algorithm 4
@@ -496,15 +527,16 @@ int count_units(const LeafSeg *segs, int nseg) {
     return u;
 }
 
-int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int cap) {
-    constexpr int64_t kBound = int64_t(1) << 24;
+int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int cap,
+                        const SegRule &rule) {
+    const int64_t kBound = rule.bound;
     const int D = ds.D;
     // span: at most 16 k-blocks and no longer than the shortest chunk, so
     // that every pair takes one unit per span where its bound allows; the
     // spans of one K are balanced (a ragged K such as 65 k-blocks becomes
     // spans of 13 rather than 16, 16, 16, 16, 1: no pair gets a unit of one
     // k-block, which would drain the accumulator after almost no MMA work)
-    int span = 16;
+    int span = rule.span_cap;
     for (int i = 0; i < D; ++i)
         for (int j = 0; j < D; ++j) span = std::min(span, std::max(1, ds.chunk_kb[i][j]));
     const int nspans = kblocks > 0 ? (kblocks + span - 1) / span : 0;
@@ -517,7 +549,7 @@ int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int ca
             bool open = false;
             for (int i = std::max(0, e - (D - 1)); i <= std::min(e, D - 1); ++i) {
                 const int j = e - i;
-                const int64_t cost = 64 * (int64_t)ds.max_digit[i] * ds.max_digit[j];
+                const int64_t cost = rule.kbw * (int64_t)ds.max_digit[i] * ds.max_digit[j];
                 for (int pos = s0; pos < s1;) {
                     int64_t avail = (kBound - used) / cost;
                     bool first = !open;
@@ -540,24 +572,25 @@ int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int ca
     return count;
 }
 
-void build_segments(const DigitScheme &ds, int kblocks, std::vector<LeafSeg> &out) {
+void build_segments(const DigitScheme &ds, int kblocks, std::vector<LeafSeg> &out,
+                    const SegRule &rule) {
     // at most D² pairs × (16 / min chunk 4) segments per span of 16 k-blocks
     const int cap = (kblocks / 16 + 1) * 9 * 4 + 16;
     const size_t base = out.size();
     out.resize(base + cap);
-    const int cnt = build_segments_into(ds, kblocks, out.data() + base, cap);
+    const int cnt = build_segments_into(ds, kblocks, out.data() + base, cap, rule);
     out.resize(base + (cnt < 0 ? 0 : cnt));
 }
 
 // Give every product its K schedule (products with equal K share one).
 void attach_segments(const DigitScheme &ds, std::vector<LeafProd> &prods,
-                     std::vector<LeafSeg> &segs) {
+                     std::vector<LeafSeg> &segs, const SegRule &rule = kSegTc) {
     std::map<int, std::pair<int64_t, int>> memo;
     for (LeafProd &pr : prods) {
         auto it = memo.find(pr.kblocks);
         if (it == memo.end()) {
             const int64_t s0 = (int64_t)segs.size();
-            build_segments(ds, pr.kblocks, segs);
+            build_segments(ds, pr.kblocks, segs, rule);
             it = memo.emplace(pr.kblocks, std::make_pair(s0, (int)((int64_t)segs.size() - s0))).first;
         }
         pr.seg0 = it->second.first;
@@ -568,11 +601,13 @@ void attach_segments(const DigitScheme &ds, std::vector<LeafProd> &prods,
 bool encode_arena_tmap(const Arena &a, void *out) {
     EncodeTiledFn fn = get_encode_fn();
     if (!fn) return false;
+    const bool i8 = a.kind == ARENA_I8;
     cuuint64_t dims[2] = {(cuuint64_t)a.kpad, (cuuint64_t)a.rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(a.kpad * 2)};
-    cuuint32_t box[2] = {64, 128};
+    cuuint64_t strides[1] = {(cuuint64_t)(a.kpad * (i8 ? 1 : 2))};
+    cuuint32_t box[2] = {i8 ? 128u : 64u, 128};  // 128-byte rows either way
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(reinterpret_cast<CUtensorMap *>(out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+    CUresult r = fn(reinterpret_cast<CUtensorMap *>(out),
+                    i8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                     a.base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -588,6 +623,7 @@ struct ffsyrk_plan_st {
     host::YChoice ych{};
     YConst yc{};
     DigitScheme ds{};
+    DigitScheme ds8{};  // the INT8 leaf's digits (FFSYRK_LEAF_I8)
     int leaf = FFSYRK_LEAF_TC_BF16;
     int levels_opt = FFSYRK_LEVELS_AUTO;
     int ctas_opt = 0;
@@ -643,6 +679,13 @@ struct ffsyrk_plan_st {
     bool autotuned = false;
     float tuned_ms = 0.f;
 };
+
+// The digit scheme of the plan's leaf operands: the INT8 leaf's bytes, or
+// the signed digits of the tensor-core leaf (also used for the uint32
+// operands of the int64 leaf, which ignore it).
+const DigitScheme &leaf_ds(const ffsyrk_plan_st *pl) {
+    return pl->leaf == FFSYRK_LEAF_I8 ? pl->ds8 : pl->ds;
+}
 
 // The geometry of one call: sizes of every depth and the levels of
 // Algorithm 1 for its general products.
@@ -916,9 +959,10 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     D = Descs();
     char *ws = pl->ws;
     const bool tc = lay.leaf == FFSYRK_LEAF_TC_BF16;
+    const bool i8 = lay.leaf == FFSYRK_LEAF_I8;
     const bool pair = tc && lay.ctas == 2;
-    const int64_t TM = tc ? (pair ? leaf_tc2_bm() : leaf_tc_bm()) : leaf_i64_tile();
-    const int64_t TN = tc ? (pair ? leaf_tc2_bn() : leaf_tc_bn()) : leaf_i64_tile();
+    const int64_t TM = tc ? (pair ? leaf_tc2_bm() : leaf_tc_bm()) : i8 ? leaf_i8_bm() : leaf_i64_tile();
+    const int64_t TN = tc ? (pair ? leaf_tc2_bn() : leaf_tc_bn()) : i8 ? leaf_i8_bn() : leaf_i64_tile();
     for (int j = 0; j <= kMaxLevels; ++j)
         if (lay.arena[j].rows > 0) lay.arena[j].base = ws + lay.arena_off[j];
 
@@ -938,7 +982,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         const int64_t h = g.h[d + 1];
         return reinterpret_cast<uint32_t *>(ws + lay.g_off[d]) + (2 * t + q) * h * h;
     };
-    int cost_mult = tc ? pl->ds.D * pl->ds.D : 1;
+    int cost_mult = tc ? pl->ds.D * pl->ds.D : i8 ? pl->ds8.D * pl->ds8.D : 1;
 
     if (g.L == 0) {
         LeafProd pr{};
@@ -948,7 +992,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         pr.a_row0 = pr.b_row0 = 0;
         if (g.gemmt) pr.b_row0 = a0.planes * a0.rpad;  // the second operand, A·Jᵀ
         pr.rows = pr.cols = g.n;
-        pr.kblocks = (int32_t)(lay.arena[0].kpad / 64);
+        pr.kblocks = (int32_t)(lay.arena[0].kpad / (i8 ? 128 : 64));
         pr.plane_rows = lay.arena[0].rpad;
         pr.out = C;
         pr.scale = pl->scale;
@@ -1038,7 +1082,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
                         pr.a_row0 = operand(ja, gb + (2 * gp) * n7 + idx).row0;
                         pr.b_row0 = operand(ja, gb + (2 * gp + 1) * n7 + idx).row0;
                         pr.rows = pr.cols = hj;
-                        pr.kblocks = (int32_t)(lay.arena[ja].kpad / 64);
+                        pr.kblocks = (int32_t)(lay.arena[ja].kpad / (i8 ? 128 : 64));
                         pr.plane_rows = lay.arena[ja].rpad;
                         pr.out = sw == 0 ? gbuf(d, t, q) : swout(sw, gp * n7 + idx);
                         pr.ldo = hj;
@@ -1068,7 +1112,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
             pr.tri = 1;
             pr.a_row0 = pr.b_row0 = operand(g.L, sb + t).row0;
             pr.rows = pr.cols = hL;
-            pr.kblocks = (int32_t)(lay.arena[g.L].kpad / 64);
+            pr.kblocks = (int32_t)(lay.arena[g.L].kpad / (i8 ? 128 : 64));
             pr.plane_rows = lay.arena[g.L].rpad;
             pr.out = rbuf(g.L, t);
             pr.ldo = hL;
@@ -1103,7 +1147,10 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
             }
         }
     }
-    attach_segments(pl->ds, D.prods, D.segs);
+    if (i8)
+        attach_segments(pl->ds8, D.prods, D.segs, kSegI8);
+    else
+        attach_segments(pl->ds, D.prods, D.segs);
     for (const LeafProd &pr : D.prods)
         D.max_units = std::max(D.max_units, count_units(D.segs.data() + pr.seg0, pr.nseg));
     // longest tiles first, then round-robin over persistent CTAs
@@ -1165,7 +1212,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         if (a.rows == 0) continue;
         reinterpret_cast<void **>(hb + D.aptr_off)[j] = a.base;
         reinterpret_cast<int64_t *>(hb + D.akpad_off)[j] = a.kpad;
-        if (tc && !encode_arena_tmap(a, hb + D.tmap_off + 128 * j)) return FFSYRK_ERR_CUDA;
+        if ((tc || i8) && !encode_arena_tmap(a, hb + D.tmap_off + 128 * j)) return FFSYRK_ERR_CUDA;
     }
     return FFSYRK_SUCCESS;
 }
@@ -1178,7 +1225,7 @@ ffsyrk_status_t validate_p(uint32_t p) {
 
 int64_t workspace_need(const ffsyrk_plan_st *pl, int64_t n, int64_t k, int L, int64_t *desc) {
     const Geometry g = plan_geometry(pl, n, k, L);
-    Layout lay = make_layout(g, pl->leaf, pl->ds.D);
+    Layout lay = make_layout(g, pl->leaf, leaf_ds(pl).D);
     *desc = desc_capacity(g, pl->leaf);
     return lay.data_bytes;
 }
@@ -1191,7 +1238,12 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
     const Geometry &g = lay.g;
     const Descs &D = pl->desc;
     char *dd = pl->ws + pl->data_cap;
-    const int kind = lay.leaf == FFSYRK_LEAF_TC_BF16 ? ARENA_BF16 : ARENA_U32;
+    const int kind = lay.leaf == FFSYRK_LEAF_TC_BF16 ? ARENA_BF16
+                     : lay.leaf == FFSYRK_LEAF_I8  ? ARENA_I8
+                                                   : ARENA_U32;
+    const DigitScheme &lds = leaf_ds(pl);
+    // row length of the operands a launch writes: a leaf arena's, or 64-aligned uint32 rows
+    auto opkpad = [&](int64_t w, bool u32) { return u32 ? rup(w, 64) : rup(w, kind == ARENA_I8 ? 128 : 64); };
     if (timed) cudaEventRecord(pl->ev[0], st);
     // the one-SM leaf's work counters start at zero; cleared first, so that
     // the leaf launch directly follows the grid that writes its operands
@@ -1204,21 +1256,22 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
     if (g.L == 0) {
         e = launch_digitize(reinterpret_cast<const DigitizeJob *>(dd + D.digit_off),
                             (int)D.digit.size(), D.digit_max_rows, D.digit_max_kpad, pl->mp,
-                            pl->ds, kind, st);
+                            lds, kind, st);
         if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
     } else {
         for (int d = 0; d < g.L; ++d) {
             // with Algorithm 1 at this depth, the general products' operands are
             // written as uint32 rows (d < L − 1: no leaf operands at this depth)
             e = launch_prep(reinterpret_cast<const PrepNode *>(dd + D.prep_off[d]),
-                            (int)D.prep[d].size(), g.h[d + 1], g.w[d + 1], rup(g.w[d + 1], 64),
-                            pl->mp, pl->yc, pl->ds, g.sw[d] > 0 ? (int)ARENA_U32 : kind,
+                            (int)D.prep[d].size(), g.h[d + 1], g.w[d + 1],
+                            opkpad(g.w[d + 1], g.sw[d] > 0 && d + 1 < g.L), pl->mp, pl->yc, lds,
+                            g.sw[d] > 0 ? (int)ARENA_U32 : kind,
                             /*reduce_input=*/true, st);
             if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
             for (int l = 1; l <= g.sw[d]; ++l) {
                 e = launch_sw_pre(reinterpret_cast<const SwPreJob *>(dd + D.swpre_off[d][l]),
                                   (int)D.swpre[d][l].size(), g.h[d + 1 + l], g.w[d + 1 + l],
-                                  rup(g.w[d + 1 + l], 64), pl->mp, pl->ds,
+                                  opkpad(g.w[d + 1 + l], l < g.sw[d]), pl->mp, lds,
                                   l < g.sw[d] ? (int)ARENA_U32 : kind, st);
                 if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
             }
@@ -1259,6 +1312,17 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
             }
             e = launch_leaf_tc(tl, pl->sms, st);
         }
+    } else if (lay.leaf == FFSYRK_LEAF_I8) {
+        I8Launch il{};
+        il.prods = reinterpret_cast<const LeafProd *>(dd + D.prods_off);
+        il.tiles = reinterpret_cast<const LeafTile *>(dd + D.tiles_off);
+        il.segs = reinterpret_cast<const LeafSeg *>(dd + D.segs_off);
+        il.ntiles = (int)D.tiles.size();
+        il.tmaps = dd + D.tmap_off;
+        il.mp = pl->mp;
+        il.ds = pl->ds8;
+        il.err = pl->err_dev;
+        e = launch_leaf_i8(il, pl->sms, st);
     } else {
         e = launch_leaf_i64_arrays(reinterpret_cast<const LeafProd *>(dd + D.prods_off),
                                    reinterpret_cast<const LeafTile *>(dd + D.tiles_off),
@@ -1348,11 +1412,14 @@ void record_work(ffsyrk_plan_st *pl) {
     pl->last_leaf_entries = D.entries.empty() ? (int)D.tiles.size() : (int)D.entries.size() - 1;
     pl->last_split_tiles = split;
     double f = 0;
+    const double kbw = lay.leaf == FFSYRK_LEAF_I8 ? 128.0 : 64.0;
     for (const LeafProd &pr : D.prods) {
-        const double K = (double)(pr.kblocks) * 64.0;
+        const double K = (double)(pr.kblocks) * kbw;
         f += (pr.tri == 0 ? (double)pr.rows * pr.cols : (double)pr.rows * (pr.rows + 1) / 2) * K;
     }
-    pl->last_tensor_macs = f * (lay.leaf == FFSYRK_LEAF_TC_BF16 ? pl->ds.D * pl->ds.D : 1);
+    pl->last_tensor_macs = f * (lay.leaf == FFSYRK_LEAF_TC_BF16 ? pl->ds.D * pl->ds.D
+                                : lay.leaf == FFSYRK_LEAF_I8   ? pl->ds8.D * pl->ds8.D
+                                                               : 1);
     // field multiply-adds of the method (padded block sizes, unpadded K at L = 0)
     pl->last_field_macs = leaf_field_macs(g);
 }
@@ -1368,7 +1435,7 @@ ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, cons
     auto key = std::make_tuple(n, k, A, lda, C, ldc, uplo, L, sc.mode, sc.alpha.w, sc.beta.w);
     if (!pl->have_last || key != pl->last_key) {
         const Geometry g = plan_geometry(pl, n, k, L);
-        Layout lay = make_layout(g, pl->leaf, pl->ds.D);
+        Layout lay = make_layout(g, pl->leaf, leaf_ds(pl).D);
         lay.ctas = choose_ctas(pl, g);
         if (lay.data_bytes > pl->data_cap) return FFSYRK_ERR_TOO_LARGE;
         // the staging blob may still be in flight from the previous upload
@@ -1588,7 +1655,7 @@ namespace {
 ffsyrk_status_t checked_options(const ffsyrk_options_t *opts, ffsyrk_options_t *o) {
     ffsyrk_options_default(o);
     if (opts) *o = *opts;
-    if (o->leaf < FFSYRK_LEAF_AUTO || o->leaf > FFSYRK_LEAF_I64) return FFSYRK_ERR_INVALID_ARG;
+    if (o->leaf < FFSYRK_LEAF_AUTO || o->leaf > FFSYRK_LEAF_I8) return FFSYRK_ERR_INVALID_ARG;
     if (o->levels < FFSYRK_LEVELS_AUTO || o->levels > kMaxLevels) return FFSYRK_ERR_INVALID_ARG;
     if (o->tile_ctas < 0 || o->tile_ctas > 2) return FFSYRK_ERR_INVALID_ARG;
     if (o->autotune < 0 || o->autotune > 1) return FFSYRK_ERR_INVALID_ARG;
@@ -1608,6 +1675,7 @@ bool plan_setup(ffsyrk_plan_st *pl, uint32_t p, int64_t max_n, int64_t max_k,
     pl->yc.a = make_mul((uint32_t)pl->ych.a, p);
     pl->yc.b = make_mul((uint32_t)pl->ych.b, p);
     pl->ds = make_digits(p);
+    pl->ds8 = make_digits_i8(p);
     pl->mp = make_modp(p, pl->ds);
     pl->leaf = (o.leaf == FFSYRK_LEAF_AUTO) ? FFSYRK_LEAF_TC_BF16 : o.leaf;
     pl->gemmt = gemmt;
@@ -1796,9 +1864,11 @@ ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t pl, ffsyrk_plan_info_t *info)
     info->y_cost = pl->ych.cost;
     info->leaf = pl->leaf;
     info->levels = pl->L_max;
-    info->digits = pl->ds.D;
-    for (int i = 0; i < pl->ds.D; ++i)
-        for (int j = 0; j < pl->ds.D; ++j) info->chunk_k[i * 3 + j] = pl->ds.chunk_kb[i][j] * 64;
+    const DigitScheme &lds = leaf_ds(pl);
+    const int kbw = pl->leaf == FFSYRK_LEAF_I8 ? kSegI8.kbw : kSegTc.kbw;
+    info->digits = lds.D;
+    for (int i = 0; i < lds.D; ++i)
+        for (int j = 0; j < lds.D; ++j) info->chunk_k[i * 3 + j] = lds.chunk_kb[i][j] * kbw;
     info->workspace_bytes = pl->ws_bytes;
     info->autotuned = pl->autotuned ? 1 : 0;
     info->tuned_ms = pl->tuned_ms;
@@ -1951,6 +2021,29 @@ int32_t ffsyrk_leaf_schedule(uint32_t p, int32_t kblocks, int32_t *out, int32_t 
         out[5 * q + 4] = segs[q].first;
     }
     return n;
+}
+
+int32_t ffsyrk_i8_schedule(uint32_t p, int32_t kblocks, int32_t *out, int32_t cap) {
+    if (validate_p(p) != FFSYRK_SUCCESS || kblocks < 0 || (cap > 0 && !out)) return -1;
+    const DigitScheme ds = make_digits_i8(p);
+    std::vector<LeafSeg> segs;
+    build_segments(ds, kblocks, segs, kSegI8);
+    const int32_t n = (int32_t)segs.size();
+    for (int32_t q = 0; q < n && q < cap; ++q) {
+        out[5 * q + 0] = segs[q].ij >> 4;
+        out[5 * q + 1] = segs[q].ij & 15;
+        out[5 * q + 2] = segs[q].kb0;
+        out[5 * q + 3] = segs[q].nkb;
+        out[5 * q + 4] = segs[q].first;
+    }
+    return n;
+}
+
+int32_t ffsyrk_i8_digit_bounds(uint32_t p, int32_t *max_digit) {
+    if (validate_p(p) != FFSYRK_SUCCESS || !max_digit) return -1;
+    const DigitScheme ds = make_digits_i8(p);
+    for (int t = 0; t < ds.D; ++t) max_digit[t] = ds.max_digit[t];
+    return ds.D;
 }
 
 int32_t ffsyrk_digit_bounds(uint32_t p, int32_t *max_digit) {

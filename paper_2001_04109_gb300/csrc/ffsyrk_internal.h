@@ -108,8 +108,11 @@ struct MatView {
     int64_t vr, vc;
 };
 
-// Element types of operand arenas.
-enum ArenaKind { ARENA_BF16 = 0, ARENA_U32 = 1 };
+// Element types of operand arenas: bf16 signed digits (tensor-core leaf),
+// uint32 residues (int64 leaf, and operands split further by Algorithm 1),
+// bytes of the two's-complement residue (INT8 leaf: unsigned low digits,
+// signed top digit).
+enum ArenaKind { ARENA_BF16 = 0, ARENA_U32 = 1, ARENA_I8 = 2 };
 
 struct Arena {
     void *base = nullptr;   // [rows][kpad] elements
@@ -118,7 +121,7 @@ struct Arena {
     int64_t rpad = 0;       // rows per digit plane of one operand
     int planes = 1;         // digit planes per operand
     int kind = ARENA_BF16;
-    int64_t bytes() const { return rows * kpad * (kind == ARENA_BF16 ? 2 : 4); }
+    int64_t bytes() const { return rows * kpad * (kind == ARENA_BF16 ? 2 : kind == ARENA_I8 ? 1 : 4); }
 };
 
 // Destination of one derived operand written by a pre-addition kernel.
@@ -189,13 +192,24 @@ struct LeafSeg {
     uint8_t first;
 };
 // The schedule for one product with `kblocks` k-blocks: balanced spans of
-// at most min(16, shortest chunk) k-blocks; inside a span the weight classes
-// e = i + j in order, the pairs of a class in order; a unit grows while its
-// worst-case |sum| Σ 64·nkb·max|d_i|·max|d_j| stays ≤ 2^24 and never crosses
-// a class.
-void build_segments(const DigitScheme &ds, int kblocks, std::vector<LeafSeg> &out);
+// at most min(span_cap, shortest chunk) k-blocks; inside a span the weight
+// classes e = i + j in order, the pairs of a class in order; a unit grows
+// while its worst-case |sum| Σ kbw·nkb·max|d_i|·max|d_j| stays ≤ bound and
+// never crosses a class.  The tensor-core leaf: k-blocks of kbw = 64, bound
+// 2^24 (exact FP32), spans ≤ 16; the INT8 leaf: kbw = 128, bound 2^30
+// (int32 with room for the reduction's offset), spans ≤ 128.
+struct SegRule {
+    int64_t bound = int64_t(1) << 24;
+    int kbw = 64;
+    int span_cap = 16;
+};
+constexpr SegRule kSegTc{};
+constexpr SegRule kSegI8{int64_t(1) << 30, 128, 128};
+void build_segments(const DigitScheme &ds, int kblocks, std::vector<LeafSeg> &out,
+                    const SegRule &rule = kSegTc);
 // The same into a caller's buffer of `cap` entries: the count, or −1 if it does not fit.
-int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int cap);
+int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int cap,
+                        const SegRule &rule = kSegTc);
 
 struct LeafTile {
     int32_t prod;
@@ -368,6 +382,25 @@ int leaf_i64_tile();
 // The signed digit scheme (base 256, or a balanced base) and chunk lengths
 // the planner uses for p.
 DigitScheme digit_scheme_for(uint32_t p);
+// The INT8 leaf's digits of p: the D bytes of the two's-complement
+// symmetric residue (max_digit 255 below the top digit), weights 256^(i+j)
+// mod p, offset the least multiple of p ≥ 2^30.
+DigitScheme digit_scheme_i8(uint32_t p);
+
+// The INT8 leaf (kern_leaf_i8.cu): 128×128 tiles, 128-byte k-blocks.
+struct I8Launch {
+    const LeafProd *prods;
+    const LeafTile *tiles;
+    const LeafSeg *segs;
+    int ntiles;
+    const void *tmaps;  // device array of CUtensorMap (uint8 arenas), 64-B aligned
+    ModP mp;
+    DigitScheme ds;     // digit_scheme_i8
+    unsigned int *err;
+};
+cudaError_t launch_leaf_i8(const I8Launch &L, int num_sms, cudaStream_t st);
+int leaf_i8_bm();
+int leaf_i8_bn();
 
 // Throughput probe of one arithmetic pipe (see kern_probe.cu): kind 0..4.
 cudaError_t launch_probe(int kind, int64_t iters, int blocks, unsigned int *sink, cudaStream_t st);
@@ -376,7 +409,8 @@ double probe_macs(int kind, int64_t iters, int blocks);
 // A kernel whose bounded wait runs out (after limit_ns) and records it in err.
 cudaError_t launch_wait_selftest(unsigned int *err, unsigned long long limit_ns, cudaStream_t st);
 
-// Build the TMA descriptor of a bf16 arena (box 64 × 128 rows, 128B swizzle).
+// Build the TMA descriptor of an arena: bf16 (box 64 × 128 rows) or uint8
+// (INT8 leaf, box 128 × 128 rows), 128B swizzle.
 bool encode_arena_tmap(const Arena &a, void *tmap_out /* 128 B */);
 
 }  // namespace fsk

@@ -117,14 +117,23 @@ __device__ __forceinline__ void ld_view8(const MatView &v, bool vec_ok, int64_t 
 }
 
 // Store four residues at (row r, columns c..c+3): one 8-byte store per digit
-// plane (bf16) or one 16-byte store (uint32).
-template <int D, bool U32>
+// plane (bf16), one 16-byte store (uint32), or one 4-byte store per byte
+// plane (INT8 leaf).
+template <int D, int OK>
 __device__ __forceinline__ void put4(const OperandDst &d, int64_t r, int64_t c, const uint32_t (&v)[4],
                                      const ModP &m) {
     if (d.arena == nullptr) return;
-    if constexpr (U32) {
+    if constexpr (OK == ARENA_U32) {
         *reinterpret_cast<uint4 *>(static_cast<uint32_t *>(d.arena) + (d.row0 + r) * d.kpad + c) =
             make_uint4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (OK == ARENA_I8) {
+        int sv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sv[e] = v[e] > m.half ? (int)v[e] - (int)m.p : (int)v[e];
+        unsigned char *base = static_cast<unsigned char *>(d.arena);
+#pragma unroll
+        for (int t = 0; t < D; ++t)
+            *reinterpret_cast<uint32_t *>(base + (d.row0 + t * d.rpad + r) * d.kpad + c) = byte_plane(sv, 0, t);
     } else {
         int sv[4];
 #pragma unroll
@@ -155,7 +164,7 @@ __device__ __forceinline__ void put4(const OperandDst &d, int64_t r, int64_t c, 
 // leaf products); rows [h, rpad) are never read into a stored result.
 // Grid: x = 4-column blocks, y = row blocks (strided), z = node.
 // RED: reduce the loaded values mod p (views of the caller's A can hold values ≥ p).
-template <int D, bool U32, int YF, bool RED>
+template <int D, int OK, int YF, bool RED>
 __global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restrict__ nodes,
                                                        int64_t h, int64_t w, int64_t kpad, ModP m,
                                                        YConst y) {
@@ -218,13 +227,13 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restric
                 s3[e] = subm(s1[e], x22[e], p);                 // S3 = S1 − A22
                 s4[e] = addm(s3[e], x12[e], p);                 // S4 = S3 + A12
             }
-            put8<D, U32>(nd.gemm[0], r, c, x22, m);
-            put8<D, U32>(nd.gemm[1], r, c, s4, m);
-            put8<D, U32>(nd.gemm[2], r, c, s1, m);
-            put8<D, U32>(nd.gemm[3], r, c, s2, m);
-            put8<D, U32>(nd.leaf[0], r, c, x11, m);
-            put8<D, U32>(nd.leaf[1], r, c, x12, m);
-            put8<D, U32>(nd.leaf[2], r, c, s3, m);
+            put8<D, OK>(nd.gemm[0], r, c, x22, m);
+            put8<D, OK>(nd.gemm[1], r, c, s4, m);
+            put8<D, OK>(nd.gemm[2], r, c, s1, m);
+            put8<D, OK>(nd.gemm[3], r, c, s2, m);
+            put8<D, OK>(nd.leaf[0], r, c, x11, m);
+            put8<D, OK>(nd.leaf[1], r, c, x12, m);
+            put8<D, OK>(nd.leaf[2], r, c, s3, m);
             if (nd.s3 != nullptr) {
 #pragma unroll
                 for (int hf = 0; hf < 2; ++hf) {
@@ -249,7 +258,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restric
 constexpr int DIG_ROWS = 4;   // rows per thread
 constexpr int DIG_COLS = 8;   // columns per thread
 constexpr int DIG_THREADS = 128;
-template <int D, bool U32>
+template <int D, int OK>
 __global__ void __launch_bounds__(DIG_THREADS) k_digitize(const DigitizeJob *__restrict__ jobs,
                                                           ModP m) {
     allow_dependents();
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(DIG_THREADS) k_digitize(const DigitizeJob *__r
                     v[i][e + 1] = x;
                 }
             }
-            put8<D, U32>(jb.dst, r, c, v[i], m);
+            put8<D, OK>(jb.dst, r, c, v[i], m);
         }
     }
 }
@@ -289,7 +298,7 @@ __global__ void __launch_bounds__(DIG_THREADS) k_digitize(const DigitizeJob *__r
 // once (rows r0, r0 + rpt, … with rpt = threads / (kpad/8)), so narrow
 // problems keep the block's threads busy; wider jobs take several blocks per
 // row band, as k_digitize does.
-template <int D, bool U32>
+template <int D, int OK>
 __global__ void __launch_bounds__(DIG_THREADS) k_digitize_flat(const DigitizeJob *__restrict__ jobs,
                                                                 int njobs, ModP m) {
     allow_dependents();
@@ -328,7 +337,7 @@ __global__ void __launch_bounds__(DIG_THREADS) k_digitize_flat(const DigitizeJob
         if (r >= jb.rows) break;
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[i][e] = red(v[i][e], m);
-        put8<D, U32>(jb.dst, r, c, v[i], m);
+        put8<D, OK>(jb.dst, r, c, v[i], m);
     }
 }
 
@@ -611,21 +620,21 @@ __global__ void k_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, int64
         }
 }
 
-template <int D, bool U32, int YF, bool RED>
+template <int D, int OK, int YF, bool RED>
 cudaError_t launch_prep_t(dim3 grid, cudaStream_t st, const PrepNode *nodes, int64_t h, int64_t w,
                           int64_t kpad, ModP mp, YConst y) {
-    k_prep<D, U32, YF, RED><<<grid, PREP_THREADS, 0, st>>>(nodes, h, w, kpad, mp, y);
+    k_prep<D, OK, YF, RED><<<grid, PREP_THREADS, 0, st>>>(nodes, h, w, kpad, mp, y);
     return cudaGetLastError();
 }
 
-template <int D, bool U32>
+template <int D, int OK>
 cudaError_t launch_prep_d(dim3 grid, cudaStream_t st, const PrepNode *nodes, int64_t h, int64_t w,
                           int64_t kpad, ModP mp, YConst y, bool reduce) {
     if (y.form == 0)
-        return reduce ? launch_prep_t<D, U32, 0, true>(grid, st, nodes, h, w, kpad, mp, y)
-                      : launch_prep_t<D, U32, 0, false>(grid, st, nodes, h, w, kpad, mp, y);
-    return reduce ? launch_prep_t<D, U32, 1, true>(grid, st, nodes, h, w, kpad, mp, y)
-                  : launch_prep_t<D, U32, 1, false>(grid, st, nodes, h, w, kpad, mp, y);
+        return reduce ? launch_prep_t<D, OK, 0, true>(grid, st, nodes, h, w, kpad, mp, y)
+                      : launch_prep_t<D, OK, 0, false>(grid, st, nodes, h, w, kpad, mp, y);
+    return reduce ? launch_prep_t<D, OK, 1, true>(grid, st, nodes, h, w, kpad, mp, y)
+                  : launch_prep_t<D, OK, 1, false>(grid, st, nodes, h, w, kpad, mp, y);
 }
 
 }  // namespace
@@ -638,11 +647,19 @@ cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_
     const int64_t gy = std::min<int64_t>((h + PREP_ROWS - 1) / PREP_ROWS, 65535);
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nnodes);
     if (arena_kind == ARENA_U32)
-        return launch_prep_d<1, true>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+        return launch_prep_d<1, ARENA_U32>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+    if (arena_kind == ARENA_I8) {
+        switch (ds.D) {
+            case 1: return launch_prep_d<1, ARENA_I8>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+            case 2: return launch_prep_d<2, ARENA_I8>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+            case 3: return launch_prep_d<3, ARENA_I8>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (ds.D) {
-        case 1: return launch_prep_d<1, false>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
-        case 2: return launch_prep_d<2, false>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
-        case 3: return launch_prep_d<3, false>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+        case 1: return launch_prep_d<1, ARENA_BF16>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+        case 2: return launch_prep_d<2, ARENA_BF16>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+        case 3: return launch_prep_d<3, ARENA_BF16>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
     }
     return cudaErrorInvalidValue;
 }
@@ -655,12 +672,19 @@ cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_
     const int64_t gy = std::min<int64_t>((max_rows + DIG_ROWS - 1) / DIG_ROWS, 65535);
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)njobs);
     if (arena_kind == ARENA_U32) {
-        k_digitize<1, true><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp);
+        k_digitize<1, ARENA_U32><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp);
+    } else if (arena_kind == ARENA_I8) {
+        switch (ds.D) {
+            case 1: k_digitize<1, ARENA_I8><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
+            case 2: k_digitize<2, ARENA_I8><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
+            case 3: k_digitize<3, ARENA_I8><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
+            default: return cudaErrorInvalidValue;
+        }
     } else {
         switch (ds.D) {
-            case 1: k_digitize<1, false><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
-            case 2: k_digitize<2, false><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
-            case 3: k_digitize<3, false><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
+            case 1: k_digitize<1, ARENA_BF16><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
+            case 2: k_digitize<2, ARENA_BF16><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
+            case 3: k_digitize<3, ARENA_BF16><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
             default: return cudaErrorInvalidValue;
         }
     }
@@ -686,12 +710,19 @@ cudaError_t launch_digitize_flat(const DigitizeJob *jobs_dev, int njobs, int64_t
     dim3 grid((unsigned)gx, (unsigned)gy);
     // blocks past the last job's range find its job and return on the row check
     if (arena_kind == ARENA_U32) {
-        k_digitize_flat<1, true><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp);
+        k_digitize_flat<1, ARENA_U32><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp);
+    } else if (arena_kind == ARENA_I8) {
+        switch (ds.D) {
+            case 1: k_digitize_flat<1, ARENA_I8><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
+            case 2: k_digitize_flat<2, ARENA_I8><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
+            case 3: k_digitize_flat<3, ARENA_I8><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
+            default: return cudaErrorInvalidValue;
+        }
     } else {
         switch (ds.D) {
-            case 1: k_digitize_flat<1, false><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
-            case 2: k_digitize_flat<2, false><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
-            case 3: k_digitize_flat<3, false><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
+            case 1: k_digitize_flat<1, ARENA_BF16><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
+            case 2: k_digitize_flat<2, ARENA_BF16><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
+            case 3: k_digitize_flat<3, ARENA_BF16><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
             default: return cudaErrorInvalidValue;
         }
     }

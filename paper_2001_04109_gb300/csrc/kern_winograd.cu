@@ -64,7 +64,7 @@ __device__ __forceinline__ void ld8(const uint32_t *base, int64_t ld, int64_t r,
 // One level of pre-additions: job z splits its hh·2 × ww·2 uint32 operand
 // into 2×2 blocks and writes the 7 operands of p1..p7 (left side or right
 // side), each hh × kpad with zeros in columns ≥ ww.
-template <int D, bool U32>
+template <int D, int OK>
 __global__ void __launch_bounds__(SWP_THREADS) k_sw_pre(const SwPreJob *__restrict__ jobs,
                                                         int64_t hh, int64_t ww, int64_t kpad,
                                                         ModP m) {
@@ -93,13 +93,13 @@ __global__ void __launch_bounds__(SWP_THREADS) k_sw_pre(const SwPreJob *__restri
                 o[2][e] = subp(x12[e], s3, p);      // s4
                 x21[e] = s2;                        // x21 is not an output: reuse for s2
             }
-            put8<D, U32>(jb.dst[0], r, c, x11, m);
-            put8<D, U32>(jb.dst[1], r, c, x12, m);
-            put8<D, U32>(jb.dst[2], r, c, x22, m);
-            put8<D, U32>(jb.dst[3], r, c, o[0], m);
-            put8<D, U32>(jb.dst[4], r, c, o[1], m);
-            put8<D, U32>(jb.dst[5], r, c, o[2], m);
-            put8<D, U32>(jb.dst[6], r, c, x21, m);
+            put8<D, OK>(jb.dst[0], r, c, x11, m);
+            put8<D, OK>(jb.dst[1], r, c, x12, m);
+            put8<D, OK>(jb.dst[2], r, c, x22, m);
+            put8<D, OK>(jb.dst[3], r, c, o[0], m);
+            put8<D, OK>(jb.dst[4], r, c, o[1], m);
+            put8<D, OK>(jb.dst[5], r, c, o[2], m);
+            put8<D, OK>(jb.dst[6], r, c, x21, m);
         } else {
             // right operands: R11, R12, R12 − T3, T1, T3, R22, T2
 #pragma unroll
@@ -112,13 +112,13 @@ __global__ void __launch_bounds__(SWP_THREADS) k_sw_pre(const SwPreJob *__restri
                 o[2][e] = t3;
                 x21[e] = t2;  // x21 is not an output: reuse for T2
             }
-            put8<D, U32>(jb.dst[0], r, c, x11, m);
-            put8<D, U32>(jb.dst[1], r, c, x12, m);
-            put8<D, U32>(jb.dst[2], r, c, o[0], m);
-            put8<D, U32>(jb.dst[3], r, c, o[1], m);
-            put8<D, U32>(jb.dst[4], r, c, o[2], m);
-            put8<D, U32>(jb.dst[5], r, c, x22, m);
-            put8<D, U32>(jb.dst[6], r, c, x21, m);
+            put8<D, OK>(jb.dst[0], r, c, x11, m);
+            put8<D, OK>(jb.dst[1], r, c, x12, m);
+            put8<D, OK>(jb.dst[2], r, c, o[0], m);
+            put8<D, OK>(jb.dst[3], r, c, o[1], m);
+            put8<D, OK>(jb.dst[4], r, c, o[2], m);
+            put8<D, OK>(jb.dst[5], r, c, x22, m);
+            put8<D, OK>(jb.dst[6], r, c, x21, m);
         }
     }
 }
@@ -161,10 +161,10 @@ __global__ void __launch_bounds__(SWQ_THREADS) k_sw_post(const SwPostJob *__rest
     }
 }
 
-template <int D, bool U32>
+template <int D, int OK>
 cudaError_t launch_pre_t(dim3 grid, cudaStream_t st, const SwPreJob *jobs, int64_t hh, int64_t ww,
                          int64_t kpad, ModP mp) {
-    k_sw_pre<D, U32><<<grid, SWP_THREADS, 0, st>>>(jobs, hh, ww, kpad, mp);
+    k_sw_pre<D, OK><<<grid, SWP_THREADS, 0, st>>>(jobs, hh, ww, kpad, mp);
     return cudaGetLastError();
 }
 
@@ -176,11 +176,19 @@ cudaError_t launch_sw_pre(const SwPreJob *jobs_dev, int njobs, int64_t hh, int64
     const int64_t gx = (kpad / SWP_COLS + SWP_THREADS - 1) / SWP_THREADS;
     const int64_t gy = std::min<int64_t>(hh, std::max<int64_t>(1, 152 * 24 / (gx * njobs)));
     dim3 grid((unsigned)gx, (unsigned)std::max<int64_t>(gy, 1), (unsigned)njobs);
-    if (out_kind == ARENA_U32) return launch_pre_t<1, true>(grid, st, jobs_dev, hh, ww, kpad, mp);
+    if (out_kind == ARENA_U32) return launch_pre_t<1, ARENA_U32>(grid, st, jobs_dev, hh, ww, kpad, mp);
+    if (out_kind == ARENA_I8) {
+        switch (ds.D) {
+            case 1: return launch_pre_t<1, ARENA_I8>(grid, st, jobs_dev, hh, ww, kpad, mp);
+            case 2: return launch_pre_t<2, ARENA_I8>(grid, st, jobs_dev, hh, ww, kpad, mp);
+            case 3: return launch_pre_t<3, ARENA_I8>(grid, st, jobs_dev, hh, ww, kpad, mp);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (ds.D) {
-        case 1: return launch_pre_t<1, false>(grid, st, jobs_dev, hh, ww, kpad, mp);
-        case 2: return launch_pre_t<2, false>(grid, st, jobs_dev, hh, ww, kpad, mp);
-        case 3: return launch_pre_t<3, false>(grid, st, jobs_dev, hh, ww, kpad, mp);
+        case 1: return launch_pre_t<1, ARENA_BF16>(grid, st, jobs_dev, hh, ww, kpad, mp);
+        case 2: return launch_pre_t<2, ARENA_BF16>(grid, st, jobs_dev, hh, ww, kpad, mp);
+        case 3: return launch_pre_t<3, ARENA_BF16>(grid, st, jobs_dev, hh, ww, kpad, mp);
     }
     return cudaErrorInvalidValue;
 }

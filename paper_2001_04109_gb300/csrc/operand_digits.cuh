@@ -40,16 +40,37 @@ __device__ __forceinline__ int low_digit(int &s, const ModP &m) {
     return d;
 }
 
+// Byte t of the two's-complement symmetric residues s[0..3], packed in one
+// word: the INT8 leaf's digit t (unsigned below the top digit, signed at
+// the top; the digit count is chosen so that the top byte holds the sign).
+template <int N>
+__device__ __forceinline__ uint32_t byte_plane(const int (&sv)[N], int e0, int t) {
+    uint32_t w = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) w |= ((uint32_t)(sv[e0 + e] >> (8 * t)) & 255u) << (8 * e);
+    return w;
+}
+
 // Store eight residues at (row r, columns c..c+7) of an operand: one
-// 16-byte store per digit plane (bf16) or two (uint32).
-template <int D, bool U32>
+// 16-byte store per digit plane (bf16), two (uint32), or one 8-byte store
+// per byte plane (INT8 leaf).
+template <int D, int OK>
 __device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, const uint32_t (&v)[8],
                                      const ModP &m) {
     if (d.arena == nullptr) return;
-    if constexpr (U32) {
+    if constexpr (OK == ARENA_U32) {
         uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(d.arena) + (d.row0 + r) * d.kpad + c);
         dst[0] = make_uint4(v[0], v[1], v[2], v[3]);
         dst[1] = make_uint4(v[4], v[5], v[6], v[7]);
+    } else if constexpr (OK == ARENA_I8) {
+        int sv[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sv[e] = v[e] > m.half ? (int)v[e] - (int)m.p : (int)v[e];
+        unsigned char *base = static_cast<unsigned char *>(d.arena);
+#pragma unroll
+        for (int t = 0; t < D; ++t)
+            *reinterpret_cast<uint2 *>(base + (d.row0 + t * d.rpad + r) * d.kpad + c) =
+                make_uint2(byte_plane(sv, 0, t), byte_plane(sv, 4, t));
     } else {
         int sv[8];
 #pragma unroll

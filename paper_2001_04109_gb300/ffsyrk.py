@@ -21,11 +21,11 @@ LIB_PATH = os.path.join(_HERE, "libffsyrk.so")
 SUCCESS, ERR_INVALID_ARG, ERR_NOT_PRIME, ERR_UNSUPPORTED_P, ERR_ALLOC, ERR_CUDA, ERR_TIMEOUT, \
     ERR_ARCH, ERR_TOO_LARGE = range(9)
 LOWER, UPPER = 0, 1
-LEAF_AUTO, LEAF_TC_BF16, LEAF_I64 = 0, 1, 2
+LEAF_AUTO, LEAF_TC_BF16, LEAF_I64, LEAF_I8 = 0, 1, 2, 3
 LEVELS_AUTO = -1
 
 _LEAVES = {None: LEAF_AUTO, "auto": LEAF_AUTO, "tc": LEAF_TC_BF16, "bf16": LEAF_TC_BF16,
-           "i64": LEAF_I64}
+           "i64": LEAF_I64, "i8": LEAF_I8}
 
 #: every entry point include/ffsyrk.h declares
 EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan",
@@ -37,7 +37,8 @@ EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsy
            "ffsyrkbd_with_plan_update", "ffsyrkbd_update", "ffsyrkbd_factor",
            "ffsyrkbd_factor_device", "ffherk_plan", "ffherk_plan_destroy", "ffherk_with_plan",
            "ffherk_sync_status", "ffherk", "ffsyrk_host", "ffsyrk_workspace_query",
-           "ffsyrk_test_inject_alloc_failure", "ffsyrk_cache_info", "ffsyrk_probe_pipe"]
+           "ffsyrk_test_inject_alloc_failure", "ffsyrk_cache_info", "ffsyrk_probe_pipe",
+           "ffsyrk_i8_schedule", "ffsyrk_i8_digit_bounds"]
 
 
 class FfsyrkError(RuntimeError):
@@ -124,7 +125,8 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_probe_pipe.restype = i32
             for name in ["ffherk_plan", "ffherk_plan_destroy", "ffherk_with_plan",
                          "ffherk_sync_status", "ffherk", "ffsyrk_host", "ffsyrk_workspace_query",
-           "ffsyrk_test_inject_alloc_failure", "ffsyrk_cache_info", "ffsyrk_probe_pipe"]:
+           "ffsyrk_test_inject_alloc_failure", "ffsyrk_cache_info", "ffsyrk_probe_pipe",
+           "ffsyrk_i8_schedule", "ffsyrk_i8_digit_bounds"]:
                 getattr(L, name).restype = i32
             L.ffsyrk_noalloc.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk_batched.argtypes = [i32, i64, P(i64), P(i64), u32, P(vp), P(i64), P(vp),
@@ -142,6 +144,10 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_leaf_schedule.restype = i32
             L.ffsyrk_digit_bounds.argtypes = [u32, P(i32)]
             L.ffsyrk_digit_bounds.restype = i32
+            L.ffsyrk_i8_schedule.argtypes = [u32, i32, P(i32), i32]
+            L.ffsyrk_i8_schedule.restype = i32
+            L.ffsyrk_i8_digit_bounds.argtypes = [u32, P(i32)]
+            L.ffsyrk_i8_digit_bounds.restype = i32
             L.ffsyrk_digit_base.argtypes = [u32]
             L.ffsyrk_digit_base.restype = i32
             for name in ["ffsyrk_plan", "ffsyrk_plan_destroy", "ffsyrk_with_plan", "ffsyrk",
@@ -395,6 +401,26 @@ def leaf_schedule(p: int, kblocks: int) -> list[tuple[int, int, int, int, bool]]
     lib().ffsyrk_leaf_schedule(int(p), int(kblocks), buf, n)
     return [(buf[5 * q], buf[5 * q + 1], buf[5 * q + 2], buf[5 * q + 3], bool(buf[5 * q + 4]))
             for q in range(n)]
+
+
+def i8_schedule(p: int, kblocks: int) -> list[tuple[int, int, int, int, bool]]:
+    """The INT8 leaf's K schedule (128-wide k-blocks): (i, j, first k-block, k-blocks, opens a unit)."""
+    n = lib().ffsyrk_i8_schedule(int(p), int(kblocks), None, 0)
+    if n < 0:
+        raise ValueError("bad p or kblocks")
+    buf = (ctypes.c_int32 * (5 * max(n, 1)))()
+    lib().ffsyrk_i8_schedule(int(p), int(kblocks), buf, n)
+    return [(buf[5 * q], buf[5 * q + 1], buf[5 * q + 2], buf[5 * q + 3], bool(buf[5 * q + 4]))
+            for q in range(n)]
+
+
+def i8_digit_bounds(p: int) -> list[int]:
+    """Bounds on the INT8 leaf's byte digits of residues mod p (255 below the signed top digit)."""
+    out = (ctypes.c_int32 * 3)()
+    D = lib().ffsyrk_i8_digit_bounds(int(p), out)
+    if D < 0:
+        raise ValueError("bad p")
+    return [out[t] for t in range(D)]
 
 
 def digit_bounds(p: int) -> list[int]:

@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path against the CPU oracle, bit-exactly (marked gpu).
 
 Sizes span several tiles of each leaf (64×64 for the int64 leaf, 128×256 for
-the tensor-core leaf) with ragged tails; every recursion depth used in
+the tensor-core leaf, 128×128 for the INT8 leaf) with ragged tails; every recursion depth used in
 practice; the three Y forms (scalar, a = 1 / b = √−2, Algorithm 3); inputs
 above p; odd strides; both triangles; the degenerate n = 0, n = 1, k = 0.
 """
@@ -15,7 +15,7 @@ from parity_util import SENTINEL, check_against_oracle, gpu_syrk, residues
 pytestmark = pytest.mark.gpu
 
 PRIMES = [65521, 131071, 8388593, 16777213, 131041, 3, 11, 251]
-LEAVES = ["i64", "tc"]
+LEAVES = ["i64", "tc", "i8"]
 
 
 @pytest.fixture(scope="module", autouse=True)

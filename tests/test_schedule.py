@@ -123,3 +123,85 @@ def test_digit_products_rebuild_the_product(p):
     assert np.array_equal(exact, S.dot(S.T))
     weighted = sum(pow(b, i + j, p) * Dt[i].dot(Dt[j].T) for i in range(D) for j in range(D))
     assert np.array_equal(weighted % p, X.dot(X.T) % p)
+
+
+# ---- the INT8 leaf: bytes of the two's complement, int32 units within 2^30 ----
+
+def twos_bytes(s, D):
+    """Digits of s as the D bytes of its two's complement: unsigned low bytes, signed top byte."""
+    out = [(s >> (8 * t)) & 255 for t in range(D - 1)]
+    out.append(s >> (8 * (D - 1)))  # floor division: the signed top digit
+    return out
+
+
+@pytest.mark.parametrize("p,D,bounds", [(251, 1, [125]), (257, 2, [255, 1]), (65521, 2, [255, 128]),
+                                        (65537, 3, [255, 255, 1]), (131071, 3, [255, 255, 1]),
+                                        (8388593, 3, [255, 255, 64]), (16777213, 3, [255, 255, 128])])
+def test_i8_digit_count_and_bounds(p, D, bounds):
+    # D is the least count whose top byte holds every symmetric residue's sign
+    assert ffsyrk.i8_digit_bounds(p) == bounds and len(bounds) == D
+    h = (p - 1) // 2
+    assert -(1 << (8 * D - 1)) <= -h and h <= (1 << (8 * D - 1)) - 1
+    if D > 1:
+        assert h > (1 << (8 * (D - 1) - 1)) - 1  # one digit fewer would not do
+
+
+@pytest.mark.parametrize("p", [3, 251, 257, 65521, 65537, 131071, 8388593, 16777213])
+def test_i8_digits_cover_every_residue(p):
+    bounds = ffsyrk.i8_digit_bounds(p)
+    D = len(bounds)
+    h = (p - 1) // 2
+    samples = range(-h, h + 1) if p < 300000 else list(range(-h, -h + 70000)) + list(range(h - 70000, h + 1))
+    seen = [0] * D
+    for s in samples:
+        d = twos_bytes(s, D)
+        assert sum(dt * 256 ** t for t, dt in enumerate(d)) == s
+        for t in range(D - 1):
+            assert 0 <= d[t] <= 255 == bounds[t]
+        assert -128 <= d[-1] <= 127 and abs(d[-1]) <= bounds[-1]   # fits a signed byte
+        seen = [max(a, abs(x)) for a, x in zip(seen, d)]
+    assert seen == bounds  # tight
+
+
+@pytest.mark.parametrize("p", [251, 257, 65521, 131071, 8388593])
+@pytest.mark.parametrize("kblocks", [1, 2, 3, 100, 128, 129, 300, 1000])
+def test_i8_schedule_units_exact_and_complete(p, kblocks):
+    bounds = ffsyrk.i8_digit_bounds(p)
+    D = len(bounds)
+    segs = ffsyrk.i8_schedule(p, kblocks)
+    assert segs and segs[0][4]
+    covered = {}
+    unit_sum, unit_class = 0, None
+    for i, j, kb0, nkb, first in segs:
+        assert nkb >= 1 and 0 <= kb0 and kb0 + nkb <= kblocks
+        if first:
+            unit_sum, unit_class = 0, i + j
+        assert i + j == unit_class
+        unit_sum += 128 * nkb * bounds[i] * bounds[j]
+        assert unit_sum <= 1 << 30                  # int32, with room for the reduction's offset
+        for kb in range(kb0, kb0 + nkb):
+            covered[(i, j, kb)] = covered.get((i, j, kb), 0) + 1
+    assert set(covered) == {(i, j, kb) for i in range(D) for j in range(D) for kb in range(kblocks)}
+    assert all(c == 1 for c in covered.values())
+
+
+def test_i8_one_unit_per_class_up_to_16384():
+    # p = 65521: K = 16384 (128 k-blocks) takes exactly one unit per weight class
+    segs = ffsyrk.i8_schedule(65521, 128)
+    assert sum(1 for s in segs if s[4]) == 3
+
+
+@pytest.mark.parametrize("p", [251, 257, 65521, 131071, 8388593, 16777213])
+def test_i8_digit_products_rebuild_the_product(p):
+    # Σ_{i,j} 256^{i+j}·D_i·D_jᵀ = S·Sᵀ over the integers with the byte digits
+    D = len(ffsyrk.i8_digit_bounds(p))
+    rng = np.random.default_rng(p + 1)
+    X = rng.integers(0, p, size=(6, 9)).astype(object)
+    h = (p - 1) // 2
+    S = np.where(X > h, X - p, X)
+    digits = np.array([[twos_bytes(int(s), D) for s in row] for row in S], dtype=object)
+    Dt = [digits[:, :, t] for t in range(D)]
+    exact = sum(256 ** (i + j) * Dt[i].dot(Dt[j].T) for i in range(D) for j in range(D))
+    assert np.array_equal(exact, S.dot(S.T))
+    weighted = sum(pow(256, i + j, p) * Dt[i].dot(Dt[j].T) for i in range(D) for j in range(D))
+    assert np.array_equal(weighted % p, X.dot(X.T) % p)
