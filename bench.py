@@ -398,7 +398,7 @@ def run_ours(args):
     step_ms = max_over_ranks(step_ms, ws)
     value = ws * n * n * k / (step_ms * 1e-3)
     leaf_ms = statistics.median(s["leaf_ms"] for s in stage)
-    tmacs = stage[-1]["field_macs"] * info["digits"] ** 2
+    tmacs = stage[-1]["field_macs"] * info["products"]
     launches = stage[-1]["launches"]
 
     # roofline of the dominant kernel (the grouped tensor-core leaf launch)
@@ -442,8 +442,14 @@ def run_ours(args):
         if any(info["winograd"]):
             # the same depth with the general products computed classically
             legs.append(("fast_tc_no_winograd", "tc", info["levels"], 0))
+        if info["products"] < info["digits"] ** 2:
+            # the same plan with the D² schoolbook digit products
+            legs.append(("fast_tc_schoolbook_digits", "tc", levels, "schoolbook"))
         for name, leaf, lv, wg in legs:
-            pl = ffsyrk.Plan(p, n, k, leaf=leaf, levels=lv, winograd=wg,
+            dp = None
+            if wg == "schoolbook":
+                dp, wg = "schoolbook", args.winograd
+            pl = ffsyrk.Plan(p, n, k, leaf=leaf, levels=lv, winograd=wg, digit_products=dp,
                              tile_ctas=args.tile_ctas if wg == 0 else None)
             slow = leaf != "tc" and n * n * k > 2 ** 36  # calls of 0.1 s or more
             st = 2 if slow else max(3, min(args.steps, 5))
@@ -550,7 +556,7 @@ def run_ours(args):
                 "dtype": "u32", "data": "synthetic",
                 "config": {"workload": args.workload, "description": describe(desc, info),
                            "n": n, "k": k, "p": p, "levels": info["levels"],
-                           "digits": info["digits"],
+                           "digits": info["digits"], "digit_products": info["products"],
                            "winograd": info["winograd"][: info["levels"]],
                            "leaf": {1: "tc_bf16", 2: "i64"}[info["leaf"]],
                            "tile_ctas": info["tile_ctas"],

@@ -97,7 +97,16 @@ typedef struct {
                           take exactly that): −1 (default) = as many as the
                           built-in cost model finds worth it; 0 = none;
                           w ≥ 1 = min(w, L − 1 − d) at every depth d.       */
-    int32_t reserved[3]; /* must be zero                                       */
+    int32_t digit_products; /* tensor-core leaf: how the digit planes of the two
+                          operands are multiplied (all exact).  0 (default):
+                          Karatsuba where it applies, else schoolbook;
+                          1 = schoolbook, the D² products X_i·Z_jᵀ;
+                          2 = Karatsuba: when every digit is at most 128 in
+                          magnitude (byte digits, e.g. p = 65521, 8388593),
+                          each operand also carries the D(D−1)/2 planes
+                          X_i + X_j and D(D+1)/2 products replace the D²
+                          (3 for 4, 6 for 9); elsewhere the same as 1.      */
+    int32_t reserved[2]; /* must be zero                                       */
 } ffsyrk_options_t;
 
 /* The defaults: automatic leaf, recursion depth and Winograd levels. */
@@ -360,6 +369,11 @@ typedef struct {
     float tuned_ms;      /* the winning candidate's time per call, or 0      */
     int32_t winograd[6]; /* levels of Algorithm 1 for the general products of
                             depth d = 0..5 at max_n × max_k (0 beyond L − 1) */
+    int32_t planes;      /* digit planes per leaf operand (D, or D(D+1)/2
+                            with Karatsuba digit products)                  */
+    int32_t products;    /* digit products per field multiply-add of the
+                            leaf: D², or D(D+1)/2 with Karatsuba; 1 for the
+                            int64 leaf                                       */
 } ffsyrk_plan_info_t;
 
 ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t plan, ffsyrk_plan_info_t *info);
@@ -440,6 +454,21 @@ ffsyrk_status_t ffsyrk_plan_selftest_timeout(ffsyrk_plan_t plan, int64_t limit_n
  * Σ 64·count·bound(i)·bound(j) ≤ 2^24 with the bounds of
  * ffsyrk_digit_bounds(). */
 int32_t ffsyrk_leaf_schedule(uint32_t p, int32_t kblocks, int32_t *out, int32_t cap);
+
+/* The same with Karatsuba digit products (option digit_products = 2), for
+ * a leaf K of 64·kblocks: every segment multiplies plane i of X by plane i
+ * of Z (i = j in the output), planes as ffsyrk_digit_planes() lists them;
+ * every unit holds one product and satisfies Σ 64·count·bound(i)² ≤ 2^24.
+ * Returns −1 for a bad p or argument. */
+int32_t ffsyrk_leaf_schedule_ks(uint32_t p, int32_t kblocks, int32_t *out, int32_t cap);
+
+/* The Karatsuba digit planes of p: 0 if they do not apply (a digit sum
+ * could exceed 256, or one digit), else the plane count P = D(D+1)/2 with
+ * max_digit[t] the bound on plane t (planes 0..D−1 the digits of
+ * ffsyrk_digit_bounds(), then the sums (0,1), (0,2), (1,2)) and weight[t]
+ * the residue w_t with X·Zᵀ ≡ Σ_t w_t·plane_t(X)·plane_t(Z)ᵀ (mod p).
+ * Arrays of 6 entries.  −1 for a bad p. */
+int32_t ffsyrk_digit_planes(uint32_t p, int32_t *max_digit, uint32_t *weight);
 
 /* The same for the INT8 leaf (FFSYRK_LEAF_I8), for a leaf K of
  * 128·kblocks: digits are the bytes of the two's-complement symmetric

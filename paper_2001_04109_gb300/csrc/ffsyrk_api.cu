@@ -52,7 +52,20 @@ MulConst make_mul(uint32_t w, uint32_t p) {
     return c;
 }
 
-DigitScheme make_digits(uint32_t p) {
+// Karatsuba digit products are possible when the sum of any two digits is
+// still an exact bf16 integer (|d_i| + |d_j| ≤ 256) with byte digits.
+bool karatsuba_eligible(const DigitScheme &ds) {
+    if (ds.D < 2 || ds.base != 256) return false;
+    for (int i = 0; i < ds.D; ++i)
+        for (int j = i + 1; j < ds.D; ++j)
+            if (ds.max_digit[i] + ds.max_digit[j] > 256) return false;
+    return true;
+}
+
+// Digit products per field multiply-add of the leaf (D², or D(D+1)/2 with Karatsuba).
+inline int nprod(const DigitScheme &ds) { return ds.ks ? ds.nplanes : ds.D * ds.D; }
+
+DigitScheme make_digits(uint32_t p, bool karatsuba = false) {
     DigitScheme ds{};
     const int64_t H = (p - 1) / 2;
     int D = 1;
@@ -84,6 +97,31 @@ DigitScheme make_digits(uint32_t p) {
             for (int e = 0; e < i + j; ++e) w = w * (uint64_t)ds.base % p;
             ds.weight[i][j] = make_mul((uint32_t)w, p);
         }
+    ds.nplanes = D;
+    if (karatsuba && karatsuba_eligible(ds)) {
+        // planes D.. hold X_i + X_j (i < j); the product of plane t with
+        // itself takes weight w_t (see DigitScheme): the schoolbook weights
+        // rearranged, X_i·Z_jᵀ + X_j·Z_iᵀ = M_ij − P_ii − P_jj
+        uint64_t pw[2 * kMaxDigits] = {1};
+        for (int e = 1; e < 2 * kMaxDigits; ++e) pw[e] = pw[e - 1] * 256u % p;
+        ds.ks = 1;
+        int t = D;
+        uint64_t wsingle[kMaxDigits];
+        for (int i = 0; i < D; ++i) wsingle[i] = pw[2 * i];
+        for (int i = 0; i < D; ++i)
+            for (int j = i + 1; j < D; ++j, ++t) {
+                ds.max_digit[t] = ds.max_digit[i] + ds.max_digit[j];
+                ds.weight[t][t] = make_mul((uint32_t)pw[i + j], p);
+                wsingle[i] = (wsingle[i] + p - pw[i + j]) % p;
+                wsingle[j] = (wsingle[j] + p - pw[i + j]) % p;
+            }
+        ds.nplanes = t;
+        for (int i = 0; i < D; ++i) ds.weight[i][i] = make_mul((uint32_t)wsingle[i], p);
+        for (int a = 0; a < ds.nplanes; ++a) {
+            const int64_t kc = (int64_t(1) << 24) / ((int64_t)ds.max_digit[a] * ds.max_digit[a]);
+            ds.chunk_kb[a][a] = (int)std::max<int64_t>(1, kc / 64);
+        }
+    }
     ds.offset = (uint32_t)(((uint64_t(1) << 24) + p - 1) / p * p);
     // sums start below 2p and grow by less than 2p per unit: m units fit
     // while 2p·(m + 1) ≤ 2^32
@@ -113,6 +151,7 @@ DigitScheme make_digits_i8(uint32_t p) {
             for (int e = 0; e < i + j; ++e) w = w * 256u % p;
             ds.weight[i][j] = make_mul((uint32_t)w, p);
         }
+    ds.nplanes = D;
     ds.offset = (uint32_t)((kSegI8.bound + p - 1) / p * p);
     ds.lazy_units = 0;  // the INT8 leaf reduces its residue sums after every unit
     return ds;
@@ -177,14 +216,15 @@ inline int64_t pow7(int d) {
 }
 
 // Levels of Algorithm 1 for a general product h×h×w.  One level removes 1/8
-// of its leaf multiply-adds (h²w·D²/8 digit products) and adds about
-// (16 + 3D)·h·w + 14·h² bytes of streaming traffic: both operands written as
-// uint32 and read back by the pre-additions, 7/4 as many digit planes, 7/4
-// as many product entries written by the leaf, read back and combined by the
+// of its leaf multiply-adds (h²w·Q/8 digit products, Q per field
+// multiply-add) and adds about (16 + 3P)·h·w + 14·h² bytes of streaming
+// traffic (P digit planes per operand): both operands written as uint32
+// and read back by the pre-additions, 7/4 as many digit planes, 7/4 as many
+// product entries written by the leaf, read back and combined by the
 // post-additions.  Rates as in level_pays.
-bool sw_level_pays(int64_t h, int64_t w, int D) {
-    const double saved = (double)h * h * w * D * D / 8.0 / 8.5e14;
-    const double extra = ((16.0 + 3.0 * D) * h * w + 14.0 * (double)h * h) / 4.0e12;
+bool sw_level_pays(int64_t h, int64_t w, int Q, int P) {
+    const double saved = (double)h * h * w * Q / 8.0 / 8.5e14;
+    const double extra = ((16.0 + 3.0 * P) * h * w + 14.0 * (double)h * h) / 4.0e12;
     return saved > extra && h >= 2048;
 }
 
@@ -192,7 +232,7 @@ bool sw_level_pays(int64_t h, int64_t w, int D) {
 // Algorithm 1 (the paper's G-i variants use L − 1 − d), so that every block
 // they split into has a size of the geometry.  opt < 0: as many levels as
 // pay; otherwise min(opt, L − 1 − d).
-void set_winograd(Geometry &g, int opt, int D) {
+void set_winograd(Geometry &g, int opt, int Q, int P) {
     for (int d = 0; d < kMaxLevels; ++d) g.sw[d] = 0;
     for (int d = 0; d + 1 < g.L; ++d) {
         const int top = g.L - 1 - d;
@@ -201,7 +241,7 @@ void set_winograd(Geometry &g, int opt, int D) {
             continue;
         }
         int sv = 0;
-        while (sv < top && sw_level_pays(g.h[d + 1 + sv], g.w[d + 1 + sv], D)) ++sv;
+        while (sv < top && sw_level_pays(g.h[d + 1 + sv], g.w[d + 1 + sv], Q, P)) ++sv;
         g.sw[d] = sv;
     }
 }
@@ -244,7 +284,8 @@ double leaf_field_macs(const Geometry &g) {
     return macs + (double)pow3(g.L) * (double)g.h[g.L] * (g.h[g.L] + 1) / 2 * (double)g.w[g.L];
 }
 
-Layout make_layout(const Geometry &g, int leaf, int D) {
+// D: digit planes per operand of the leaf (with Karatsuba sum planes: ks).
+Layout make_layout(const Geometry &g, int leaf, int D, bool ks = false) {
     Layout lay;
     lay.g = g;
     lay.leaf = leaf;
@@ -260,7 +301,7 @@ Layout make_layout(const Geometry &g, int leaf, int D) {
     lay.narenas = g.L == 0 ? 1 : g.L;
     for (int j = j0; j <= (g.L == 0 ? 0 : g.L); ++j) {
         Arena &a = lay.arena[j];
-        a.kind = tc ? ARENA_BF16 : i8 ? ARENA_I8 : ARENA_U32;
+        a.kind = tc ? (ks ? ARENA_BF16_KS : ARENA_BF16) : i8 ? ARENA_I8 : ARENA_U32;
         a.planes = (tc || i8) ? D : 1;
         a.rpad = rup(std::max<int64_t>(g.h[j], 1), 256);
         // 128-byte rows of k-blocks: 64 bf16 digits or 128 byte digits
@@ -541,6 +582,28 @@ int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int ca
         for (int j = 0; j < D; ++j) span = std::min(span, std::max(1, ds.chunk_kb[i][j]));
     const int nspans = kblocks > 0 ? (kblocks + span - 1) / span : 0;
     int count = 0;
+    if (ds.ks) {
+        // Karatsuba: every product P_t (plane t with itself) has its own
+        // weight, so its own units; the span follows the single digits'
+        // chunks (above), and a product with a shorter chunk (a digit sum)
+        // takes several units of balanced length inside the span
+        for (int sp = 0, s0 = 0; sp < nspans; ++sp) {
+            const int len = kblocks / nspans + (sp < kblocks % nspans ? 1 : 0);
+            for (int t = 0; t < ds.nplanes; ++t) {
+                const int64_t cost = rule.kbw * (int64_t)ds.max_digit[t] * ds.max_digit[t];
+                const int most = (int)std::max<int64_t>(1, kBound / cost);
+                const int nu = (len + most - 1) / most;
+                for (int u = 0, pos = s0; u < nu; ++u) {
+                    const int nkb = len / nu + (u < len % nu ? 1 : 0);
+                    if (count >= cap) return -1;
+                    out[count++] = LeafSeg{pos, (uint16_t)nkb, (uint8_t)(t << 4 | t), 1};
+                    pos += nkb;
+                }
+            }
+            s0 += len;
+        }
+        return count;
+    }
     for (int sp = 0, s0 = 0; sp < nspans; ++sp) {
         const int len = kblocks / nspans + (sp < kblocks % nspans ? 1 : 0);
         const int s1 = s0 + len;
@@ -601,7 +664,7 @@ void attach_segments(const DigitScheme &ds, std::vector<LeafProd> &prods,
 bool encode_arena_tmap(const Arena &a, void *out) {
     EncodeTiledFn fn = get_encode_fn();
     if (!fn) return false;
-    const bool i8 = a.kind == ARENA_I8;
+    const bool i8 = a.kind == ARENA_I8;  // otherwise bf16 planes (ARENA_BF16 or ARENA_BF16_KS)
     cuuint64_t dims[2] = {(cuuint64_t)a.kpad, (cuuint64_t)a.rows};
     cuuint64_t strides[1] = {(cuuint64_t)(a.kpad * (i8 ? 1 : 2))};
     cuuint32_t box[2] = {i8 ? 128u : 64u, 128};  // 128-byte rows either way
@@ -628,6 +691,7 @@ struct ffsyrk_plan_st {
     int levels_opt = FFSYRK_LEVELS_AUTO;
     int ctas_opt = 0;
     int sw_opt = -1;  // levels of Algorithm 1: −1 automatic, else the cap
+    int dp_opt = 0;   // digit products: 0 automatic, 1 schoolbook, 2 Karatsuba
     bool gemmt = false;  // the imaginary-part plan of a Hermitian product (L = 0)
     int64_t max_n = 0, max_k = 0;
     int L_max = 0;  // levels used at the max shape
@@ -691,7 +755,7 @@ const DigitScheme &leaf_ds(const ffsyrk_plan_st *pl) {
 // Algorithm 1 for its general products.
 Geometry plan_geometry(const ffsyrk_plan_st *pl, int64_t n, int64_t k, int L) {
     Geometry g = make_geometry(n, k, L);
-    set_winograd(g, pl->sw_opt, pl->ds.D);
+    set_winograd(g, pl->sw_opt, nprod(pl->ds), pl->ds.nplanes);
     g.gemmt = pl->gemmt && L == 0;
     return g;
 }
@@ -699,21 +763,22 @@ Geometry plan_geometry(const ffsyrk_plan_st *pl, int64_t n, int64_t k, int L) {
 namespace {
 
 // One more level of Algorithm 2 on an n×k (sub)problem pays when the leaf
-// multiply-adds it saves (1/8 of the classical n²k/2·D², Thm 4.1 / Table 1)
-// take longer than the bytes it adds: the post-additions (≈ 9n² bytes) and
-// the extra digit planes of the pre-additions (≈ 1.5·D·n·k bytes).  Rates
-// measured on GB300: ≈ 8.5e14 issued digit multiply-adds/s in the leaf,
-// ≈ 4 TB/s in the addition kernels.
-bool level_pays(int64_t n, int64_t k, int D) {
-    const double leaf_saved = 0.125 * 0.5 * (double)n * n * k * D * D / 8.5e14;
-    const double extra = (9.0 * n * n + 1.5 * D * (double)n * k) / 4.0e12;
+// multiply-adds it saves (1/8 of the classical n²k/2·Q, Q digit products
+// per field multiply-add; Thm 4.1 / Table 1) take longer than the bytes it
+// adds: the post-additions (≈ 9n² bytes) and the extra digit planes of the
+// pre-additions (≈ 1.5·P·n·k bytes, P planes per operand).  Rates measured
+// on GB300: ≈ 8.5e14 issued digit multiply-adds/s in the leaf, ≈ 4 TB/s in
+// the addition kernels.
+bool level_pays(int64_t n, int64_t k, int Q, int P) {
+    const double leaf_saved = 0.125 * 0.5 * (double)n * n * k * Q / 8.5e14;
+    const double extra = (9.0 * n * n + 1.5 * P * (double)n * k) / 4.0e12;
     return leaf_saved > extra && n >= 1024 && k >= 256;
 }
 
 int choose_levels(const ffsyrk_plan_st *pl, int64_t n, int64_t k) {
     if (pl->levels_opt >= 0) return pl->levels_opt;
     int L = 0;
-    while (L < 4 && level_pays(n >> L, k >> L, pl->ds.D)) ++L;
+    while (L < 4 && level_pays(n >> L, k >> L, nprod(pl->ds), pl->ds.nplanes)) ++L;
     return L;
 }
 
@@ -736,7 +801,7 @@ int choose_ctas(const ffsyrk_plan_st *pl, const Geometry &g) {
     if (leaf_tiles_bound(g, pl->leaf) < pl->sms) return 1;
     // digit multiply-adds of the leaf over a measured ≈ 9e14 per second
     const double macs = leaf_field_macs(g);
-    const double est_ms = macs * pl->ds.D * pl->ds.D / 9e14 * 1e3;
+    const double est_ms = macs * nprod(pl->ds) / 9e14 * 1e3;
     return est_ms < 40.0 ? 2 : 1;
 }
 
@@ -982,7 +1047,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         const int64_t h = g.h[d + 1];
         return reinterpret_cast<uint32_t *>(ws + lay.g_off[d]) + (2 * t + q) * h * h;
     };
-    int cost_mult = tc ? pl->ds.D * pl->ds.D : i8 ? pl->ds8.D * pl->ds8.D : 1;
+    int cost_mult = tc ? nprod(pl->ds) : i8 ? pl->ds8.D * pl->ds8.D : 1;
 
     if (g.L == 0) {
         LeafProd pr{};
@@ -1225,7 +1290,7 @@ ffsyrk_status_t validate_p(uint32_t p) {
 
 int64_t workspace_need(const ffsyrk_plan_st *pl, int64_t n, int64_t k, int L, int64_t *desc) {
     const Geometry g = plan_geometry(pl, n, k, L);
-    Layout lay = make_layout(g, pl->leaf, leaf_ds(pl).D);
+    Layout lay = make_layout(g, pl->leaf, leaf_ds(pl).nplanes, leaf_ds(pl).ks != 0);
     *desc = desc_capacity(g, pl->leaf);
     return lay.data_bytes;
 }
@@ -1238,7 +1303,7 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
     const Geometry &g = lay.g;
     const Descs &D = pl->desc;
     char *dd = pl->ws + pl->data_cap;
-    const int kind = lay.leaf == FFSYRK_LEAF_TC_BF16 ? ARENA_BF16
+    const int kind = lay.leaf == FFSYRK_LEAF_TC_BF16 ? (pl->ds.ks ? ARENA_BF16_KS : ARENA_BF16)
                      : lay.leaf == FFSYRK_LEAF_I8  ? ARENA_I8
                                                    : ARENA_U32;
     const DigitScheme &lds = leaf_ds(pl);
@@ -1417,7 +1482,7 @@ void record_work(ffsyrk_plan_st *pl) {
         const double K = (double)(pr.kblocks) * kbw;
         f += (pr.tri == 0 ? (double)pr.rows * pr.cols : (double)pr.rows * (pr.rows + 1) / 2) * K;
     }
-    pl->last_tensor_macs = f * (lay.leaf == FFSYRK_LEAF_TC_BF16 ? pl->ds.D * pl->ds.D
+    pl->last_tensor_macs = f * (lay.leaf == FFSYRK_LEAF_TC_BF16 ? nprod(pl->ds)
                                 : lay.leaf == FFSYRK_LEAF_I8   ? pl->ds8.D * pl->ds8.D
                                                                : 1);
     // field multiply-adds of the method (padded block sizes, unpadded K at L = 0)
@@ -1435,7 +1500,7 @@ ffsyrk_status_t enqueue(ffsyrk_plan_st *pl, int uplo, int64_t n, int64_t k, cons
     auto key = std::make_tuple(n, k, A, lda, C, ldc, uplo, L, sc.mode, sc.alpha.w, sc.beta.w);
     if (!pl->have_last || key != pl->last_key) {
         const Geometry g = plan_geometry(pl, n, k, L);
-        Layout lay = make_layout(g, pl->leaf, leaf_ds(pl).D);
+        Layout lay = make_layout(g, pl->leaf, leaf_ds(pl).nplanes, leaf_ds(pl).ks != 0);
         lay.ctas = choose_ctas(pl, g);
         if (lay.data_bytes > pl->data_cap) return FFSYRK_ERR_TOO_LARGE;
         // the staging blob may still be in flight from the previous upload
@@ -1494,24 +1559,31 @@ void destroy_plan(ffsyrk_plan_st *pl) {
 }
 
 
-// ---- autotuning: time every candidate (depth, tile variant) at the plan's size ----
+// ---- autotuning: time every candidate plan variant at the plan's size ----
+// A candidate: depth L, SMs per tile (1 or 2), Winograd cap (−1 = the cost
+// model's levels, 0 = none) and digit products (Karatsuba or schoolbook).
+struct TuneChoice {
+    int L = 0, ctas = 1, sw = -1, ks = 0;
+    float ms = 0;
+};
 std::mutex g_tune_mu;
-std::map<std::string, std::tuple<int, int, float>> g_tune;  // key -> (levels, ctas, ms)
+std::map<std::string, TuneChoice> g_tune;  // key -> best candidate
 bool g_tune_loaded = false;
 
 std::string tune_key(const ffsyrk_plan_st *pl) {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, pl->device);
     char buf[512];
-    snprintf(buf, sizeof buf, "%s|sm%d|D%d|Y%d|n%lld|k%lld|leaf%d", prop.name,
+    snprintf(buf, sizeof buf, "%s|sm%d|D%d|Y%d|n%lld|k%lld|leaf%d|sw%d|dp%d", prop.name,
              prop.multiProcessorCount, pl->ds.D, pl->yc.form, (long long)pl->max_n,
-             (long long)pl->max_k, pl->leaf);
+             (long long)pl->max_k, pl->leaf, pl->sw_opt, pl->dp_opt);
     std::string key(buf);
     for (char &c : key)
         if (c == ' ') c = '_';
     return key;
 }
 
+// The cache file holds one line per key: key L ctas sw ks ms.
 void tune_cache_load() {
     if (g_tune_loaded) return;
     g_tune_loaded = true;
@@ -1519,20 +1591,22 @@ void tune_cache_load() {
     if (!path || !*path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    char key[512];
-    int L = 0, c = 0;
-    float ms = 0;
-    while (fscanf(f, "%511s %d %d %f", key, &L, &c, &ms) == 4) g_tune[key] = std::make_tuple(L, c, ms);
+    char line[768], key[512];
+    while (fgets(line, sizeof line, f)) {
+        TuneChoice t;
+        if (sscanf(line, "%511s %d %d %d %d %f", key, &t.L, &t.ctas, &t.sw, &t.ks, &t.ms) == 6)
+            g_tune[key] = t;
+    }
     fclose(f);
 }
 
-void tune_cache_store(const std::string &key, int L, int c, float ms) {
-    g_tune[key] = std::make_tuple(L, c, ms);
+void tune_cache_store(const std::string &key, const TuneChoice &t) {
+    g_tune[key] = t;
     const char *path = getenv("FFSYRK_TUNE_CACHE");
     if (!path || !*path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %.6f\n", key.c_str(), L, c, ms);
+    fprintf(f, "%s %d %d %d %d %.6f\n", key.c_str(), t.L, t.ctas, t.sw, t.ks, t.ms);
     fclose(f);
 }
 
@@ -1544,15 +1618,52 @@ std::vector<int> tune_levels(int64_t n, int64_t k) {
     return Ls;
 }
 
+// Every candidate of a plan: depths × tile variants, and where the caller
+// left them automatic, Winograd on/off (only where the cost model would
+// take a level) and Karatsuba/schoolbook digit products (where they apply).
+std::vector<TuneChoice> tune_candidates(const ffsyrk_plan_st *pl) {
+    std::vector<TuneChoice> out;
+    const bool tc = pl->leaf == FFSYRK_LEAF_TC_BF16;
+    std::vector<int> kss{pl->ds.ks};
+    if (tc && pl->dp_opt == 0 && karatsuba_eligible(make_digits(pl->p, false))) kss = {1, 0};
+    for (int L : tune_levels(pl->max_n, pl->max_k))
+        for (int ks : kss) {
+            const DigitScheme ds = make_digits(pl->p, ks != 0);
+            std::vector<int> sws{pl->sw_opt};
+            if (pl->sw_opt < 0 && L >= 2) {
+                Geometry g = make_geometry(pl->max_n, pl->max_k, L);
+                set_winograd(g, -1, nprod(ds), ds.nplanes);
+                bool any = false;
+                for (int d = 0; d < L; ++d) any = any || g.sw[d] > 0;
+                if (any) sws.push_back(0);
+            }
+            for (int sw : sws)
+                for (int c = 1; c <= (tc ? 2 : 1); ++c) {
+                    TuneChoice t;
+                    t.L = L;
+                    t.ctas = c;
+                    t.sw = sw;
+                    t.ks = ks;
+                    out.push_back(t);
+                }
+        }
+    return out;
+}
+
 ffsyrk_status_t autotune(ffsyrk_plan_st *pl) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_cache_load();
     const std::string key = tune_key(pl);
+    auto apply = [&](const TuneChoice &t) {
+        pl->levels_opt = t.L;
+        pl->ctas_opt = t.ctas;
+        pl->sw_opt = t.sw;
+        pl->ds = make_digits(pl->p, t.ks != 0);
+        pl->tuned_ms = t.ms;
+    };
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-        pl->levels_opt = std::get<0>(it->second);
-        pl->ctas_opt = std::get<1>(it->second);
-        pl->tuned_ms = std::get<2>(it->second);
+        apply(it->second);
         pl->autotuned = true;
         return FFSYRK_SUCCESS;
     }
@@ -1567,39 +1678,33 @@ ffsyrk_status_t autotune(ffsyrk_plan_st *pl) {
         cudaGetLastError();
         result = FFSYRK_ERR_ALLOC;
     }
-    int bestL = 0, bestC = 1;
-    float best = 1e30f;
+    TuneChoice best;
+    best.ms = 1e30f;
     if (result == FFSYRK_SUCCESS) {
-        cudaMemsetAsync(A, 0x5A, (size_t)n * k * 4, st);  // values reduce mod p; timing only
+        // uniform residues: the candidates' power draw and clocks (which
+        // decide between some of them) follow the operands' values
+        if (launch_fill_residues(A, n * k, pl->p, 0x7f4a7c15ull, st) != cudaSuccess) result = FFSYRK_ERR_CUDA;
         pl->direct = true;
-        std::vector<int> cs{1};
-        if (pl->leaf == FFSYRK_LEAF_TC_BF16) cs.push_back(2);
-        for (int L : tune_levels(n, k)) {
-            for (int c : cs) {
-                pl->levels_opt = L;
-                pl->ctas_opt = c;
-                pl->have_last = false;
-                ffsyrk_status_t s = enqueue(pl, FFSYRK_LOWER, n, k, A, k, C, n, st);
-                if (s != FFSYRK_SUCCESS) continue;  // e.g. a depth that does not fit
-                cudaEventRecord(e0, st);
-                const int reps = 3;
-                for (int r = 0; r < reps && s == FFSYRK_SUCCESS; ++r)
-                    s = enqueue(pl, FFSYRK_LOWER, n, k, A, k, C, n, st);
-                cudaEventRecord(e1, st);
-                if (cudaEventSynchronize(e1) != cudaSuccess || s != FFSYRK_SUCCESS) {
-                    result = FFSYRK_ERR_CUDA;
-                    break;
-                }
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms /= reps;
-                if (ms < best) {
-                    best = ms;
-                    bestL = L;
-                    bestC = c;
-                }
-            }
+        for (const TuneChoice &cand : tune_candidates(pl)) {
             if (result != FFSYRK_SUCCESS) break;
+            TuneChoice t = cand;
+            apply(t);
+            pl->have_last = false;
+            ffsyrk_status_t s = enqueue(pl, FFSYRK_LOWER, n, k, A, k, C, n, st);
+            if (s != FFSYRK_SUCCESS) continue;  // e.g. a variant that does not fit
+            cudaEventRecord(e0, st);
+            const int reps = 3;
+            for (int r = 0; r < reps && s == FFSYRK_SUCCESS; ++r)
+                s = enqueue(pl, FFSYRK_LOWER, n, k, A, k, C, n, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess || s != FFSYRK_SUCCESS) {
+                result = FFSYRK_ERR_CUDA;
+                break;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t.ms = ms / reps;
+            if (t.ms < best.ms) best = t;
         }
         pl->direct = false;
         pl->have_last = false;
@@ -1613,11 +1718,10 @@ ffsyrk_status_t autotune(ffsyrk_plan_st *pl) {
     if (e1) cudaEventDestroy(e1);
     if (result != FFSYRK_SUCCESS) return result;
     if (pl->err_host[0] != 0) return FFSYRK_ERR_TIMEOUT;
-    pl->levels_opt = bestL;
-    pl->ctas_opt = bestC;
-    pl->tuned_ms = best;
+    if (best.ms >= 1e30f) return FFSYRK_ERR_TOO_LARGE;  // no candidate fitted the workspace
+    apply(best);
     pl->autotuned = true;
-    tune_cache_store(key, bestL, bestC, best);
+    tune_cache_store(key, best);
     return FFSYRK_SUCCESS;
 }
 
@@ -1660,7 +1764,8 @@ ffsyrk_status_t checked_options(const ffsyrk_options_t *opts, ffsyrk_options_t *
     if (o->tile_ctas < 0 || o->tile_ctas > 2) return FFSYRK_ERR_INVALID_ARG;
     if (o->autotune < 0 || o->autotune > 1) return FFSYRK_ERR_INVALID_ARG;
     if (o->winograd < -1 || o->winograd > kMaxLevels) return FFSYRK_ERR_INVALID_ARG;
-    for (int i = 0; i < 3; ++i)
+    if (o->digit_products < 0 || o->digit_products > 2) return FFSYRK_ERR_INVALID_ARG;
+    for (int i = 0; i < 2; ++i)
         if (o->reserved[i] != 0) return FFSYRK_ERR_INVALID_ARG;
     return FFSYRK_SUCCESS;
 }
@@ -1674,10 +1779,12 @@ bool plan_setup(ffsyrk_plan_st *pl, uint32_t p, int64_t max_n, int64_t max_k,
     pl->yc.form = pl->ych.form;
     pl->yc.a = make_mul((uint32_t)pl->ych.a, p);
     pl->yc.b = make_mul((uint32_t)pl->ych.b, p);
-    pl->ds = make_digits(p);
+    pl->leaf = (o.leaf == FFSYRK_LEAF_AUTO) ? FFSYRK_LEAF_TC_BF16 : o.leaf;
+    // Karatsuba digit products on the tensor-core leaf unless asked otherwise
+    pl->dp_opt = o.digit_products;
+    pl->ds = make_digits(p, pl->leaf == FFSYRK_LEAF_TC_BF16 && o.digit_products != 1);
     pl->ds8 = make_digits_i8(p);
     pl->mp = make_modp(p, pl->ds);
-    pl->leaf = (o.leaf == FFSYRK_LEAF_AUTO) ? FFSYRK_LEAF_TC_BF16 : o.leaf;
     pl->gemmt = gemmt;
     pl->levels_opt = gemmt ? 0 : o.levels;
     pl->ctas_opt = o.tile_ctas;
@@ -1689,17 +1796,29 @@ bool plan_setup(ffsyrk_plan_st *pl, uint32_t p, int64_t max_n, int64_t max_k,
            max_k > 0 && !gemmt;
 }
 
-// Workspace capacity: the largest layout over the depths the plan may use.
+// Workspace capacity: the largest layout over the variants the plan may
+// use (its own depth, or every autotuning candidate).
 void plan_capacity(const ffsyrk_plan_st *pl, bool tuning, int64_t *data, int64_t *desc) {
-    std::vector<int> Ls{pl->L_max};
+    std::vector<TuneChoice> cands;
+    TuneChoice own;
+    own.L = pl->L_max;
+    own.sw = pl->sw_opt;
+    own.ks = pl->ds.ks;
+    cands.push_back(own);
     if (tuning)
-        for (int L : tune_levels(pl->max_n, pl->max_k)) Ls.push_back(L);
+        for (const TuneChoice &t : tune_candidates(pl)) cands.push_back(t);
     *data = 0;
     *desc = 0;
-    for (int L : Ls) {
+    ffsyrk_plan_st tmp;  // sizes only: the candidate's digits and Winograd cap
+    tmp.leaf = pl->leaf;
+    tmp.ds8 = pl->ds8;
+    tmp.gemmt = pl->gemmt;
+    for (const TuneChoice &t : cands) {
+        tmp.ds = make_digits(pl->p, t.ks != 0);
+        tmp.sw_opt = t.sw;
         int64_t dc = 0;
-        const int64_t db = workspace_need(pl, std::max<int64_t>(pl->max_n, 1),
-                                          std::max<int64_t>(pl->max_k, 1), L, &dc);
+        const int64_t db = workspace_need(&tmp, std::max<int64_t>(pl->max_n, 1),
+                                          std::max<int64_t>(pl->max_k, 1), t.L, &dc);
         *data = std::max(*data, db);
         *desc = std::max(*desc, dc);
     }
@@ -1709,7 +1828,7 @@ void plan_capacity(const ffsyrk_plan_st *pl, bool tuning, int64_t *data, int64_t
 // than the units of all tiles at the largest shape.
 int part_slots_for(const ffsyrk_plan_st *pl, int sms) {
     const Geometry g0 = make_geometry(std::max<int64_t>(pl->max_n, 1), std::max<int64_t>(pl->max_k, 1), 0);
-    const int64_t units = leaf_tiles_bound(g0, pl->leaf) * ((g0.kp / 64 + 15) / 16 + 1) * pl->ds.D * pl->ds.D;
+    const int64_t units = leaf_tiles_bound(g0, pl->leaf) * ((g0.kp / 64 + 15) / 16 + 1) * 4 * nprod(pl->ds);
     return (int)std::min<int64_t>(std::min<int64_t>(2 * sms, 2 * kMaxCtas), units);
 }
 }  // namespace
@@ -1875,6 +1994,8 @@ ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t pl, ffsyrk_plan_info_t *info)
     const Geometry g = plan_geometry(pl, pl->max_n, pl->max_k, pl->L_max);
     info->tile_ctas = pl->leaf == FFSYRK_LEAF_TC_BF16 ? choose_ctas(pl, g) : 1;
     for (int d = 0; d < 6 && d < kMaxLevels; ++d) info->winograd[d] = g.sw[d];
+    info->planes = pl->leaf == FFSYRK_LEAF_I64 ? 1 : lds.nplanes;
+    info->products = pl->leaf == FFSYRK_LEAF_I64 ? 1 : pl->leaf == FFSYRK_LEAF_I8 ? lds.D * lds.D : nprod(lds);
     return FFSYRK_SUCCESS;
 }
 
@@ -2021,6 +2142,32 @@ int32_t ffsyrk_leaf_schedule(uint32_t p, int32_t kblocks, int32_t *out, int32_t 
         out[5 * q + 4] = segs[q].first;
     }
     return n;
+}
+
+int32_t ffsyrk_leaf_schedule_ks(uint32_t p, int32_t kblocks, int32_t *out, int32_t cap) {
+    if (validate_p(p) != FFSYRK_SUCCESS || kblocks < 0 || (cap > 0 && !out)) return -1;
+    const DigitScheme ds = make_digits(p, true);
+    std::vector<LeafSeg> segs;
+    build_segments(ds, kblocks, segs);
+    const int32_t n = (int32_t)segs.size();
+    for (int32_t q = 0; q < n && q < cap; ++q) {
+        out[5 * q + 0] = segs[q].ij >> 4;
+        out[5 * q + 1] = segs[q].ij & 15;
+        out[5 * q + 2] = segs[q].kb0;
+        out[5 * q + 3] = segs[q].nkb;
+        out[5 * q + 4] = segs[q].first;
+    }
+    return n;
+}
+
+int32_t ffsyrk_digit_planes(uint32_t p, int32_t *max_digit, uint32_t *weight) {
+    if (validate_p(p) != FFSYRK_SUCCESS || !max_digit || !weight) return -1;
+    const DigitScheme ds = make_digits(p, true);
+    for (int t = 0; t < ds.nplanes; ++t) {
+        max_digit[t] = ds.max_digit[t];
+        weight[t] = ds.ks ? ds.weight[t][t].w : 0u;
+    }
+    return ds.ks ? ds.nplanes : 0;
 }
 
 int32_t ffsyrk_i8_schedule(uint32_t p, int32_t kblocks, int32_t *out, int32_t cap) {

@@ -23,6 +23,7 @@ namespace fsk {
 
 constexpr int kMaxLevels = 6;
 constexpr int kMaxDigits = 3;
+constexpr int kMaxPlanes = 6;  // digit planes per operand: D, plus D(D−1)/2 digit sums
 
 // Barrett-style reduction constants for p < 2^24.
 struct ModP {
@@ -80,13 +81,25 @@ struct YConst {
 // the shortest exact K-chunk, is no worse than the others (p = 131071:
 // base 362, digits ≤ 181, every pair 8 k-blocks per chunk instead of 4 for
 // the top pair of byte digits).
+//
+// Digit products.  Schoolbook: the D² pairs (i, j) of single digit planes,
+// X·Zᵀ = Σ b^(i+j)·X_i·Z_jᵀ.  Karatsuba (when every |digit| ≤ 128, so that
+// a sum of two digits stays an exact bf16 integer ≤ 256): each operand also
+// carries the D(D−1)/2 planes X_i + X_j (i < j), and the D(D+1)/2 products
+// P_t = plane_t(X)·plane_t(Z)ᵀ give X·Zᵀ = Σ_t w_t·P_t with
+//   w_t = b^(2i) − Σ_{j≠i} b^(i+j) for the single plane t = i,
+//   w_t = b^(i+j) for the sum plane of (i, j),
+// since X_i·Z_jᵀ + X_j·Z_iᵀ = (X_i + X_j)·(Z_i + Z_j)ᵀ − X_i·Z_iᵀ − X_j·Z_jᵀ.
+// Planes: 0..D−1 the digits, then the sums (0,1), (0,2), (1,2).
 struct DigitScheme {
     int D;
     int base;                                  // 256, or the balanced base for D = 2
-    int max_digit[kMaxDigits];                 // bound of |digit t|
-    int chunk_kb[kMaxDigits][kMaxDigits];      // K-chunk per pair, in 64-wide k-blocks
-    MulConst weight[kMaxDigits][kMaxDigits];   // base^(i+j) mod p
-    uint32_t offset;                           // a multiple of p ≥ 2^24
+    int ks;                                    // 1: Karatsuba digit products
+    int nplanes;                               // planes per operand: D, or D(D+1)/2 with ks
+    int max_digit[kMaxPlanes];                 // bound of |plane t| entries
+    int chunk_kb[kMaxPlanes][kMaxPlanes];      // K-chunk per plane pair, in k-blocks
+    MulConst weight[kMaxPlanes][kMaxPlanes];   // weight of the product of planes (i, j) mod p
+    uint32_t offset;                           // a multiple of p ≥ the accumulator bound
     int lazy_units;  // units the epilogue may add (each < 2p) before its uint32 sums need a reduction
 };
 
@@ -112,7 +125,9 @@ struct MatView {
 // uint32 residues (int64 leaf, and operands split further by Algorithm 1),
 // bytes of the two's-complement residue (INT8 leaf: unsigned low digits,
 // signed top digit).
-enum ArenaKind { ARENA_BF16 = 0, ARENA_U32 = 1, ARENA_I8 = 2 };
+enum ArenaKind { ARENA_BF16 = 0, ARENA_U32 = 1, ARENA_I8 = 2, ARENA_BF16_KS = 3 };
+// ARENA_BF16_KS: bf16 digit planes followed by the Karatsuba sum planes
+// (DigitScheme::ks); the same element type as ARENA_BF16.
 
 struct Arena {
     void *base = nullptr;   // [rows][kpad] elements
@@ -121,7 +136,9 @@ struct Arena {
     int64_t rpad = 0;       // rows per digit plane of one operand
     int planes = 1;         // digit planes per operand
     int kind = ARENA_BF16;
-    int64_t bytes() const { return rows * kpad * (kind == ARENA_BF16 ? 2 : kind == ARENA_I8 ? 1 : 4); }
+    int64_t bytes() const {
+        return rows * kpad * ((kind == ARENA_BF16 || kind == ARENA_BF16_KS) ? 2 : kind == ARENA_I8 ? 1 : 4);
+    }
 };
 
 // Destination of one derived operand written by a pre-addition kernel.
@@ -281,6 +298,8 @@ int64_t digitize_flat_blocks(int64_t rows, int64_t kpad);
 cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP mp,
                         cudaStream_t st, bool upper);
 cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st);
+// count uniform residues in [0, p) from a counter hash (the autotuner's operands)
+cudaError_t launch_fill_residues(uint32_t *A, int64_t count, uint32_t p, uint64_t seed, cudaStream_t st);
 // One operand of a general product L·Rᵀ split by one level of Algorithm 1
 // (Winograd's variant of Strassen's product): X is 2hh × 2ww uint32
 // residues (row stride ldx, a multiple of 4); side 0 writes the left

@@ -474,22 +474,24 @@ __global__ void __launch_bounds__(256) k_post(const PostNode *__restrict__ nodes
     }
 }
 
-// Post-additions for the lower triangle, one 64×64 tile pair per block:
+// Post-additions for the lower triangle, one 32×32 tile pair per block:
 // block (I, J), J ≤ I, reads P1, P2, P5 at (I, J) and P3, P4 at (I, J) and
 // (J, I) -- every product entry exactly once -- and writes C11 = Low(U3) and
 // C22 = Low(U5) at (I, J) and C21 = U4 at (I, J) and (J, I).  The transposed
 // operands, Up(U1) = Low(U1)ᵀ for C21 above the diagonal and P4ᵀ for U5,
-// come from the same tiles through shared memory.  Grid: x = I·(I+1)/2 + J
-// over the lower tile triangle, y = node.
-constexpr int FT = 64;  // fused post tile
-__device__ __forceinline__ void ld4c(const uint32_t *base, int64_t ld, int64_t i, int64_t j, int64_t h,
-                                     uint32_t (&x)[4]) {
-    if (i < h && j < h) {  // h and j are multiples of 4
-        const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(base + i * ld + j));
-        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-    } else {
-        x[0] = x[1] = x[2] = x[3] = 0u;
-    }
+// are read across the staged tiles.  All seven tiles are staged in shared
+// memory by cp.async (16-byte copies, no registers held while they are in
+// flight), so a block keeps 28 KB of loads in flight and an SM runs seven
+// blocks: the loads of some overlap the arithmetic and stores of others.
+// Grid: x = I·(I+1)/2 + J over the lower tile triangle, y = node.
+constexpr int FT = 32;             // fused post tile
+constexpr int FLD = FT + 4;        // shared row stride in words: 16-byte aligned rows
+constexpr int FTHREADS = 128;      // 8 threads × 4 columns per row, 16 rows per pass
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g, bool valid) {
+    // src-size 0 copies nothing and zero-fills the 16 bytes
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
 }
 __device__ __forceinline__ void st4(uint32_t *out, int64_t ldo, int64_t cend, int64_t R, int64_t Cc,
                                     const uint32_t (&v)[4], bool lower_only, const OutScale &sc,
@@ -506,7 +508,7 @@ __device__ __forceinline__ void st4(uint32_t *out, int64_t ldo, int64_t cend, in
             *q = make_uint4(scale_out(v[0], o.x, sc, p), scale_out(v[1], o.y, sc, p),
                             scale_out(v[2], o.z, sc, p), scale_out(v[3], o.w, sc, p));
         } else {
-            *q = make_uint4(v[0], v[1], v[2], v[3]);
+            __stcs(q, make_uint4(v[0], v[1], v[2], v[3]));
         }
     } else {
 #pragma unroll
@@ -516,10 +518,10 @@ __device__ __forceinline__ void st4(uint32_t *out, int64_t ldo, int64_t cend, in
     }
 }
 
-__global__ void __launch_bounds__(256) k_post_fused(const PostNode *__restrict__ nodes, int64_t h,
-                                                    ModP m) {
-    __shared__ uint32_t sU[FT][FT + 1];   // U1 = P1 + P5 of tile (I, J), for its transpose
-    __shared__ uint32_t sP4[FT][FT + 1];  // P4 of tile (J, I), for P4ᵀ
+__global__ void __launch_bounds__(FTHREADS) k_post_fused(const PostNode *__restrict__ nodes, int64_t h,
+                                                         ModP m) {
+    // 0: P1, 1: P5, 2: P2, 3: P3, 4: P4 of tile (I, J); 5: P4, 6: P3 of tile (J, I)
+    __shared__ __align__(16) uint32_t s[7][FT][FLD];
     const PostNode &nd = nodes[blockIdx.y];
     // lower tile triangle: x = I(I+1)/2 + J
     const int64_t x = blockIdx.x;
@@ -529,81 +531,87 @@ __global__ void __launch_bounds__(256) k_post_fused(const PostNode *__restrict__
     const int64_t J = x - I * (I + 1) / 2;
     const bool diag = I == J;
     const int tid = threadIdx.x;
-    const int tr = tid >> 4, tc = 4 * (tid & 15);  // rows tr + 16q, columns tc..tc+3
+    const int tr = tid >> 3, tc = 4 * (tid & 7);  // rows tr and tr + 16, columns tc..tc+3
     const uint32_t p = m.p;
     const int64_t iI = I * FT, iJ = J * FT;
-    uint32_t u1[4][4], p4[4][4], p3[4][4], c11[4][4];
+    // stage the tiles (h and every column offset are multiples of 4: a
+    // 16-byte group lies wholly inside or outside the h×h buffer)
+    {
+        const uint32_t *src[7] = {nd.P1, nd.P5, nd.P2, nd.P3, nd.P4, nd.P4, nd.P3};
+        const int64_t ld[7] = {nd.ldr, nd.ldr, nd.ldr, nd.ldg, nd.ldg, nd.ldg, nd.ldg};
+        const int ntile = diag ? 5 : 7;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int r = tr + 16 * q;
-        uint32_t a[4], b[4], c[4];
-        ld4c(nd.P1, nd.ldr, iI + r, iJ + tc, h, a);
-        ld4c(nd.P5, nd.ldr, iI + r, iJ + tc, h, b);
-        ld4c(nd.P2, nd.ldr, iI + r, iJ + tc, h, c);
+        for (int t = 0; t < 7; ++t) {
+            if (t >= ntile) break;
+            const int64_t r0 = t < 5 ? iI : iJ, c0 = t < 5 ? iJ : iI;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            u1[q][e] = a[e] + b[e];  // < 2p
-            c11[q][e] = addm(a[e], c[e], p);
-            sU[r][tc + e] = u1[q][e];
+            for (int q = 0; q < 2; ++q) {
+                const int r = tr + 16 * q;
+                const bool ok = r0 + r < h && c0 + tc < h;
+                const uint32_t *g = ok ? src[t] + (r0 + r) * ld[t] + c0 + tc : src[t];
+                cp_async16((uint32_t)__cvta_generic_to_shared(&s[t][r][tc]), g, ok);
+            }
         }
-        ld4c(nd.P3, nd.ldg, iI + r, iJ + tc, h, p3[q]);
-        ld4c(nd.P4, nd.ldg, iI + r, iJ + tc, h, p4[q]);
-    }
-    uint32_t p4t[4][4], p3t[4][4];  // tile (J, I), direct layout
-    if (diag) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) sP4[tr + 16 * q][tc + e] = p4[q][e];
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int r = tr + 16 * q;
-            ld4c(nd.P4, nd.ldg, iJ + r, iI + tc, h, p4t[q]);
-            ld4c(nd.P3, nd.ldg, iJ + r, iI + tc, h, p3t[q]);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) sP4[r][tc + e] = p4t[q][e];
-        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
-    // quadrant row/column offsets in the 2h×2h result
+    const int64_t c_lo = h < nd.vn ? h : nd.vn, c_hi = 2 * h < nd.vn ? 2 * h : nd.vn;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 2; ++q) {
         const int r = tr + 16 * q;
         const int64_t i = iI + r;
         if (i >= h) continue;
-        uint32_t o21[4], o22[4];
+        uint32_t c11[4], o21[4], o22[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int c = tc + e;
+            const uint32_t p1 = s[0][r][c], p5 = s[1][r][c], p2 = s[2][r][c], p3 = s[3][r][c],
+                           p4 = s[4][r][c];
+            c11[e] = addm(p1, p2, p);  // Low(U3) = Low(P1 + P2)
             // U1 at (i, iJ + c): the lower half directly, the upper half of a
-            // diagonal tile from the mirrored entry
-            const uint32_t u = (!diag || c <= r) ? u1[q][e] : sU[c][r];
-            o21[e] = red(u + p4[q][e] + p3[q][e], m);          // U4 = U1 + P4 + P3
-            o22[e] = red(u + p4[q][e] + sP4[c][r], m);         // U5 = U1 + P4 + P4ᵀ
+            // diagonal tile from the mirrored entry (Up(U1) = Low(U1)ᵀ)
+            const uint32_t u = (!diag || c <= r) ? p1 + p5 : s[0][c][r] + s[1][c][r];
+            const uint32_t p4t = diag ? s[4][c][r] : s[5][c][r];
+            o21[e] = red(u + p4 + p3, m);   // U4 = U1 + P4 + P3
+            o22[e] = red(u + p4 + p4t, m);  // U5 = U1 + P4 + P4ᵀ
         }
         // the quadrants end at column h (C11, C21) and 2h (C22); the result
         // has vn rows and columns
-        const int64_t c_lo = h < nd.vn ? h : nd.vn, c_hi = 2 * h < nd.vn ? 2 * h : nd.vn;
-        if (i < nd.vn) st4(nd.out, nd.ldo, c_lo, i, iJ + tc, c11[q], diag, nd.scale, p);  // C11 = Low(U3)
+        if (i < nd.vn) st4(nd.out, nd.ldo, c_lo, i, iJ + tc, c11, diag, nd.scale, p);  // C11 = Low(U3)
         if (h + i < nd.vn) {
-            st4(nd.out, nd.ldo, c_lo, h + i, iJ + tc, o21, false, nd.scale, p);              // C21 = U4
-            st4(nd.out, nd.ldo, c_hi, h + i, h + iJ + tc, o22, diag, nd.scale, p);           // C22 = Low(U5)
+            st4(nd.out, nd.ldo, c_lo, h + i, iJ + tc, o21, false, nd.scale, p);        // C21 = U4
+            st4(nd.out, nd.ldo, c_hi, h + i, h + iJ + tc, o22, diag, nd.scale, p);     // C22 = Low(U5)
         }
     }
     if (!diag) {
         // C21 at (J, I): Up(U1) there is the transpose of U1 at (I, J)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 2; ++q) {
             const int r = tr + 16 * q;
             const int64_t i = iJ + r;
             if (i >= h) continue;
             uint32_t o[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) o[e] = red(sU[tc + e][r] + p4t[q][e] + p3t[q][e], m);
-            if (h + i < nd.vn)
-                st4(nd.out, nd.ldo, h < nd.vn ? h : nd.vn, h + i, iI + tc, o, false, nd.scale, p);
+            for (int e = 0; e < 4; ++e) {
+                const int c = tc + e;
+                o[e] = red(s[0][c][r] + s[1][c][r] + s[5][r][c] + s[6][r][c], m);
+            }
+            if (h + i < nd.vn) st4(nd.out, nd.ldo, c_lo, h + i, iI + tc, o, false, nd.scale, p);
         }
+    }
+}
+
+// count residues uniform in [0, p) from a counter-based hash (SplitMix64's
+// finaliser of seed + index): synthetic operands for the autotuner, whose
+// timings must see the value distribution of real inputs.
+__global__ void k_fill_residues(uint32_t *A, int64_t count, uint32_t p, uint64_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (uint64_t)i * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        A[i] = (uint32_t)(((z >> 32) * (uint64_t)p) >> 32);
     }
 }
 
@@ -648,6 +656,13 @@ cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nnodes);
     if (arena_kind == ARENA_U32)
         return launch_prep_d<1, ARENA_U32>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+    if (arena_kind == ARENA_BF16_KS) {
+        switch (ds.D) {
+            case 2: return launch_prep_d<2, ARENA_BF16_KS>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+            case 3: return launch_prep_d<3, ARENA_BF16_KS>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (arena_kind == ARENA_I8) {
         switch (ds.D) {
             case 1: return launch_prep_d<1, ARENA_I8>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
@@ -673,6 +688,12 @@ cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)njobs);
     if (arena_kind == ARENA_U32) {
         k_digitize<1, ARENA_U32><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp);
+    } else if (arena_kind == ARENA_BF16_KS) {
+        switch (ds.D) {
+            case 2: k_digitize<2, ARENA_BF16_KS><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
+            case 3: k_digitize<3, ARENA_BF16_KS><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
+            default: return cudaErrorInvalidValue;
+        }
     } else if (arena_kind == ARENA_I8) {
         switch (ds.D) {
             case 1: k_digitize<1, ARENA_I8><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp); break;
@@ -735,13 +756,20 @@ cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP m
     if (!upper) {
         const int64_t T = (h + FT - 1) / FT, ntri = T * (T + 1) / 2;
         if (ntri > 0x7fffffff || nnodes > 65535) return cudaErrorInvalidValue;
-        k_post_fused<<<dim3((unsigned)ntri, (unsigned)nnodes), 256, 0, st>>>(nodes_dev, h, mp);
+        k_post_fused<<<dim3((unsigned)ntri, (unsigned)nnodes), FTHREADS, 0, st>>>(nodes_dev, h, mp);
         return cudaGetLastError();
     }
     const int64_t TI = (h + PR - 1) / PR, TJ = (h + PC - 1) / PC;
     if (TI > 65535 || TJ > 65535 || 3 * (int64_t)nnodes > 65535) return cudaErrorInvalidValue;
     dim3 grid((unsigned)TJ, (unsigned)TI, (unsigned)(3 * nnodes));
     k_post<<<grid, 256, 0, st>>>(nodes_dev, h, mp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_residues(uint32_t *A, int64_t count, uint32_t p, uint64_t seed, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((count + 255) / 256, 152 * 16);
+    k_fill_residues<<<(unsigned)blocks, 256, 0, st>>>(A, count, p, seed);
     return cudaGetLastError();
 }
 

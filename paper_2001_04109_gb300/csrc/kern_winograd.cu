@@ -177,6 +177,13 @@ cudaError_t launch_sw_pre(const SwPreJob *jobs_dev, int njobs, int64_t hh, int64
     const int64_t gy = std::min<int64_t>(hh, std::max<int64_t>(1, 152 * 24 / (gx * njobs)));
     dim3 grid((unsigned)gx, (unsigned)std::max<int64_t>(gy, 1), (unsigned)njobs);
     if (out_kind == ARENA_U32) return launch_pre_t<1, ARENA_U32>(grid, st, jobs_dev, hh, ww, kpad, mp);
+    if (out_kind == ARENA_BF16_KS) {
+        switch (ds.D) {
+            case 2: return launch_pre_t<2, ARENA_BF16_KS>(grid, st, jobs_dev, hh, ww, kpad, mp);
+            case 3: return launch_pre_t<3, ARENA_BF16_KS>(grid, st, jobs_dev, hh, ww, kpad, mp);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (out_kind == ARENA_I8) {
         switch (ds.D) {
             case 1: return launch_pre_t<1, ARENA_I8>(grid, st, jobs_dev, hh, ww, kpad, mp);

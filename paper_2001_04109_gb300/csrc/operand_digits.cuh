@@ -72,27 +72,39 @@ __device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, 
             *reinterpret_cast<uint2 *>(base + (d.row0 + t * d.rpad + r) * d.kpad + c) =
                 make_uint2(byte_plane(sv, 0, t), byte_plane(sv, 4, t));
     } else {
+        // bf16 digit planes; with ARENA_BF16_KS also the Karatsuba sum planes
+        // (0,1), (0,2), (1,2) after the D digits (every sum is ≤ 256 in
+        // magnitude, so still an exact bf16 integer)
         int sv[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) sv[e] = v[e] > m.half ? (int)v[e] - (int)m.p : (int)v[e];
-        uint32_t *base = static_cast<uint32_t *>(d.arena);
+        int dg[D][8];
 #pragma unroll
-        for (int t = 0; t < D; ++t) {
+        for (int t = 0; t < D; ++t)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) dg[t][e] = (t == D - 1) ? sv[e] : low_digit(sv[e], m);
+        uint32_t *base = static_cast<uint32_t *>(d.arena);
+        auto store_plane = [&](int t, const int (&x)[8]) {
             uint32_t w[4];
 #pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-                int d0, d1;
-                if (t == D - 1) {
-                    d0 = sv[e];
-                    d1 = sv[e + 1];
-                } else {
-                    d0 = low_digit(sv[e], m);
-                    d1 = low_digit(sv[e + 1], m);
-                }
-                w[e / 2] = __byte_perm(small_int_f32_bits(d0), small_int_f32_bits(d1), 0x7632);
-            }
+            for (int e = 0; e < 8; e += 2)
+                w[e / 2] = __byte_perm(small_int_f32_bits(x[e]), small_int_f32_bits(x[e + 1]), 0x7632);
             *reinterpret_cast<uint4 *>(base + (((d.row0 + t * d.rpad + r) * d.kpad + c) >> 1)) =
                 make_uint4(w[0], w[1], w[2], w[3]);
+        };
+#pragma unroll
+        for (int t = 0; t < D; ++t) store_plane(t, dg[t]);
+        if constexpr (OK == ARENA_BF16_KS) {
+            int t = D;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = i + 1; j < D; ++j, ++t) {
+                    int sm[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) sm[e] = dg[i][e] + dg[j][e];
+                    store_plane(t, sm);
+                }
         }
     }
 }

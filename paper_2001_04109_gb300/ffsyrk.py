@@ -38,7 +38,8 @@ EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsy
            "ffsyrkbd_factor_device", "ffherk_plan", "ffherk_plan_destroy", "ffherk_with_plan",
            "ffherk_sync_status", "ffherk", "ffsyrk_host", "ffsyrk_workspace_query",
            "ffsyrk_test_inject_alloc_failure", "ffsyrk_cache_info", "ffsyrk_probe_pipe",
-           "ffsyrk_i8_schedule", "ffsyrk_i8_digit_bounds"]
+           "ffsyrk_i8_schedule", "ffsyrk_i8_digit_bounds", "ffsyrk_leaf_schedule_ks",
+           "ffsyrk_digit_planes"]
 
 
 class FfsyrkError(RuntimeError):
@@ -50,7 +51,8 @@ class FfsyrkError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("tile_ctas", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("winograd", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("winograd", ctypes.c_int32), ("digit_products", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -59,7 +61,8 @@ class PlanInfo(ctypes.Structure):
                 ("levels", ctypes.c_int32), ("digits", ctypes.c_int32),
                 ("chunk_k", ctypes.c_int32 * 9), ("workspace_bytes", ctypes.c_int64),
                 ("tile_ctas", ctypes.c_int32), ("autotuned", ctypes.c_int32),
-                ("tuned_ms", ctypes.c_float), ("winograd", ctypes.c_int32 * 6)]
+                ("tuned_ms", ctypes.c_float), ("winograd", ctypes.c_int32 * 6),
+                ("planes", ctypes.c_int32), ("products", ctypes.c_int32)]
 
 
 class Timing(ctypes.Structure):
@@ -124,9 +127,7 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_probe_pipe.argtypes = [i32, i64, i32, vp, vp, P(ctypes.c_double)]
             L.ffsyrk_probe_pipe.restype = i32
             for name in ["ffherk_plan", "ffherk_plan_destroy", "ffherk_with_plan",
-                         "ffherk_sync_status", "ffherk", "ffsyrk_host", "ffsyrk_workspace_query",
-           "ffsyrk_test_inject_alloc_failure", "ffsyrk_cache_info", "ffsyrk_probe_pipe",
-           "ffsyrk_i8_schedule", "ffsyrk_i8_digit_bounds"]:
+                         "ffherk_sync_status", "ffherk", "ffsyrk_host", "ffsyrk_workspace_query"]:
                 getattr(L, name).restype = i32
             L.ffsyrk_noalloc.argtypes = [i32, i64, i64, u32, vp, i64, vp, i64, vp]
             L.ffsyrk_batched.argtypes = [i32, i64, P(i64), P(i64), u32, P(vp), P(i64), P(vp),
@@ -144,6 +145,10 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_leaf_schedule.restype = i32
             L.ffsyrk_digit_bounds.argtypes = [u32, P(i32)]
             L.ffsyrk_digit_bounds.restype = i32
+            L.ffsyrk_leaf_schedule_ks.argtypes = [u32, i32, P(i32), i32]
+            L.ffsyrk_leaf_schedule_ks.restype = i32
+            L.ffsyrk_digit_planes.argtypes = [u32, P(i32), P(u32)]
+            L.ffsyrk_digit_planes.restype = i32
             L.ffsyrk_i8_schedule.argtypes = [u32, i32, P(i32), i32]
             L.ffsyrk_i8_schedule.restype = i32
             L.ffsyrk_i8_digit_bounds.argtypes = [u32, P(i32)]
@@ -190,9 +195,13 @@ def _mat_args(X: torch.Tensor, name: str):
     return X.data_ptr(), ld
 
 
+_PRODUCTS = {None: 0, "auto": 0, "schoolbook": 1, "karatsuba": 2}
+
+
 def make_options(leaf=None, levels=None, tile_ctas=None, autotune=False,
-                 winograd=None) -> Options:
-    """Plan options; winograd: None = automatic, 0 = off, w = at most w levels of Algorithm 1."""
+                 winograd=None, digit_products=None) -> Options:
+    """Plan options; winograd: None = automatic, 0 = off, w = at most w levels of Algorithm 1;
+    digit_products: None/"auto", "schoolbook" or "karatsuba" (tensor-core leaf)."""
     o = Options()
     lib().ffsyrk_options_default(ctypes.byref(o))
     o.leaf = _LEAVES[leaf] if not isinstance(leaf, int) else leaf
@@ -200,6 +209,7 @@ def make_options(leaf=None, levels=None, tile_ctas=None, autotune=False,
     o.tile_ctas = 0 if tile_ctas is None else int(tile_ctas)
     o.autotune = 1 if autotune else 0
     o.winograd = -1 if winograd is None else int(winograd)
+    o.digit_products = _PRODUCTS[digit_products]
     return o
 
 
@@ -207,10 +217,10 @@ class Plan:
     """An ffsyrk plan: p, Y, digits, depth and workspace for n ≤ max_n, k ≤ max_k."""
 
     def __init__(self, p: int, max_n: int, max_k: int, leaf=None, levels=None, tile_ctas=None,
-                 autotune=False, winograd=None):
+                 autotune=False, winograd=None, digit_products=None):
         self.p = int(p)
         self._h = ctypes.c_void_p()
-        o = make_options(leaf, levels, tile_ctas, autotune, winograd)
+        o = make_options(leaf, levels, tile_ctas, autotune, winograd, digit_products)
         _check(lib().ffsyrk_plan(ctypes.byref(self._h), self.p, int(max_n), int(max_k),
                                  ctypes.byref(o)), "ffsyrk_plan")
 
@@ -221,7 +231,7 @@ class Plan:
                 "leaf": i.leaf, "levels": i.levels, "digits": i.digits,
                 "chunk_k": list(i.chunk_k), "workspace_bytes": i.workspace_bytes,
                 "tile_ctas": i.tile_ctas, "autotuned": i.autotuned, "tuned_ms": i.tuned_ms,
-                "winograd": list(i.winograd)}
+                "winograd": list(i.winograd), "planes": i.planes, "products": i.products}
 
     def __call__(self, A: torch.Tensor, C: torch.Tensor | None = None, uplo: str = "lower",
                  stream=None, alpha: int = 1, beta: int = 0) -> torch.Tensor:
@@ -383,9 +393,10 @@ def herk(A: torch.Tensor, p: int, r: int, uplo: str = "lower", Cre: torch.Tensor
 
 
 def workspace_query(p: int, max_n: int, max_k: int, leaf=None, levels=None, tile_ctas=None,
-                    autotune=False, winograd=None, sms: int = 0) -> tuple[int, int]:
+                    autotune=False, winograd=None, sms: int = 0,
+                    digit_products=None) -> tuple[int, int]:
     """(workspace bytes, shared-tile slot bytes) a Plan with these arguments allocates (no GPU)."""
-    o = make_options(leaf, levels, tile_ctas, autotune, winograd)
+    o = make_options(leaf, levels, tile_ctas, autotune, winograd, digit_products)
     ws, sl = ctypes.c_int64(), ctypes.c_int64()
     _check(lib().ffsyrk_workspace_query(int(p), int(max_n), int(max_k), ctypes.byref(o), int(sms),
                                         ctypes.byref(ws), ctypes.byref(sl)), "ffsyrk_workspace_query")
@@ -401,6 +412,26 @@ def leaf_schedule(p: int, kblocks: int) -> list[tuple[int, int, int, int, bool]]
     lib().ffsyrk_leaf_schedule(int(p), int(kblocks), buf, n)
     return [(buf[5 * q], buf[5 * q + 1], buf[5 * q + 2], buf[5 * q + 3], bool(buf[5 * q + 4]))
             for q in range(n)]
+
+
+def leaf_schedule_ks(p: int, kblocks: int) -> list[tuple[int, int, int, int, bool]]:
+    """The tensor-core leaf's K schedule with Karatsuba digit products: (i, i, first, count, opens a unit)."""
+    n = lib().ffsyrk_leaf_schedule_ks(int(p), int(kblocks), None, 0)
+    if n < 0:
+        raise ValueError("bad p or kblocks")
+    buf = (ctypes.c_int32 * (5 * max(n, 1)))()
+    lib().ffsyrk_leaf_schedule_ks(int(p), int(kblocks), buf, n)
+    return [(buf[5 * q], buf[5 * q + 1], buf[5 * q + 2], buf[5 * q + 3], bool(buf[5 * q + 4]))
+            for q in range(n)]
+
+
+def digit_planes(p: int) -> tuple[list[int], list[int]]:
+    """Karatsuba digit planes of p: (bounds per plane, weight w_t per plane), or ([], []) if not used."""
+    md, wt = (ctypes.c_int32 * 6)(), (ctypes.c_uint32 * 6)()
+    n = lib().ffsyrk_digit_planes(int(p), md, wt)
+    if n < 0:
+        raise ValueError("bad p")
+    return [md[t] for t in range(n)], [wt[t] for t in range(n)]
 
 
 def i8_schedule(p: int, kblocks: int) -> list[tuple[int, int, int, int, bool]]:

@@ -64,9 +64,12 @@ def test_bad_arguments_rejected(lib):
     h = ctypes.c_void_p()
     assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
     o.levels = 1
-    o.reserved[2] = 5
+    o.reserved[1] = 5
     assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
-    o.reserved[2] = 0
+    o.reserved[1] = 0
+    o.digit_products = 3
+    assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
+    o.digit_products = 0
     o.winograd = -2
     assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
     # batched argument checks happen before any device call
@@ -104,9 +107,13 @@ def test_workspace_query_without_gpu(lib):
     ws = {n: ffsyrk.workspace_query(65521, n, n)[0] for n in (1024, 4096, 8192)}
     assert 0 < ws[1024] < ws[4096] < ws[8192]
     # Winograd levels add their uint32 operands, pieces and products
-    on = ffsyrk.workspace_query(8388593, 32768, 32768, levels=3)[0]
-    off = ffsyrk.workspace_query(8388593, 32768, 32768, levels=3, winograd=0)[0]
+    sb = "schoolbook"
+    on = ffsyrk.workspace_query(8388593, 32768, 32768, levels=3, digit_products=sb)[0]
+    off = ffsyrk.workspace_query(8388593, 32768, 32768, levels=3, winograd=0, digit_products=sb)[0]
     assert on > 2 * off > 0
+    # Karatsuba digit products add the digit-sum planes (6 planes per operand instead of 3)
+    ks = ffsyrk.workspace_query(8388593, 32768, 32768, levels=3, winograd=0, digit_products="karatsuba")[0]
+    assert ks > off
     # the int64 leaf has no shared-tile slots; the tensor leaf scales them with the SMs
     assert ffsyrk.workspace_query(65521, 4096, 4096, leaf="i64")[1] == 0
     s152 = ffsyrk.workspace_query(65521, 4096, 4096)[1]

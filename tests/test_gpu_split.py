@@ -44,11 +44,13 @@ def run_timed(A_host, p, levels, uplo, calls=2):
 
 
 @pytest.mark.parametrize("n,k,p,levels,uplo", [
-    (1000, 5000, 65521, 0, "lower"),
-    (1000, 5000, 65521, 0, "upper"),
+    # ≥ 256 k-blocks of digit products per tile: with Karatsuba digits
+    # (3 products for p = 65521, 6 for 8388593) and schoolbook (4 for 131071)
+    (1000, 7000, 65521, 0, "lower"),
+    (1000, 7000, 65521, 0, "upper"),
     (700, 4097, 131071, 0, "lower"),
     (300, 3000, 8388593, 0, "upper"),
-    (1536, 8192, 65521, 1, "lower"),
+    (1536, 12288, 65521, 1, "lower"),
 ])
 def test_split_matches_oracle(n, k, p, levels, uplo):
     A = residues(n, k, p, seed=n + k + p % 97)

@@ -205,3 +205,82 @@ def test_i8_digit_products_rebuild_the_product(p):
     assert np.array_equal(exact, S.dot(S.T))
     weighted = sum(pow(256, i + j, p) * Dt[i].dot(Dt[j].T) for i in range(D) for j in range(D))
     assert np.array_equal(weighted % p, X.dot(X.T) % p)
+
+
+# ---- Karatsuba digit products: D(D+1)/2 plane products with weights ----
+
+KS_PRIMES = [521, 65521, 8388593, 16777213, 3, 131071, 509]
+
+
+@pytest.mark.parametrize("p", KS_PRIMES)
+def test_karatsuba_planes_and_bounds(p):
+    bounds, weights = ffsyrk.digit_planes(p)
+    dig = ffsyrk.digit_bounds(p)
+    D = len(dig)
+    eligible = D >= 2 and ffsyrk.digit_base(p) == 256 and all(
+        dig[i] + dig[j] <= 256 for i in range(D) for j in range(i + 1, D))
+    if not eligible:
+        assert bounds == [] and weights == []
+        return
+    assert len(bounds) == D * (D + 1) // 2
+    assert bounds[:D] == dig
+    sums = [(i, j) for i in range(D) for j in range(i + 1, D)]
+    assert bounds[D:] == [dig[i] + dig[j] for i, j in sums]
+    assert max(bounds) <= 256          # every plane entry an exact bf16 integer
+
+
+@pytest.mark.parametrize("p", [521, 65521, 8388593, 16777213])
+def test_karatsuba_weights_rebuild_the_product(p):
+    # Σ_t w_t·plane_t(X)·plane_t(Z)ᵀ ≡ X·Zᵀ (mod p) for the library's weights,
+    # with the planes formed here from the balanced digits (X and Z unequal,
+    # as for the general products P3, P4)
+    bounds, w = ffsyrk.digit_planes(p)
+    b = ffsyrk.digit_base(p)
+    D = len(ffsyrk.digit_bounds(p))
+    rng = np.random.default_rng(p + 7)
+    h = (p - 1) // 2
+    X = rng.integers(0, p, size=(5, 11)).astype(object)
+    Z = rng.integers(0, p, size=(7, 11)).astype(object)
+
+    def planes(M):
+        S = np.where(M > h, M - p, M)
+        dg = np.array([[balanced_digits(int(s), D, b) for s in row] for row in S], dtype=object)
+        out = [dg[:, :, t] for t in range(D)]
+        out += [dg[:, :, i] + dg[:, :, j] for i in range(D) for j in range(i + 1, D)]
+        assert all(abs(int(v)) <= bd for P, bd in zip(out, bounds) for v in P.ravel())
+        return out
+
+    PX, PZ = planes(X), planes(Z)
+    total = sum(int(wt) * PX[t].dot(PZ[t].T) for t, wt in enumerate(w))
+    assert np.array_equal(total % p, X.dot(Z.T) % p)
+    # the schoolbook weights are what the rearrangement starts from
+    assert len(w) == D * (D + 1) // 2
+
+
+@pytest.mark.parametrize("p", [521, 65521, 8388593, 16777213])
+@pytest.mark.parametrize("kblocks", [1, 3, 4, 5, 16, 17, 33, 64, 513])
+def test_karatsuba_schedule_units_exact_and_complete(p, kblocks):
+    bounds, _ = ffsyrk.digit_planes(p)
+    P = len(bounds)
+    segs = ffsyrk.leaf_schedule_ks(p, kblocks)
+    assert segs and segs[0][4]
+    covered = {}
+    unit_sum, unit_plane = 0, None
+    for i, j, kb0, nkb, first in segs:
+        assert i == j and 0 <= i < P
+        assert nkb >= 1 and 0 <= kb0 and kb0 + nkb <= kblocks
+        if first:
+            unit_sum, unit_plane = 0, i
+        assert i == unit_plane                      # one product (one weight) per accumulator
+        unit_sum += 64 * nkb * bounds[i] * bounds[i]
+        assert unit_sum <= 1 << 24                  # every FP32 partial sum exact
+        for kb in range(kb0, kb0 + nkb):
+            covered[(i, kb)] = covered.get((i, kb), 0) + 1
+    assert set(covered) == {(t, kb) for t in range(P) for kb in range(kblocks)}
+    assert all(c == 1 for c in covered.values())
+
+
+def test_karatsuba_units_per_span():
+    # p = 65521: per 16 k-blocks P00 and P11 one unit each, the sum plane (≤ 256) four of 4
+    segs = ffsyrk.leaf_schedule_ks(65521, 16)
+    assert [(s[0], s[3]) for s in segs] == [(0, 16), (1, 16), (2, 4), (2, 4), (2, 4), (2, 4)]
