@@ -382,7 +382,8 @@ def run_ours(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
     plan = ffsyrk.Plan(p, n, k, leaf=args.leaf, levels=levels, tile_ctas=args.tile_ctas,
-                       winograd=args.winograd)
+                       winograd=args.winograd, digit_products=args.digit_products,
+                       autotune=args.autotune, epilogue_warps=args.epilogue_warps)
     info = plan.info()
     sampler = ClockSampler(local)
     if ws > 1:
@@ -560,6 +561,7 @@ def run_ours(args):
                            "winograd": info["winograd"][: info["levels"]],
                            "leaf": {1: "tc_bf16", 2: "i64"}[info["leaf"]],
                            "tile_ctas": info["tile_ctas"],
+                           "autotuned": bool(info["autotuned"]),
                            "y_form": "scalar" if info["y_form"] == 0 else "2x2",
                            "l2": "flushed between steps (512 MiB write)",
                            "timing": "median of the timed steps",
@@ -858,6 +860,12 @@ def main():
     ap.add_argument("--leaf", choices=["tc", "i64"], default="tc")
     ap.add_argument("--tile-ctas", type=int, choices=[0, 1, 2], default=0,
                     help="tensor-core leaf tiles: 0 auto, 1 one SM, 2 SM pairs")
+    ap.add_argument("--digit-products", choices=["auto", "schoolbook", "karatsuba"], default="auto",
+                    help="tensor-core leaf digit products (default: Karatsuba where it applies)")
+    ap.add_argument("--epilogue-warps", type=int, choices=[0, 8, 16], default=0,
+                    help="one-SM tensor-core leaf: epilogue warps (0 = automatic)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="let the plan time its candidate variants at the workload's size")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")

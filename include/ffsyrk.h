@@ -106,7 +106,10 @@ typedef struct {
                           each operand also carries the D(D−1)/2 planes
                           X_i + X_j and D(D+1)/2 products replace the D²
                           (3 for 4, 6 for 9); elsewhere the same as 1.      */
-    int32_t reserved[2]; /* must be zero                                       */
+    int32_t epilogue_warps; /* one-SM tensor-core leaf: warps that drain the
+                          accumulators, 8 or 16; 0 (default) = 16 with
+                          Karatsuba digit products (frequent drains), else 8 */
+    int32_t reserved;    /* must be zero                                       */
 } ffsyrk_options_t;
 
 /* The defaults: automatic leaf, recursion depth and Winograd levels. */

@@ -385,7 +385,8 @@ struct TcLaunch {
     int max_units;            // most units (accumulator drains) of any tile's K schedule
     bool scaled;              // a product updates the caller's C (OutScale mode 1)
     bool short_tiles;         // 1-CTA leaf: many tiles of few k-blocks (a batch of small
-                              // problems): drain with 16 epilogue warps
+                              // problems)
+    int epi_warps;            // 1-CTA leaf: epilogue warps, 8 or 16 (frequent drains)
 };
 // Units (segments that open an accumulator) of a K schedule.
 int count_units(const LeafSeg *segs, int nseg);

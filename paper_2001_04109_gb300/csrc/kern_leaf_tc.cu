@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(Roles<EW>::NUM_THREADS, 1) k_leaf_tc(const Lea
                     tmem_wait_ld();
 #pragma unroll
                     for (int e = 0; e < LD_COLS; ++e) {
-                        // exact integer |x| ≤ 2^24 → shifted into [0, 2^26) → ·256^(i+j) mod p
+                        // exact integer |x| ≤ 2^24 → shifted into [0, 2^26) → ·weight mod p
                         const int xi = __float2int_rn(__uint_as_float(v[e]));
                         const uint32_t a = (uint32_t)(xi + (int)off);
                         const uint32_t q = __umulhi(a, wsh);
@@ -406,7 +406,8 @@ cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st) {
     cudaError_t ea = once_per_device(attr_once, nullptr, [smem](int *) {
         cudaError_t e = cudaSuccess;
         for (auto fn : {k_leaf_tc<true, false, 8>, k_leaf_tc<false, false, 8>, k_leaf_tc<true, true, 8>,
-                        k_leaf_tc<false, true, 8>, k_leaf_tc<true, false, 16>})
+                        k_leaf_tc<false, true, 8>, k_leaf_tc<true, false, 16>, k_leaf_tc<false, false, 16>,
+                        k_leaf_tc<true, true, 16>, k_leaf_tc<false, true, 16>})
             if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         return e;
     });
@@ -414,11 +415,14 @@ cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st) {
     const int nwork = L.entries ? L.nentries : L.ntiles;
     const int grid = nwork < num_sms ? nwork : num_sms;
     const bool lazy = L.max_units <= L.ds.lazy_units;
-    // many short tiles: the 16-warp epilogue (plain lazy stores only)
-    const bool wide_epi = L.short_tiles && lazy && !L.scaled;
-    auto kern = wide_epi ? k_leaf_tc<true, false, 16>
-                : L.scaled ? (lazy ? k_leaf_tc<true, true, 8> : k_leaf_tc<false, true, 8>)
-                           : (lazy ? k_leaf_tc<true, false, 8> : k_leaf_tc<false, false, 8>);
+    // frequent accumulator drains (many short tiles, or the short units of
+    // Karatsuba's digit-sum products): the 16-warp epilogue, four warps per
+    // scheduler, drains a unit in about half the time
+    const bool wide_epi = L.epi_warps == 16;
+    auto kern = wide_epi ? (L.scaled ? (lazy ? k_leaf_tc<true, true, 16> : k_leaf_tc<false, true, 16>)
+                                     : (lazy ? k_leaf_tc<true, false, 16> : k_leaf_tc<false, false, 16>))
+                         : (L.scaled ? (lazy ? k_leaf_tc<true, true, 8> : k_leaf_tc<false, true, 8>)
+                                     : (lazy ? k_leaf_tc<true, false, 8> : k_leaf_tc<false, false, 8>));
     // programmatic dependent launch: the prologue may overlap the grid that
     // writes the operands (the producer waits for it before its first load)
     cudaLaunchAttribute attr[1];

@@ -278,6 +278,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
                     tmem_wait_ld();
 #pragma unroll
                     for (int e = 0; e < LD_COLS; ++e) {
+                        // exact integer |x| ≤ 2^24 → shifted into [0, 2^26) → ·weight mod p
                         const int xi = __float2int_rn(__uint_as_float(v[e]));
                         const uint32_t a = (uint32_t)(xi + (int)off);
                         const uint32_t q = __umulhi(a, wsh);

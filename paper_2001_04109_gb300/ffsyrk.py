@@ -52,7 +52,7 @@ class Options(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("tile_ctas", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("winograd", ctypes.c_int32), ("digit_products", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("epilogue_warps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -199,7 +199,7 @@ _PRODUCTS = {None: 0, "auto": 0, "schoolbook": 1, "karatsuba": 2}
 
 
 def make_options(leaf=None, levels=None, tile_ctas=None, autotune=False,
-                 winograd=None, digit_products=None) -> Options:
+                 winograd=None, digit_products=None, epilogue_warps=0) -> Options:
     """Plan options; winograd: None = automatic, 0 = off, w = at most w levels of Algorithm 1;
     digit_products: None/"auto", "schoolbook" or "karatsuba" (tensor-core leaf)."""
     o = Options()
@@ -210,6 +210,7 @@ def make_options(leaf=None, levels=None, tile_ctas=None, autotune=False,
     o.autotune = 1 if autotune else 0
     o.winograd = -1 if winograd is None else int(winograd)
     o.digit_products = _PRODUCTS[digit_products]
+    o.epilogue_warps = int(epilogue_warps or 0)
     return o
 
 
@@ -217,10 +218,10 @@ class Plan:
     """An ffsyrk plan: p, Y, digits, depth and workspace for n ≤ max_n, k ≤ max_k."""
 
     def __init__(self, p: int, max_n: int, max_k: int, leaf=None, levels=None, tile_ctas=None,
-                 autotune=False, winograd=None, digit_products=None):
+                 autotune=False, winograd=None, digit_products=None, epilogue_warps=0):
         self.p = int(p)
         self._h = ctypes.c_void_p()
-        o = make_options(leaf, levels, tile_ctas, autotune, winograd, digit_products)
+        o = make_options(leaf, levels, tile_ctas, autotune, winograd, digit_products, epilogue_warps)
         _check(lib().ffsyrk_plan(ctypes.byref(self._h), self.p, int(max_n), int(max_k),
                                  ctypes.byref(o)), "ffsyrk_plan")
 

@@ -64,9 +64,12 @@ def test_bad_arguments_rejected(lib):
     h = ctypes.c_void_p()
     assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
     o.levels = 1
-    o.reserved[1] = 5
+    o.reserved = 5
     assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
-    o.reserved[1] = 0
+    o.reserved = 0
+    o.epilogue_warps = 12
+    assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
+    o.epilogue_warps = 0
     o.digit_products = 3
     assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
     o.digit_products = 0
