@@ -531,6 +531,10 @@ def run_ours(args):
                            f"buffers, {nfly} plan(s) and stream(s) in rotation: one step's "
                            "copies overlap another's product"}
 
+    batched = None
+    if not args.no_batched and args.workload == DEFAULT_WORKLOAD:
+        batched = batched_leg(steps=max(3, min(args.steps, 10)), warmup=3, check=not args.no_check)
+
     cpu, parity = None, None
     if rank == 0:
         rows = vals = None
@@ -567,7 +571,8 @@ def run_ours(args):
                            "timing": "median of the timed steps",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "e2e": e2e, "gpu_launches": launches * args.steps, "roofline": roofline,
-                "cpu_baseline": cpu, "clocks": clocks, "parity": parity, "compare": compare}
+                "cpu_baseline": cpu, "clocks": clocks, "parity": parity, "compare": compare,
+                "batched": batched}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -802,6 +807,83 @@ def run_batched(args):
     return 0
 
 
+def batched_leg(steps, warmup, check=True):
+    """The 2048-problem batch (seeded shapes, p = 65521) as one ffsyrk_batched call per step.
+
+    Device-resident inputs, L2 flushed between steps, CUDA events on the
+    launching stream; the result checked against the oracle's stored digest
+    of every problem's triangle (tests/golden) when present.
+    """
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_2001_04109_gb300 import ffsyrk, inputs
+    p = BATCH["p"]
+    shapes = inputs.batch_shapes(BATCH["count"], BATCH["lo"], BATCH["hi"], BATCH["seed"])
+    count = len(shapes)
+    a_off = np.cumsum([0] + [n * k for n, k in shapes])
+    c_off = np.cumsum([0] + [n * n for n, _ in shapes])
+    A_all = torch.empty(int(a_off[-1]), dtype=torch.int32, device="cuda")
+    C_all = torch.zeros(int(c_off[-1]), dtype=torch.int32, device="cuda")
+    As = [A_all[a_off[t]:a_off[t + 1]].view(n, k) for t, (n, k) in enumerate(shapes)]
+    Cs = [C_all[c_off[t]:c_off[t + 1]].view(n, n) for t, (n, _) in enumerate(shapes)]
+    for t in range(count):
+        As[t].copy_(batch_problem(t, shapes, p, "cuda"))
+    I64, VP = ctypes.c_int64 * count, ctypes.c_void_p * count
+    args = (0, count, I64(*[n for n, _ in shapes]), I64(*[k for _, k in shapes]), p,
+            VP(*[a.data_ptr() for a in As]), I64(*[max(1, k) for _, k in shapes]),
+            VP(*[c.data_ptr() for c in Cs]), I64(*[max(1, n) for n, _ in shapes]))
+    lib = ffsyrk.lib()
+    stream = torch.cuda.current_stream()
+
+    def call():
+        rc = lib.ffsyrk_batched(*args, stream.cuda_stream)
+        if rc != ffsyrk.SUCCESS:
+            raise ffsyrk.FfsyrkError(rc, "ffsyrk_batched")
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for s_ in range(steps):
+        flush.zero_()
+        ev[s_][0].record(stream)
+        call()
+        ev[s_][1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    ops = float(sum(n * n * k for n, k in shapes))
+    out = {"workload": "batched", "description": BATCH["description"], "value": ops / (ms * 1e-3),
+           "unit": UNIT, "ms_per_step": ms, "steps": steps, "sum_n2k": ops,
+           "scheduling": "digit split of every problem, then one persistent leaf launch over "
+                         "every problem's tiles from a device work queue, replayed as a CUDA graph"}
+    if check:
+        want = None
+        try:
+            for line in open(os.path.join(ROOT, "tests", "golden", "fullsize_sha256.txt")):
+                f = line.split()
+                if f and f[0] == "batched" and f[1:6] == [str(BATCH[x]) for x in
+                                                          ("count", "lo", "hi", "p", "seed")]:
+                    want = f[6]
+        except OSError:
+            pass
+        if want is not None:
+            h = hashlib.sha256()
+            C_host = C_all.cpu().numpy().view(np.uint32)
+            for t, (n, _) in enumerate(shapes):
+                Ct = C_host[c_off[t]:c_off[t + 1]].reshape(n, n).astype("<u4", copy=False)
+                for i in range(n):
+                    h.update(Ct[i, : i + 1].tobytes())
+            out["triangles_sha256_match_oracle"] = h.hexdigest() == want
+    del A_all, C_all, flush
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_batched_rate(shapes, p, budget_s):
     """The oracle on whole problems of the batch (spread over the size range) within a budget."""
     import oracle
@@ -870,6 +952,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 2048-problem batch the default workload's line also reports")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--ref-budget", type=float, default=6.0)
     ap.add_argument("--batch-count", type=int, default=None,

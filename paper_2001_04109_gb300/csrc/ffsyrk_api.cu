@@ -808,16 +808,16 @@ int choose_ctas(const ffsyrk_plan_st *pl, const Geometry &g) {
 
 ffsyrk_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? FFSYRK_SUCCESS : FFSYRK_ERR_CUDA; }
 
-// Tiles of one product in bands of kBand tile rows, column by column inside
-// a band: the CTAs of one wave then share a few row and column panels,
-// which stay in L2.
+// Tiles of one product in bands of `band` tile rows, column by column
+// inside a band: the CTAs of one wave then share a few row and column
+// panels, which stay in L2, and every column panel is fetched once per band.
 constexpr int64_t kBand = 8;
 void tri_tiles(std::vector<LeafTile> &out, int prod, int64_t rows, int64_t cols, int tri,
-               int64_t tm, int64_t tn, int cost) {
+               int64_t tm, int64_t tn, int cost, int64_t band_rows = kBand) {
     const int64_t TM = (rows + tm - 1) / tm, TN = (cols + tn - 1) / tn;
-    for (int64_t band = 0; band < TM; band += kBand)
+    for (int64_t band = 0; band < TM; band += band_rows)
         for (int64_t b = 0; b < TN; ++b)
-            for (int64_t a = band; a < std::min(TM, band + kBand); ++a) {
+            for (int64_t a = band; a < std::min(TM, band + band_rows); ++a) {
                 const int64_t r0 = a * tm, r1 = std::min(rows, r0 + tm) - 1;
                 const int64_t c0 = b * tn, c1 = std::min(cols, c0 + tn) - 1;
                 if (tri == 1 && r1 < c0) continue;  // no entry with c ≤ r
@@ -1049,6 +1049,14 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         return reinterpret_cast<uint32_t *>(ws + lay.g_off[d]) + (2 * t + q) * h * h;
     };
     int cost_mult = tc ? nprod(pl->ds) : i8 ? pl->ds8.D * pl->ds8.D : 1;
+    // bands of tile rows whose operand panel takes about 48 MB of L2 (never
+    // fewer than kBand rows): short-K products (A 16384 × 4096) then fetch
+    // each column panel once per band of 24 tile rows instead of 8
+    auto band_for = [&](const Arena &a) {
+        const double row_bytes = (double)a.kpad * a.planes * (a.kind == ARENA_U32 ? 4 : a.kind == ARENA_I8 ? 1 : 2);
+        const int64_t b = (int64_t)(48.0 * (1 << 20) / (row_bytes * (double)TM));
+        return std::min<int64_t>(64, std::max<int64_t>(kBand, b));
+    };
 
     if (g.L == 0) {
         LeafProd pr{};
@@ -1064,7 +1072,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         pr.scale = pl->scale;
         pr.ldo = ldc;
         D.prods.push_back(pr);
-        tri_tiles(D.tiles, 0, g.n, g.n, pr.tri, TM, TN, pr.kblocks * cost_mult);
+        tri_tiles(D.tiles, 0, g.n, g.n, pr.tri, TM, TN, pr.kblocks * cost_mult, band_for(a0));
         D.digit.push_back(DigitizeJob{MatView{A, lda, g.n, g.k}, g.n,
                                       OperandDst{a0.base, 0, a0.kpad, a0.rpad}});
         if (g.gemmt)
@@ -1154,7 +1162,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
                         pr.ldo = hj;
                         D.prods.push_back(pr);
                         tri_tiles(D.tiles, (int)D.prods.size() - 1, hj, hj, 0, TM, TN,
-                                  pr.kblocks * cost_mult);
+                                  pr.kblocks * cost_mult, band_for(lay.arena[ja]));
                     }
                     // post-additions, deepest level first, down to P3 or P4
                     for (int l = sw; l >= 1; --l) {
@@ -1183,7 +1191,8 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
             pr.out = rbuf(g.L, t);
             pr.ldo = hL;
             D.prods.push_back(pr);
-            tri_tiles(D.tiles, (int)D.prods.size() - 1, hL, hL, 1, TM, TN, pr.kblocks * cost_mult);
+            tri_tiles(D.tiles, (int)D.prods.size() - 1, hL, hL, 1, TM, TN, pr.kblocks * cost_mult,
+                      band_for(lay.arena[g.L]));
         }
         // post-additions, node results of depth d from depth d+1
         for (int d = g.L - 1; d >= 0; --d) {
@@ -2779,7 +2788,7 @@ struct BatchState {
     std::vector<int64_t> key;
     struct Launch {
         int64_t jobs_off = 0, prods_off = 0, tiles_off = 0, tmap_off = 0, aptr_off = 0,
-                akpad_off = 0, ctr_off = 0, segs_off = 0;
+                akpad_off = 0, ctr_off = 0, segs_off = 0, bjob_off = 0;
         int64_t off = 0;  // arenas end, blob start
         int njobs = 0, ntiles = 0, max_units = 0;
         int64_t max_rows = 0, max_kpad = 0, digit_blocks = 0;
@@ -2804,7 +2813,8 @@ cudaError_t batch_issue(BatchState *b, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     e = launch_digitize_flat(reinterpret_cast<const DigitizeJob *>(dd + L.jobs_off), L.njobs,
-                             L.digit_blocks, b->mp, b->ds, kind, st);
+                             L.digit_blocks, b->mp, b->ds, kind, st,
+                             reinterpret_cast<const int32_t *>(dd + L.bjob_off));
     if (e != cudaSuccess) return e;
     if (tc) {
         TcLaunch tl{};
@@ -3029,6 +3039,7 @@ extern "C" ffsyrk_status_t ffsyrk_batched(ffsyrk_uplo_t uplo, int64_t count, con
     const int64_t akpad_off = slot((int64_t)arenas.size() * sizeof(int64_t), 64);
     const int64_t ctr_off = slot(16, 16);
     const int64_t segs_off = slot((int64_t)segs.size() * sizeof(LeafSeg), 64);
+    const int64_t bjob_off = slot(digit_blocks * (int64_t)sizeof(int32_t), 64);
     const int64_t blob = rup(boff, 256);
     const int64_t need = off + blob;
     if (b->pending) {
@@ -3068,6 +3079,13 @@ extern "C" ffsyrk_status_t ffsyrk_batched(ffsyrk_uplo_t uplo, int64_t count, con
     memcpy(hb + tiles_off, tiles.data(), tiles.size() * sizeof(LeafTile));
     memcpy(hb + jobs_off, jobs.data(), jobs.size() * sizeof(DigitizeJob));
     memcpy(hb + segs_off, segs.data(), segs.size() * sizeof(LeafSeg));
+    {
+        int32_t *bj = reinterpret_cast<int32_t *>(hb + bjob_off);
+        for (size_t q = 0; q < jobs.size(); ++q) {
+            const int64_t e1 = q + 1 < jobs.size() ? jobs[q + 1].block0 : digit_blocks;
+            for (int64_t x = jobs[q].block0; x < e1; ++x) bj[x] = (int32_t)q;
+        }
+    }
     for (size_t j = 0; j < arenas.size(); ++j) {
         reinterpret_cast<void **>(hb + aptr_off)[j] = arenas[j].base;
         reinterpret_cast<int64_t *>(hb + akpad_off)[j] = arenas[j].kpad;
@@ -3087,6 +3105,7 @@ extern "C" ffsyrk_status_t ffsyrk_batched(ffsyrk_uplo_t uplo, int64_t count, con
     L.akpad_off = akpad_off;
     L.ctr_off = ctr_off;
     L.segs_off = segs_off;
+    L.bjob_off = bjob_off;
     L.off = off;
     L.njobs = (int)jobs.size();
     L.ntiles = (int)tiles.size();

@@ -289,8 +289,11 @@ cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_
                             cudaStream_t st);
 // Digit split of many matrices in one flattened launch: exactly the blocks
 // the jobs need (jobs[t].block0 = blocks of jobs 0..t−1; total_blocks in all).
+// block_job (optional, device): the job of every block, saving each block a
+// binary search over the jobs.
 cudaError_t launch_digitize_flat(const DigitizeJob *jobs_dev, int njobs, int64_t total_blocks,
-                                 ModP mp, DigitScheme ds, int arena_kind, cudaStream_t st);
+                                 ModP mp, DigitScheme ds, int arena_kind, cudaStream_t st,
+                                 const int32_t *block_job = nullptr);
 // blocks one job needs in launch_digitize_flat
 int64_t digitize_flat_blocks(int64_t rows, int64_t kpad);
 // upper: a node writes the upper triangle (transposed); otherwise the

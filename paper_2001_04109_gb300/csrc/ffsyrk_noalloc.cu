@@ -11,9 +11,10 @@
 // What it computes is what ffsyrk_with_plan computes with levels = 0 and the
 // tensor-core leaf: the digit split of A followed by one lower- (or upper-)
 // tile leaf launch writing C.  It reuses those two kernels unchanged, with
-// one-SM 128×256 tiles taken whole from the leaf's device work queue in the
-// planned path's band order (the planned path may instead use SM-pair tiles
-// or share long tiles among idle SMs; the result is the same).
+// one-SM 128×256 tiles taken whole from the leaf's device work queue in
+// bands of 8 tile rows (the planned path may instead use SM-pair tiles,
+// taller bands for short K, Karatsuba digit products, or share long tiles
+// among idle SMs; the result is the same).
 //
 // Nothing is copied from host memory: a one-block set-up kernel receives the
 // launch descriptors (tensor map, digit-split job, product, K schedule) as
@@ -60,7 +61,7 @@ constexpr size_t kSegOff = 2048;   // the K schedule (LeafSeg table)
 constexpr int kMaxSegs = 1024;
 constexpr size_t kTileOff = kSegOff + kMaxSegs * sizeof(LeafSeg);  // the tile list
 constexpr int64_t kMaxTiles = (int64_t)((kHeaderBytes - kTileOff) / sizeof(LeafTile));
-constexpr int kBandRows = 8;  // tile rows per band, as in the planned path
+constexpr int kBandRows = 8;  // tile rows per band (the planned path's band for long K)
 
 struct DeviceState {
     bool ready;
@@ -125,7 +126,7 @@ __host__ __device__ inline int item_tiles(int64_t item, int64_t TM, int64_t TN, 
 
 // One block: copy the descriptors, zero the counters, and list the live
 // tiles in band order (bands of kBandRows tile rows, column by column inside
-// a band, rows in order), the order the planned path uses.
+// a band, rows in order), the planned path's order for long-K products.
 constexpr int kSetupThreads = 1024;
 __global__ void __launch_bounds__(kSetupThreads) k_noalloc_setup(const __grid_constant__ SetupArgs a,
                                                                   unsigned char *hdr) {

@@ -292,21 +292,29 @@ __global__ void __launch_bounds__(DIG_THREADS) k_digitize(const DigitizeJob *__r
 }
 
 // The same digit split over a flattened block list: block b belongs to the
-// job t with block0[t] ≤ b < block0[t+1] (binary search), then to a band of
-// rows of that job.  A job of width kpad has kpad/8 threads per row; when
+// job t with block0[t] ≤ b < block0[t+1] (read from block_job[b] when the
+// caller provides that table, else found by binary search), then to a band
+// of rows of that job.  A job of width kpad has kpad/8 threads per row; when
 // that is fewer than the block's threads, one block covers several rows at
 // once (rows r0, r0 + rpt, … with rpt = threads / (kpad/8)), so narrow
 // problems keep the block's threads busy; wider jobs take several blocks per
 // row band, as k_digitize does.
 template <int D, int OK>
 __global__ void __launch_bounds__(DIG_THREADS) k_digitize_flat(const DigitizeJob *__restrict__ jobs,
-                                                                int njobs, ModP m) {
+                                                                int njobs, const int32_t *__restrict__ block_job,
+                                                                int64_t total_blocks, ModP m) {
     allow_dependents();
     const int64_t b = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].block0 <= b) lo = mid; else hi = mid - 1;
+    if (b >= total_blocks) return;
+    int lo = 0;
+    if (block_job) {
+        lo = __ldg(block_job + b);
+    } else {
+        int hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].block0 <= b) lo = mid; else hi = mid - 1;
+        }
     }
     const DigitizeJob &jb = jobs[lo];
     const int64_t local = b - jb.block0;
@@ -723,7 +731,8 @@ int64_t digitize_flat_blocks(int64_t rows, int64_t kpad) {
 }
 
 cudaError_t launch_digitize_flat(const DigitizeJob *jobs_dev, int njobs, int64_t total_blocks,
-                                 ModP mp, DigitScheme ds, int arena_kind, cudaStream_t st) {
+                                 ModP mp, DigitScheme ds, int arena_kind, cudaStream_t st,
+                                 const int32_t *block_job) {
     if (njobs == 0 || total_blocks == 0) return cudaSuccess;
     const int64_t gx = std::min<int64_t>(total_blocks, 65535);
     const int64_t gy = (total_blocks + gx - 1) / gx;
@@ -731,19 +740,19 @@ cudaError_t launch_digitize_flat(const DigitizeJob *jobs_dev, int njobs, int64_t
     dim3 grid((unsigned)gx, (unsigned)gy);
     // blocks past the last job's range find its job and return on the row check
     if (arena_kind == ARENA_U32) {
-        k_digitize_flat<1, ARENA_U32><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp);
+        k_digitize_flat<1, ARENA_U32><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, block_job, total_blocks, mp);
     } else if (arena_kind == ARENA_I8) {
         switch (ds.D) {
-            case 1: k_digitize_flat<1, ARENA_I8><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
-            case 2: k_digitize_flat<2, ARENA_I8><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
-            case 3: k_digitize_flat<3, ARENA_I8><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
+            case 1: k_digitize_flat<1, ARENA_I8><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, block_job, total_blocks, mp); break;
+            case 2: k_digitize_flat<2, ARENA_I8><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, block_job, total_blocks, mp); break;
+            case 3: k_digitize_flat<3, ARENA_I8><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, block_job, total_blocks, mp); break;
             default: return cudaErrorInvalidValue;
         }
     } else {
         switch (ds.D) {
-            case 1: k_digitize_flat<1, ARENA_BF16><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
-            case 2: k_digitize_flat<2, ARENA_BF16><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
-            case 3: k_digitize_flat<3, ARENA_BF16><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, mp); break;
+            case 1: k_digitize_flat<1, ARENA_BF16><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, block_job, total_blocks, mp); break;
+            case 2: k_digitize_flat<2, ARENA_BF16><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, block_job, total_blocks, mp); break;
+            case 3: k_digitize_flat<3, ARENA_BF16><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, njobs, block_job, total_blocks, mp); break;
             default: return cudaErrorInvalidValue;
         }
     }
