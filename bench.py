@@ -381,10 +381,23 @@ def run_ours(args):
     C = torch.zeros((n, n), dtype=torch.int32, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
+    # the default workload takes the plan's autotuner (depth, tiles, Winograd
+    # levels, digit products timed at this size when the plan is made, outside
+    # the timed region) unless options pin them
+    autotune = args.autotune or (args.workload == DEFAULT_WORKLOAD and not args.no_autotune and
+                                 levels is None and args.tile_ctas == 0 and args.winograd is None
+                                 and args.digit_products == "auto" and args.leaf == "tc")
+    t_plan = time.perf_counter()
     plan = ffsyrk.Plan(p, n, k, leaf=args.leaf, levels=levels, tile_ctas=args.tile_ctas,
                        winograd=args.winograd, digit_products=args.digit_products,
-                       autotune=args.autotune, epilogue_warps=args.epilogue_warps)
+                       autotune=autotune, epilogue_warps=args.epilogue_warps)
+    plan_s = time.perf_counter() - t_plan
     info = plan.info()
+    # the options that reproduce the plan's (tuned) choice, for the other plans of this run
+    same_opts = dict(leaf=args.leaf, levels=info["levels"], tile_ctas=info["tile_ctas"],
+                     winograd=None if any(info["winograd"]) else 0,
+                     digit_products="karatsuba" if info["products"] < info["digits"] ** 2
+                     else "schoolbook")
     sampler = ClockSampler(local)
     if ws > 1:
         dist.barrier()
@@ -437,15 +450,15 @@ def run_ours(args):
         from paper_2001_04109_gb300.ffsyrk import probe_pipe
         pipe_peak = {"i8": probe_pipe("mma_s8s8", iters=2048, reps=3),
                      "i64": probe_pipe("mad_wide_u32", iters=512, reps=3)}
-        legs = [("classical_tc", "tc", 0, None), ("fast_i8", "i8", levels, None),
-                ("classical_i8", "i8", 0, None), ("fast_i64", "i64", levels, None),
+        legs = [("classical_tc", "tc", 0, None), ("fast_i8", "i8", info["levels"], None),
+                ("classical_i8", "i8", 0, None), ("fast_i64", "i64", info["levels"], None),
                 ("classical_i64", "i64", 0, None)]
         if any(info["winograd"]):
             # the same depth with the general products computed classically
             legs.append(("fast_tc_no_winograd", "tc", info["levels"], 0))
         if info["products"] < info["digits"] ** 2:
             # the same plan with the D² schoolbook digit products
-            legs.append(("fast_tc_schoolbook_digits", "tc", levels, "schoolbook"))
+            legs.append(("fast_tc_schoolbook_digits", "tc", info["levels"], "schoolbook"))
         for name, leaf, lv, wg in legs:
             dp = None
             if wg == "schoolbook":
@@ -482,16 +495,14 @@ def run_ours(args):
     if not args.no_e2e:
         del C
         torch.cuda.empty_cache()
-        ws_b, slot_b = ffsyrk.workspace_query(p, n, k, leaf=args.leaf, levels=levels,
-                                              tile_ctas=args.tile_ctas, winograd=args.winograd)
+        ws_b, slot_b = ffsyrk.workspace_query(p, n, k, **same_opts)
         need = ws_b + slot_b + 4 * n * (k + 3) + 4 * n * n
         free, _ = torch.cuda.mem_get_info()
         nfly = int(max(1, min(3, (0.9 * free) // need)))
         ceiling = copy_ceiling(n, k, stream)
         A_pin = A_host.pin_memory()
         C_pins = [torch.empty((n, n), dtype=torch.int32).pin_memory() for _ in range(nfly)]
-        plans = [ffsyrk.Plan(p, n, k, leaf=args.leaf, levels=levels, tile_ctas=args.tile_ctas,
-                             winograd=args.winograd)
+        plans = [ffsyrk.Plan(p, n, k, epilogue_warps=args.epilogue_warps, **same_opts)
                  for _ in range(nfly)]
         streams = [torch.cuda.Stream() for _ in range(nfly)]
 
@@ -566,6 +577,7 @@ def run_ours(args):
                            "leaf": {1: "tc_bf16", 2: "i64"}[info["leaf"]],
                            "tile_ctas": info["tile_ctas"],
                            "autotuned": bool(info["autotuned"]),
+                           "plan_s": plan_s,
                            "y_form": "scalar" if info["y_form"] == 0 else "2x2",
                            "l2": "flushed between steps (512 MiB write)",
                            "timing": "median of the timed steps",
@@ -946,8 +958,11 @@ def main():
                     help="tensor-core leaf digit products (default: Karatsuba where it applies)")
     ap.add_argument("--epilogue-warps", type=int, choices=[0, 8, 16], default=0,
                     help="one-SM tensor-core leaf: epilogue warps (0 = automatic)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="the default workload without the autotuner (depth from the cost model)")
     ap.add_argument("--autotune", action="store_true",
-                    help="let the plan time its candidate variants at the workload's size")
+                    help="let the plan time its candidate variants at the workload's size "
+                         "(the default for the default workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")

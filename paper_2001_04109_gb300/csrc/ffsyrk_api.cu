@@ -1663,6 +1663,23 @@ std::vector<TuneChoice> tune_candidates(const ffsyrk_plan_st *pl) {
     return out;
 }
 
+// Apply the cached choice for pl's problem if there is one (sets the
+// options the autotuner would); false if it has to be timed.
+bool tune_cached(ffsyrk_plan_st *pl) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_load();
+    auto it = g_tune.find(tune_key(pl));
+    if (it == g_tune.end()) return false;
+    const TuneChoice &t = it->second;
+    pl->levels_opt = t.L;
+    pl->ctas_opt = t.ctas;
+    pl->sw_opt = t.sw;
+    pl->ds = make_digits(pl->p, t.ks != 0);
+    pl->tuned_ms = t.ms;
+    pl->autotuned = true;
+    return true;
+}
+
 ffsyrk_status_t autotune(ffsyrk_plan_st *pl) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_cache_load();
@@ -1931,7 +1948,13 @@ ffsyrk_status_t plan_create(ffsyrk_plan_t *plan, uint32_t p, int64_t max_n, int6
     pl->sms = sms;
     pl->p = p;
 
-    const bool tuning = plan_setup(pl, p, max_n, max_k, o, gemmt);
+    bool tuning = plan_setup(pl, p, max_n, max_k, o, gemmt);
+    if (tuning && tune_cached(pl)) {
+        // a choice already timed for this problem (this process or the
+        // cache file): the workspace is sized for it alone
+        tuning = false;
+        pl->L_max = choose_levels(pl, max_n, max_k);
+    }
     int64_t data = 0, desc = 0;
     plan_capacity(pl, tuning, &data, &desc);
     pl->data_cap = data;
