@@ -390,14 +390,15 @@ def run_ours(args):
     t_plan = time.perf_counter()
     plan = ffsyrk.Plan(p, n, k, leaf=args.leaf, levels=levels, tile_ctas=args.tile_ctas,
                        winograd=args.winograd, digit_products=args.digit_products,
-                       autotune=autotune, epilogue_warps=args.epilogue_warps)
+                       autotune=autotune, epilogue_warps=args.epilogue_warps,
+                       unit_bounds=args.unit_bounds)
     plan_s = time.perf_counter() - t_plan
     info = plan.info()
     # the options that reproduce the plan's (tuned) choice, for the other plans of this run
     same_opts = dict(leaf=args.leaf, levels=info["levels"], tile_ctas=info["tile_ctas"],
                      winograd=None if any(info["winograd"]) else 0,
                      digit_products="karatsuba" if info["products"] < info["digits"] ** 2
-                     else "schoolbook")
+                     else "schoolbook", unit_bounds=args.unit_bounds)
     sampler = ClockSampler(local)
     if ws > 1:
         dist.barrier()
@@ -439,6 +440,8 @@ def run_ours(args):
     # oracle's stored digest where tests/golden has one, and the rows the CPU
     # baseline computes with the oracle below
     C_res = C.cpu() if rank == 0 and not args.no_check else None
+    # accumulator units of the leaf: the worst-case schedule's and those it ran
+    units = plan.units() if args.leaf == "tc" else None
     plan.close()
     del plan
 
@@ -495,7 +498,8 @@ def run_ours(args):
     if not args.no_e2e:
         del C
         torch.cuda.empty_cache()
-        ws_b, slot_b = ffsyrk.workspace_query(p, n, k, **same_opts)
+        ws_b, slot_b = ffsyrk.workspace_query(
+            p, n, k, **{kk: v for kk, v in same_opts.items() if kk != "unit_bounds"})
         need = ws_b + slot_b + 4 * n * (k + 3) + 4 * n * n
         free, _ = torch.cuda.mem_get_info()
         nfly = int(max(1, min(3, (0.9 * free) // need)))
@@ -576,6 +580,9 @@ def run_ours(args):
                            "winograd": info["winograd"][: info["levels"]],
                            "leaf": {1: "tc_bf16", 2: "i64"}[info["leaf"]],
                            "tile_ctas": info["tile_ctas"],
+                           "unit_bounds": args.unit_bounds,
+                           "leaf_units": (None if units is None else
+                                          {"worst_case": units[0], "run": units[1]}),
                            "autotuned": bool(info["autotuned"]),
                            "plan_s": plan_s,
                            "y_form": "scalar" if info["y_form"] == 0 else "2x2",
@@ -958,6 +965,9 @@ def main():
                     help="tensor-core leaf digit products (default: Karatsuba where it applies)")
     ap.add_argument("--epilogue-warps", type=int, choices=[0, 8, 16], default=0,
                     help="one-SM tensor-core leaf: epilogue warps (0 = automatic)")
+    ap.add_argument("--unit-bounds", choices=["data", "worst"], default="data",
+                    help="tensor-core leaf: accumulator units from the operands' digits "
+                         "(default) or from the worst-case digit magnitudes")
     ap.add_argument("--no-autotune", action="store_true",
                     help="the default workload without the autotuner (depth from the cost model)")
     ap.add_argument("--autotune", action="store_true",

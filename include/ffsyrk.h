@@ -109,6 +109,17 @@ typedef struct {
     int32_t epilogue_warps; /* one-SM tensor-core leaf: warps that drain the
                           accumulators, 8 or 16; 0 (default) = 16 with
                           Karatsuba digit products (frequent drains), else 8 */
+    int32_t unit_bounds; /* tensor-core leaf: how long an FP32 accumulator runs
+                          before the epilogue reduces it (a unit; every unit
+                          is exact, its partial sums ≤ 2^24 in magnitude).
+                          0 (default): from the digits of the call's
+                          operands -- before the leaf, a pass takes per digit
+                          plane and 256-column block the largest row sum of
+                          squares, and consecutive segments of one weight
+                          class share a unit while Cauchy–Schwarz on those
+                          sums keeps the unit ≤ 2^24 (never more units than
+                          1); 1: from the largest digit magnitudes alone
+                          (K-chunk × max|d_i| × max|d_j| ≤ 2^24).          */
     int32_t reserved;    /* must be zero                                       */
 } ffsyrk_options_t;
 
@@ -409,6 +420,16 @@ typedef struct {
 /* Timing of the most recent call with timing enabled: waits for its last
  * event.  FFSYRK_ERR_INVALID_ARG if timing is off or no call was made. */
 ffsyrk_status_t ffsyrk_plan_get_timing(ffsyrk_plan_t plan, ffsyrk_timing_t *timing);
+
+/* Accumulator units of the most recent call's tensor-core leaf, summed over
+ * its distinct K schedules (the delayed reduction of Section 4.2: one
+ * reduction per unit): *host_units as the worst-case schedule has them,
+ * *units as the leaf ran them (equal with unit_bounds = 1; with 0, after the
+ * data-driven merge of that call).  Synchronises `stream` and reads the
+ * schedule back from the device.  FFSYRK_ERR_INVALID_ARG if no tensor-core
+ * call was made with the plan. */
+ffsyrk_status_t ffsyrk_plan_units(ffsyrk_plan_t plan, ffsyrk_stream_t stream, int64_t *host_units,
+                                  int64_t *units);
 
 /* Throughput probe of an arithmetic pipe a leaf can use (the paper has no
  * counterpart; it measures the roofline denominators that no measured peak

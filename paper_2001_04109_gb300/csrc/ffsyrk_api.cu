@@ -341,11 +341,18 @@ struct Descs {
     std::vector<int32_t> entries;
     int nslots = 0;
     int max_units = 0;  // most accumulator drains of any product's K schedule
+    // unit lengths from the operands' digits (tensor-core leaf; empty: the
+    // host schedule as built)
+    std::vector<uint8_t> links;
+    std::vector<UnitJob> ujobs;
+    int32_t norm_arena_off[kMaxLevels + 1] = {}, norm_nb[kMaxLevels + 1] = {};
+    int64_t norm_entries = 0;
     int64_t digit_max_rows = 0, digit_max_kpad = 0;
     // blob offsets (bytes) inside the descriptor region
     int64_t prep_off[kMaxLevels] = {}, post_off[kMaxLevels] = {};
     int64_t prods_off = 0, tiles_off = 0, tmap_off = 0, aptr_off = 0, akpad_off = 0, digit_off = 0;
     int64_t ctr_off = 0, segs_off = 0, pieces_off = 0, entries_off = 0;
+    int64_t links_off = 0, ujobs_off = 0, norm_off = 0;
     int64_t ctr_bytes = 16;  // work counter + 8 counters per split tile, zeroed every call
     int64_t bytes = 0;
 };
@@ -391,8 +398,12 @@ int64_t desc_capacity(const Geometry &g, int leaf) {
     b += (ntiles + 2 * kMaxCtas) * (int64_t)(sizeof(LeafTile) + sizeof(LeafPiece)) +
          (ntiles + kMaxCtas + 2) * 4 + 2 * kMaxCtas * 32 + 4 * 256;
     b += (kMaxLevels + 1) * (128 + 16) + 10 * 256 + 2 * sizeof(DigitizeJob);
-    // segment tables: at most L + 1 distinct K per call, ≤ 40 segments per 16 k-blocks
-    b += (int64_t)(g.L + 1) * ((g.kp / 64 + 16) / 16 + 1) * 40 * (int64_t)sizeof(LeafSeg);
+    // segment tables: at most L + 1 distinct K per call, ≤ 40 segments per 16 k-blocks,
+    // with a link byte each
+    b += (int64_t)(g.L + 1) * ((g.kp / 64 + 16) / 16 + 1) * 40 * (int64_t)(sizeof(LeafSeg) + 1);
+    // unit jobs and the norm tables: ≤ 6 planes × ⌈kpad_j / 256⌉ blocks per arena, Σ_j kpad_j ≤ 2·kp + 64·(L + 1)
+    b += (int64_t)(g.L + 1) * sizeof(UnitJob) + 3 * 256;
+    b += (int64_t)kMaxPlanes * (2 * (g.kp / kNormCols) + 2 * (kMaxLevels + 1)) * 4;
     return rup(b, kAlign);
 }
 
@@ -693,6 +704,7 @@ struct ffsyrk_plan_st {
     int sw_opt = -1;  // levels of Algorithm 1: −1 automatic, else the cap
     int dp_opt = 0;   // digit products: 0 automatic, 1 schoolbook, 2 Karatsuba
     int ew_opt = 0;   // one-SM leaf epilogue warps: 0 automatic, 8 or 16
+    int ub_opt = 0;   // unit lengths: 0 from the operands' digits, 1 worst case
     bool gemmt = false;  // the imaginary-part plan of a Hermitian product (L = 0)
     int64_t max_n = 0, max_k = 0;
     int L_max = 0;  // levels used at the max shape
@@ -1016,6 +1028,46 @@ void split_pairs(Descs &D, int P, int slot_cap) {
     D.nslots = 2 * slots;
 }
 
+// Links and jobs of the data-driven unit schedule (see UnitJob), and the
+// norm tables' layout.  A segment may continue the unit before it when both
+// belong to one K schedule and one weight class (Karatsuba: the same plane
+// product; schoolbook: the same i + j) and it does not start a piece of a
+// shared tile (pieces are cut at the host schedule's unit boundaries).
+void unit_links(Descs &D, const DigitScheme &ds, const Layout &lay) {
+    D.links.assign(D.segs.size(), 0);
+    D.ujobs.clear();
+    std::map<int64_t, size_t> job_of;  // seg0 → job
+    for (const LeafProd &pr : D.prods) {
+        auto it = job_of.find(pr.seg0);
+        if (it == job_of.end()) {
+            it = job_of.emplace(pr.seg0, D.ujobs.size()).first;
+            D.ujobs.push_back(UnitJob{pr.seg0, pr.nseg, 0u});
+        }
+        D.ujobs[it->second].arenas |= 1u << pr.arena;
+    }
+    for (const UnitJob &J : D.ujobs)
+        for (int32_t s = 1; s < J.nseg; ++s) {
+            const LeafSeg &a = D.segs[J.seg0 + s - 1], &b = D.segs[J.seg0 + s];
+            const bool same = ds.ks ? a.ij == b.ij
+                                    : (a.ij >> 4) + (a.ij & 15) == (b.ij >> 4) + (b.ij & 15);
+            D.links[J.seg0 + s] = same ? 1 : 0;
+        }
+    for (size_t q = 0; q < D.pieces.size(); ++q) {
+        const LeafProd &pr = D.prods[D.tiles[q].prod];
+        if (D.pieces[q].sx0 > 0) D.links[pr.seg0 + D.pieces[q].sx0] = 0;
+    }
+    int64_t n = 0;
+    for (int j = 0; j <= kMaxLevels; ++j) {
+        const Arena &a = lay.arena[j];
+        D.norm_arena_off[j] = (int32_t)n;
+        D.norm_nb[j] = 0;
+        if (a.rows == 0 || (a.kind != ARENA_BF16 && a.kind != ARENA_BF16_KS)) continue;
+        D.norm_nb[j] = (int32_t)((a.kpad + kNormCols - 1) / kNormCols);
+        n += (int64_t)a.planes * D.norm_nb[j];
+    }
+    D.norm_entries = n;
+}
+
 // Build every descriptor of one call into pl->desc and the staging blob.
 ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int64_t lda,
                             uint32_t *C, int64_t ldc) {
@@ -1234,6 +1286,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     if (tc && !pair) split_tail(D, pl->sms, pl->part_slots);
     if (pair) split_pairs(D, pl->sms / 2, pl->part_slots);
     D.ctr_bytes = 16 + (int64_t)D.nslots * 16 * 4;  // a counter per slot and epilogue warp (≤ 16)
+    if (tc && pl->ub_opt == 0) unit_links(D, pl->ds, lay);
 
     // pack the blob
     int64_t off = 0;
@@ -1261,6 +1314,9 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     D.segs_off = slot((int64_t)D.segs.size() * sizeof(LeafSeg), 64);
     D.pieces_off = slot((int64_t)D.pieces.size() * sizeof(LeafPiece), 64);
     D.entries_off = slot((int64_t)D.entries.size() * sizeof(int32_t), 64);
+    D.links_off = slot((int64_t)D.links.size(), 64);
+    D.ujobs_off = slot((int64_t)D.ujobs.size() * sizeof(UnitJob), 64);
+    D.norm_off = slot(D.norm_entries * 4, 256);
     D.bytes = rup(off, 256);
     if (D.bytes > pl->desc_cap) return FFSYRK_ERR_TOO_LARGE;
 
@@ -1282,6 +1338,8 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     memcpy(hb + D.segs_off, D.segs.data(), D.segs.size() * sizeof(LeafSeg));
     memcpy(hb + D.pieces_off, D.pieces.data(), D.pieces.size() * sizeof(LeafPiece));
     memcpy(hb + D.entries_off, D.entries.data(), D.entries.size() * sizeof(int32_t));
+    memcpy(hb + D.links_off, D.links.data(), D.links.size());
+    memcpy(hb + D.ujobs_off, D.ujobs.data(), D.ujobs.size() * sizeof(UnitJob));
     for (int j = 0; j <= kMaxLevels; ++j) {
         const Arena &a = lay.arena[j];
         if (a.rows == 0) continue;
@@ -1328,6 +1386,9 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
     if ((tc1 || tc2_split) &&
         cudaMemsetAsync(dd + D.ctr_off, 0, (size_t)D.ctr_bytes, st) != cudaSuccess)
         return FFSYRK_ERR_CUDA;
+    const bool data_units = !D.ujobs.empty();
+    if (data_units && cudaMemsetAsync(dd + D.norm_off, 0, (size_t)D.norm_entries * 4, st) != cudaSuccess)
+        return FFSYRK_ERR_CUDA;
     if (g.L == 0) {
         e = launch_digitize(reinterpret_cast<const DigitizeJob *>(dd + D.digit_off),
                             (int)D.digit.size(), D.digit_max_rows, D.digit_max_kpad, pl->mp,
@@ -1351,6 +1412,25 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
                 if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
             }
         }
+    }
+    if (data_units) {
+        // unit lengths from the digits just written (see UnitJob)
+        NormTables nt{};
+        nt.base = reinterpret_cast<uint32_t *>(dd + D.norm_off);
+        for (int j = 0; j <= kMaxLevels; ++j) {
+            nt.off[j] = D.norm_arena_off[j];
+            nt.nb[j] = D.norm_nb[j];
+        }
+        for (int j = 0; j <= kMaxLevels; ++j) {
+            if (D.norm_nb[j] == 0) continue;
+            e = launch_plane_norms(lay.arena[j], g.h[j], nt, j, pl->ds.D, pl->ds.ks != 0, st);
+            if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+        }
+        e = launch_unit_schedule(reinterpret_cast<const UnitJob *>(dd + D.ujobs_off),
+                                 (int)D.ujobs.size(), nt,
+                                 reinterpret_cast<const uint8_t *>(dd + D.links_off),
+                                 reinterpret_cast<LeafSeg *>(dd + D.segs_off), pl->ds, st);
+        if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
     }
     if (timed) cudaEventRecord(pl->ev[1], st);
     if (lay.leaf == FFSYRK_LEAF_TC_BF16) {
@@ -1480,6 +1560,10 @@ void record_work(ffsyrk_plan_st *pl) {
     const Descs &D = pl->desc;
     pl->last_launches = g.L == 0 ? 2 : 2 * g.L + 1;
     for (int d = 0; d < g.L; ++d) pl->last_launches += 2 * g.sw[d];
+    if (!D.ujobs.empty()) {
+        pl->last_launches += 1;  // the unit schedule
+        for (int j = 0; j <= kMaxLevels; ++j) pl->last_launches += D.norm_nb[j] > 0 ? 1 : 0;
+    }
     pl->last_leaf_launches = 1;
     int split = 0, whole = 0;
     for (const LeafPiece &q : D.pieces) {
@@ -1797,6 +1881,7 @@ ffsyrk_status_t checked_options(const ffsyrk_options_t *opts, ffsyrk_options_t *
     if (o->digit_products < 0 || o->digit_products > 2) return FFSYRK_ERR_INVALID_ARG;
     if (o->epilogue_warps != 0 && o->epilogue_warps != 8 && o->epilogue_warps != 16)
         return FFSYRK_ERR_INVALID_ARG;
+    if (o->unit_bounds < 0 || o->unit_bounds > 1) return FFSYRK_ERR_INVALID_ARG;
     if (o->reserved != 0) return FFSYRK_ERR_INVALID_ARG;
     return FFSYRK_SUCCESS;
 }
@@ -1814,6 +1899,7 @@ bool plan_setup(ffsyrk_plan_st *pl, uint32_t p, int64_t max_n, int64_t max_k,
     // Karatsuba digit products on the tensor-core leaf unless asked otherwise
     pl->dp_opt = o.digit_products;
     pl->ew_opt = o.epilogue_warps;
+    pl->ub_opt = o.unit_bounds;
     pl->ds = make_digits(p, pl->leaf == FFSYRK_LEAF_TC_BF16 && o.digit_products != 1);
     pl->ds8 = make_digits_i8(p);
     pl->mp = make_modp(p, pl->ds);
@@ -2128,6 +2214,30 @@ ffsyrk_status_t ffsyrk_plan_set_timing(ffsyrk_plan_t pl, int32_t enable) {
     }
     pl->timing = enable != 0;
     pl->timed_call = false;
+    return FFSYRK_SUCCESS;
+}
+
+ffsyrk_status_t ffsyrk_plan_units(ffsyrk_plan_t pl, ffsyrk_stream_t stream, int64_t *host_units,
+                                  int64_t *units) {
+    if (!pl || !host_units || !units) return FFSYRK_ERR_INVALID_ARG;
+    const Descs &D = pl->desc;
+    if (pl->lay.leaf != FFSYRK_LEAF_TC_BF16 || D.segs.empty() || !pl->ws) return FFSYRK_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<LeafSeg> dev(D.segs.size());
+    const char *dd = pl->ws + pl->data_cap;
+    if (cudaStreamSynchronize(st) != cudaSuccess ||
+        cudaMemcpy(dev.data(), dd + D.segs_off, dev.size() * sizeof(LeafSeg), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return FFSYRK_ERR_CUDA;
+    std::map<int64_t, int32_t> scheds;  // seg0 → nseg
+    for (const LeafProd &pr : D.prods) scheds[pr.seg0] = pr.nseg;
+    int64_t h = 0, u = 0;
+    for (const auto &kv : scheds) {
+        h += count_units(D.segs.data() + kv.first, kv.second);
+        u += count_units(dev.data() + kv.first, kv.second);
+    }
+    *host_units = h;
+    *units = u;
     return FFSYRK_SUCCESS;
 }
 

@@ -228,6 +228,37 @@ void build_segments(const DigitScheme &ds, int kblocks, std::vector<LeafSeg> &ou
 int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int cap,
                         const SegRule &rule = kSegTc);
 
+// ---- unit lengths from the operands' digits ----
+// The worst-case schedule above bounds a unit's partial sums by
+// Σ nkb·kbw·max|d_i|·max|d_j|.  The digits a call actually holds give a
+// bound that is never larger: for one pair over a K range, every partial sum
+// of Σ_k x_k·z_k, in any order, is at most Σ_k |x_k|·|z_k| ≤
+// sqrt(Σ_k x_k²)·sqrt(Σ_k z_k²) (Cauchy–Schwarz), and Σ_k x_k² over a range
+// is at most the sum, over the 256-column blocks the range touches, of the
+// largest row sum of squares of that plane in the block.  Before the leaf,
+// one pass takes those block maxima per arena and digit plane; a second
+// merges consecutive segments of one weight class into one unit while the
+// data bound of the unit stays ≤ 2^24 (exact FP32), so uniform residues
+// take about one drain per product and 16 k-blocks instead of one per
+// 4 k-blocks for the digit-sum products.  The units never outnumber the
+// worst-case schedule's (greedy packing of a sequence whose worst-case
+// packing is feasible), so the leaf's lazy-sum bound still holds.
+constexpr int kNormCols = 256;  // columns per block of the norm tables (4 k-blocks)
+struct NormTables {
+    uint32_t *base;                   // [arena][plane][block] maxima, zeroed before each call
+    int32_t off[kMaxLevels + 1];      // first entry of arena j
+    int32_t nb[kMaxLevels + 1];       // blocks per plane of arena j (ceil(kpad / 256))
+};
+// One K schedule shared by the products whose arenas are in `arenas` (bit j).
+struct UnitJob {
+    int64_t seg0;
+    int32_t nseg;
+    uint32_t arenas;
+};
+// links[s] (one byte per segment of the launch's table): 1 if segment s may
+// continue the unit of segment s − 1 (same schedule, same weight class, and
+// not the first segment of a shared tile's piece), else 0.
+
 struct LeafTile {
     int32_t prod;
     int32_t tm, tn;
@@ -303,6 +334,16 @@ cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP m
 cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st);
 // count uniform residues in [0, p) from a counter hash (the autotuner's operands)
 cudaError_t launch_fill_residues(uint32_t *A, int64_t count, uint32_t p, uint64_t seed, cudaStream_t st);
+// Block maxima of arena j's bf16 digit planes into t.base + t.off[j]
+// ([plane][block], max-accumulated: the table starts at zero); h: the rows
+// of each operand plane that hold digits (the rest is padding); D digits,
+// ks: the planes after them are Karatsuba digit sums.
+cudaError_t launch_plane_norms(const Arena &a, int64_t h, const NormTables &t, int j, int D, bool ks,
+                               cudaStream_t st);
+// The `first` flags of every job's segments from the tables (see UnitJob).
+cudaError_t launch_unit_schedule(const UnitJob *jobs_dev, int njobs, const NormTables &t,
+                                 const uint8_t *links, LeafSeg *segs, const DigitScheme &ds,
+                                 cudaStream_t st);
 // One operand of a general product L·Rᵀ split by one level of Algorithm 1
 // (Winograd's variant of Strassen's product): X is 2hh × 2ww uint32
 // residues (row stride ldx, a multiple of 4); side 0 writes the left

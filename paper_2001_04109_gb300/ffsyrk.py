@@ -39,7 +39,7 @@ EXPORTS = ["ffsyrk_options_default", "ffsyrk_plan", "ffsyrk_plan_destroy", "ffsy
            "ffherk_sync_status", "ffherk", "ffsyrk_host", "ffsyrk_workspace_query",
            "ffsyrk_test_inject_alloc_failure", "ffsyrk_cache_info", "ffsyrk_probe_pipe",
            "ffsyrk_i8_schedule", "ffsyrk_i8_digit_bounds", "ffsyrk_leaf_schedule_ks",
-           "ffsyrk_digit_planes"]
+           "ffsyrk_digit_planes", "ffsyrk_plan_units"]
 
 
 class FfsyrkError(RuntimeError):
@@ -52,7 +52,8 @@ class Options(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("tile_ctas", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("winograd", ctypes.c_int32), ("digit_products", ctypes.c_int32),
-                ("epilogue_warps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("epilogue_warps", ctypes.c_int32), ("unit_bounds", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -126,6 +127,8 @@ def lib() -> ctypes.CDLL:
             L.ffsyrk_cache_info.restype = i32
             L.ffsyrk_probe_pipe.argtypes = [i32, i64, i32, vp, vp, P(ctypes.c_double)]
             L.ffsyrk_probe_pipe.restype = i32
+            L.ffsyrk_plan_units.argtypes = [vp, vp, P(i64), P(i64)]
+            L.ffsyrk_plan_units.restype = i32
             for name in ["ffherk_plan", "ffherk_plan_destroy", "ffherk_with_plan",
                          "ffherk_sync_status", "ffherk", "ffsyrk_host", "ffsyrk_workspace_query"]:
                 getattr(L, name).restype = i32
@@ -196,12 +199,14 @@ def _mat_args(X: torch.Tensor, name: str):
 
 
 _PRODUCTS = {None: 0, "auto": 0, "schoolbook": 1, "karatsuba": 2}
+_UNIT_BOUNDS = {None: 0, "data": 0, "worst": 1}
 
 
 def make_options(leaf=None, levels=None, tile_ctas=None, autotune=False,
-                 winograd=None, digit_products=None, epilogue_warps=0) -> Options:
+                 winograd=None, digit_products=None, epilogue_warps=0, unit_bounds=None) -> Options:
     """Plan options; winograd: None = automatic, 0 = off, w = at most w levels of Algorithm 1;
-    digit_products: None/"auto", "schoolbook" or "karatsuba" (tensor-core leaf)."""
+    digit_products: None/"auto", "schoolbook" or "karatsuba" (tensor-core leaf);
+    unit_bounds: None/"data" (accumulator units from the operands' digits) or "worst"."""
     o = Options()
     lib().ffsyrk_options_default(ctypes.byref(o))
     o.leaf = _LEAVES[leaf] if not isinstance(leaf, int) else leaf
@@ -211,6 +216,7 @@ def make_options(leaf=None, levels=None, tile_ctas=None, autotune=False,
     o.winograd = -1 if winograd is None else int(winograd)
     o.digit_products = _PRODUCTS[digit_products]
     o.epilogue_warps = int(epilogue_warps or 0)
+    o.unit_bounds = _UNIT_BOUNDS[unit_bounds]
     return o
 
 
@@ -218,10 +224,12 @@ class Plan:
     """An ffsyrk plan: p, Y, digits, depth and workspace for n ≤ max_n, k ≤ max_k."""
 
     def __init__(self, p: int, max_n: int, max_k: int, leaf=None, levels=None, tile_ctas=None,
-                 autotune=False, winograd=None, digit_products=None, epilogue_warps=0):
+                 autotune=False, winograd=None, digit_products=None, epilogue_warps=0,
+                 unit_bounds=None):
         self.p = int(p)
         self._h = ctypes.c_void_p()
-        o = make_options(leaf, levels, tile_ctas, autotune, winograd, digit_products, epilogue_warps)
+        o = make_options(leaf, levels, tile_ctas, autotune, winograd, digit_products, epilogue_warps,
+                         unit_bounds)
         _check(lib().ffsyrk_plan(ctypes.byref(self._h), self.p, int(max_n), int(max_k),
                                  ctypes.byref(o)), "ffsyrk_plan")
 
@@ -304,6 +312,13 @@ class Plan:
         t = Timing()
         _check(lib().ffsyrk_plan_get_timing(self._h, ctypes.byref(t)), "ffsyrk_plan_get_timing")
         return {f: getattr(t, f) for f, _ in Timing._fields_}
+
+    def units(self, stream=None) -> tuple[int, int]:
+        """(worst-case units, units the leaf ran) of the last tensor-core call (synchronises)."""
+        h, u = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().ffsyrk_plan_units(self._h, _stream_handle(stream), ctypes.byref(h),
+                                       ctypes.byref(u)), "ffsyrk_plan_units")
+        return h.value, u.value
 
     def selftest_timeout(self, limit_ns: int, stream=None) -> None:
         _check(lib().ffsyrk_plan_selftest_timeout(self._h, int(limit_ns), _stream_handle(stream)),

@@ -73,6 +73,10 @@ def test_bad_arguments_rejected(lib):
     o.digit_products = 3
     assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
     o.digit_products = 0
+    o.unit_bounds = 2
+    assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
+    o.unit_bounds = 0
+    assert lib.ffsyrk_plan_units(None, None, None, None) == ffsyrk.ERR_INVALID_ARG
     o.winograd = -2
     assert lib.ffsyrk_plan(ctypes.byref(h), 65521, 4, 4, ctypes.byref(o)) == ffsyrk.ERR_INVALID_ARG
     # batched argument checks happen before any device call
