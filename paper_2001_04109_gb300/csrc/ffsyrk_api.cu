@@ -583,14 +583,16 @@ int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int ca
                         const SegRule &rule) {
     const int64_t kBound = rule.bound;
     const int D = ds.D;
-    // span: at most 16 k-blocks and no longer than the shortest chunk, so
-    // that every pair takes one unit per span where its bound allows; the
+    // span: at most rule.span_cap k-blocks and (clip_span) no longer than the
+    // shortest chunk, so that every pair takes one unit per span where its
+    // bound allows (without clipping a pair may take several); the
     // spans of one K are balanced (a ragged K such as 65 k-blocks becomes
     // spans of 13 rather than 16, 16, 16, 16, 1: no pair gets a unit of one
     // k-block, which would drain the accumulator after almost no MMA work)
     int span = rule.span_cap;
-    for (int i = 0; i < D; ++i)
-        for (int j = 0; j < D; ++j) span = std::min(span, std::max(1, ds.chunk_kb[i][j]));
+    if (rule.clip_span)
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) span = std::min(span, std::max(1, ds.chunk_kb[i][j]));
     const int nspans = kblocks > 0 ? (kblocks + span - 1) / span : 0;
     int count = 0;
     if (ds.ks) {
@@ -1277,7 +1279,7 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     if (i8)
         attach_segments(pl->ds8, D.prods, D.segs, kSegI8);
     else
-        attach_segments(pl->ds, D.prods, D.segs);
+        attach_segments(pl->ds, D.prods, D.segs, tc && pl->ub_opt == 0 ? kSegTcData : kSegTc);
     for (const LeafProd &pr : D.prods)
         D.max_units = std::max(D.max_units, count_units(D.segs.data() + pr.seg0, pr.nseg));
     // longest tiles first, then round-robin over persistent CTAs

@@ -214,13 +214,19 @@ struct LeafSeg {
 // while its worst-case |sum| Σ kbw·nkb·max|d_i|·max|d_j| stays ≤ bound and
 // never crosses a class.  The tensor-core leaf: k-blocks of kbw = 64, bound
 // 2^24 (exact FP32), spans ≤ 16; the INT8 leaf: kbw = 128, bound 2^30
-// (int32 with room for the reduction's offset), spans ≤ 128.
+// (int32 with room for the reduction's offset), spans ≤ 128.  With units
+// from the operands' digits (below) the tensor-core spans are 32 k-blocks
+// whatever the shortest worst-case chunk (clip_span false): the worst-case
+// units inside a span are as many as before, and the data-driven merge can
+// join them across twice the K.
 struct SegRule {
     int64_t bound = int64_t(1) << 24;
     int kbw = 64;
     int span_cap = 16;
+    bool clip_span = true;  // spans no longer than the shortest worst-case chunk
 };
 constexpr SegRule kSegTc{};
+constexpr SegRule kSegTcData{int64_t(1) << 24, 64, 32, false};
 constexpr SegRule kSegI8{int64_t(1) << 30, 128, 128};
 void build_segments(const DigitScheme &ds, int kblocks, std::vector<LeafSeg> &out,
                     const SegRule &rule = kSegTc);

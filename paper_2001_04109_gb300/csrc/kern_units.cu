@@ -55,7 +55,7 @@ __device__ __forceinline__ void unpack8(uint4 v, float (&d)[8]) {
 // result reads): skipped.  Grid: x = column block, y = (operand, 128-row
 // block of its planes).
 template <int D, bool KS>
-__global__ void __launch_bounds__(NORM_THREADS) k_plane_norms(const uint16_t *__restrict__ base,
+__global__ void __launch_bounds__(NORM_THREADS, 5) k_plane_norms(const uint16_t *__restrict__ base,
                                                               int64_t kpad, int64_t rpad, int64_t h,
                                                               int planes, int64_t nry,
                                                               uint32_t *table, int32_t nb) {
