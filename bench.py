@@ -398,7 +398,8 @@ def run_ours(args):
     same_opts = dict(leaf=args.leaf, levels=info["levels"], tile_ctas=info["tile_ctas"],
                      winograd=None if any(info["winograd"]) else 0,
                      digit_products="karatsuba" if info["products"] < info["digits"] ** 2
-                     else "schoolbook", unit_bounds=args.unit_bounds)
+                     else "schoolbook", unit_bounds=args.unit_bounds,
+                     epilogue_warps=info["epilogue_warps"] if info["tile_ctas"] == 1 else 0)
     sampler = ClockSampler(local)
     if ws > 1:
         dist.barrier()
@@ -499,14 +500,15 @@ def run_ours(args):
         del C
         torch.cuda.empty_cache()
         ws_b, slot_b = ffsyrk.workspace_query(
-            p, n, k, **{kk: v for kk, v in same_opts.items() if kk != "unit_bounds"})
+            p, n, k, **{kk: v for kk, v in same_opts.items()
+                        if kk not in ("unit_bounds", "epilogue_warps")})
         need = ws_b + slot_b + 4 * n * (k + 3) + 4 * n * n
         free, _ = torch.cuda.mem_get_info()
         nfly = int(max(1, min(3, (0.9 * free) // need)))
         ceiling = copy_ceiling(n, k, stream)
         A_pin = A_host.pin_memory()
         C_pins = [torch.empty((n, n), dtype=torch.int32).pin_memory() for _ in range(nfly)]
-        plans = [ffsyrk.Plan(p, n, k, epilogue_warps=args.epilogue_warps, **same_opts)
+        plans = [ffsyrk.Plan(p, n, k, **same_opts)
                  for _ in range(nfly)]
         streams = [torch.cuda.Stream() for _ in range(nfly)]
 
@@ -580,6 +582,7 @@ def run_ours(args):
                            "winograd": info["winograd"][: info["levels"]],
                            "leaf": {1: "tc_bf16", 2: "i64"}[info["leaf"]],
                            "tile_ctas": info["tile_ctas"],
+                           "epilogue_warps": info["epilogue_warps"],
                            "unit_bounds": args.unit_bounds,
                            "leaf_units": (None if units is None else
                                           {"worst_case": units[0], "run": units[1]}),

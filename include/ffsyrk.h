@@ -85,7 +85,8 @@ typedef struct {
                           pair of SMs (tcgen05 cta_group::2)                    */
     int32_t autotune;  /* 1 (with levels = FFSYRK_LEVELS_AUTO and tile_ctas = 0):
                           ffsyrk_plan times every candidate depth and tile
-                          variant at max_n × max_k on synthetic data in its own
+                          variant (and, for one-SM tiles, 8 or 16 epilogue
+                          warps) at max_n × max_k on synthetic data in its own
                           workspace and keeps the fastest.  Results are cached
                           per process and, if the environment variable
                           FFSYRK_TUNE_CACHE names a file, in that file.
@@ -388,6 +389,9 @@ typedef struct {
     int32_t products;    /* digit products per field multiply-add of the
                             leaf: D², or D(D+1)/2 with Karatsuba; 1 for the
                             int64 leaf                                       */
+    int32_t epilogue_warps; /* one-SM tensor-core leaf: epilogue warps (8 or
+                            16; 0 for the other leaves)                      */
+    int32_t unit_bounds; /* the unit_bounds option the plan runs with       */
 } ffsyrk_plan_info_t;
 
 ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t plan, ffsyrk_plan_info_t *info);

@@ -1662,7 +1662,7 @@ void destroy_plan(ffsyrk_plan_st *pl) {
 // A candidate: depth L, SMs per tile (1 or 2), Winograd cap (−1 = the cost
 // model's levels, 0 = none) and digit products (Karatsuba or schoolbook).
 struct TuneChoice {
-    int L = 0, ctas = 1, sw = -1, ks = 0;
+    int L = 0, ctas = 1, sw = -1, ks = 0, ew = 0;
     float ms = 0;
 };
 std::mutex g_tune_mu;
@@ -1673,16 +1673,17 @@ std::string tune_key(const ffsyrk_plan_st *pl) {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, pl->device);
     char buf[512];
-    snprintf(buf, sizeof buf, "%s|sm%d|D%d|Y%d|n%lld|k%lld|leaf%d|sw%d|dp%d", prop.name,
+    snprintf(buf, sizeof buf, "%s|sm%d|D%d|Y%d|n%lld|k%lld|leaf%d|sw%d|dp%d|ew%d|ub%d", prop.name,
              prop.multiProcessorCount, pl->ds.D, pl->yc.form, (long long)pl->max_n,
-             (long long)pl->max_k, pl->leaf, pl->sw_opt, pl->dp_opt);
+             (long long)pl->max_k, pl->leaf, pl->sw_opt, pl->dp_opt, pl->ew_opt, pl->ub_opt);
     std::string key(buf);
     for (char &c : key)
         if (c == ' ') c = '_';
     return key;
 }
 
-// The cache file holds one line per key: key L ctas sw ks ms.
+// The cache file holds one line per key: key L ctas sw ks ew ms (lines of
+// any other shape are skipped).
 void tune_cache_load() {
     if (g_tune_loaded) return;
     g_tune_loaded = true;
@@ -1690,10 +1691,11 @@ void tune_cache_load() {
     if (!path || !*path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    char line[768], key[512];
+    char line[768], key[512], extra[8];
     while (fgets(line, sizeof line, f)) {
         TuneChoice t;
-        if (sscanf(line, "%511s %d %d %d %d %f", key, &t.L, &t.ctas, &t.sw, &t.ks, &t.ms) == 6)
+        if (sscanf(line, "%511s %d %d %d %d %d %f %7s", key, &t.L, &t.ctas, &t.sw, &t.ks, &t.ew, &t.ms,
+                   extra) == 7)
             g_tune[key] = t;
     }
     fclose(f);
@@ -1705,7 +1707,7 @@ void tune_cache_store(const std::string &key, const TuneChoice &t) {
     if (!path || !*path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %.6f\n", key.c_str(), t.L, t.ctas, t.sw, t.ks, t.ms);
+    fprintf(f, "%s %d %d %d %d %d %.6f\n", key.c_str(), t.L, t.ctas, t.sw, t.ks, t.ew, t.ms);
     fclose(f);
 }
 
@@ -1738,12 +1740,18 @@ std::vector<TuneChoice> tune_candidates(const ffsyrk_plan_st *pl) {
             }
             for (int sw : sws)
                 for (int c = 1; c <= (tc ? 2 : 1); ++c) {
-                    TuneChoice t;
-                    t.L = L;
-                    t.ctas = c;
-                    t.sw = sw;
-                    t.ks = ks;
-                    out.push_back(t);
+                    // one-SM tiles: 8 or 16 epilogue warps, unless the caller fixed it
+                    std::vector<int> ews{pl->ew_opt};
+                    if (tc && c == 1 && pl->ew_opt == 0) ews = {8, 16};
+                    for (int ew : ews) {
+                        TuneChoice t;
+                        t.L = L;
+                        t.ctas = c;
+                        t.sw = sw;
+                        t.ks = ks;
+                        t.ew = ew;
+                        out.push_back(t);
+                    }
                 }
         }
     return out;
@@ -1760,6 +1768,7 @@ bool tune_cached(ffsyrk_plan_st *pl) {
     pl->levels_opt = t.L;
     pl->ctas_opt = t.ctas;
     pl->sw_opt = t.sw;
+    pl->ew_opt = t.ew;
     pl->ds = make_digits(pl->p, t.ks != 0);
     pl->tuned_ms = t.ms;
     pl->autotuned = true;
@@ -1774,6 +1783,7 @@ ffsyrk_status_t autotune(ffsyrk_plan_st *pl) {
         pl->levels_opt = t.L;
         pl->ctas_opt = t.ctas;
         pl->sw_opt = t.sw;
+        pl->ew_opt = t.ew;
         pl->ds = make_digits(pl->p, t.ks != 0);
         pl->tuned_ms = t.ms;
     };
@@ -2122,6 +2132,8 @@ ffsyrk_status_t ffsyrk_plan_get_info(ffsyrk_plan_t pl, ffsyrk_plan_info_t *info)
     for (int d = 0; d < 6 && d < kMaxLevels; ++d) info->winograd[d] = g.sw[d];
     info->planes = pl->leaf == FFSYRK_LEAF_I64 ? 1 : lds.nplanes;
     info->products = pl->leaf == FFSYRK_LEAF_I64 ? 1 : pl->leaf == FFSYRK_LEAF_I8 ? lds.D * lds.D : nprod(lds);
+    info->epilogue_warps = pl->leaf != FFSYRK_LEAF_TC_BF16 ? 0 : pl->ew_opt ? pl->ew_opt : (pl->ds.ks ? 16 : 8);
+    info->unit_bounds = pl->ub_opt;
     return FFSYRK_SUCCESS;
 }
 

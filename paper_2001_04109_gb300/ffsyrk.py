@@ -63,7 +63,8 @@ class PlanInfo(ctypes.Structure):
                 ("chunk_k", ctypes.c_int32 * 9), ("workspace_bytes", ctypes.c_int64),
                 ("tile_ctas", ctypes.c_int32), ("autotuned", ctypes.c_int32),
                 ("tuned_ms", ctypes.c_float), ("winograd", ctypes.c_int32 * 6),
-                ("planes", ctypes.c_int32), ("products", ctypes.c_int32)]
+                ("planes", ctypes.c_int32), ("products", ctypes.c_int32),
+                ("epilogue_warps", ctypes.c_int32), ("unit_bounds", ctypes.c_int32)]
 
 
 class Timing(ctypes.Structure):
@@ -240,7 +241,8 @@ class Plan:
                 "leaf": i.leaf, "levels": i.levels, "digits": i.digits,
                 "chunk_k": list(i.chunk_k), "workspace_bytes": i.workspace_bytes,
                 "tile_ctas": i.tile_ctas, "autotuned": i.autotuned, "tuned_ms": i.tuned_ms,
-                "winograd": list(i.winograd), "planes": i.planes, "products": i.products}
+                "winograd": list(i.winograd), "planes": i.planes, "products": i.products,
+                "epilogue_warps": i.epilogue_warps, "unit_bounds": i.unit_bounds}
 
     def __call__(self, A: torch.Tensor, C: torch.Tensor | None = None, uplo: str = "lower",
                  stream=None, alpha: int = 1, beta: int = 0) -> torch.Tensor:
