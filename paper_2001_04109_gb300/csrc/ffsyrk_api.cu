@@ -810,14 +810,20 @@ int choose_levels(const ffsyrk_plan_st *pl, int64_t n, int64_t k) {
 // So pairs are used for launches that fill the SMs, with byte digits and an
 // estimated leaf time under 40 ms; one-SM tiles otherwise (small launches can
 // then also share long tiles' K among idle SMs, split_tail).
+// Whether a leaf launch at geometry g runs long enough to settle at the
+// 1.4 kW power cap (estimated over 40 ms: digit multiply-adds over a
+// measured ≈ 9e14 per second), where SM-pair tiles, which draw more power
+// per multiply-add, clock lower and lose to one-SM tiles.
+bool power_capped_leaf(const Geometry &g, const DigitScheme &ds) {
+    const double est_ms = leaf_field_macs(g) * nprod(ds) / 9e14 * 1e3;
+    return est_ms >= 40.0;
+}
+
 int choose_ctas(const ffsyrk_plan_st *pl, const Geometry &g) {
     if (pl->ctas_opt == 1 || pl->ctas_opt == 2) return pl->ctas_opt;
     if (pl->leaf != FFSYRK_LEAF_TC_BF16 || pl->ds.base != 256) return 1;
     if (leaf_tiles_bound(g, pl->leaf) < pl->sms) return 1;
-    // digit multiply-adds of the leaf over a measured ≈ 9e14 per second
-    const double macs = leaf_field_macs(g);
-    const double est_ms = macs * nprod(pl->ds) / 9e14 * 1e3;
-    return est_ms < 40.0 ? 2 : 1;
+    return power_capped_leaf(g, pl->ds) ? 1 : 2;
 }
 
 ffsyrk_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? FFSYRK_SUCCESS : FFSYRK_ERR_CUDA; }
@@ -1738,8 +1744,11 @@ std::vector<TuneChoice> tune_candidates(const ffsyrk_plan_st *pl) {
                 for (int d = 0; d < L; ++d) any = any || g.sw[d] > 0;
                 if (any) sws.push_back(0);
             }
+            // a few timed calls do not reach the power cap that decides
+            // between the tile widths of long launches: one-SM tiles there
+            const int max_c = tc && !power_capped_leaf(make_geometry(pl->max_n, pl->max_k, L), ds) ? 2 : 1;
             for (int sw : sws)
-                for (int c = 1; c <= (tc ? 2 : 1); ++c) {
+                for (int c = 1; c <= max_c; ++c) {
                     // one-SM tiles: 8 or 16 epilogue warps, unless the caller fixed it
                     std::vector<int> ews{pl->ew_opt};
                     if (tc && c == 1 && pl->ew_opt == 0) ews = {8, 16};
