@@ -68,7 +68,12 @@ __device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontro
 
 constexpr int PREP_THREADS = 128;  // threads per block
 constexpr int PREP_COLS = 8;       // columns per thread
-constexpr int PREP_ROWS = 2;       // rows per thread (independent loads in flight)
+// rows per thread (independent loads in flight); one with Karatsuba sum
+// planes, whose longer digit split otherwise needs ~160 registers and leaves
+// fewer warps to cover the loads (measured 0.81 → 0.78 ms for the A 8192²
+// depth-2 mix, 14.9 → 14.4 ms of pre-additions at 32768²)
+template <int OK>
+constexpr int prep_rows() { return OK == ARENA_BF16_KS ? 1 : 2; }
 
 
 // Eight consecutive entries (row r, columns c..c+7) of a view, zero outside.
@@ -180,6 +185,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restric
     // quadrant column offsets 0 and w keep 16-byte alignment when w % 4 == 0
     const bool vec_ok = ((reinterpret_cast<uintptr_t>(nd.X.ptr) & 15u) == 0) &&
                         ((nd.X.ld & 3) == 0) && ((w & 3) == 0);
+    constexpr int PREP_ROWS = prep_rows<OK>();
     const int64_t nrb = (h + PREP_ROWS - 1) / PREP_ROWS;
     for (int64_t rb = blockIdx.y; rb < nrb; rb += gridDim.y) {
         uint32_t a[PREP_ROWS][4][8];  // [row][quadrant A11, A12, A21, A22][column]
@@ -660,7 +666,8 @@ cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_
                         bool reduce_input, cudaStream_t st) {
     if (h == 0 || kpad == 0 || nnodes == 0) return cudaSuccess;
     const int64_t gx = (kpad / PREP_COLS + PREP_THREADS - 1) / PREP_THREADS;
-    const int64_t gy = std::min<int64_t>((h + PREP_ROWS - 1) / PREP_ROWS, 65535);
+    const int rows = arena_kind == ARENA_BF16_KS ? prep_rows<ARENA_BF16_KS>() : prep_rows<ARENA_BF16>();
+    const int64_t gy = std::min<int64_t>((h + rows - 1) / rows, 65535);
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nnodes);
     if (arena_kind == ARENA_U32)
         return launch_prep_d<1, ARENA_U32>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
