@@ -1064,6 +1064,16 @@ void unit_links(Descs &D, const DigitScheme &ds, const Layout &lay) {
         const LeafProd &pr = D.prods[D.tiles[q].prod];
         if (D.pieces[q].sx0 > 0) D.links[pr.seg0 + D.pieces[q].sx0] = 0;
     }
+    // no unit of the worst-case schedule could join the one before it (short
+    // K: one unit per weight class): the passes would only cost time
+    bool mergeable = false;
+    for (size_t s = 0; s < D.segs.size() && !mergeable; ++s) mergeable = D.segs[s].first && D.links[s];
+    if (!mergeable) {
+        D.links.clear();
+        D.ujobs.clear();
+        D.norm_entries = 0;
+        return;
+    }
     int64_t n = 0;
     for (int j = 0; j <= kMaxLevels; ++j) {
         const Arena &a = lay.arena[j];
