@@ -206,6 +206,11 @@ struct Layout {
     // products at level l ≥ 1 (2·3^d·7^l of h_{d+1+l}²)
     int64_t swin_off[kMaxLevels][kMaxLevels + 1] = {};
     int64_t swout_off[kMaxLevels][kMaxLevels + 1] = {};
+    // norm tables of the bf16 arenas (see NormTables): arena j's
+    // planes × nb[j] entries start at entry norm_arena[j] of the region at
+    // norm_off; norm_entries in all
+    int64_t norm_off = 0, norm_entries = 0;
+    int32_t norm_arena[kMaxLevels + 1] = {}, norm_nb[kMaxLevels + 1] = {};
     int64_t data_bytes = 0;
 };
 
@@ -309,6 +314,15 @@ Layout make_layout(const Geometry &g, int leaf, int D, bool ks = false) {
         a.rows = arena_nops(g, j) * a.planes * a.rpad;
         lay.arena_off[j] = take(a.bytes());
     }
+    if (tc) {
+        for (int j = j0; j <= (g.L == 0 ? 0 : g.L); ++j) {
+            const Arena &a = lay.arena[j];
+            lay.norm_arena[j] = (int32_t)lay.norm_entries;
+            lay.norm_nb[j] = (int32_t)((a.kpad + kNormCols - 1) / kNormCols);
+            lay.norm_entries += (int64_t)a.planes * lay.norm_nb[j];
+        }
+        lay.norm_off = take(lay.norm_entries * 4);
+    }
     for (int d = 1; d <= g.L - 1; ++d) lay.s3_off[d] = take(pow3(d - 1) * g.h[d] * g.w[d] * 4);
     for (int d = 1; d <= g.L; ++d) lay.r_off[d] = take(pow3(d) * g.h[d] * g.h[d] * 4);
     for (int d = 0; d <= g.L - 1; ++d)
@@ -345,14 +359,12 @@ struct Descs {
     // host schedule as built)
     std::vector<uint8_t> links;
     std::vector<UnitJob> ujobs;
-    int32_t norm_arena_off[kMaxLevels + 1] = {}, norm_nb[kMaxLevels + 1] = {};
-    int64_t norm_entries = 0;
     int64_t digit_max_rows = 0, digit_max_kpad = 0;
     // blob offsets (bytes) inside the descriptor region
     int64_t prep_off[kMaxLevels] = {}, post_off[kMaxLevels] = {};
     int64_t prods_off = 0, tiles_off = 0, tmap_off = 0, aptr_off = 0, akpad_off = 0, digit_off = 0;
     int64_t ctr_off = 0, segs_off = 0, pieces_off = 0, entries_off = 0;
-    int64_t links_off = 0, ujobs_off = 0, norm_off = 0;
+    int64_t links_off = 0, ujobs_off = 0;
     int64_t ctr_bytes = 16;  // work counter + 8 counters per split tile, zeroed every call
     int64_t bytes = 0;
 };
@@ -401,9 +413,8 @@ int64_t desc_capacity(const Geometry &g, int leaf) {
     // segment tables: at most L + 1 distinct K per call, ≤ 40 segments per 16 k-blocks,
     // with a link byte each
     b += (int64_t)(g.L + 1) * ((g.kp / 64 + 16) / 16 + 1) * 40 * (int64_t)(sizeof(LeafSeg) + 1);
-    // unit jobs and the norm tables: ≤ 6 planes × ⌈kpad_j / 256⌉ blocks per arena, Σ_j kpad_j ≤ 2·kp + 64·(L + 1)
-    b += (int64_t)(g.L + 1) * sizeof(UnitJob) + 3 * 256;
-    b += (int64_t)kMaxPlanes * (2 * (g.kp / kNormCols) + 2 * (kMaxLevels + 1)) * 4;
+    // unit jobs
+    b += (int64_t)(g.L + 1) * sizeof(UnitJob) + 2 * 256;
     return rup(b, kAlign);
 }
 
@@ -1071,19 +1082,9 @@ void unit_links(Descs &D, const DigitScheme &ds, const Layout &lay) {
     if (!mergeable) {
         D.links.clear();
         D.ujobs.clear();
-        D.norm_entries = 0;
         return;
     }
-    int64_t n = 0;
-    for (int j = 0; j <= kMaxLevels; ++j) {
-        const Arena &a = lay.arena[j];
-        D.norm_arena_off[j] = (int32_t)n;
-        D.norm_nb[j] = 0;
-        if (a.rows == 0 || (a.kind != ARENA_BF16 && a.kind != ARENA_BF16_KS)) continue;
-        D.norm_nb[j] = (int32_t)((a.kpad + kNormCols - 1) / kNormCols);
-        n += (int64_t)a.planes * D.norm_nb[j];
-    }
-    D.norm_entries = n;
+    (void)lay;
 }
 
 // Build every descriptor of one call into pl->desc and the staging blob.
@@ -1102,6 +1103,13 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     for (int j = 0; j <= kMaxLevels; ++j)
         if (lay.arena[j].rows > 0) lay.arena[j].base = ws + lay.arena_off[j];
 
+    // the norm table of arena j (bf16 arenas of the tensor-core leaf with
+    // data-driven units), taken by whichever kernel writes its digits
+    auto norm_of = [&](int j) {
+        return tc && pl->ub_opt == 0 && lay.norm_nb[j] > 0
+                   ? reinterpret_cast<uint32_t *>(ws + lay.norm_off) + lay.norm_arena[j]
+                   : nullptr;
+    };
     auto operand = [&](int j, int64_t o) {
         const Arena &a = lay.arena[j];
         OperandDst d;
@@ -1109,6 +1117,8 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         d.row0 = o * a.planes * a.rpad;
         d.kpad = a.kpad;
         d.rpad = a.rpad;
+        d.norm = norm_of(j);
+        d.nb = lay.norm_nb[j];
         return d;
     };
     auto rbuf = [&](int d, int64_t t) {
@@ -1144,10 +1154,12 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         D.prods.push_back(pr);
         tri_tiles(D.tiles, 0, g.n, g.n, pr.tri, TM, TN, pr.kblocks * cost_mult, band_for(a0));
         D.digit.push_back(DigitizeJob{MatView{A, lda, g.n, g.k}, g.n,
-                                      OperandDst{a0.base, 0, a0.kpad, a0.rpad}});
+                                      OperandDst{a0.base, 0, a0.kpad, a0.rpad, norm_of(0), lay.norm_nb[0]}});
         if (g.gemmt)
             D.digit.push_back(DigitizeJob{MatView{A, lda, g.n, g.k}, g.n,
-                                          OperandDst{a0.base, pr.b_row0, a0.kpad, a0.rpad}, 0, 1});
+                                          OperandDst{a0.base, pr.b_row0, a0.kpad, a0.rpad, norm_of(0),
+                                                     lay.norm_nb[0]},
+                                          0, 1});
         D.digit_max_rows = g.n;
         D.digit_max_kpad = a0.kpad;
     } else {
@@ -1304,7 +1316,22 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     if (tc && !pair) split_tail(D, pl->sms, pl->part_slots);
     if (pair) split_pairs(D, pl->sms / 2, pl->part_slots);
     D.ctr_bytes = 16 + (int64_t)D.nslots * 16 * 4;  // a counter per slot and epilogue warp (≤ 16)
-    if (tc && pl->ub_opt == 0) unit_links(D, pl->ds, lay);
+    if (tc && pl->ub_opt == 0) {
+        unit_links(D, pl->ds, lay);
+        if (D.ujobs.empty()) {
+            // nothing can merge: the digit writers skip the norms
+            for (int d = 0; d < kMaxLevels; ++d) {
+                for (PrepNode &nd : D.prep[d]) {
+                    for (OperandDst &o : nd.gemm) o.norm = nullptr;
+                    for (OperandDst &o : nd.leaf) o.norm = nullptr;
+                }
+                for (int l = 0; l <= kMaxLevels; ++l)
+                    for (SwPreJob &jb : D.swpre[d][l])
+                        for (OperandDst &o : jb.dst) o.norm = nullptr;
+            }
+            for (DigitizeJob &jb : D.digit) jb.dst.norm = nullptr;
+        }
+    }
 
     // pack the blob
     int64_t off = 0;
@@ -1334,7 +1361,6 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     D.entries_off = slot((int64_t)D.entries.size() * sizeof(int32_t), 64);
     D.links_off = slot((int64_t)D.links.size(), 64);
     D.ujobs_off = slot((int64_t)D.ujobs.size() * sizeof(UnitJob), 64);
-    D.norm_off = slot(D.norm_entries * 4, 256);
     D.bytes = rup(off, 256);
     if (D.bytes > pl->desc_cap) return FFSYRK_ERR_TOO_LARGE;
 
@@ -1404,8 +1430,10 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
     if ((tc1 || tc2_split) &&
         cudaMemsetAsync(dd + D.ctr_off, 0, (size_t)D.ctr_bytes, st) != cudaSuccess)
         return FFSYRK_ERR_CUDA;
+    // the norm tables start at zero: the digit writers max-accumulate into them
     const bool data_units = !D.ujobs.empty();
-    if (data_units && cudaMemsetAsync(dd + D.norm_off, 0, (size_t)D.norm_entries * 4, st) != cudaSuccess)
+    if (data_units &&
+        cudaMemsetAsync(pl->ws + lay.norm_off, 0, (size_t)lay.norm_entries * 4, st) != cudaSuccess)
         return FFSYRK_ERR_CUDA;
     if (g.L == 0) {
         e = launch_digitize(reinterpret_cast<const DigitizeJob *>(dd + D.digit_off),
@@ -1432,17 +1460,12 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
         }
     }
     if (data_units) {
-        // unit lengths from the digits just written (see UnitJob)
+        // unit lengths from the norms the digit writers took (see UnitJob)
         NormTables nt{};
-        nt.base = reinterpret_cast<uint32_t *>(dd + D.norm_off);
+        nt.base = reinterpret_cast<uint32_t *>(pl->ws + lay.norm_off);
         for (int j = 0; j <= kMaxLevels; ++j) {
-            nt.off[j] = D.norm_arena_off[j];
-            nt.nb[j] = D.norm_nb[j];
-        }
-        for (int j = 0; j <= kMaxLevels; ++j) {
-            if (D.norm_nb[j] == 0) continue;
-            e = launch_plane_norms(lay.arena[j], g.h[j], nt, j, pl->ds.D, pl->ds.ks != 0, st);
-            if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
+            nt.off[j] = lay.norm_arena[j];
+            nt.nb[j] = lay.norm_nb[j];
         }
         e = launch_unit_schedule(reinterpret_cast<const UnitJob *>(dd + D.ujobs_off),
                                  (int)D.ujobs.size(), nt,
@@ -1578,10 +1601,7 @@ void record_work(ffsyrk_plan_st *pl) {
     const Descs &D = pl->desc;
     pl->last_launches = g.L == 0 ? 2 : 2 * g.L + 1;
     for (int d = 0; d < g.L; ++d) pl->last_launches += 2 * g.sw[d];
-    if (!D.ujobs.empty()) {
-        pl->last_launches += 1;  // the unit schedule
-        for (int j = 0; j <= kMaxLevels; ++j) pl->last_launches += D.norm_nb[j] > 0 ? 1 : 0;
-    }
+    if (!D.ujobs.empty()) pl->last_launches += 1;  // the unit schedule
     pl->last_leaf_launches = 1;
     int split = 0, whole = 0;
     for (const LeafPiece &q : D.pieces) {

@@ -147,6 +147,11 @@ struct OperandDst {
     int64_t row0;      // first row of digit plane 0
     int64_t kpad;      // row length in elements
     int64_t rpad;      // rows per digit plane
+    // bf16 digit planes: the arena's norm table ([plane][256-column block],
+    // nb blocks per plane; see NormTables), max-accumulated by the writer;
+    // nullptr: none
+    uint32_t *norm = nullptr;
+    int32_t nb = 0;
 };
 
 // One node of a recursion depth for the pre-addition kernel.
@@ -241,8 +246,9 @@ int build_segments_into(const DigitScheme &ds, int kblocks, LeafSeg *out, int ca
 // of Σ_k x_k·z_k, in any order, is at most Σ_k |x_k|·|z_k| ≤
 // sqrt(Σ_k x_k²)·sqrt(Σ_k z_k²) (Cauchy–Schwarz), and Σ_k x_k² over a range
 // is at most the sum, over the 256-column blocks the range touches, of the
-// largest row sum of squares of that plane in the block.  Before the leaf,
-// one pass takes those block maxima per arena and digit plane; a second
+// largest row sum of squares of that plane in the block.  The kernels that
+// write the digit planes also take those block maxima per arena and plane
+// (OperandDst::norm); before the leaf one pass
 // merges consecutive segments of one weight class into one unit while the
 // data bound of the unit stays ≤ 2^24 (exact FP32), so uniform residues
 // take about one drain per product and 16 k-blocks instead of one per
@@ -340,12 +346,6 @@ cudaError_t launch_post(const PostNode *nodes_dev, int nnodes, int64_t h, ModP m
 cudaError_t launch_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, cudaStream_t st);
 // count uniform residues in [0, p) from a counter hash (the autotuner's operands)
 cudaError_t launch_fill_residues(uint32_t *A, int64_t count, uint32_t p, uint64_t seed, cudaStream_t st);
-// Block maxima of arena j's bf16 digit planes into t.base + t.off[j]
-// ([plane][block], max-accumulated: the table starts at zero); h: the rows
-// of each operand plane that hold digits (the rest is padding); D digits,
-// ks: the planes after them are Karatsuba digit sums.
-cudaError_t launch_plane_norms(const Arena &a, int64_t h, const NormTables &t, int j, int D, bool ks,
-                               cudaStream_t st);
 // The `first` flags of every job's segments from the tables (see UnitJob).
 cudaError_t launch_unit_schedule(const UnitJob *jobs_dev, int njobs, const NormTables &t,
                                  const uint8_t *links, LeafSeg *segs, const DigitScheme &ds,

@@ -179,6 +179,9 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restric
     const int64_t c = PREP_COLS * ((int64_t)blockIdx.x * PREP_THREADS + threadIdx.x);
     if (c >= kpad) return;
     const PrepNode &nd = nodes[blockIdx.z];
+    const int64_t c0 = c - PREP_COLS * (threadIdx.x & 31);  // the warp's first column
+    NormAcc acc;
+    acc.mask = norm_lanes(c0, kpad);
     const uint32_t p = m.p;
     // w is a multiple of 4: each 4-column half lies wholly inside or outside
     const bool in0 = c < w, in1 = c + 4 < w;
@@ -233,13 +236,13 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restric
                 s3[e] = subm(s1[e], x22[e], p);                 // S3 = S1 − A22
                 s4[e] = addm(s3[e], x12[e], p);                 // S4 = S3 + A12
             }
-            put8<D, OK>(nd.gemm[0], r, c, x22, m);
-            put8<D, OK>(nd.gemm[1], r, c, s4, m);
-            put8<D, OK>(nd.gemm[2], r, c, s1, m);
-            put8<D, OK>(nd.gemm[3], r, c, s2, m);
-            put8<D, OK>(nd.leaf[0], r, c, x11, m);
-            put8<D, OK>(nd.leaf[1], r, c, x12, m);
-            put8<D, OK>(nd.leaf[2], r, c, s3, m);
+            put8<D, OK>(nd.gemm[0], r, c, x22, m, &acc);
+            put8<D, OK>(nd.gemm[1], r, c, s4, m, &acc);
+            put8<D, OK>(nd.gemm[2], r, c, s1, m, &acc);
+            put8<D, OK>(nd.gemm[3], r, c, s2, m, &acc);
+            put8<D, OK>(nd.leaf[0], r, c, x11, m, &acc);
+            put8<D, OK>(nd.leaf[1], r, c, x12, m, &acc);
+            put8<D, OK>(nd.leaf[2], r, c, s3, m, &acc);
             if (nd.s3 != nullptr) {
 #pragma unroll
                 for (int hf = 0; hf < 2; ++hf) {
@@ -255,6 +258,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restric
             }
         }
     }
+    norm_flush(acc, OK == ARENA_BF16_KS ? D + D * (D - 1) / 2 : D, c0);
 }
 
 
@@ -271,6 +275,9 @@ __global__ void __launch_bounds__(DIG_THREADS) k_digitize(const DigitizeJob *__r
     const DigitizeJob &jb = jobs[blockIdx.z];
     const int64_t c = DIG_COLS * ((int64_t)blockIdx.x * DIG_THREADS + threadIdx.x);
     if (c >= jb.dst.kpad) return;
+    const int64_t c0 = c - DIG_COLS * (threadIdx.x & 31);  // the warp's first column
+    NormAcc acc;
+    acc.mask = norm_lanes(c0, jb.dst.kpad);
     const bool vec_ok = ((reinterpret_cast<uintptr_t>(jb.X.ptr) & 15u) == 0) && ((jb.X.ld & 3) == 0);
     const int64_t nrb = (jb.rows + DIG_ROWS - 1) / DIG_ROWS;
     for (int64_t rb = blockIdx.y; rb < nrb; rb += gridDim.y) {
@@ -292,9 +299,10 @@ __global__ void __launch_bounds__(DIG_THREADS) k_digitize(const DigitizeJob *__r
                     v[i][e + 1] = x;
                 }
             }
-            put8<D, OK>(jb.dst, r, c, v[i], m);
+            put8<D, OK>(jb.dst, r, c, v[i], m, &acc);
         }
     }
+    norm_flush(acc, OK == ARENA_BF16_KS ? D + D * (D - 1) / 2 : D, c0);
 }
 
 // The same digit split over a flattened block list: block b belongs to the

@@ -72,6 +72,9 @@ __global__ void __launch_bounds__(SWP_THREADS) k_sw_pre(const SwPreJob *__restri
     const int64_t c = SWP_COLS * ((int64_t)blockIdx.x * SWP_THREADS + threadIdx.x);
     if (c >= kpad) return;
     const SwPreJob &jb = jobs[blockIdx.z];
+    const int64_t c0 = c - SWP_COLS * (threadIdx.x & 31);  // the warp's first column
+    NormAcc acc;
+    acc.mask = norm_lanes(c0, kpad);
     const uint32_t p = m.p;
     // ww is a multiple of 4: each 4-column half lies wholly inside or outside
     const int n4 = c >= ww ? 0 : (c + 4 >= ww ? 1 : 2);
@@ -93,13 +96,13 @@ __global__ void __launch_bounds__(SWP_THREADS) k_sw_pre(const SwPreJob *__restri
                 o[2][e] = subp(x12[e], s3, p);      // s4
                 x21[e] = s2;                        // x21 is not an output: reuse for s2
             }
-            put8<D, OK>(jb.dst[0], r, c, x11, m);
-            put8<D, OK>(jb.dst[1], r, c, x12, m);
-            put8<D, OK>(jb.dst[2], r, c, x22, m);
-            put8<D, OK>(jb.dst[3], r, c, o[0], m);
-            put8<D, OK>(jb.dst[4], r, c, o[1], m);
-            put8<D, OK>(jb.dst[5], r, c, o[2], m);
-            put8<D, OK>(jb.dst[6], r, c, x21, m);
+            put8<D, OK>(jb.dst[0], r, c, x11, m, &acc);
+            put8<D, OK>(jb.dst[1], r, c, x12, m, &acc);
+            put8<D, OK>(jb.dst[2], r, c, x22, m, &acc);
+            put8<D, OK>(jb.dst[3], r, c, o[0], m, &acc);
+            put8<D, OK>(jb.dst[4], r, c, o[1], m, &acc);
+            put8<D, OK>(jb.dst[5], r, c, o[2], m, &acc);
+            put8<D, OK>(jb.dst[6], r, c, x21, m, &acc);
         } else {
             // right operands: R11, R12, R12 − T3, T1, T3, R22, T2
 #pragma unroll
@@ -112,15 +115,16 @@ __global__ void __launch_bounds__(SWP_THREADS) k_sw_pre(const SwPreJob *__restri
                 o[2][e] = t3;
                 x21[e] = t2;  // x21 is not an output: reuse for T2
             }
-            put8<D, OK>(jb.dst[0], r, c, x11, m);
-            put8<D, OK>(jb.dst[1], r, c, x12, m);
-            put8<D, OK>(jb.dst[2], r, c, o[0], m);
-            put8<D, OK>(jb.dst[3], r, c, o[1], m);
-            put8<D, OK>(jb.dst[4], r, c, o[2], m);
-            put8<D, OK>(jb.dst[5], r, c, x22, m);
-            put8<D, OK>(jb.dst[6], r, c, x21, m);
+            put8<D, OK>(jb.dst[0], r, c, x11, m, &acc);
+            put8<D, OK>(jb.dst[1], r, c, x12, m, &acc);
+            put8<D, OK>(jb.dst[2], r, c, o[0], m, &acc);
+            put8<D, OK>(jb.dst[3], r, c, o[1], m, &acc);
+            put8<D, OK>(jb.dst[4], r, c, o[2], m, &acc);
+            put8<D, OK>(jb.dst[5], r, c, x22, m, &acc);
+            put8<D, OK>(jb.dst[6], r, c, x21, m, &acc);
         }
     }
+    norm_flush(acc, OK == ARENA_BF16_KS ? D + D * (D - 1) / 2 : D, c0);
 }
 
 // One level of post-additions: job z combines its 7 hh × hh products into

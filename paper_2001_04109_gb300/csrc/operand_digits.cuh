@@ -52,11 +52,37 @@ __device__ __forceinline__ uint32_t byte_plane(const int (&sv)[N], int e0, int t
 }
 
 // Store eight residues at (row r, columns c..c+7) of an operand: one
+// A warp's share of the norm tables (see OperandDst::norm): the 32 lanes
+// of a warp write 256 consecutive columns of one row (8 each), which is one
+// block of the table.  Per row and operand the lanes' sums of squares of
+// every plane are added across the warp; lane t keeps the running maximum
+// of plane t.  `mask`: the lanes that took part (columns below kpad).
+struct NormAcc {
+    uint32_t mask = 0;
+    uint32_t best = 0;       // lane t: plane t's largest row sum so far
+    uint32_t *table = nullptr;
+    int32_t nb = 0;
+};
+// The lanes of the warp whose first column is c0 that hold columns below kpad.
+__device__ __forceinline__ uint32_t norm_lanes(int64_t c0, int64_t kpad) {
+    const int64_t n = (kpad - c0 + 7) / 8;
+    return n >= 32 ? 0xffffffffu : n <= 0 ? 0u : ((1u << n) - 1u);
+}
+// Lanes t < planes add their maximum into the table (block = c0 / 256).
+__device__ __forceinline__ void norm_flush(const NormAcc &acc, int planes, int64_t c0) {
+    const int lane = threadIdx.x & 31;
+    if (acc.table != nullptr && lane < planes && acc.best != 0)
+        atomicMax(acc.table + (int64_t)lane * acc.nb + c0 / 256, acc.best);
+}
+
 // 16-byte store per digit plane (bf16), two (uint32), or one 8-byte store
-// per byte plane (INT8 leaf).
+// per byte plane (INT8 leaf).  With `acc` and a destination that has a norm
+// table, the warp also takes its row's sums of squares of every plane
+// (integers ≤ 2^24: 256 columns of digits ≤ 256 in magnitude); every lane of
+// acc.mask must make the same calls.
 template <int D, int OK>
 __device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, const uint32_t (&v)[8],
-                                     const ModP &m) {
+                                     const ModP &m, NormAcc *acc = nullptr) {
     if (d.arena == nullptr) return;
     if constexpr (OK == ARENA_U32) {
         uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(d.arena) + (d.row0 + r) * d.kpad + c);
@@ -92,8 +118,22 @@ __device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, 
             *reinterpret_cast<uint4 *>(base + (((d.row0 + t * d.rpad + r) * d.kpad + c) >> 1)) =
                 make_uint4(w[0], w[1], w[2], w[3]);
         };
+        const bool norms = acc != nullptr && d.norm != nullptr;
+        const int lane = threadIdx.x & 31;
+        uint32_t mine = 0;  // this lane's plane's row sum (lane t: plane t)
+        auto take = [&](int t, const int (&x)[8]) {
+            if (!norms) return;
+            int q = 0;
 #pragma unroll
-        for (int t = 0; t < D; ++t) store_plane(t, dg[t]);
+            for (int e = 0; e < 8; ++e) q += x[e] * x[e];
+            const uint32_t tot = __reduce_add_sync(acc->mask, (uint32_t)q);
+            mine = lane == t ? tot : mine;
+        };
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+            store_plane(t, dg[t]);
+            take(t, dg[t]);
+        }
         if constexpr (OK == ARENA_BF16_KS) {
             int t = D;
 #pragma unroll
@@ -104,7 +144,13 @@ __device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, 
 #pragma unroll
                     for (int e = 0; e < 8; ++e) sm[e] = dg[i][e] + dg[j][e];
                     store_plane(t, sm);
+                    take(t, sm);
                 }
+        }
+        if (norms) {
+            acc->best = max(acc->best, mine);
+            acc->table = d.norm;
+            acc->nb = d.nb;
         }
     }
 }
