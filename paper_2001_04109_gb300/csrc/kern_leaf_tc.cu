@@ -43,16 +43,25 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;            // 16 KB
 constexpr int B_BYTES = BN * BK * 2;            // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // 48 KB
-// Epilogue warps: EW = 8 (the default: 128 running sums per thread in 168
-// registers) or 16 (64 per thread, four warps per scheduler instead of two,
-// for launches of many short tiles, whose accumulator drains come every few
-// k-blocks).  Warps 0..EW−1 drain, warp EW produces, warp EW + 1 issues MMAs.
+// Epilogue warps: EW = 8 (128 running sums per thread) or 16 (64 per thread,
+// four warps per scheduler instead of two, for launches of many short tiles,
+// whose accumulator drains come every few k-blocks).  Warps 0..EW−1 drain,
+// warp EW produces, warp EW + 1 issues MMAs.
+// With 8 epilogue warps the CTA has 12 warps, three warpgroups: the third
+// (producer, MMA issuer and two idle warps) gives registers to the two
+// epilogue warpgroups with setmaxnreg, 168 at launch becoming 56 and 224
+// (2·128·224 + 128·56 = 384·168 = 64,512; per scheduler 3·32·168 = 16,128
+// ≤ 16,384), so an epilogue thread holds its 128 sums and two 16-column
+// accumulator chunks: it loads the next chunk from tensor memory while it
+// reduces the current one.  The 16-warp CTA (18 warps) keeps 96 registers.
 template <int EW>
 struct Roles {
     static constexpr int EPI_WARPS = EW;
     static constexpr int PRODUCER_WARP = EW, MMA_WARP = EW + 1;
-    static constexpr int NUM_THREADS = 32 * (EW + 2);  // every warp has exactly one role
+    static constexpr bool SPLIT_REGS = EW == 8;
+    static constexpr int NUM_THREADS = SPLIT_REGS ? 384 : 32 * (EW + 2);
     static constexpr int EPI_COLS = BN / (EW / 4);     // columns per epilogue thread
+    static constexpr int ISSUE_REGS = 56, EPI_REGS = 224;  // SPLIT_REGS: after setmaxnreg
 };
 constexpr int LD_COLS = 16;  // TMEM columns per tcgen05.ld
 constexpr int RING = 4;      // tiles handed from the producer to the MMA and epilogue warps
@@ -122,6 +131,9 @@ __global__ void __launch_bounds__(Roles<EW>::NUM_THREADS, 1) k_leaf_tc(const Lea
     fence_after();
     const uint32_t tmem_base = tmem_slot;
 
+    if (warp >= EPI_WARPS) {
+    if constexpr (Roles<EW>::SPLIT_REGS)
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(Roles<EW>::ISSUE_REGS));
     if (warp == PRODUCER_WARP) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
@@ -242,8 +254,11 @@ __global__ void __launch_bounds__(Roles<EW>::NUM_THREADS, 1) k_leaf_tc(const Lea
             mma_commit(&drain_bar);
             mbar_drain(&drain_bar, 0);
         }
-    } else if (warp < EPI_WARPS) {
+    }  // warps past the MMA issuer (SPLIT_REGS) have no role
+    } else {
         // ---------------- epilogue ----------------
+        if constexpr (Roles<EW>::SPLIT_REGS)
+            asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(Roles<EW>::EPI_REGS));
         const uint32_t p = m.p, twop = 2 * m.p, off = ds.offset;
         const int quad = warp & 3, colq = warp >> 2;
         uint32_t unit = 0;
@@ -280,27 +295,56 @@ __global__ void __launch_bounds__(Roles<EW>::NUM_THREADS, 1) k_leaf_tc(const Lea
                 const uint32_t w = wt.w, wsh = wt.w_sh;
                 const uint32_t taddr =
                     tmem_base + b * BN + ((uint32_t)(quad * 32) << 16) + colq * EPI_COLS;
+                // one 16-column chunk: exact integer |x| ≤ 2^24 → shifted into
+                // [0, 2^26) → ·weight mod p → added to the running sums
+#define FSK_REDUCE_CHUNK(CC, V)                                                  \
+    _Pragma("unroll") for (int e = 0; e < LD_COLS; ++e) {                        \
+        const int xi = __float2int_rn(__uint_as_float((V)[e]));                  \
+        const uint32_t a = (uint32_t)(xi + (int)off);                            \
+        const uint32_t q = __umulhi(a, wsh);                                     \
+        const uint32_t r = a * w - q * p; /* [0, 2p) */                          \
+        if constexpr (LAZY) {                                                    \
+            acc[(CC) * LD_COLS + e] += r;                                        \
+        } else {                                                                 \
+            const uint32_t s = acc[(CC) * LD_COLS + e] + r;                      \
+            acc[(CC) * LD_COLS + e] = min(s, s - twop);                          \
+        }                                                                        \
+    }
+                if constexpr (Roles<EW>::SPLIT_REGS) {
+                    // two chunk buffers: chunk cc + 1 loads while chunk cc is reduced
+                    // (tcgen05.wait::ld waits for every load of the thread, so the
+                    // next load is issued after the wait)
+                    uint32_t va[LD_COLS], vb[LD_COLS];
 #pragma unroll
-                for (int cc = 0; cc < EPI_COLS / LD_COLS; ++cc) {
-                    if (cc < lo || cc >= hi) continue;
-                    uint32_t v[LD_COLS];
-                    tmem_ld16(taddr + cc * LD_COLS, v);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int e = 0; e < LD_COLS; ++e) {
-                        // exact integer |x| ≤ 2^24 → shifted into [0, 2^26) → ·weight mod p
-                        const int xi = __float2int_rn(__uint_as_float(v[e]));
-                        const uint32_t a = (uint32_t)(xi + (int)off);
-                        const uint32_t q = __umulhi(a, wsh);
-                        const uint32_t r = a * w - q * p;  // [0, 2p)
-                        if constexpr (LAZY) {
-                            acc[cc * LD_COLS + e] += r;
+                    for (int cc = 0; cc < EPI_COLS / LD_COLS; ++cc) {
+                        if (cc < lo || cc >= hi) continue;
+                        if (cc == lo) {
+                            if (cc & 1) tmem_ld16(taddr + cc * LD_COLS, vb);
+                            else tmem_ld16(taddr + cc * LD_COLS, va);
+                        }
+                        if (cc & 1) tmem_wait_ld_tied(vb);
+                        else tmem_wait_ld_tied(va);
+                        if (cc + 1 < hi) {
+                            if (cc & 1) tmem_ld16(taddr + (cc + 1) * LD_COLS, va);
+                            else tmem_ld16(taddr + (cc + 1) * LD_COLS, vb);
+                        }
+                        if (cc & 1) {
+                            FSK_REDUCE_CHUNK(cc, vb)
                         } else {
-                            const uint32_t s = acc[cc * LD_COLS + e] + r;
-                            acc[cc * LD_COLS + e] = min(s, s - twop);
+                            FSK_REDUCE_CHUNK(cc, va)
                         }
                     }
+                } else {
+#pragma unroll
+                    for (int cc = 0; cc < EPI_COLS / LD_COLS; ++cc) {
+                        if (cc < lo || cc >= hi) continue;
+                        uint32_t v[LD_COLS];
+                        tmem_ld16(taddr + cc * LD_COLS, v);
+                        tmem_wait_ld();
+                        FSK_REDUCE_CHUNK(cc, v)
+                    }
                 }
+#undef FSK_REDUCE_CHUNK
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acce_bar[b]);
@@ -409,6 +453,18 @@ cudaError_t launch_leaf_tc(const TcLaunch &L, int num_sms, cudaStream_t st) {
                         k_leaf_tc<false, true, 8>, k_leaf_tc<true, false, 16>, k_leaf_tc<false, false, 16>,
                         k_leaf_tc<true, true, 16>, k_leaf_tc<false, true, 16>})
             if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        // the 8-warp instances hand registers between warpgroups with
+        // setmaxnreg, whose budget assumes exactly 168 registers per thread
+        // at launch (384 · 168): with fewer, setmaxnreg.inc would wait forever
+        for (auto fn : {k_leaf_tc<true, false, 8>, k_leaf_tc<false, false, 8>, k_leaf_tc<true, true, 8>,
+                        k_leaf_tc<false, true, 8>}) {
+            cudaFuncAttributes fa{};
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+            if (e == cudaSuccess &&
+                fa.numRegs * Roles<8>::NUM_THREADS !=
+                    2 * 128 * Roles<8>::EPI_REGS + 128 * Roles<8>::ISSUE_REGS)
+                e = cudaErrorInvalidConfiguration;
+        }
         return e;
     });
     if (ea != cudaSuccess) return ea;

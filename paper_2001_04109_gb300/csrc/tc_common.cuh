@@ -146,6 +146,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// The same wait with the loaded registers as its operands, so that no use of
+// them can be scheduled before it (a load's registers are written when the
+// wait completes, not when tcgen05.ld issues).
+__device__ __forceinline__ void tmem_wait_ld_tied(uint32_t (&v)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
+                   "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]),
+                   "+r"(v[14]), "+r"(v[15])
+                 :
+                 : "memory");
+}
 
 // 16-column chunks [lo, hi) of an epilogue warp's 32 rows × (nch·16) columns
 // that hold stored entries: rows below `rows`, columns below `cols`, and for
