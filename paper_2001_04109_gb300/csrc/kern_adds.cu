@@ -262,153 +262,6 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const PrepNode *__restric
 }
 
 
-// The 7 operands of one level of Algorithm 1 for one side of a general
-// product, from the side's quadrants x11, x12, x21, x22 at one position
-// (Algorithm 1's pre-additions; side 0 the left operand's s- and a-terms,
-// side 1 the right operand's t-terms as rows of Zᵀ), each stored at once.
-template <int D, int OK>
-__device__ __forceinline__ void put_sw_pieces(const OperandDst (&dst)[7], int side, int64_t r, int64_t c,
-                                              const uint32_t (&x11)[8], const uint32_t (&x12)[8],
-                                              const uint32_t (&x21)[8], const uint32_t (&x22)[8],
-                                              const ModP &m, NormAcc *acc) {
-    const uint32_t p = m.p;
-    uint32_t a[8], b[8];
-    put8<D, OK>(dst[0], r, c, x11, m, acc);
-    put8<D, OK>(dst[1], r, c, x12, m, acc);
-    if (side == 0) {
-        put8<D, OK>(dst[2], r, c, x22, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = subm(x11[e], x21[e], p);  // s1
-        put8<D, OK>(dst[3], r, c, a, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            b[e] = addm(x21[e], x22[e], p);  // s2
-            a[e] = subm(b[e], x11[e], p);    // s3
-        }
-        put8<D, OK>(dst[4], r, c, a, m, acc);
-        put8<D, OK>(dst[6], r, c, b, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = subm(x12[e], a[e], p);  // s4
-        put8<D, OK>(dst[5], r, c, a, m, acc);
-    } else {
-        put8<D, OK>(dst[5], r, c, x22, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = subm(x21[e], x11[e], p);  // t2
-        put8<D, OK>(dst[6], r, c, a, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = subm(x22[e], x21[e], p);  // t1
-        put8<D, OK>(dst[3], r, c, a, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) b[e] = addm(x11[e], a[e], p);  // t3
-        put8<D, OK>(dst[4], r, c, b, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = subm(x12[e], b[e], p);  // t4ᵀ
-        put8<D, OK>(dst[2], r, c, a, m, acc);
-    }
-}
-
-// Pre-additions of one depth fused with one level of Algorithm 1 on both
-// general products (PrepSwNode).  Thread: row r of the h/2 × w/2 pieces and
-// columns c..c+7; it forms each of X22, S1, S2, S4 at the four positions
-// (r | hh + r, c | ww + c) of the h × w operands -- the node's quadrant
-// values are re-read from L1 for each operand rather than all kept in
-// registers -- splits it into its 7 pieces, and writes S3 at the four
-// positions.  Columns [ww, kpad) of the pieces are K padding (zeros).
-// Grid: x = column blocks, y = rows (strided), z = node.
-template <int D, int OK, int YF, bool RED>
-__global__ void __launch_bounds__(PREP_THREADS) k_prep_sw(const PrepSwNode *__restrict__ nodes,
-                                                          int64_t hh, int64_t ww, int64_t kpad, ModP m,
-                                                          YConst y) {
-    allow_dependents();
-    const int64_t c = PREP_COLS * ((int64_t)blockIdx.x * PREP_THREADS + threadIdx.x);
-    if (c >= kpad) return;
-    const PrepSwNode &nd = nodes[blockIdx.z];
-    const int64_t c0 = c - PREP_COLS * (threadIdx.x & 31);  // the warp's first column
-    NormAcc acc;
-    acc.mask = norm_lanes(c0, kpad);
-    const uint32_t p = m.p;
-    const int64_t h = 2 * hh, w = 2 * ww;
-    // ww is a multiple of 4: each 4-column half lies wholly inside or outside
-    const bool in0 = c < ww, in1 = c + 4 < ww;
-    const bool vec_ok = ((reinterpret_cast<uintptr_t>(nd.X.ptr) & 15u) == 0) &&
-                        ((nd.X.ld & 3) == 0) && ((ww & 3) == 0);
-    // node quadrant (a, b) at operand position (i, j), reduced, zero in the K padding
-    auto q = [&](int a, int b, int64_t i, int64_t j, uint32_t (&x)[8]) {
-        if (in0) {
-            ld_view8(nd.X, vec_ok, a * h + i, b * w + j, x);
-            if (!in1)
-#pragma unroll
-                for (int e = 4; e < 8; ++e) x[e] = 0u;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) x[e] = RED ? red(x[e], m) : x[e];
-        } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) x[e] = 0u;
-        }
-    };
-    for (int64_t r = blockIdx.y; r < hh; r += gridDim.y) {
-        const int64_t pi[4] = {r, r, hh + r, hh + r}, pj[4] = {c, ww + c, c, ww + c};
-        uint32_t o[4][8];  // an operand at the four positions: its quadrants x11, x12, x21, x22
-        uint32_t t0[8], t1[8];
-        // X22: P3's left operand
-#pragma unroll
-        for (int s = 0; s < 4; ++s) q(1, 1, pi[s], pj[s], o[s]);
-        put_sw_pieces<D, OK>(nd.dst[0], 0, r, c, o[0], o[1], o[2], o[3], m, &acc);
-        // S1 = (A21 − A11)·Y: P4's left operand
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            q(1, 0, pi[s], pj[s], t0);
-            q(0, 0, pi[s], pj[s], t1);
-#pragma unroll
-            for (int e = 0; e < 8; e += 2)
-                ymul<YF>(y, subm(t0[e], t1[e], p), subm(t0[e + 1], t1[e + 1], p), o[s][e], o[s][e + 1], p);
-        }
-        put_sw_pieces<D, OK>(nd.dst[2], 0, r, c, o[0], o[1], o[2], o[3], m, &acc);
-        // S3 = S1 − A22 (uint32, the next depth's node) and S4 = S3 + A12: P3's right operand
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            q(1, 1, pi[s], pj[s], t0);
-            q(0, 1, pi[s], pj[s], t1);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const uint32_t s3 = subm(o[s][e], t0[e], p);
-                t0[e] = s3;
-                o[s][e] = addm(s3, t1[e], p);
-            }
-            if (nd.s3 != nullptr) {
-#pragma unroll
-                for (int hf = 0; hf < 2; ++hf) {
-                    if (!(hf ? in1 : in0)) continue;
-                    uint32_t *dst = nd.s3 + pi[s] * nd.s3_ld + pj[s] + 4 * hf;
-                    const uint32_t *v = t0 + 4 * hf;
-                    if (((reinterpret_cast<uintptr_t>(dst)) & 15u) == 0)
-                        *reinterpret_cast<uint4 *>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
-                    else
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) dst[e] = v[e];
-                }
-            }
-        }
-        put_sw_pieces<D, OK>(nd.dst[1], 1, r, c, o[0], o[1], o[2], o[3], m, &acc);
-        // S2 = A22 − A21·Y: P4's right operand
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            q(1, 0, pi[s], pj[s], t0);
-            q(1, 1, pi[s], pj[s], t1);
-#pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-                uint32_t u0, u1;
-                ymul<YF>(y, t0[e], t0[e + 1], u0, u1, p);
-                o[s][e] = subm(t1[e], u0, p);
-                o[s][e + 1] = subm(t1[e + 1], u1, p);
-            }
-        }
-        put_sw_pieces<D, OK>(nd.dst[3], 1, r, c, o[0], o[1], o[2], o[3], m, &acc);
-    }
-    norm_flush(acc, OK == ARENA_BF16_KS ? D + D * (D - 1) / 2 : D, c0);
-}
-
-
 // Digit split of whole matrices (the classical path's operands): rows
 // [0, rows) × columns [0, kpad) of each destination, zero beyond the view.
 // Grid: x = column-pair blocks, y = row blocks (strided), z = matrix.
@@ -814,54 +667,7 @@ cudaError_t launch_prep_d(dim3 grid, cudaStream_t st, const PrepNode *nodes, int
                   : launch_prep_t<D, OK, 1, false>(grid, st, nodes, h, w, kpad, mp, y);
 }
 
-template <int D, int OK>
-cudaError_t launch_prep_sw_d(dim3 grid, cudaStream_t st, const PrepSwNode *nodes, int64_t hh, int64_t ww,
-                             int64_t kpad, ModP mp, YConst y, bool reduce) {
-    if (y.form == 0) {
-        if (reduce) k_prep_sw<D, OK, 0, true><<<grid, PREP_THREADS, 0, st>>>(nodes, hh, ww, kpad, mp, y);
-        else k_prep_sw<D, OK, 0, false><<<grid, PREP_THREADS, 0, st>>>(nodes, hh, ww, kpad, mp, y);
-    } else {
-        if (reduce) k_prep_sw<D, OK, 1, true><<<grid, PREP_THREADS, 0, st>>>(nodes, hh, ww, kpad, mp, y);
-        else k_prep_sw<D, OK, 1, false><<<grid, PREP_THREADS, 0, st>>>(nodes, hh, ww, kpad, mp, y);
-    }
-    return cudaGetLastError();
-}
-
 }  // namespace
-
-cudaError_t launch_prep_sw(const PrepSwNode *nodes_dev, int nnodes, int64_t h, int64_t w,
-                           int64_t kpad, ModP mp, YConst y, DigitScheme ds, int arena_kind,
-                           bool reduce_input, cudaStream_t st) {
-    if (h == 0 || kpad == 0 || nnodes == 0) return cudaSuccess;
-    if ((h & 1) || (w & 7)) return cudaErrorInvalidValue;  // pieces h/2 × w/2, w/2 a multiple of 4
-    const int64_t hh = h / 2, ww = w / 2;
-    const int64_t gx = (kpad / PREP_COLS + PREP_THREADS - 1) / PREP_THREADS;
-    const int64_t gy = std::min<int64_t>(hh, 65535);
-    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nnodes);
-    if (arena_kind == ARENA_BF16_KS) {
-        switch (ds.D) {
-            case 2: return launch_prep_sw_d<2, ARENA_BF16_KS>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-            case 3: return launch_prep_sw_d<3, ARENA_BF16_KS>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-        }
-        return cudaErrorInvalidValue;
-    }
-    if (arena_kind == ARENA_I8) {
-        switch (ds.D) {
-            case 1: return launch_prep_sw_d<1, ARENA_I8>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-            case 2: return launch_prep_sw_d<2, ARENA_I8>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-            case 3: return launch_prep_sw_d<3, ARENA_I8>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-        }
-        return cudaErrorInvalidValue;
-    }
-    if (arena_kind == ARENA_U32)
-        return launch_prep_sw_d<1, ARENA_U32>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-    switch (ds.D) {
-        case 1: return launch_prep_sw_d<1, ARENA_BF16>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-        case 2: return launch_prep_sw_d<2, ARENA_BF16>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-        case 3: return launch_prep_sw_d<3, ARENA_BF16>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-    }
-    return cudaErrorInvalidValue;
-}
 
 cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_t w,
                         int64_t kpad, ModP mp, YConst y, DigitScheme ds, int arena_kind,
