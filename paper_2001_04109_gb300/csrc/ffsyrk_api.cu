@@ -341,7 +341,6 @@ Layout make_layout(const Geometry &g, int leaf, int D, bool ks = false) {
 // ---- descriptors of one call ----
 struct Descs {
     std::vector<PrepNode> prep[kMaxLevels];
-    std::vector<PrepSwNode> prepsw[kMaxLevels];  // depths with exactly one level of Algorithm 1
     std::vector<PostNode> post[kMaxLevels];
     // Algorithm 1 jobs of depth d, level l (1 ≤ l ≤ sw[d])
     std::vector<SwPreJob> swpre[kMaxLevels][kMaxLevels + 1];
@@ -362,7 +361,7 @@ struct Descs {
     std::vector<UnitJob> ujobs;
     int64_t digit_max_rows = 0, digit_max_kpad = 0;
     // blob offsets (bytes) inside the descriptor region
-    int64_t prep_off[kMaxLevels] = {}, post_off[kMaxLevels] = {}, prepsw_off[kMaxLevels] = {};
+    int64_t prep_off[kMaxLevels] = {}, post_off[kMaxLevels] = {};
     int64_t prods_off = 0, tiles_off = 0, tmap_off = 0, aptr_off = 0, akpad_off = 0, digit_off = 0;
     int64_t ctr_off = 0, segs_off = 0, pieces_off = 0, entries_off = 0;
     int64_t links_off = 0, ujobs_off = 0;
@@ -400,7 +399,7 @@ int64_t desc_capacity(const Geometry &g, int leaf) {
     // generous bound for the descriptor blob of any shape ≤ g
     int64_t b = 0;
     for (int d = 0; d < g.L; ++d) {
-        b += pow3(d) * (sizeof(PrepNode) + sizeof(PrepSwNode) + sizeof(PostNode)) + 3 * 256;
+        b += pow3(d) * (sizeof(PrepNode) + sizeof(PostNode)) + 2 * 256;
         for (int l = 1; l <= g.sw[d]; ++l)
             b += pow3(d) * pow7(l - 1) * (4 * sizeof(SwPreJob) + 2 * sizeof(SwPostJob)) + 2 * 256;
     }
@@ -1167,15 +1166,8 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
         // node views, depth by depth
         std::vector<MatView> views{MatView{A, lda, g.n, g.k}};
         const int64_t sb = syrk_base(g);
-        bool fused_sw_ok[kMaxLevels] = {};
         for (int d = 0; d < g.L; ++d) {
             const int64_t h = g.h[d + 1], w = g.w[d + 1];
-            // the fused pre-addition kernel stages whole node rows by 16-byte
-            // copies: every node of the depth must be a whole, aligned view
-            fused_sw_ok[d] = (w % 4) == 0;
-            for (const MatView &v : views)
-                fused_sw_ok[d] = fused_sw_ok[d] && v.vr >= 2 * h && v.vc >= 2 * w && (v.ld % 4) == 0 &&
-                                 (reinterpret_cast<uintptr_t>(v.ptr) % 16) == 0;
             const int sw = g.sw[d];            // levels of Algorithm 1 for this depth
             const int ja = gen_arena(g, d);    // arena of its general-product operands
             const int64_t gb = gen_base(g, d);
@@ -1195,12 +1187,8 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
                 nd.X = X;
                 // X22, S4 (P3 = X22·S4ᵀ) and S1, S2 (P4 = S1·S2ᵀ): digit planes, or
                 // uint32 rows that Algorithm 1's pre-additions split further
-                // (one level over a whole, 16-byte aligned node: split in the same
-                // kernel, PrepSwNode)
-                const bool fused = sw == 1 && fused_sw_ok[d];
                 for (int q = 0; q < 4; ++q)
                     nd.gemm[q] = sw == 0 ? operand(ja, gb + 4 * t + q)
-                               : fused   ? OperandDst{}
                                          : OperandDst{swin(0, 4 * t + q), 0, rup(w, 64), h};
                 if (d == g.L - 1) {
                     for (int q = 0; q < 3; ++q)
@@ -1218,23 +1206,12 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
                     next.push_back(x12);
                     next.push_back(s3);
                 }
-                if (fused) {
-                    // operand op = 2q + side of product q: X22, S4 (P3), S1, S2 (P4)
-                    PrepSwNode sn{};
-                    sn.X = X;
-                    for (int op = 0; op < 4; ++op)
-                        for (int mm = 0; mm < 7; ++mm) sn.dst[op][mm] = operand(ja, gb + (4 * t + op) * 7 + mm);
-                    sn.s3 = nd.s3;
-                    sn.s3_ld = nd.s3_ld;
-                    D.prepsw[d].push_back(sn);
-                } else {
-                    D.prep[d].push_back(nd);
-                }
+                D.prep[d].push_back(nd);
                 // the two general products of this node (gp = 2t + q), each
                 // directly, or as the 7^sw products of sw levels of Algorithm 1
                 for (int q = 0; q < 2; ++q) {
                     const int64_t gp = 2 * t + q, n7 = pow7(sw);
-                    for (int l = fused ? 2 : 1; l <= sw; ++l) {
+                    for (int l = 1; l <= sw; ++l) {
                         // pre-additions: level l − 1 operands into 7 pieces each
                         const int64_t npar = pow7(l - 1);
                         for (int side = 0; side < 2; ++side)
@@ -1348,9 +1325,6 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
                     for (OperandDst &o : nd.gemm) o.norm = nullptr;
                     for (OperandDst &o : nd.leaf) o.norm = nullptr;
                 }
-                for (PrepSwNode &sn : D.prepsw[d])
-                    for (auto &side : sn.dst)
-                        for (OperandDst &o : side) o.norm = nullptr;
                 for (int l = 0; l <= kMaxLevels; ++l)
                     for (SwPreJob &jb : D.swpre[d][l])
                         for (OperandDst &o : jb.dst) o.norm = nullptr;
@@ -1369,7 +1343,6 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     };
     for (int d = 0; d < g.L; ++d) {
         D.prep_off[d] = slot((int64_t)D.prep[d].size() * sizeof(PrepNode), 256);
-        D.prepsw_off[d] = slot((int64_t)D.prepsw[d].size() * sizeof(PrepSwNode), 256);
         D.post_off[d] = slot((int64_t)D.post[d].size() * sizeof(PostNode), 256);
         for (int l = 1; l <= g.sw[d]; ++l) {
             D.swpre_off[d][l] = slot((int64_t)D.swpre[d][l].size() * sizeof(SwPreJob), 256);
@@ -1395,7 +1368,6 @@ ffsyrk_status_t build_descs(ffsyrk_plan_st *pl, int uplo, const uint32_t *A, int
     memset(hb, 0, (size_t)D.bytes);
     for (int d = 0; d < g.L; ++d) {
         memcpy(hb + D.prep_off[d], D.prep[d].data(), D.prep[d].size() * sizeof(PrepNode));
-        memcpy(hb + D.prepsw_off[d], D.prepsw[d].data(), D.prepsw[d].size() * sizeof(PrepSwNode));
         memcpy(hb + D.post_off[d], D.post[d].data(), D.post[d].size() * sizeof(PostNode));
         for (int l = 1; l <= g.sw[d]; ++l) {
             memcpy(hb + D.swpre_off[d][l], D.swpre[d][l].data(),
@@ -1470,15 +1442,6 @@ ffsyrk_status_t issue_launches(ffsyrk_plan_st *pl, cudaStream_t st, bool timed) 
         if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
     } else {
         for (int d = 0; d < g.L; ++d) {
-            if (!D.prepsw[d].empty()) {
-                // one level of Algorithm 1: its pieces straight from the node
-                e = launch_prep_sw(reinterpret_cast<const PrepSwNode *>(dd + D.prepsw_off[d]),
-                                   (int)D.prepsw[d].size(), g.h[d + 1], g.w[d + 1],
-                                   opkpad(g.w[d + 2], false), pl->mp, pl->yc, lds, kind,
-                                   /*reduce_input=*/true, st);
-                if (e != cudaSuccess) return FFSYRK_ERR_CUDA;
-                continue;
-            }
             // with Algorithm 1 at this depth, the general products' operands are
             // written as uint32 rows (d < L − 1: no leaf operands at this depth)
             e = launch_prep(reinterpret_cast<const PrepNode *>(dd + D.prep_off[d]),
@@ -1637,7 +1600,7 @@ void record_work(ffsyrk_plan_st *pl) {
     const Geometry &g = lay.g;
     const Descs &D = pl->desc;
     pl->last_launches = g.L == 0 ? 2 : 2 * g.L + 1;
-    for (int d = 0; d < g.L; ++d) pl->last_launches += 2 * g.sw[d] - (D.prepsw[d].empty() ? 0 : 1);
+    for (int d = 0; d < g.L; ++d) pl->last_launches += 2 * g.sw[d];
     if (!D.ujobs.empty()) pl->last_launches += 1;  // the unit schedule
     pl->last_leaf_launches = 1;
     int split = 0, whole = 0;

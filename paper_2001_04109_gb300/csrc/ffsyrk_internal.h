@@ -360,23 +360,6 @@ struct SwPreJob {
     int side;
     OperandDst dst[7];
 };
-// The pre-additions of one node of Algorithm 2 fused with one level of
-// Algorithm 1 on both of its general products: from the node's matrix X
-// (2h × 2w, read once) the kernel forms X22, S4, S1, S2 (h × w) and splits
-// each at once into the 7 operands of Algorithm 1 (each h/2 × w/2):
-// dst[0] the left operands of P3 = X22·S4ᵀ, dst[1] its right operands,
-// dst[2] the left operands of P4 = S1·S2ᵀ, dst[3] its right operands (the
-// order of SwPreJob::dst).  S3 (h × w uint32) goes to s3 for the next depth.
-// This removes the uint32 round trip of X22, S4, S1, S2 through HBM.
-struct PrepSwNode {
-    MatView X;
-    OperandDst dst[4][7];
-    uint32_t *s3;
-    int64_t s3_ld;
-};
-cudaError_t launch_prep_sw(const PrepSwNode *nodes_dev, int nnodes, int64_t h, int64_t w,
-                           int64_t kpad, ModP mp, YConst y, DigitScheme ds, int arena_kind,
-                           bool reduce_input, cudaStream_t st);
 // The post-additions of one level of Algorithm 1: the 7 products p1..p7
 // (hh × hh, row stride hh) into C = [[c3, c7], [c4, c5]] (2hh × 2hh, row
 // stride 2hh).

@@ -650,186 +650,6 @@ __global__ void k_zero_tri(uint32_t *C, int64_t n, int64_t ldc, int upper, int64
         }
 }
 
-// The 7 operands of one level of Algorithm 1 for one side of a general
-// product, from the side's quadrants x11, x12, x21, x22 at one position
-// (Algorithm 1's pre-additions; side 0 the left operand's a- and s-terms,
-// side 1 the right operand's t-terms as rows of Zᵀ), each stored at once.
-template <int D, int OK>
-__device__ __forceinline__ void put_sw_pieces(const OperandDst (&dst)[7], int side, int64_t r, int64_t c,
-                                              const uint32_t (&x11)[8], const uint32_t (&x12)[8],
-                                              const uint32_t (&x21)[8], const uint32_t (&x22)[8],
-                                              const ModP &m, NormAcc *acc) {
-    const uint32_t p = m.p;
-    uint32_t a[8], b[8];
-    put8<D, OK>(dst[0], r, c, x11, m, acc);
-    put8<D, OK>(dst[1], r, c, x12, m, acc);
-    if (side == 0) {
-        put8<D, OK>(dst[2], r, c, x22, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = subm(x11[e], x21[e], p);  // s1
-        put8<D, OK>(dst[3], r, c, a, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            b[e] = addm(x21[e], x22[e], p);  // s2
-            a[e] = subm(b[e], x11[e], p);    // s3
-        }
-        put8<D, OK>(dst[4], r, c, a, m, acc);
-        put8<D, OK>(dst[6], r, c, b, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = subm(x12[e], a[e], p);  // s4
-        put8<D, OK>(dst[5], r, c, a, m, acc);
-    } else {
-        put8<D, OK>(dst[5], r, c, x22, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = subm(x21[e], x11[e], p);  // t2
-        put8<D, OK>(dst[6], r, c, a, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = subm(x22[e], x21[e], p);  // t1
-        put8<D, OK>(dst[3], r, c, a, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) b[e] = addm(x11[e], a[e], p);  // t3
-        put8<D, OK>(dst[4], r, c, b, m, acc);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] = subm(x12[e], b[e], p);  // t4ᵀ
-        put8<D, OK>(dst[2], r, c, a, m, acc);
-    }
-}
-
-// Pre-additions of one depth fused with one level of Algorithm 1 on both
-// general products (PrepSwNode), for nodes that are whole, 16-byte aligned
-// views.  A block takes one row r of the hh × ww pieces and SWF_COLS of
-// their columns.  The 16 node-row segments those need -- node rows
-// a·h + {r, hh + r}, columns b·w + {0, ww} + [cb, cb + SWF_COLS) for the
-// node quadrants (a, b) -- are staged in shared memory by cp.async (64 KB),
-// columns ≥ ww (the pieces' K padding) as zeros.  Each thread then forms,
-// for its 8 columns, X22, S1, S2 and S4 at the four positions of the h × w
-// operands, splits each into its 7 pieces, and writes S3 (the next depth's
-// node) at the four positions.  Grid: x = column blocks, y = rows
-// (strided), z = node; dynamic shared memory 16·SWF_COLS words.
-constexpr int SWF_COLS = PREP_THREADS * PREP_COLS;  // 1024
-template <int D, int OK, int YF, bool RED>
-__global__ void __launch_bounds__(PREP_THREADS) k_prep_sw(const PrepSwNode *__restrict__ nodes,
-                                                          int64_t hh, int64_t ww, int64_t kpad, ModP m,
-                                                          YConst y) {
-    allow_dependents();
-    extern __shared__ __align__(16) uint32_t sx[];  // [16 segments][SWF_COLS]
-    const PrepSwNode &nd = nodes[blockIdx.z];
-    const uint32_t p = m.p;
-    const int64_t h = 2 * hh, w = 2 * ww;
-    const int64_t cb = (int64_t)blockIdx.x * SWF_COLS;
-    const int tid = threadIdx.x;
-    const int64_t c = cb + PREP_COLS * tid;  // this thread's 8 piece columns
-    const bool active = c < kpad;
-    const int64_t c0 = c - PREP_COLS * (tid & 31);  // the warp's first column
-    NormAcc acc;
-    acc.mask = norm_lanes(c0, kpad);
-    // ww is a multiple of 4: each 4-column half lies wholly inside or outside
-    const bool in0 = c < ww, in1 = c + 4 < ww;
-    // segment of node quadrant (a, b) at position (ri, ci): rows a·h + ri·hh + r,
-    // columns b·w + ci·ww + cb + [0, SWF_COLS)
-    auto seg = [](int a, int b, int ri, int ci) { return ((a * 2 + ri) * 2 + b) * 2 + ci; };
-    for (int64_t r = blockIdx.y; r < hh; r += gridDim.y) {
-        for (int q = tid; q < 16 * SWF_COLS / 4; q += PREP_THREADS) {
-            const int sg = q / (SWF_COLS / 4), j = (q % (SWF_COLS / 4)) * 4;
-            const int a = sg >> 3, ri = (sg >> 2) & 1, b = (sg >> 1) & 1, ci = sg & 1;
-            const bool ok = cb + j < ww;
-            const uint32_t *g = ok ? nd.X.ptr + (a * h + ri * hh + r) * nd.X.ld + b * w + ci * ww + cb + j
-                                   : nd.X.ptr;
-            cp_async16((uint32_t)__cvta_generic_to_shared(&sx[sg * SWF_COLS + j]), g, ok);
-        }
-        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-        __syncthreads();
-        if (active) {
-            // node quadrant (a, b) at position (ri, ci), reduced
-            auto q = [&](int a, int b, int ri, int ci, uint32_t (&x)[8]) {
-                const uint4 *v = reinterpret_cast<const uint4 *>(&sx[seg(a, b, ri, ci) * SWF_COLS + (c - cb)]);
-                const uint4 u0 = v[0], u1 = v[1];
-                x[0] = u0.x; x[1] = u0.y; x[2] = u0.z; x[3] = u0.w;
-                x[4] = u1.x; x[5] = u1.y; x[6] = u1.z; x[7] = u1.w;
-#pragma unroll
-                for (int e = 0; e < 8; ++e) x[e] = RED ? red(x[e], m) : x[e];
-            };
-            uint32_t o[4][8];  // an operand at the four positions: its quadrants x11, x12, x21, x22
-            uint32_t t0[8], t1[8];
-            // X22: P3's left operand
-#pragma unroll
-            for (int s = 0; s < 4; ++s) q(1, 1, s >> 1, s & 1, o[s]);
-            put_sw_pieces<D, OK>(nd.dst[0], 0, r, c, o[0], o[1], o[2], o[3], m, &acc);
-            // S1 = (A21 − A11)·Y: P4's left operand
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                q(1, 0, s >> 1, s & 1, t0);
-                q(0, 0, s >> 1, s & 1, t1);
-#pragma unroll
-                for (int e = 0; e < 8; e += 2)
-                    ymul<YF>(y, subm(t0[e], t1[e], p), subm(t0[e + 1], t1[e + 1], p), o[s][e], o[s][e + 1], p);
-            }
-            put_sw_pieces<D, OK>(nd.dst[2], 0, r, c, o[0], o[1], o[2], o[3], m, &acc);
-            // S3 = S1 − A22 (uint32, the next depth's node) and S4 = S3 + A12: P3's right operand
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                q(1, 1, s >> 1, s & 1, t0);
-                q(0, 1, s >> 1, s & 1, t1);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const uint32_t s3 = subm(o[s][e], t0[e], p);
-                    t0[e] = s3;
-                    o[s][e] = addm(s3, t1[e], p);
-                }
-                if (nd.s3 != nullptr) {
-                    const int64_t pr = (s >> 1) * hh + r, pc = (s & 1) * ww + c;
-#pragma unroll
-                    for (int hf = 0; hf < 2; ++hf) {
-                        if (!(hf ? in1 : in0)) continue;
-                        uint32_t *dst = nd.s3 + pr * nd.s3_ld + pc + 4 * hf;
-                        const uint32_t *v = t0 + 4 * hf;
-                        if (((reinterpret_cast<uintptr_t>(dst)) & 15u) == 0)
-                            *reinterpret_cast<uint4 *>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
-                        else
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) dst[e] = v[e];
-                    }
-                }
-            }
-            put_sw_pieces<D, OK>(nd.dst[1], 1, r, c, o[0], o[1], o[2], o[3], m, &acc);
-            // S2 = A22 − A21·Y: P4's right operand
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                q(1, 0, s >> 1, s & 1, t0);
-                q(1, 1, s >> 1, s & 1, t1);
-#pragma unroll
-                for (int e = 0; e < 8; e += 2) {
-                    uint32_t u0, u1;
-                    ymul<YF>(y, t0[e], t0[e + 1], u0, u1, p);
-                    o[s][e] = subm(t1[e], u0, p);
-                    o[s][e + 1] = subm(t1[e + 1], u1, p);
-                }
-            }
-            put_sw_pieces<D, OK>(nd.dst[3], 1, r, c, o[0], o[1], o[2], o[3], m, &acc);
-        }
-        __syncthreads();  // the next row's copies overwrite the segments
-    }
-    if (active) norm_flush(acc, OK == ARENA_BF16_KS ? D + D * (D - 1) / 2 : D, c0);
-}
-
-template <int D, int OK>
-cudaError_t launch_prep_sw_d(dim3 grid, cudaStream_t st, const PrepSwNode *nodes, int64_t hh, int64_t ww,
-                             int64_t kpad, ModP mp, YConst y, bool reduce) {
-    const size_t smem = 16 * SWF_COLS * sizeof(uint32_t);
-    auto k00 = k_prep_sw<D, OK, 0, false>, k01 = k_prep_sw<D, OK, 0, true>;
-    auto k10 = k_prep_sw<D, OK, 1, false>, k11 = k_prep_sw<D, OK, 1, true>;
-    auto kern = y.form == 0 ? (reduce ? k01 : k00) : (reduce ? k11 : k10);
-    // 64 KB of dynamic shared memory: the opt-in, once per device and instance
-    static DeviceOnce attr_once[4];
-    const int which = (y.form == 0 ? 0 : 2) + (reduce ? 1 : 0);
-    cudaError_t e = once_per_device(attr_once[which], nullptr, [kern, smem](int *) {
-        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    });
-    if (e != cudaSuccess) return e;
-    kern<<<grid, PREP_THREADS, smem, st>>>(nodes, hh, ww, kpad, mp, y);
-    return cudaGetLastError();
-}
-
 template <int D, int OK, int YF, bool RED>
 cudaError_t launch_prep_t(dim3 grid, cudaStream_t st, const PrepNode *nodes, int64_t h, int64_t w,
                           int64_t kpad, ModP mp, YConst y) {
@@ -848,40 +668,6 @@ cudaError_t launch_prep_d(dim3 grid, cudaStream_t st, const PrepNode *nodes, int
 }
 
 }  // namespace
-
-cudaError_t launch_prep_sw(const PrepSwNode *nodes_dev, int nnodes, int64_t h, int64_t w,
-                           int64_t kpad, ModP mp, YConst y, DigitScheme ds, int arena_kind,
-                           bool reduce_input, cudaStream_t st) {
-    if (h == 0 || kpad == 0 || nnodes == 0) return cudaSuccess;
-    if ((h & 1) || (w & 7)) return cudaErrorInvalidValue;  // pieces h/2 × w/2, w/2 a multiple of 4
-    const int64_t hh = h / 2, ww = w / 2;
-    const int64_t gx = (kpad + SWF_COLS - 1) / SWF_COLS;
-    const int64_t gy = std::min<int64_t>(hh, 65535);
-    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nnodes);
-    if (arena_kind == ARENA_BF16_KS) {
-        switch (ds.D) {
-            case 2: return launch_prep_sw_d<2, ARENA_BF16_KS>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-            case 3: return launch_prep_sw_d<3, ARENA_BF16_KS>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-        }
-        return cudaErrorInvalidValue;
-    }
-    if (arena_kind == ARENA_I8) {
-        switch (ds.D) {
-            case 1: return launch_prep_sw_d<1, ARENA_I8>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-            case 2: return launch_prep_sw_d<2, ARENA_I8>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-            case 3: return launch_prep_sw_d<3, ARENA_I8>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-        }
-        return cudaErrorInvalidValue;
-    }
-    if (arena_kind == ARENA_U32)
-        return launch_prep_sw_d<1, ARENA_U32>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-    switch (ds.D) {
-        case 1: return launch_prep_sw_d<1, ARENA_BF16>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-        case 2: return launch_prep_sw_d<2, ARENA_BF16>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-        case 3: return launch_prep_sw_d<3, ARENA_BF16>(grid, st, nodes_dev, hh, ww, kpad, mp, y, reduce_input);
-    }
-    return cudaErrorInvalidValue;
-}
 
 cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_t w,
                         int64_t kpad, ModP mp, YConst y, DigitScheme ds, int arena_kind,
