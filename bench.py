@@ -69,8 +69,18 @@ def kernel_source_hash(kernel_file: str):
     return h.hexdigest()[:16]
 
 
-def kernel_traffic(kernel_file: str, workload: str):
-    """dram bytes per launch recorded under profiles/ for this kernel source, else None."""
+def plan_signature(info: dict, unit_bounds: str) -> str:
+    """The plan choices a leaf capture depends on, as a profile's `plan:` line states them."""
+    lv = info["levels"]
+    wg = ",".join(str(x) for x in info["winograd"][:lv]) or "-"
+    return (f"levels={lv} winograd={wg} tile_ctas={info['tile_ctas']} "
+            f"epilogue_warps={info['epilogue_warps']} products={info['products']} "
+            f"unit_bounds={unit_bounds}")
+
+
+def kernel_traffic(kernel_file: str, workload: str, plan: str | None = None):
+    """dram bytes per launch recorded under profiles/ for this kernel source (and, where the
+    profile states one, this plan), else None."""
     h = kernel_source_hash(kernel_file)
     if h is None:
         return None
@@ -85,8 +95,9 @@ def kernel_traffic(kernel_file: str, workload: str):
         m_wl = re.search(r"workload:\s*(\S+)", text)
         m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
         m_k = re.search(r"kernel_file:\s*(\S+)", text)
+        m_plan = re.search(r"^plan:\s*(.+?)\s*$", text, re.M)
         if m_src and m_tr and m_k and m_wl and m_src.group(1) == h and m_k.group(1) == kernel_file \
-                and m_wl.group(1) == workload:
+                and m_wl.group(1) == workload and (m_plan is None or m_plan.group(1) == plan):
             return float(m_tr.group(1))
     return None
 
@@ -426,7 +437,9 @@ def run_ours(args):
     kernel_file = "kern_leaf_tc2.cu" if pair else "kern_leaf_tc.cu"
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": kernel_traffic(kernel_file, args.workload),
+                "traffic": kernel_traffic(kernel_file, args.workload,
+                                          plan_signature(info, args.unit_bounds)),
+                "plan": plan_signature(info, args.unit_bounds),
                 "kernel": ("k_leaf_tc2 (tcgen05 kind::f16 cta_group::2, 256x256 tiles on SM pairs, "
                            "bf16 digits, fp32 TMEM)" if pair else
                            "k_leaf_tc (tcgen05 kind::f16, 128x256 tiles, bf16 digits, fp32 TMEM)"),
