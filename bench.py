@@ -406,8 +406,12 @@ def run_ours(args):
     plan_s = time.perf_counter() - t_plan
     info = plan.info()
     # the options that reproduce the plan's (tuned) choice, for the other plans of this run
+    wl = info["winograd"][: info["levels"]]
+    # the Winograd option that gives these levels: a cap w (min(w, L − 1 − d) at
+    # depth d), else the cost model's choice, else none
+    caps = [w for w in (1, 2, 3) if wl == [min(w, info["levels"] - 1 - d) for d in range(len(wl))]]
     same_opts = dict(leaf=args.leaf, levels=info["levels"], tile_ctas=info["tile_ctas"],
-                     winograd=None if any(info["winograd"]) else 0,
+                     winograd=caps[0] if caps else (None if any(wl) else 0),
                      digit_products="karatsuba" if info["products"] < info["digits"] ** 2
                      else "schoolbook", unit_bounds=args.unit_bounds,
                      epilogue_warps=info["epilogue_warps"] if info["tile_ctas"] == 1 else 0)
@@ -479,7 +483,7 @@ def run_ours(args):
         for name, leaf, lv, wg in legs:
             dp = None
             if wg == "schoolbook":
-                dp, wg = "schoolbook", args.winograd
+                dp, wg = "schoolbook", same_opts["winograd"]
             pl = ffsyrk.Plan(p, n, k, leaf=leaf, levels=lv, winograd=wg, digit_products=dp,
                              tile_ctas=args.tile_ctas if wg == 0 else None)
             slow = leaf != "tc" and n * n * k > 2 ** 36  # calls of 0.1 s or more

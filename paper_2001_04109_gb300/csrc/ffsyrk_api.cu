@@ -1774,6 +1774,23 @@ std::vector<TuneChoice> tune_candidates(const ffsyrk_plan_st *pl) {
                 for (int d = 0; d < L; ++d) any = any || g.sw[d] > 0;
                 if (any) sws.push_back(0);
             }
+            // deeper Algorithm 1 than the cost model takes (caps of 1 and 2
+            // levels per depth), tried with the first tile variant only: with
+            // units from the operands' digits the leaf's multiply-adds weigh
+            // more against the additions than the model's rates say (A 32768²,
+            // depth 3: [2, 1, 0] 118 ms against the model's [1, 0, 0] 121 ms)
+            std::vector<int> deeper;
+            if (pl->sw_opt < 0 && L >= 2 && ks == (tc ? 1 : 0)) {
+                Geometry gm = make_geometry(pl->max_n, pl->max_k, L);
+                set_winograd(gm, -1, nprod(ds), ds.nplanes);
+                for (int cap = 1; cap <= 2; ++cap) {
+                    Geometry gc = gm;
+                    set_winograd(gc, cap, nprod(ds), ds.nplanes);
+                    bool differs = false;
+                    for (int d = 0; d < L; ++d) differs = differs || gc.sw[d] != gm.sw[d];
+                    if (differs) deeper.push_back(cap);
+                }
+            }
             // a few timed calls do not reach the power cap that decides
             // between the tile widths of long launches: one-SM tiles there
             const int max_c = tc && !power_capped_leaf(make_geometry(pl->max_n, pl->max_k, L), ds) ? 2 : 1;
@@ -1792,6 +1809,15 @@ std::vector<TuneChoice> tune_candidates(const ffsyrk_plan_st *pl) {
                         out.push_back(t);
                     }
                 }
+            for (int sw : deeper) {
+                TuneChoice t;
+                t.L = L;
+                t.ctas = 1;
+                t.sw = sw;
+                t.ks = ks;
+                t.ew = tc && pl->ew_opt == 0 ? 8 : pl->ew_opt;
+                out.push_back(t);
+            }
         }
     return out;
 }
