@@ -226,10 +226,14 @@ inline int64_t pow7(int d) {
 // traffic (P digit planes per operand): both operands written as uint32
 // and read back by the pre-additions, 7/4 as many digit planes, 7/4 as many
 // product entries written by the leaf, read back and combined by the
-// post-additions.  Rates as in level_pays.
+// post-additions.  Rates measured on GB300 with units from the operands'
+// digits, at the power cap of the long launches where these levels matter:
+// ≈ 6.6e14 digit multiply-adds/s saved per leaf multiply-add removed (A 32768²,
+// depth 3: Winograd [2, 1, 0] against [1, 0, 0] took 12.4 ms off the leaf)
+// and ≈ 6 TB/s in the addition kernels (11.2 ms more for the same change).
 bool sw_level_pays(int64_t h, int64_t w, int Q, int P) {
-    const double saved = (double)h * h * w * Q / 8.0 / 8.5e14;
-    const double extra = ((16.0 + 3.0 * P) * h * w + 14.0 * (double)h * h) / 4.0e12;
+    const double saved = (double)h * h * w * Q / 8.0 / 6.6e14;
+    const double extra = ((16.0 + 3.0 * P) * h * w + 14.0 * (double)h * h) / 6.0e12;
     return saved > extra && h >= 2048;
 }
 
