@@ -70,12 +70,12 @@ def kernel_source_hash(kernel_file: str):
 
 
 def plan_signature(info: dict, unit_bounds: str) -> str:
-    """The plan choices a leaf capture depends on, as a profile's `plan:` line states them."""
+    """The plan choices a leaf's DRAM traffic depends on (not the epilogue warp count), as a
+    profile's `plan:` line states them."""
     lv = info["levels"]
     wg = ",".join(str(x) for x in info["winograd"][:lv]) or "-"
     return (f"levels={lv} winograd={wg} tile_ctas={info['tile_ctas']} "
-            f"epilogue_warps={info['epilogue_warps']} products={info['products']} "
-            f"unit_bounds={unit_bounds}")
+            f"products={info['products']} unit_bounds={unit_bounds}")
 
 
 def kernel_traffic(kernel_file: str, workload: str, plan: str | None = None):
