@@ -39,7 +39,7 @@ def _stale(extra: list[str]) -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + [
+    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + [
         os.path.join(ROOT, "include", "ffsyrk.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps) or bool(extra)
 

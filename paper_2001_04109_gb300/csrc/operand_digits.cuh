@@ -109,42 +109,51 @@ __device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, 
         for (int t = 0; t < D; ++t)
 #pragma unroll
             for (int e = 0; e < 8; ++e) dg[t][e] = (t == D - 1) ? sv[e] : low_digit(sv[e], m);
+        // Every entry of a plane is an exact small integer in FP32 (|x| ≤ 256), so
+        // the planes are formed, summed (Karatsuba planes) and squared (norms)
+        // two entries at a time in packed FP32, all exactly: a sum of squares
+        // stays below 2^24.  The bf16 encoding is the high half of the FP32 bits.
         uint32_t *base = static_cast<uint32_t *>(d.arena);
-        auto store_plane = [&](int t, const int (&x)[8]) {
-            uint32_t w[4];
-#pragma unroll
-            for (int e = 0; e < 8; e += 2)
-                w[e / 2] = __byte_perm(small_int_f32_bits(x[e]), small_int_f32_bits(x[e + 1]), 0x7632);
-            *reinterpret_cast<uint4 *>(base + (((d.row0 + t * d.rpad + r) * d.kpad + c) >> 1)) =
-                make_uint4(w[0], w[1], w[2], w[3]);
-        };
         const bool norms = acc != nullptr && d.norm != nullptr;
         const int lane = threadIdx.x & 31;
+        // the float bits of 2^23 + q, summed over the acc->mask lanes, carry
+        // popc(mask)·0x4B000000 beside Σq (mod 2^32; Σq ≤ 2^24)
+        const uint32_t bias = norms ? (uint32_t)__popc(acc->mask) * 0x4B000000u : 0u;
         uint32_t mine = 0;  // this lane's plane's row sum (lane t: plane t)
-        auto take = [&](int t, const int (&x)[8]) {
-            if (!norms) return;
-            int q = 0;
+        auto store_plane = [&](int t, const float2 (&x)[4]) {
+            uint32_t w[4];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) q += x[e] * x[e];
-            const uint32_t tot = __reduce_add_sync(acc->mask, (uint32_t)q);
+            for (int k = 0; k < 4; ++k) w[k] = __byte_perm(__float_as_uint(x[k].x), __float_as_uint(x[k].y), 0x7632);
+            *reinterpret_cast<uint4 *>(base + (((d.row0 + t * d.rpad + r) * d.kpad + c) >> 1)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+            if (!norms) return;
+            float2 q = make_float2(8388608.0f, 0.0f);  // 2^23: the sum's float bits are 0x4B000000 + q
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q = __ffma2_rn(x[k], x[k], q);
+            const uint32_t tot = __reduce_add_sync(acc->mask, __float_as_uint(__fadd_rn(q.x, q.y))) - bias;
             mine = lane == t ? tot : mine;
         };
+        // 1.5·2^23 + d is exact in FP32 for |d| < 2^22; subtracting 1.5·2^23 leaves d
+        float2 fd[D][4];
 #pragma unroll
-        for (int t = 0; t < D; ++t) {
-            store_plane(t, dg[t]);
-            take(t, dg[t]);
-        }
+        for (int t = 0; t < D; ++t)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                fd[t][k] = __fadd2_rn(make_float2(__int_as_float(0x4B400000 + dg[t][2 * k]),
+                                                  __int_as_float(0x4B400000 + dg[t][2 * k + 1])),
+                                      make_float2(-12582912.0f, -12582912.0f));
+#pragma unroll
+        for (int t = 0; t < D; ++t) store_plane(t, fd[t]);
         if constexpr (OK == ARENA_BF16_KS) {
             int t = D;
 #pragma unroll
             for (int i = 0; i < D; ++i)
 #pragma unroll
                 for (int j = i + 1; j < D; ++j, ++t) {
-                    int sm[8];
+                    float2 sm[4];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) sm[e] = dg[i][e] + dg[j][e];
+                    for (int k = 0; k < 4; ++k) sm[k] = __fadd2_rn(fd[i][k], fd[j][k]);
                     store_plane(t, sm);
-                    take(t, sm);
                 }
         }
         if (norms) {
