@@ -67,6 +67,16 @@ __device__ __forceinline__ void ymul(const YConst &y, uint32_t t0, uint32_t t1, 
 __device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
 
 constexpr int PREP_THREADS = 128;  // threads per block
+// Row-block grids of the digit-writing kernels: about this many blocks per SM
+// in all, each looping over its share of the rows.  Every block ends with one
+// atomicMax per warp and plane into the norm table, and the blocks of one
+// column range all hit the same entries, so the number of blocks per column
+// range is kept small instead of one per row block.
+constexpr int64_t ROW_GRID_BLOCKS_PER_SM = 24;
+inline int64_t row_grid(int64_t row_blocks, int64_t gx, int64_t gz) {
+    const int64_t cap = std::max<int64_t>(1, 152 * ROW_GRID_BLOCKS_PER_SM / std::max<int64_t>(1, gx * gz));
+    return std::min<int64_t>(std::min<int64_t>(row_blocks, cap), 65535);
+}
 constexpr int PREP_COLS = 8;       // columns per thread
 // rows per thread (independent loads in flight); one with Karatsuba sum
 // planes, whose longer digit split otherwise needs ~160 registers and leaves
@@ -675,7 +685,7 @@ cudaError_t launch_prep(const PrepNode *nodes_dev, int nnodes, int64_t h, int64_
     if (h == 0 || kpad == 0 || nnodes == 0) return cudaSuccess;
     const int64_t gx = (kpad / PREP_COLS + PREP_THREADS - 1) / PREP_THREADS;
     const int rows = arena_kind == ARENA_BF16_KS ? prep_rows<ARENA_BF16_KS>() : prep_rows<ARENA_BF16>();
-    const int64_t gy = std::min<int64_t>((h + rows - 1) / rows, 65535);
+    const int64_t gy = row_grid((h + rows - 1) / rows, gx, nnodes);
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nnodes);
     if (arena_kind == ARENA_U32)
         return launch_prep_d<1, ARENA_U32>(grid, st, nodes_dev, h, w, kpad, mp, y, reduce_input);
@@ -707,7 +717,7 @@ cudaError_t launch_digitize(const DigitizeJob *jobs_dev, int njobs, int64_t max_
                             cudaStream_t st) {
     if (njobs == 0 || max_rows == 0 || max_kpad == 0) return cudaSuccess;
     const int64_t gx = (max_kpad / DIG_COLS + DIG_THREADS - 1) / DIG_THREADS;
-    const int64_t gy = std::min<int64_t>((max_rows + DIG_ROWS - 1) / DIG_ROWS, 65535);
+    const int64_t gy = row_grid((max_rows + DIG_ROWS - 1) / DIG_ROWS, gx, njobs);
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)njobs);
     if (arena_kind == ARENA_U32) {
         k_digitize<1, ARENA_U32><<<grid, DIG_THREADS, 0, st>>>(jobs_dev, mp);
