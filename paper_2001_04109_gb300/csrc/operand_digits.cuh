@@ -104,11 +104,6 @@ __device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, 
         int sv[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) sv[e] = v[e] > m.half ? (int)v[e] - (int)m.p : (int)v[e];
-        int dg[D][8];
-#pragma unroll
-        for (int t = 0; t < D; ++t)
-#pragma unroll
-            for (int e = 0; e < 8; ++e) dg[t][e] = (t == D - 1) ? sv[e] : low_digit(sv[e], m);
         // Every entry of a plane is an exact small integer in FP32 (|x| ≤ 256), so
         // the planes are formed, summed (Karatsuba planes) and squared (norms)
         // two entries at a time in packed FP32, all exactly: a sum of squares
@@ -133,15 +128,54 @@ __device__ __forceinline__ void put8(const OperandDst &d, int64_t r, int64_t c, 
             const uint32_t tot = __reduce_add_sync(acc->mask, __float_as_uint(__fadd_rn(q.x, q.y))) - bias;
             mine = lane == t ? tot : mine;
         };
-        // 1.5·2^23 + d is exact in FP32 for |d| < 2^22; subtracting 1.5·2^23 leaves d
-        float2 fd[D][4];
-#pragma unroll
-        for (int t = 0; t < D; ++t)
+        // The digits, in packed FP32 too, from s (|s| ≤ (p − 1)/2 < 2^23, exact in
+        // FP32).  A low digit and the quotient that carries on are the same as
+        // low_digit's: with byte digits the quotient is floor((s + 128)/256)
+        // (s + 128 and its product with 2^-8 are exact, and adding 1.5·2^23
+        // rounding down floors it), so s − 256·q is s's low byte read as
+        // signed; with a balanced base b it is the float quotient s·(1/b)
+        // rounded to nearest (adding 1.5·2^23, then taking it off, rounds any
+        // |x| < 2^22 to an integer, ties to even).  s − b·q is exact: b·q and s
+        // are integers below 2^24.
+        const float2 M = make_float2(12582912.0f, 12582912.0f), negM = make_float2(-12582912.0f, -12582912.0f);
+        float2 sf[4];
+        if (m.p < (1u << 23)) {
+            // |s| < 2^22: 1.5·2^23 + s is exact, so subtracting 1.5·2^23 leaves s
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                fd[t][k] = __fadd2_rn(make_float2(__int_as_float(0x4B400000 + dg[t][2 * k]),
-                                                  __int_as_float(0x4B400000 + dg[t][2 * k + 1])),
-                                      make_float2(-12582912.0f, -12582912.0f));
+                sf[k] = __fadd2_rn(make_float2(__int_as_float(0x4B400000 + sv[2 * k]),
+                                               __int_as_float(0x4B400000 + sv[2 * k + 1])),
+                                   negM);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sf[k] = make_float2(__int2float_rn(sv[2 * k]), __int2float_rn(sv[2 * k + 1]));
+        }
+        float2 fd[D][4];
+        if (m.dbase == 256u) {
+            const float2 half = make_float2(128.0f, 128.0f), inv = make_float2(0.00390625f, 0.00390625f);
+            const float2 negb = make_float2(-256.0f, -256.0f);
+#pragma unroll
+            for (int t = 0; t < D - 1; ++t)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 q = __fadd2_rn(__ffma2_rd(__fadd2_rn(sf[k], half), inv, M), negM);
+                    fd[t][k] = __ffma2_rn(negb, q, sf[k]);
+                    sf[k] = q;
+                }
+        } else {
+            const float2 inv = make_float2(m.dinv, m.dinv);
+            const float2 negb = make_float2(-(float)m.dbase, -(float)m.dbase);
+#pragma unroll
+            for (int t = 0; t < D - 1; ++t)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 q = __fadd2_rn(__fadd2_rn(__fmul2_rn(sf[k], inv), M), negM);
+                    fd[t][k] = __ffma2_rn(negb, q, sf[k]);
+                    sf[k] = q;
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) fd[D - 1][k] = sf[k];
 #pragma unroll
         for (int t = 0; t < D; ++t) store_plane(t, fd[t]);
         if constexpr (OK == ARENA_BF16_KS) {
