@@ -51,7 +51,6 @@ __device__ __forceinline__ uint32_t byte_plane(const int (&sv)[N], int e0, int t
     return w;
 }
 
-// Store eight residues at (row r, columns c..c+7) of an operand: one
 // A warp's share of the norm tables (see OperandDst::norm): the 32 lanes
 // of a warp write 256 consecutive columns of one row (8 each), which is one
 // block of the table.  Per row and operand the lanes' sums of squares of
@@ -69,12 +68,16 @@ __device__ __forceinline__ uint32_t norm_lanes(int64_t c0, int64_t kpad) {
     return n >= 32 ? 0xffffffffu : n <= 0 ? 0u : ((1u << n) - 1u);
 }
 // Lanes t < planes add their maximum into the table (block = c0 / 256).
+// Every warp of every block that wrote this column block flushes into the
+// same entries, so a kernel calls this once per thread at its end and its
+// launcher keeps the number of blocks per column block small.
 __device__ __forceinline__ void norm_flush(const NormAcc &acc, int planes, int64_t c0) {
     const int lane = threadIdx.x & 31;
     if (acc.table != nullptr && lane < planes && acc.best != 0)
         atomicMax(acc.table + (int64_t)lane * acc.nb + c0 / 256, acc.best);
 }
 
+// Store eight residues at (row r, columns c..c+7) of an operand: one
 // 16-byte store per digit plane (bf16), two (uint32), or one 8-byte store
 // per byte plane (INT8 leaf).  With `acc` and a destination that has a norm
 // table, the warp also takes its row's sums of squares of every plane
