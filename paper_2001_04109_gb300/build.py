@@ -35,13 +35,19 @@ def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def dependencies() -> list[str]:
+    """Every file the library is built from: the CUDA sources, the headers
+    they include (.h and .cuh), the public header and this script."""
+    return (sources() + sorted(glob.glob(os.path.join(CSRC, "*.h")))
+            + sorted(glob.glob(os.path.join(CSRC, "*.cuh")))
+            + [os.path.join(ROOT, "include", "ffsyrk.h"), __file__])
+
+
 def _stale(extra: list[str]) -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + [
-        os.path.join(ROOT, "include", "ffsyrk.h"), __file__]
-    return any(os.path.getmtime(d) > t for d in deps) or bool(extra)
+    return any(os.path.getmtime(d) > t for d in dependencies()) or bool(extra)
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:

@@ -161,3 +161,15 @@ def test_other_entry_points_check_arguments_first(lib):
     assert lib.ffsyrkbd_update(0, 4, -1, 65521, 1, None, 4, None, None, 0, None, 4, None) == \
         E.ERR_INVALID_ARG
     assert lib.ffsyrk_update(0, 4, 4, 2, 1, None, 4, 0, None, 4, None) == E.ERR_UNSUPPORTED_P
+
+
+def test_rebuild_tracks_every_included_header():
+    """The library is rebuilt when any file it is compiled from changes: every
+    header a source includes by a quoted name must be among the build's
+    dependencies, .cuh device helpers included."""
+    from paper_2001_04109_gb300 import build as b
+    deps = {os.path.abspath(d) for d in b.dependencies()}
+    for src in b.sources():
+        for m in re.finditer(r'#include\s+"([^"]+)"', open(src).read()):
+            path = os.path.abspath(os.path.join(os.path.dirname(src), m.group(1)))
+            assert path in deps, f"{os.path.basename(src)} includes {m.group(1)}, not a build dependency"
