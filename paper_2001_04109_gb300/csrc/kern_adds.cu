@@ -67,6 +67,14 @@ __device__ __forceinline__ void ymul(const YConst &y, uint32_t t0, uint32_t t1, 
 __device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
 
 constexpr int PREP_THREADS = 128;  // threads per block
+constexpr int PREP_COLS = 8;       // columns per thread
+// rows per thread (independent loads in flight); one with Karatsuba sum
+// planes, whose longer digit split otherwise needs ~160 registers and leaves
+// fewer warps to cover the loads (measured 0.81 → 0.78 ms for the A 8192²
+// depth-2 mix, 14.9 → 14.4 ms of pre-additions at 32768²)
+template <int OK>
+constexpr int prep_rows() { return OK == ARENA_BF16_KS ? 1 : 2; }
+
 // Row-block grids of the digit-writing kernels: about this many blocks per SM
 // in all, each looping over its share of the rows.  Every block ends with one
 // atomicMax per warp and plane into the norm table, and the blocks of one
@@ -77,13 +85,6 @@ inline int64_t row_grid(int64_t row_blocks, int64_t gx, int64_t gz) {
     const int64_t cap = std::max<int64_t>(1, 152 * ROW_GRID_BLOCKS_PER_SM / std::max<int64_t>(1, gx * gz));
     return std::min<int64_t>(std::min<int64_t>(row_blocks, cap), 65535);
 }
-constexpr int PREP_COLS = 8;       // columns per thread
-// rows per thread (independent loads in flight); one with Karatsuba sum
-// planes, whose longer digit split otherwise needs ~160 registers and leaves
-// fewer warps to cover the loads (measured 0.81 → 0.78 ms for the A 8192²
-// depth-2 mix, 14.9 → 14.4 ms of pre-additions at 32768²)
-template <int OK>
-constexpr int prep_rows() { return OK == ARENA_BF16_KS ? 1 : 2; }
 
 
 // Eight consecutive entries (row r, columns c..c+7) of a view, zero outside.
